@@ -1,0 +1,212 @@
+"""Seeded synthetic inputs for the hybridization workloads.
+
+This module is the only code shared by the CUDA path and the CPU oracle. It
+holds no arithmetic of the method itself (no quadrature, no basis, no Piola
+map, no elimination): it draws random numbers and lays out the structured
+hexahedral mesh that both sides read.
+
+Random numbers come from a counter-based SplitMix64 generator (Steele, Lea,
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014): value i
+of stream s under seed S is mix64(key(S, s) + (i + 1) * GOLDEN), where mix64 is
+SplitMix64's finaliser. Uniforms on [0, 1) take the top 53 bits; normals use
+the Box-Muller transform on consecutive pairs of uniforms.
+
+Mesh recipe (the paper's soft-hard and SPE10 workloads use structured hex
+meshes, Sec. 6.1 and 6.4; none of its geometries ship with it): an nx*ny*nz
+grid on [0,1]^3 with vertex (i,j,l) at (i/nx, j/ny, l/nz); every coordinate of
+every interior vertex moves by U(-gamma*h, +gamma*h) with h the grid spacing of
+that axis, drawn in vertex-lexicographic order (i fastest), x then y then z.
+Boundary vertices stay put, so boundary faces are planar axis-aligned
+rectangles.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+_FNV = np.uint64(0x100000001B3)
+
+# stream ids
+STREAM_JITTER = 1
+STREAM_ALPHA = 2
+STREAM_CONTRAST = 3
+STREAM_LOAD = 4
+STREAM_BATCH = 5
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = z.astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        z ^= z >> np.uint64(30)
+        z *= _M1
+        z ^= z >> np.uint64(27)
+        z *= _M2
+        z ^= z >> np.uint64(31)
+    return z
+
+
+def splitmix64(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
+    """Raw 64-bit draws number offset..offset+count-1 of (seed, stream)."""
+    with np.errstate(over="ignore"):
+        key = _mix64(np.array([np.uint64(seed) * _FNV + np.uint64(stream)], dtype=np.uint64))[0]
+        i = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+        return _mix64(key + i * _GOLDEN)
+
+
+def uniform(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
+    """U[0,1) in float64 from the top 53 bits of each draw."""
+    r = splitmix64(seed, stream, count, offset)
+    return (r >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, stream: int, count: int) -> np.ndarray:
+    """N(0,1) by Box-Muller on consecutive uniform pairs (cos branch then sin branch)."""
+    npair = (count + 1) // 2
+    u = uniform(seed, stream, 2 * npair)
+    u1 = 1.0 - u[0::2]            # (0, 1]: log is finite
+    u2 = u[1::2]
+    rad = np.sqrt(-2.0 * np.log(u1))
+    out = np.empty(2 * npair)
+    out[0::2] = rad * np.cos(2.0 * np.pi * u2)
+    out[1::2] = rad * np.sin(2.0 * np.pi * u2)
+    return out[:count]
+
+
+@dataclass
+class Problem:
+    """One hybridization problem: mesh, coefficients, load and boundary data.
+
+    vertices : ((nz+1)*(ny+1)*(nx+1), 3) float64, vertex (i,j,l) at row i + (nx+1)*(j + (ny+1)*l)
+    alpha    : (E,) mass coefficient per element, element (i,j,l) at i + nx*(j + ny*l)
+    beta     : (E,) divergence coefficient per element
+    load     : (E, n_loc) coefficients of f in the broken RT_k basis (element-local dof order)
+    ess      : (E, n_loc) essential normal-trace values, read only at boundary-face dofs, or None (= 0)
+    """
+    nx: int
+    ny: int
+    nz: int
+    order: int
+    vertices: np.ndarray
+    alpha: np.ndarray
+    beta: np.ndarray
+    load: np.ndarray
+    ess: np.ndarray | None
+    name: str = ""
+
+    @property
+    def n_elem(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def n_loc(self) -> int:
+        k = self.order
+        return 3 * (k + 1) * (k + 1) * (k + 2)
+
+
+def n_local_dofs(order: int) -> int:
+    return 3 * (order + 1) ** 2 * (order + 2)
+
+
+def mesh_vertices(nx: int, ny: int, nz: int, gamma: float, seed: int) -> np.ndarray:
+    """Structured grid on [0,1]^3 with seeded jitter of interior vertices (recipe in the module doc)."""
+    hx, hy, hz = 1.0 / nx, 1.0 / ny, 1.0 / nz
+    i = np.arange(nx + 1, dtype=np.float64)
+    j = np.arange(ny + 1, dtype=np.float64)
+    l = np.arange(nz + 1, dtype=np.float64)
+    L, J, I = np.meshgrid(l, j, i, indexing="ij")          # i fastest when flattened
+    v = np.stack([I.ravel() * hx, J.ravel() * hy, L.ravel() * hz], axis=1)
+    if gamma != 0.0:
+        interior = ((I > 0) & (I < nx) & (J > 0) & (J < ny) & (L > 0) & (L < nz)).ravel()
+        nint = int(interior.sum())
+        u = uniform(seed, STREAM_JITTER, 3 * nint).reshape(nint, 3)
+        v[interior] += (2.0 * u - 1.0) * gamma * np.array([hx, hy, hz])
+    return v
+
+
+def random_problem(n: int, order: int, gamma: float, seed: int,
+                   contrast_lo: float, contrast_hi: float,
+                   lognormal_alpha: bool = True, name: str = "") -> Problem:
+    """alpha ~ lognormal(0,1) per element, beta/alpha ~ 10^U(lo,hi), N(0,1) load coefficients, zero essential BC."""
+    E = n * n * n
+    nl = n_local_dofs(order)
+    verts = mesh_vertices(n, n, n, gamma, seed)
+    alpha = np.exp(normal(seed, STREAM_ALPHA, E)) if lognormal_alpha else np.ones(E)
+    lo, hi = np.log10(contrast_lo), np.log10(contrast_hi)
+    beta = alpha * 10.0 ** (lo + (hi - lo) * uniform(seed, STREAM_CONTRAST, E))
+    load = normal(seed, STREAM_LOAD, E * nl).reshape(E, nl)
+    return Problem(n, n, n, order, verts, alpha, beta, load, None, name)
+
+
+def _u_exact(x, y, z):
+    return np.stack([1.0 + 2.0 * x, 3.0 - y, 0.5 + z], axis=-1)
+
+
+def manufactured_rt0_problem(n: int, gamma: float, seed: int) -> Problem:
+    """RT_0 workload with u_exact = (1+2x, 3-y, 0.5+z), alpha = beta = 1.
+
+    The RT_0 reference dofs sit at the face centres (closed nodes {0,1} along the
+    component's axis, the open node 1/2 across it). Both the load coefficients
+    and the essential values are h_a*h_b * u_exact(face centre of the unjittered
+    grid) . e_axis, where h_a, h_b are the grid spacings across the face: the
+    face's normal flux density. With gamma = 0 this is the exact RT_0
+    interpolant of u_exact (the field is in RT_0 on affine cells), so the load
+    f = sum c_j phi_j equals u_exact = alpha u - grad(beta div u). With
+    gamma > 0 it is a smooth synthetic load; the boundary values stay exact
+    because boundary faces are never jittered.
+    """
+    order = 0
+    nx = ny = nz = n
+    E = nx * ny * nz
+    h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
+    verts = mesh_vertices(nx, ny, nz, gamma, seed)
+    e = np.arange(E)
+    ei, ej, el = e % nx, (e // nx) % ny, e // (nx * ny)
+    load = np.zeros((E, 6))
+    # local face order: x0, x1, y0, y1, z0, z1 (k = 0: no interior dofs)
+    for f in range(6):
+        axis, side = f // 2, f % 2
+        c = np.stack([ei + 0.5, ej + 0.5, el + 0.5], axis=1).astype(np.float64)
+        c[:, axis] = (np.stack([ei, ej, el], axis=1)[:, axis] + side)
+        pos = c * h
+        u = _u_exact(pos[:, 0], pos[:, 1], pos[:, 2])
+        area = np.prod(np.delete(h, axis))
+        load[:, f] = area * u[:, axis]
+    ess = load.copy()
+    return Problem(nx, ny, nz, order, verts, np.ones(E), np.ones(E), load, ess, "manufactured")
+
+
+# The five workloads (sizes as the benchmark definitions state them).
+CONFIGS = {
+    1: dict(kind="manufactured", n=4, order=0, gamma=0.0, seed=1000),
+    "1j": dict(kind="manufactured", n=4, order=0, gamma=0.15, seed=1000),
+    2: dict(kind="random", n=32, order=1, gamma=0.2, seed=2000, contrast=(1e-2, 1e4)),
+    3: dict(kind="random", n=96, order=2, gamma=0.2, seed=3000, contrast=(1e-2, 1e6)),
+    5: dict(kind="random", n=64, order=3, gamma=0.2, seed=5000, contrast=(1e-2, 1e6)),
+}
+
+
+def make_config(cfg, n: int | None = None) -> Problem:
+    """Build a named workload; n overrides the mesh size (scaled-down parity cases)."""
+    c = CONFIGS[cfg]
+    nn = c["n"] if n is None else n
+    if c["kind"] == "manufactured":
+        return manufactured_rt0_problem(nn, c["gamma"], c["seed"])
+    lo, hi = c["contrast"]
+    return random_problem(nn, c["order"], c["gamma"], c["seed"], lo, hi, name=f"config{cfg}")
+
+
+def batch_problems(count: int = 256, seed0: int = 4000, nmin: int = 6, nmax: int = 24,
+                   contrast=(1e-2, 1e4)) -> list[Problem]:
+    """Many independent problems of uneven size and order: n ~ U{nmin..nmax}, k ~ U{0..3}."""
+    probs = []
+    for p in range(count):
+        s = seed0 + p
+        u = uniform(s, STREAM_BATCH, 2)
+        n = nmin + int(u[0] * (nmax - nmin + 1))
+        k = int(u[1] * 4)
+        probs.append(random_problem(n, k, 0.2, s, contrast[0], contrast[1], name=f"batch{p}"))
+    return probs
