@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark: hybridized elements/s of the full hot path on one GB300 (per rank).
+
+A step is one pass of the whole path over the 32x32x32 jittered hex mesh with
+RT_1 (the bench workload): hyb_assemble_reduced (element elimination + atomic-free
+scatter), hyb_solve_reduced (diagonal PCG to ||r|| <= 1e-12 ||r0||) and
+hyb_recover, all through the C ABI with inputs resident in HBM. L2 is flushed
+(a 512 MiB write) before every timed step, outside its events.
+
+Output: one JSON line (rank 0). Under torchrun every rank runs an independent
+replica (the path has no exchange step on one GPU per problem) and the slowest
+rank's time is reported; value = all ranks' elements / that time.
+
+--impl reference times the CPU FP64 oracle, as it stands, on a bounded sample of
+the same workload (the same recipe on a 20^3 mesh) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "32x32x32 jittered hex mesh (+-0.2h), RT_1, FP64 hybridization: assemble + diag-PCG 1e-12 + recover"
+METRIC = "hybridized elements/s (FP64 GPU path)"
+SAMPLE_N = 20          # oracle sample mesh (same recipe, 8000 elements)
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rtol", type=float, default=1e-12)
+    ap.add_argument("--maxit", type=int, default=100000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="mesh size override (parity / profiling runs)")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, local, world = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return rank, local, world
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device="cpu") -> float:
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
+def aggregate(units_per_rank: int, times_ms_rank: float, world: int, device="cpu"):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    t = max_over_ranks(times_ms_rank, device)
+    return world * units_per_rank / (t * 1e-3), t
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample_step(n=SAMPLE_N):
+    """One full step of the CPU FP64 oracle (hybridize, diag-PCG 1e-12, recover) on the n^3 sample."""
+    from oracle.hybrid import Discretization, pcg_diag
+    from paper_1801_08914_gb300 import inputs
+    p = inputs.make_config(2, n=n)
+    t0 = time.perf_counter()
+    D = Discretization.from_problem(p)
+    H, g = D.hybridize()
+    lam, it, _ = pcg_diag(H, g, rtol=1e-12)
+    D.recover(lam)
+    return p.n_elem, time.perf_counter() - t0, it
+
+
+def _oracle_worker(n, steps):
+    out = []
+    for _ in range(steps):
+        E, t, it = oracle_sample_step(n)
+        out.append((E, t, it))
+    print(json.dumps(out))
+
+
+def run_oracle_subprocess(n, steps):
+    """Runs the oracle in a fresh single-threaded process (1 core, BLAS threads pinned to 1)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = f"import bench; bench._oracle_worker({n}, {steps})"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(steps=1):
+    res = run_oracle_subprocess(SAMPLE_N, steps)
+    E = sum(r[0] for r in res)
+    t = sum(r[1] for r in res)
+    return {"value": E / t, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "sample": f"full step (hybridize, diag-PCG 1e-12 [{res[0][2]} it], recover) on the "
+                      f"{SAMPLE_N}^3 mesh of the same recipe ({res[0][0]} elements), {len(res)} run(s), "
+                      f"{t:.1f} s on 1 host core"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    W, K = args.warmup, args.steps
+    res = run_oracle_subprocess(SAMPLE_N, W + K)[W:]
+    E = sum(r[0] for r in res)
+    t = sum(r[1] for r in res)
+    v = E / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{SAMPLE_N}^3 mesh of the same recipe", "parallelism": "none"},
+            "cpu_baseline": {"value": v, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{SAMPLE_N}^3 mesh, full step per sample"},
+            "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def spmv_bytes(n, nnz, nfn):
+    """Algorithmic bytes of one SpMV launch: the values (8 B per nonzero), the shared column
+    list of each face (4 B per nonzero / rows per face), two row pointers per face, one read
+    of the gathered vector and of p_i, one write of the result."""
+    return 8 * nnz + 4 * nnz // nfn + 16 * (n // nfn) + 8 * n + 8 * n
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    rank, local, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", 1)) > 1 else "gloo")
+    __graft_entry__.build()
+    from paper_1801_08914_gb300 import hyb, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    p = inputs.make_config(2, n=args.n)
+    tt = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    verts, alpha, beta, load = tt(p.vertices), tt(p.alpha), tt(p.beta), tt(p.load)
+    ctx = hyb.hyb_setup(verts, p.nx, p.ny, p.nz, p.order, alpha, beta)
+    sz = ctx.sizes()
+    E, n_loc, N, nnz = sz["n_elem"], sz["n_loc"], sz["n_lambda"], sz["nnz"]
+    lam = torch.zeros(N, dtype=torch.float64, device=dev)
+    u = torch.zeros(E, n_loc, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    iters = []
+
+    def step(load_dev):
+        hyb.hyb_assemble_reduced(ctx, load_dev, None)
+        it, rr, st = hyb.hyb_solve_reduced(ctx, args.rtol, args.maxit, lam, check=False)
+        if st not in (hyb.HYB_OK,):
+            raise hyb.HybError(st, "hyb_solve_reduced")
+        iters.append(it)
+        hyb.hyb_recover(ctx, lam, u)
+
+    for _ in range(args.warmup):
+        step(load)
+    torch.cuda.synchronize()
+    hyb.hyb_set_profiling(ctx, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters.clear()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        step(load)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    it_total = sum(iters)
+    iters_timed = list(iters)
+    ck = clocks.stop()
+    prof = hyb.hyb_get_profile(ctx)
+    hyb.hyb_set_profiling(ctx, False)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    value, ms_max = aggregate(E * args.steps, ms, world, device=dev)
+
+    # end to end through the C ABI with host buffers: H2D of the load, D2H of u, every step
+    load_h = torch.from_numpy(np.ascontiguousarray(p.load)).pin_memory()
+    u_h = torch.empty(E, n_loc, dtype=torch.float64).pin_memory()
+    load_d = torch.empty_like(load)
+    ke = max(1, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(ke):
+        load_d.copy_(load_h, non_blocking=True)
+        step(load_d)
+        u_h.copy_(u, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_value, _ = aggregate(E * ke, e2e_ms, world, device=dev)
+
+    # roofline of the dominant kernel class
+    spmv_ms, spmv_launches = prof["spmv"]
+    dominant = max(prof, key=lambda k: prof[k][0])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    per_launch_ms = spmv_ms / max(1, it_total)            # no-op launches after convergence charged to real ones
+    nfn = (p.order + 1) ** 2
+    achieved = spmv_bytes(N, nnz, nfn) / (per_launch_ms * 1e-3) / 1e9
+    roof = {"kernel": "spmv_face_kernel (CSR SpMV fused with p^T H p)", "bound": "hbm", "achieved": achieved,
+            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+            "traffic": None, "algorithmic_bytes_per_launch": spmv_bytes(N, nnz, nfn),
+            "avg_launch_ms": per_launch_ms, "dominant_class": dominant}
+    launches = sum(v[1] for v in prof.values())
+    phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
+    elem_ms = prof["element"][0] / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": E, "order": p.order, "n_loc": n_loc, "n_lambda": N,
+                   "nnz": nnz, "pcg_rtol": args.rtol, "pcg_iterations": iters_timed[0] if iters_timed else None,
+                   "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) before each step"},
+        "e2e": {"value": e2e_value, "unit": "elements/s", "h2d_bytes_per_step": int(p.load.nbytes),
+                "d2h_bytes_per_step": int(E * n_loc * 8)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "phases": phases,
+        "assembly_elements_per_s": E / (elem_ms * 1e-3) if elem_ms > 0 else None,
+        "reduced_dofs_per_s": N / (prof["spmv"][0] / args.steps * 1e-3 + prof["pcg_vector"][0] / args.steps * 1e-3),
+        "clocks": ck,
+        "wall_s": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as exc:  # reported, not fatal
+            line["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

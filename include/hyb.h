@@ -1,0 +1,196 @@
+/*
+ * hyb.h -- C ABI of the GB300 library for algebraic hybridization and static
+ * condensation of the H(div) form a(u,v) = (alpha u, v) + (beta div u, div v)
+ * on structured hexahedral meshes with broken Raviart-Thomas RT_k spaces,
+ * k = 0..3 (Dobrev, Kolev, Lee, Tomov, Vassilevski, arXiv:1801.08914).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an int status: HYB_OK (0) or a negative HYB_ERR_* code.
+ *    No C++ exception crosses this boundary. hyb_status_string() names a code.
+ *  - Array arguments are DEVICE pointers (CUDA global memory) to contiguous
+ *    float64 / int arrays unless a comment says "host". The caller owns them;
+ *    the library never frees or retains a caller pointer beyond the calls
+ *    documented to keep it (hyb_setup keeps vertices, alpha and beta).
+ *  - The context owns every internal device buffer (reduced CSR system, stored
+ *    element factors, solver vectors); hyb_destroy releases them.
+ *  - All work is enqueued on the CUDA stream given to hyb_setup. A call returns
+ *    after its status word has been copied back, so on return its device work
+ *    is complete and its outputs are valid.
+ *  - A context is not thread-safe: do not call into one context from two
+ *    host threads at once.
+ *
+ * Numbering (identical on every entry point)
+ *  - Element (i,j,l) of an nx*ny*nz mesh has index e = i + nx*(j + ny*l).
+ *  - Vertex (i,j,l) has index i + (nx+1)*(j + (ny+1)*l); a vertex is 3 doubles.
+ *  - Element-local dofs (n_loc = 3(k+1)^2(k+2)): interior dofs first
+ *    (x-component nodes a=1..k, then y, then z; first index fastest), then the
+ *    (k+1)^2 dofs of each face in the order x=0, x=1, y=0, y=1, z=0, z=1,
+ *    lower tangential axis fastest. A dof is the value of the reference
+ *    component along that axis at its node (closed Gauss-Lobatto nodes along
+ *    the component, open Gauss-Legendre nodes across it).
+ *  - Multipliers (one per Gauss-Legendre node of each interior face): faces by
+ *    normal axis x, y, z; within an axis by plane index along the normal
+ *    (fastest), then the lower and then the higher tangential cell index;
+ *    within a face by node, lower tangential axis fastest. Static
+ *    condensation numbers its global face dofs the same way.
+ */
+#ifndef HYB_H
+#define HYB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HYB_OK = 0,
+  HYB_ERR_INVALID_ARG = -1,       /* null pointer, bad size, bad enum, wrong phase order */
+  HYB_ERR_UNSUPPORTED_ORDER = -2, /* order outside 0..3 */
+  HYB_ERR_MESH = -3,              /* det J <= 0 at a corner or quadrature point */
+  HYB_ERR_NOT_SPD = -4,           /* an element matrix failed Cholesky (see hyb_last_error_element) */
+  HYB_ERR_NOT_CONVERGED = -5,     /* PCG hit maxit; outputs are still written */
+  HYB_ERR_BREAKDOWN = -6,         /* PCG p^T H p <= 0 or non-finite */
+  HYB_ERR_CUDA = -7,              /* a CUDA runtime call failed */
+  HYB_ERR_OOM = -8,               /* device allocation failed */
+  HYB_ERR_TIMEOUT = -9            /* a bounded device-side wait gave up */
+};
+
+enum { HYB_FP64 = 0, HYB_MIXED = 1 };
+
+/* Structured hexahedral mesh: (nx+1)(ny+1)(nz+1) vertices, device pointer. */
+typedef struct {
+  int nx, ny, nz;
+  const double* vertices;
+} hyb_mesh;
+
+typedef struct hyb_ctx hyb_ctx;
+
+/*
+ * hyb_setup -- build the reduced-system pattern and the element metadata.
+ *  Paper: the multiplier space and constraint matrix C of Example 2.2 (Sec. 2.4),
+ *  the element 2x2 (interior/interface) ordering of Sec. 5.
+ *  m          : mesh (nx, ny, nz >= 1); vertices must stay valid until hyb_destroy.
+ *  order      : k in 0..3.
+ *  alpha,beta : device, nx*ny*nz doubles each, per-element mass and divergence
+ *               coefficients (> 0); kept until hyb_destroy.
+ *  precision  : HYB_FP64 (HYB_MIXED returns HYB_ERR_INVALID_ARG in this version).
+ *  contrast_threshold : reserved for the mixed path; ignored for HYB_FP64.
+ *  cuda_stream: cudaStream_t to enqueue on (NULL = legacy default stream).
+ *  out        : host, receives the new context.
+ *  Builds the CSR pattern of H (int64 row pointers, int32 columns), per-element
+ *  face / scatter tables and checks det J > 0 at every corner and quadrature
+ *  point (HYB_ERR_MESH otherwise; hyb_last_error_element gives the element).
+ */
+int hyb_setup(const hyb_mesh* m, int order, const double* alpha, const double* beta,
+              int precision, double contrast_threshold, void* cuda_stream, hyb_ctx** out);
+
+/*
+ * hyb_assemble_reduced -- element-by-element elimination and assembly of
+ *  H lambda = C A^-1 C^T lambda = C A^-1 f  (Thm 2.1, eq. 2.4; Sec. 5).
+ *  Per element: A_T by Gauss quadrature through the Piola map, essential dofs
+ *  eliminated, Cholesky A_T = L L^T (interior dofs first), S_T = C_T A_T^-1 C_T^T
+ *  and g_T = C_T A_T^-1 f_T, added into the CSR values / right-hand side without
+ *  atomics (two element colours).
+ *  load : device, E*n_loc doubles: coefficients of f in the broken RT_k basis;
+ *         the element load is f_T = M_T c_T with M_T the unit-coefficient mass.
+ *  ess  : device, E*n_loc doubles of essential normal-trace dof values, read only
+ *         at dofs on boundary faces; NULL means zero.
+ *  Keeps the element factors for hyb_recover. HYB_ERR_NOT_SPD names an element.
+ */
+int hyb_assemble_reduced(hyb_ctx* ctx, const double* load, const double* ess);
+
+/*
+ * hyb_solve_reduced -- diagonal-preconditioned CG on the assembled reduced
+ *  system (H after hyb_assemble_reduced, S after staticcond_assemble), x0 = 0,
+ *  stopping when ||r||_2 <= rtol ||r_0||_2 (the paper's criterion, Sec. 6.1).
+ *  lambda : device, N_lambda doubles, receives the solution.
+ *  iters, rel_res : host, may be NULL.
+ *  Returns HYB_ERR_NOT_CONVERGED after maxit iterations (lambda still written).
+ */
+int hyb_solve_reduced(hyb_ctx* ctx, double rtol, int maxit, double* lambda,
+                      int* iters, double* rel_res);
+
+/*
+ * hyb_recover -- back substitution x_T = A_T^-1 (f_T - C_T^T lambda_T) (Thm 2.1)
+ *  with essential dofs re-inserted.
+ *  lambda : device, N_lambda doubles.   u : device, E*n_loc doubles (broken RT_k dofs).
+ *  Requires a preceding hyb_assemble_reduced on this context.
+ */
+int hyb_recover(hyb_ctx* ctx, const double* lambda, double* u);
+
+/*
+ * staticcond_assemble -- static condensation S_hat = A_bb - A_bi A_ii^-1 A_ib per
+ *  element and S = [I;W]^T S_hat [I;W] (Sec. 3.1, eq. 3.1-3.2), assembled on the
+ *  same CSR pattern as H with right-hand side f_b - A_bi A_ii^-1 f_i.
+ *  load, ess : as for hyb_assemble_reduced.
+ */
+int staticcond_assemble(hyb_ctx* ctx, const double* load, const double* ess);
+
+/*
+ * staticcond_recover -- u_i = A_ii^-1 (f_i - A_ib u_b) per element (Sec. 3.1).
+ *  u_face : device, N_lambda doubles, the solved global face dofs.
+ *  u      : device, E*n_loc doubles, the broken RT_k dofs (face dofs copied).
+ *  Requires a preceding staticcond_assemble on this context.
+ */
+int staticcond_recover(hyb_ctx* ctx, const double* u_face, double* u);
+
+/*
+ * hyb_get_reduced -- borrow the context's reduced system (device pointers owned
+ *  by the context, valid until the next assemble or hyb_destroy). Any output
+ *  pointer may be NULL. n = N_lambda, nnz = number of stored entries.
+ */
+int hyb_get_reduced(hyb_ctx* ctx, const int64_t** row_ptr, const int32_t** col,
+                    const double** val, const double** rhs, int64_t* n, int64_t* nnz);
+
+/*
+ * hyb_export_reduced -- copy the reduced system into caller-owned device arrays
+ *  (row_ptr: N_lambda+1 int64, col: nnz int32, val: nnz doubles, rhs: N_lambda
+ *  doubles); any pointer may be NULL. Enqueued on the context stream and
+ *  complete on return.
+ */
+int hyb_export_reduced(hyb_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val, double* rhs);
+
+/* Kernel classes for the launch profile. */
+enum {
+  HYB_K_ELEMENT = 0,     /* element elimination (assemble / static condensation) */
+  HYB_K_SPMV = 1,        /* CSR SpMV fused with p^T H p (one per PCG iteration) */
+  HYB_K_PCG_VECTOR = 2,  /* PCG vector updates, reductions, initialisation */
+  HYB_K_RECOVER = 3,     /* back substitution */
+  HYB_K_SETUP = 4,       /* set-up kernels (column expansion, geometry check) */
+  HYB_K_COUNT = 5
+};
+
+/*
+ * hyb_set_profiling -- enable (1) or disable (0) the launch profile and reset it.
+ *  While enabled, every kernel launch of the context is bracketed by CUDA events
+ *  recorded on the context stream; elapsed times are added up when each call
+ *  synchronises. Costs about one event pair per launch.
+ */
+int hyb_set_profiling(hyb_ctx* ctx, int enable);
+
+/*
+ * hyb_get_profile -- host outputs for kernel class `kernel_class` (HYB_K_*):
+ *  summed device time in milliseconds and number of launches since profiling
+ *  was enabled. Either output may be NULL.
+ */
+int hyb_get_profile(const hyb_ctx* ctx, int kernel_class, double* total_ms, int64_t* launches);
+
+/* hyb_get_sizes -- host outputs (any may be NULL): elements, n_loc, N_lambda, nnz. */
+int hyb_get_sizes(const hyb_ctx* ctx, int64_t* n_elem, int* n_loc, int64_t* n_lambda, int64_t* nnz);
+
+/* hyb_last_error_element -- element behind the last HYB_ERR_NOT_SPD / HYB_ERR_MESH, or -1. */
+int hyb_last_error_element(const hyb_ctx* ctx, int64_t* element);
+
+/* hyb_destroy -- free every buffer the context owns; NULL is a no-op. */
+void hyb_destroy(hyb_ctx* ctx);
+
+/* hyb_status_string -- static name of a status code. */
+const char* hyb_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYB_H */

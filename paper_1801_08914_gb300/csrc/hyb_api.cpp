@@ -1,0 +1,536 @@
+// Host side of libhyb: context, set-up of the reduced-system pattern and the
+// C ABI entry points declared in include/hyb.h.
+//
+// Set-up derives, for a structured nx*ny*nz hex mesh, everything the element
+// kernels need to scatter without atomics (arXiv:1801.08914, Sec. 5):
+//   * interior-face (multiplier) numbering: faces by normal axis, then plane
+//     index, then the lower and the higher tangential cell index;
+//   * per element its six interior-face ids (-1 on the boundary);
+//   * the CSR pattern of H: row (f, m) couples face f with every interior
+//     face of its two neighbours (at most 11), columns sorted; every row of a
+//     face has the same column list, so the rows of a face form one dense
+//     (k+1)^2 x len block of the value array;
+//   * per element the value offset of each face block (a, b);
+//   * a two-colouring by (i + j + l) mod 2: the two neighbours of a face
+//     always differ in colour.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hyb_internal.h"
+
+using namespace hyb;
+
+namespace hyb {
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;              // event pairs: 2 t, 2 t + 1
+  std::vector<int> cls;                       // class of pending pair t
+  size_t used = 0;
+  double ms[HYB_K_COUNT] = {0};
+  int64_t launches[HYB_K_COUNT] = {0};
+  bool failed = false;
+
+  // Add up the pending pairs (call after the stream has synchronised).
+  void collect() {
+    for (size_t t = 0; t < used; ++t) {
+      float v = 0.f;
+      if (cudaEventElapsedTime(&v, pool[2 * t], pool[2 * t + 1]) == cudaSuccess) ms[cls[t]] += v;
+      else failed = true;
+    }
+    used = 0;
+  }
+  void reset() {
+    for (int c = 0; c < HYB_K_COUNT; ++c) { ms[c] = 0; launches[c] = 0; }
+    used = 0;
+  }
+  ~Prof() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+int prof_begin(Prof* p, int c, cudaStream_t s) {
+  if (!p || !p->on) return -1;
+  p->launches[c] += 1;
+  if (p->used * 2 + 2 > p->pool.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
+    p->pool.push_back(a);
+    p->pool.push_back(b);
+    p->cls.push_back(0);
+  }
+  const size_t t = p->used++;
+  p->cls[t] = c;
+  cudaEventRecord(p->pool[2 * t], s);
+  return (int)t;
+}
+
+void prof_end(Prof* p, int token, cudaStream_t s) {
+  if (!p || token < 0) return;
+  cudaEventRecord(p->pool[2 * token + 1], s);
+}
+
+}  // namespace hyb
+
+struct hyb_ctx {
+  int nx = 0, ny = 0, nz = 0, k = 0;
+  Sizes sz{};
+  int64_t E = 0, n_lambda = 0, nnz = 0, n_ifaces = 0;
+  int64_t n_iface_axis[3] = {0, 0, 0};
+  cudaStream_t stream = nullptr;
+  const double* vertices = nullptr;
+  const double* alpha = nullptr;
+  const double* beta = nullptr;
+  int64_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  double* rhs = nullptr;
+  int32_t* elem_face = nullptr;
+  int64_t* blockoff = nullptr;
+  int32_t* colour_list[2] = {nullptr, nullptr};
+  int64_t n_colour[2] = {0, 0};
+  double* Lstore = nullptr;
+  double* zstore = nullptr;
+  int* status = nullptr;
+  long long* err_elem = nullptr;
+  double *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *partial = nullptr, *scal = nullptr;
+  int* flags = nullptr;
+  int nblocks = 0;
+  int mode = MODE_NONE;
+  int64_t last_err_elem = -1;
+  RefTables tabs[kMaxOrder + 1];
+  std::vector<void*> allocs;
+  Prof prof;
+};
+
+namespace {
+
+template <class T>
+int dalloc(hyb_ctx* c, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return HYB_ERR_OOM;
+  }
+  c->allocs.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return HYB_OK;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return HYB_OK;
+  if (e == cudaErrorMemoryAllocation) return HYB_ERR_OOM;
+  return HYB_ERR_CUDA;
+}
+
+// Read back and clear the device status word; records the element id.
+int finish_phase(hyb_ctx* c) {
+  int st = 0;
+  long long el = -1;
+  cudaError_t e = cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&el, c->err_elem, sizeof(long long), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  c->prof.collect();
+  if (st != 0) c->last_err_elem = el;
+  return st;
+}
+
+int reset_status(hyb_ctx* c) {
+  cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->err_elem, 0xff, sizeof(long long), c->stream);
+  return cuda_status(e);
+}
+
+// interior-face index of the axis-d face at plane pl with tangential cells (a, b), or -1
+int64_t iface(const hyb_ctx* c, int d, int pl, int a, int b) {
+  const int dims[3] = {c->nx, c->ny, c->nz};
+  if (pl <= 0 || pl >= dims[d]) return -1;
+  const int across0 = d == 0 ? c->ny : c->nx;
+  int64_t off = 0;
+  for (int t = 0; t < d; ++t) off += c->n_iface_axis[t];
+  return off + (pl - 1) + (int64_t)(dims[d] - 1) * (a + (int64_t)across0 * b);
+}
+
+// the six interior-face ids of element (i, j, l) in local face order x0 x1 y0 y1 z0 z1
+void element_faces(const hyb_ctx* c, int i, int j, int l, int64_t out[6]) {
+  out[0] = iface(c, 0, i, j, l);
+  out[1] = iface(c, 0, i + 1, j, l);
+  out[2] = iface(c, 1, j, i, l);
+  out[3] = iface(c, 1, j + 1, i, l);
+  out[4] = iface(c, 2, l, i, j);
+  out[5] = iface(c, 2, l + 1, i, j);
+}
+
+ElemArgs elem_args(hyb_ctx* c, const double* load, const double* ess, int colour) {
+  ElemArgs a{};
+  a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+  a.n_elem = c->E;
+  a.vertices = c->vertices;
+  a.alpha = c->alpha;
+  a.beta = c->beta;
+  a.load = load;
+  a.ess = ess;
+  a.elem_list = c->colour_list[colour];
+  a.n_list = c->n_colour[colour];
+  a.colour = colour;
+  a.elem_face = c->elem_face;
+  a.blockoff = c->blockoff;
+  a.row_ptr = c->row_ptr;
+  a.val = c->val;
+  a.rhs = c->rhs;
+  a.Lstore = c->Lstore;
+  a.zstore = c->zstore;
+  a.status = c->status;
+  a.err_elem = c->err_elem;
+  return a;
+}
+
+int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, const double* beta) {
+  c->nx = m->nx; c->ny = m->ny; c->nz = m->nz; c->k = order;
+  c->sz = Sizes::of(order);
+  c->vertices = m->vertices;
+  c->alpha = alpha;
+  c->beta = beta;
+  const int nx = c->nx, ny = c->ny, nz = c->nz, nfn = c->sz.nfn;
+  c->E = (int64_t)nx * ny * nz;
+  c->n_iface_axis[0] = (int64_t)(nx - 1) * ny * nz;
+  c->n_iface_axis[1] = (int64_t)nx * (ny - 1) * nz;
+  c->n_iface_axis[2] = (int64_t)nx * ny * (nz - 1);
+  c->n_ifaces = c->n_iface_axis[0] + c->n_iface_axis[1] + c->n_iface_axis[2];
+  c->n_lambda = c->n_ifaces * nfn;
+  const int64_t E = c->E;
+
+  // element face table and colour lists
+  std::vector<int32_t> elem_face(6 * E);
+  std::vector<int32_t> lists[2];
+  lists[0].reserve(E / 2 + 1);
+  lists[1].reserve(E / 2 + 1);
+  for (int l = 0; l < nz; ++l)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const int64_t e = i + (int64_t)nx * (j + (int64_t)ny * l);
+        int64_t f[6];
+        element_faces(c, i, j, l, f);
+        for (int a = 0; a < 6; ++a) elem_face[6 * e + a] = (int32_t)f[a];
+        lists[(i + j + l) & 1].push_back((int32_t)e);
+      }
+
+  // face adjacency: interior faces of the two neighbours, sorted, unique
+  const int64_t F = c->n_ifaces;
+  std::vector<int32_t> adj(11 * F, -1), adj_count(F, 0);
+  std::vector<int64_t> nb(2 * F, -1);                 // low / high neighbour element
+  for (int64_t e = 0; e < E; ++e)
+    for (int a = 0; a < 6; ++a) {
+      const int32_t f = elem_face[6 * e + a];
+      if (f >= 0) nb[2 * f + (a & 1 ? 0 : 1)] = e;   // face at x_hat = 1 of e: e is the low side
+    }
+  for (int64_t f = 0; f < F; ++f) {
+    int32_t tmp[12];
+    int n = 0;
+    for (int s = 0; s < 2; ++s) {
+      const int64_t e = nb[2 * f + s];
+      for (int a = 0; a < 6; ++a) {
+        const int32_t g = elem_face[6 * e + a];
+        if (g >= 0) tmp[n++] = g;
+      }
+    }
+    std::sort(tmp, tmp + n);
+    const int u = (int)(std::unique(tmp, tmp + n) - tmp);
+    for (int t = 0; t < u; ++t) adj[11 * f + t] = tmp[t];
+    adj_count[f] = u;
+  }
+  // row pointers
+  std::vector<int64_t> row_ptr(c->n_lambda + 1);
+  row_ptr[0] = 0;
+  for (int64_t f = 0; f < F; ++f)
+    for (int mm = 0; mm < nfn; ++mm) {
+      const int64_t r = f * nfn + mm;
+      row_ptr[r + 1] = row_ptr[r] + (int64_t)adj_count[f] * nfn;
+    }
+  c->nnz = row_ptr[c->n_lambda];
+  // block offsets: value index of (face a row node 0, column block of face b)
+  std::vector<int64_t> blockoff(36 * E, -1);
+  for (int64_t e = 0; e < E; ++e)
+    for (int a = 0; a < 6; ++a) {
+      const int32_t fa = elem_face[6 * e + a];
+      if (fa < 0) continue;
+      for (int b = 0; b < 6; ++b) {
+        const int32_t fb = elem_face[6 * e + b];
+        if (fb < 0) continue;
+        const int32_t* lst = &adj[11 * (int64_t)fa];
+        const int pos = (int)(std::lower_bound(lst, lst + adj_count[fa], fb) - lst);
+        blockoff[36 * e + 6 * a + b] = row_ptr[(int64_t)fa * nfn] + (int64_t)pos * nfn;
+      }
+    }
+
+  // device buffers
+  int st;
+  int32_t *d_adj = nullptr, *d_adjc = nullptr;
+  const Sizes& s = c->sz;
+  if ((st = dalloc(c, &c->row_ptr, c->n_lambda + 1))) return st;
+  if ((st = dalloc(c, &c->col, c->nnz))) return st;
+  if ((st = dalloc(c, &c->val, c->nnz))) return st;
+  if ((st = dalloc(c, &c->rhs, c->n_lambda))) return st;
+  if ((st = dalloc(c, &c->elem_face, 6 * E))) return st;
+  if ((st = dalloc(c, &c->blockoff, 36 * E))) return st;
+  for (int t = 0; t < 2; ++t) {
+    c->n_colour[t] = (int64_t)lists[t].size();
+    if ((st = dalloc(c, &c->colour_list[t], lists[t].size()))) return st;
+  }
+  if ((st = dalloc(c, &c->Lstore, (size_t)E * (size_t)tri_size(s.n)))) return st;
+  if ((st = dalloc(c, &c->zstore, (size_t)E * s.n))) return st;
+  if ((st = dalloc(c, &c->status, 1))) return st;
+  if ((st = dalloc(c, &c->err_elem, 1))) return st;
+  if ((st = dalloc(c, &d_adj, 11 * F))) return st;
+  if ((st = dalloc(c, &d_adjc, F))) return st;
+  c->nblocks = 152 * 8;
+  if ((st = dalloc(c, &c->r, c->n_lambda))) return st;
+  if ((st = dalloc(c, &c->p, c->n_lambda))) return st;
+  if ((st = dalloc(c, &c->q, c->n_lambda))) return st;
+  if ((st = dalloc(c, &c->dinv, c->n_lambda))) return st;
+  if ((st = dalloc(c, &c->partial, 2 * c->nblocks))) return st;
+  if ((st = dalloc(c, &c->scal, 8))) return st;
+  if ((st = dalloc(c, &c->flags, 4))) return st;
+
+  cudaStream_t S = c->stream;
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, S);
+  };
+  up(c->row_ptr, row_ptr.data(), row_ptr.size() * sizeof(int64_t));
+  up(c->elem_face, elem_face.data(), elem_face.size() * sizeof(int32_t));
+  up(c->blockoff, blockoff.data(), blockoff.size() * sizeof(int64_t));
+  up(c->colour_list[0], lists[0].data(), lists[0].size() * sizeof(int32_t));
+  up(c->colour_list[1], lists[1].data(), lists[1].size() * sizeof(int32_t));
+  up(d_adj, adj.data(), adj.size() * sizeof(int32_t));
+  up(d_adjc, adj_count.data(), adj_count.size() * sizeof(int32_t));
+  for (int t = 0; t <= kMaxOrder; ++t) build_ref_tables(t, &c->tabs[t]);
+  if (e == cudaSuccess) e = upload_ref_tables(c->tabs, kMaxOrder + 1, S);
+  if (e == cudaSuccess) e = launch_expand_cols(c->row_ptr, d_adj, d_adjc, F, nfn, c->col, S, &c->prof);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S);   // host vectors die at return
+  if (e != cudaSuccess) return cuda_status(e);
+  if ((st = reset_status(c))) return st;
+  ElemArgs a = elem_args(c, nullptr, nullptr, 0);
+  if ((e = launch_check_geometry(order, a, S, &c->prof)) != cudaSuccess) return cuda_status(e);
+  return finish_phase(c);
+}
+
+int assemble_impl(hyb_ctx* c, const double* load, const double* ess, int mode) {
+  if (!c || !load) return HYB_ERR_INVALID_ARG;
+  int st = reset_status(c);
+  if (st) return st;
+  c->mode = MODE_NONE;
+  for (int colour = 0; colour < 2; ++colour) {
+    ElemArgs a = elem_args(c, load, ess, colour);
+    cudaError_t e = launch_element(c->k, mode, a, c->stream, &c->prof);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  st = finish_phase(c);
+  if (st == HYB_OK) c->mode = mode;
+  return st;
+}
+
+int recover_impl(hyb_ctx* c, const double* lam, double* u, int mode) {
+  if (!c || !lam || !u) return HYB_ERR_INVALID_ARG;
+  if (c->mode != mode) return HYB_ERR_INVALID_ARG;
+  RecoverArgs a{};
+  a.k = c->k;
+  a.n_elem = c->E;
+  a.mode = mode;
+  a.elem_face = c->elem_face;
+  a.lambda = lam;
+  a.Lstore = c->Lstore;
+  a.zstore = c->zstore;
+  a.u = u;
+  std::memcpy(a.wf, c->tabs[c->k].wf, sizeof(a.wf));
+  cudaError_t e = launch_recover(a, c->stream, &c->prof);
+  if (e != cudaSuccess) return cuda_status(e);
+  return finish_phase(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hyb_setup(const hyb_mesh* m, int order, const double* alpha, const double* beta, int precision,
+              double contrast_threshold, void* cuda_stream, hyb_ctx** out) {
+  (void)contrast_threshold;
+  if (!out) return HYB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!m || !m->vertices || !alpha || !beta) return HYB_ERR_INVALID_ARG;
+  if (m->nx < 1 || m->ny < 1 || m->nz < 1) return HYB_ERR_INVALID_ARG;
+  if ((int64_t)m->nx * m->ny * m->nz > INT32_MAX) return HYB_ERR_INVALID_ARG;
+  if (order < 0 || order > kMaxOrder) return HYB_ERR_UNSUPPORTED_ORDER;
+  if (precision != HYB_FP64) return HYB_ERR_INVALID_ARG;
+  hyb_ctx* c = new (std::nothrow) hyb_ctx();
+  if (!c) return HYB_ERR_OOM;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  int st;
+  try {
+    st = setup_impl(c, m, order, alpha, beta);
+  } catch (const std::bad_alloc&) {
+    st = HYB_ERR_OOM;
+  } catch (...) {
+    st = HYB_ERR_CUDA;
+  }
+  if (st != HYB_OK && st != HYB_ERR_MESH) {
+    hyb_destroy(c);
+    return st;
+  }
+  *out = c;   // on HYB_ERR_MESH the context is returned so the element can be queried
+  return st;
+}
+
+int hyb_assemble_reduced(hyb_ctx* ctx, const double* load, const double* ess) {
+  return assemble_impl(ctx, load, ess, MODE_HYB);
+}
+
+int staticcond_assemble(hyb_ctx* ctx, const double* load, const double* ess) {
+  return assemble_impl(ctx, load, ess, MODE_SC);
+}
+
+int hyb_solve_reduced(hyb_ctx* c, double rtol, int maxit, double* lambda, int* iters, double* rel_res) {
+  if (!c || !lambda || maxit < 0 || !(rtol >= 0.0)) return HYB_ERR_INVALID_ARG;
+  if (c->mode == MODE_NONE) return HYB_ERR_INVALID_ARG;
+  PcgArgs a{};
+  a.n = c->n_lambda;
+  a.row_ptr = c->row_ptr;
+  a.col = c->col;
+  a.val = c->val;
+  a.b = c->rhs;
+  a.x = lambda;
+  a.r = c->r;
+  a.p = c->p;
+  a.q = c->q;
+  a.dinv = c->dinv;
+  a.partial = c->partial;
+  a.scal = c->scal;
+  a.flags = c->flags;
+  a.nblocks = c->nblocks;
+  a.nfn = c->sz.nfn;
+  cudaError_t e = pcg_init(a, c->stream, &c->prof);
+  if (e != cudaSuccess) return cuda_status(e);
+  int hf[4] = {0, 0, 0, 0};
+  double hs[8] = {0};
+  int done = 0;
+  const int chunk = 32;
+  for (;;) {
+    e = cudaMemcpyAsync(hf, c->flags, sizeof(hf), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    c->prof.collect();
+    done = hf[0];
+    if (hf[1] || hf[2] || done >= maxit) break;
+    const int n = std::min(chunk, maxit - done);
+    e = pcg_iterations(a, n, rtol, c->stream, &c->prof);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  e = cudaMemcpyAsync(hs, c->scal, sizeof(hs), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (iters) *iters = done;
+  if (rel_res) *rel_res = hs[1] > 0.0 ? std::sqrt(hs[2] / hs[1]) : 0.0;
+  if (hf[2]) return HYB_ERR_BREAKDOWN;
+  if (!hf[1]) return HYB_ERR_NOT_CONVERGED;
+  return HYB_OK;
+}
+
+int hyb_recover(hyb_ctx* ctx, const double* lambda, double* u) {
+  return recover_impl(ctx, lambda, u, MODE_HYB);
+}
+
+int staticcond_recover(hyb_ctx* ctx, const double* u_face, double* u) {
+  return recover_impl(ctx, u_face, u, MODE_SC);
+}
+
+int hyb_get_reduced(hyb_ctx* c, const int64_t** row_ptr, const int32_t** col, const double** val,
+                    const double** rhs, int64_t* n, int64_t* nnz) {
+  if (!c) return HYB_ERR_INVALID_ARG;
+  if (row_ptr) *row_ptr = c->row_ptr;
+  if (col) *col = c->col;
+  if (val) *val = c->val;
+  if (rhs) *rhs = c->rhs;
+  if (n) *n = c->n_lambda;
+  if (nnz) *nnz = c->nnz;
+  return HYB_OK;
+}
+
+int hyb_export_reduced(hyb_ctx* c, int64_t* row_ptr, int32_t* col, double* val, double* rhs) {
+  if (!c) return HYB_ERR_INVALID_ARG;
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    if (dst && e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  };
+  cp(row_ptr, c->row_ptr, (c->n_lambda + 1) * sizeof(int64_t));
+  cp(col, c->col, c->nnz * sizeof(int32_t));
+  cp(val, c->val, c->nnz * sizeof(double));
+  cp(rhs, c->rhs, c->n_lambda * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_status(e);
+}
+
+int hyb_set_profiling(hyb_ctx* c, int enable) {
+  if (!c) return HYB_ERR_INVALID_ARG;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  c->prof.collect();
+  c->prof.reset();
+  c->prof.on = enable != 0;
+  return HYB_OK;
+}
+
+int hyb_get_profile(const hyb_ctx* c, int kernel_class, double* total_ms, int64_t* launches) {
+  if (!c || kernel_class < 0 || kernel_class >= HYB_K_COUNT) return HYB_ERR_INVALID_ARG;
+  if (total_ms) *total_ms = c->prof.ms[kernel_class];
+  if (launches) *launches = c->prof.launches[kernel_class];
+  return HYB_OK;
+}
+
+int hyb_get_sizes(const hyb_ctx* c, int64_t* n_elem, int* n_loc, int64_t* n_lambda, int64_t* nnz) {
+  if (!c) return HYB_ERR_INVALID_ARG;
+  if (n_elem) *n_elem = c->E;
+  if (n_loc) *n_loc = c->sz.n;
+  if (n_lambda) *n_lambda = c->n_lambda;
+  if (nnz) *nnz = c->nnz;
+  return HYB_OK;
+}
+
+int hyb_last_error_element(const hyb_ctx* c, int64_t* element) {
+  if (!c || !element) return HYB_ERR_INVALID_ARG;
+  *element = c->last_err_elem;
+  return HYB_OK;
+}
+
+void hyb_destroy(hyb_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+const char* hyb_status_string(int s) {
+  switch (s) {
+    case HYB_OK: return "HYB_OK";
+    case HYB_ERR_INVALID_ARG: return "HYB_ERR_INVALID_ARG";
+    case HYB_ERR_UNSUPPORTED_ORDER: return "HYB_ERR_UNSUPPORTED_ORDER";
+    case HYB_ERR_MESH: return "HYB_ERR_MESH";
+    case HYB_ERR_NOT_SPD: return "HYB_ERR_NOT_SPD";
+    case HYB_ERR_NOT_CONVERGED: return "HYB_ERR_NOT_CONVERGED";
+    case HYB_ERR_BREAKDOWN: return "HYB_ERR_BREAKDOWN";
+    case HYB_ERR_CUDA: return "HYB_ERR_CUDA";
+    case HYB_ERR_OOM: return "HYB_ERR_OOM";
+    case HYB_ERR_TIMEOUT: return "HYB_ERR_TIMEOUT";
+  }
+  return "HYB_ERR_UNKNOWN";
+}
+
+}  // extern "C"

@@ -1,0 +1,647 @@
+// Element-by-element elimination for algebraic hybridization and static
+// condensation (arXiv:1801.08914, Thm 2.1 / eq. 2.4, Sec. 3.1, Sec. 5), FP64.
+//
+// One CTA eliminates one hexahedron:
+//   1. geometry at the (k+2)^3 Gauss points: w J^T J / det J and w / det J;
+//   2. A_T = alpha M_T + beta K_T by sum factorisation over the three
+//      directions (the RT_k basis and the rule are tensor products);
+//   3. f_T = M_T c_T matrix-free (load given by broken-RT_k coefficients);
+//   4. essential dofs: f -= A_{:,e} u_e, rows / columns of A replaced by I;
+//   5. right-looking Cholesky of the packed lower triangle (interior dofs
+//      first, the 2x2 block form of Sec. 5), fused with z = L^{-1} f;
+//      static condensation stops after the interior columns, leaving
+//      S_hat = A_bb - A_bi A_ii^{-1} A_ib in the trailing block;
+//   6. hybridization: Y = L_bb^{-1}, S_T = D Y^T Y D, g_T = D Y^T z_b where
+//      C_T = [0 D] is diagonal (signed face Gauss weights, zero on boundary faces);
+//   7. atomic-free scatter into the CSR values of the face-multiplier system:
+//      a face block shared by two elements is stored by colour 0 and
+//      incremented by colour 1 in a later launch, every other block has one owner.
+// The factor (with Y in place of L_bb for hybridization) and z are stored for
+// the back substitution.
+#include <cuda_runtime.h>
+
+#include "hyb_internal.h"
+
+namespace hyb {
+
+__constant__ RefTables c_ref[kMaxOrder + 1];
+
+cudaError_t upload_ref_tables(const RefTables* tabs, int count, cudaStream_t s) {
+  return cudaMemcpyToSymbolAsync(c_ref, tabs, sizeof(RefTables) * count, 0, cudaMemcpyHostToDevice, s);
+}
+
+namespace {
+
+__device__ __forceinline__ int64_t tri(int i, int j) { return (int64_t)i * (i + 1) / 2 + j; }
+
+template <int K>
+struct EK {
+  static constexpr int P = K + 2, p = K + 1, Q = K + 2, NQ = Q * Q * Q;
+  static constexpr int NFN = p * p, NI = 3 * K * p * p, NB = 6 * NFN, N = NI + NB;
+  static constexpr int NC = P * p * p;                 // functions per component
+  static constexpr int NT = K == 0 ? 32 : K == 1 ? 64 : K == 2 ? 128 : 256;
+  static constexpr bool A_SMEM = K <= 2;
+  static constexpr int TRI = N * (N + 1) / 2;
+  static constexpr int TRIB = NB * (NB + 1) / 2;
+  // assembly scratch
+  static constexpr int T1SZ = 2 * Q * Q * P * P;
+  static constexpr int T2SZ = Q * P * P * p * p;
+  static constexpr int GEO = 13 * NQ;                  // Gu[6], Ga[6], Gd
+  static constexpr int ASM = T1SZ + T2SZ + GEO + 6 * NQ + p * p * Q;   // + Uq, Wq, VoVo
+  static constexpr int POST = 2 * TRIB;                // Y (column-major packed), Y^T Y (row packed)
+  static constexpr int UNION = ASM > POST ? ASM : POST;
+  // persistent: A (if in smem), f, colbuf, invdiag, X8, tables
+  static constexpr int TAB = 2 * P * Q + p * Q + 2 * Q + NFN;
+  static constexpr int SMEM_DOUBLES = (A_SMEM ? TRI : 0) + 3 * N + 24 + TAB + UNION + 4;
+  static constexpr size_t SMEM_BYTES = sizeof(double) * SMEM_DOUBLES;
+};
+
+// Local dof index of the component-c function with 1-D node indices (i0, i1, i2).
+template <int K>
+__device__ __forceinline__ int local_index(int c, int i0, int i1, int i2) {
+  constexpr int P = K + 2, p = K + 1, NI = 3 * K * p * p, NFN = p * p;
+  const int ic = c == 0 ? i0 : c == 1 ? i1 : i2;
+  if (ic > 0 && ic < P - 1) {
+    const int r0 = c == 0 ? K : p, r1 = c == 1 ? K : p;
+    const int j0 = i0 - (c == 0), j1 = i1 - (c == 1), j2 = i2 - (c == 2);
+    return c * K * p * p + j0 + r0 * (j1 + r1 * j2);
+  }
+  const int side = ic == 0 ? 0 : 1;
+  const int t0 = c == 0 ? i1 : i0;
+  const int t1 = c == 2 ? i1 : i2;
+  return NI + (2 * c + side) * NFN + t0 + p * t1;
+}
+
+// 1-D node indices of the f-th function of component c (first index fastest).
+template <int K>
+__device__ __forceinline__ void func_index(int c, int f, int& i0, int& i1, int& i2) {
+  constexpr int P = K + 2, p = K + 1;
+  const int n0 = c == 0 ? P : p, n1 = c == 1 ? P : p;
+  i0 = f % n0;
+  f /= n0;
+  i1 = f % n1;
+  i2 = f / n1;
+}
+
+// slot of the symmetric pair (a, b) in the 6-vector (00, 11, 22, 10, 20, 21)
+__device__ __forceinline__ int gslot(int a, int b) {
+  if (a == b) return a;
+  const int hi = a > b ? a : b, lo = a > b ? b : a;
+  return hi == 1 ? 3 : (lo == 0 ? 4 : 5);
+}
+
+struct Tabs {
+  const double* Vc;   // [P][Q]
+  const double* Dc;   // [P][Q]
+  const double* Vo;   // [p][Q]
+  const double* qx;
+  const double* qw;
+  const double* wf;   // [NFN]
+};
+
+// Block (c, cp) of alpha M + beta K, c >= cp, written into the packed lower triangle of A.
+template <int K>
+__device__ void assemble_block(int c, int cp, const Tabs& tb, const double* Ga, const double* Gd,
+                               const double* VoVo, double* T1, double* T2, double* A) {
+  using S = EK<K>;
+  constexpr int P = S::P, p = S::p, Q = S::Q, NT = S::NT;
+  const int tid = threadIdx.x;
+  const bool diag = c == cp;
+  const int da = c;
+  const int db = diag ? (c + 1) % 3 : cp;
+  const int dL = 3 - da - db;
+  const int nia = P, nja = diag ? P : p;                   // along da (== c)
+  const int nib = p, njb = diag ? p : P;                   // along db
+  const int niL = p, njL = p;                              // along dL (neither c nor cp)
+  const int sa = da == 0 ? 1 : da == 1 ? Q : Q * Q;
+  const int sb = db == 0 ? 1 : db == 1 ? Q : Q * Q;
+  const int sL = dL == 0 ? 1 : dL == 1 ? Q : Q * Q;
+  const double* Gm = Ga + gslot(c, cp) * S::NQ;
+
+  // stage 1: contract q_a
+  const int n1 = Q * Q * nia * nja;
+  for (int idx = tid; idx < n1; idx += NT) {
+    int r = idx;
+    const int ja = r % nja; r /= nja;
+    const int ia = r % nia; r /= nia;
+    const int qL = r % Q;
+    const int qb = r / Q;
+    double accm = 0.0, accd = 0.0;
+#pragma unroll
+    for (int qa = 0; qa < Q; ++qa) {
+      const int q = qa * sa + qb * sb + qL * sL;
+      const double rm = tb.Vc[ia * Q + qa];
+      const double rd = tb.Dc[ia * Q + qa];
+      const double cm = diag ? tb.Vc[ja * Q + qa] : tb.Vo[ja * Q + qa];
+      const double cd = diag ? tb.Dc[ja * Q + qa] : tb.Vo[ja * Q + qa];
+      accm = fma(Gm[q] * rm, cm, accm);
+      accd = fma(Gd[q] * rd, cd, accd);
+    }
+    if (diag) {
+      T1[idx] = accm + accd;
+    } else {
+      T1[idx] = accm;
+      T1[n1 + idx] = accd;
+    }
+  }
+  __syncthreads();
+
+  // stage 2: contract q_b
+  const int n2 = Q * nia * nja * nib * njb;
+  for (int idx = tid; idx < n2; idx += NT) {
+    int r = idx;
+    const int jb = r % njb; r /= njb;
+    const int ib = r % nib; r /= nib;
+    const int ja = r % nja; r /= nja;
+    const int ia = r % nia;
+    const int qL = r / nia;
+    double acc = 0.0;
+#pragma unroll
+    for (int qb = 0; qb < Q; ++qb) {
+      const int t1 = ((qb * Q + qL) * nia + ia) * nja + ja;
+      const double ro = tb.Vo[ib * Q + qb];
+      if (diag) {
+        acc = fma(T1[t1] * ro, tb.Vo[jb * Q + qb], acc);
+      } else {
+        acc = fma(ro, fma(T1[t1], tb.Vc[jb * Q + qb], T1[n1 + t1] * tb.Dc[jb * Q + qb]), acc);
+      }
+    }
+    T2[idx] = acc;
+  }
+  __syncthreads();
+
+  // stage 3: contract q_L and write
+  const int n3 = nia * nja * nib * njb * niL * njL;
+  for (int idx = tid; idx < n3; idx += NT) {
+    int r = idx;
+    const int jL = r % njL; r /= njL;
+    const int iL = r % niL; r /= niL;
+    const int jb = r % njb; r /= njb;
+    const int ib = r % nib; r /= nib;
+    const int ja = r % nja;
+    const int ia = r / nja;
+    const int i0 = da == 0 ? ia : db == 0 ? ib : iL;
+    const int i1 = da == 1 ? ia : db == 1 ? ib : iL;
+    const int i2 = da == 2 ? ia : db == 2 ? ib : iL;
+    const int j0 = da == 0 ? ja : db == 0 ? jb : jL;
+    const int j1 = da == 1 ? ja : db == 1 ? jb : jL;
+    const int j2 = da == 2 ? ja : db == 2 ? jb : jL;
+    const int rr = local_index<K>(c, i0, i1, i2);
+    const int ss = local_index<K>(cp, j0, j1, j2);
+    if (diag && rr < ss) continue;
+    const int t2 = (((ia * nja + ja) * nib + ib) * njb + jb);
+    double acc = 0.0;
+#pragma unroll
+    for (int qL = 0; qL < Q; ++qL)
+      acc = fma(T2[qL * (nia * nja * nib * njb) + t2], VoVo[(iL * p + jL) * Q + qL], acc);
+    A[rr >= ss ? tri(rr, ss) : tri(ss, rr)] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void set_error(int* status, long long* err_elem, int code, long long e) {
+  if (atomicCAS(status, 0, code) == 0) *err_elem = e;
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
+  using S = EK<K>;
+  constexpr int P = S::P, p = S::p, Q = S::Q, NQ = S::NQ, NFN = S::NFN, NI = S::NI, NB = S::NB, N = S::N;
+  constexpr int NT = S::NT;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
+  extern __shared__ double smem[];
+
+  const int64_t li = blockIdx.x;
+  if (li >= args.n_list) return;
+  const int64_t e = args.elem_list[li];
+  const int ex = (int)(e % args.nx), ey = (int)((e / args.nx) % args.ny), ez = (int)(e / ((int64_t)args.nx * args.ny));
+
+  // ---- shared memory carve-up
+  double* sp = smem;
+  double* A = S::A_SMEM ? sp : args.Lstore + e * (int64_t)S::TRI;
+  if (S::A_SMEM) sp += S::TRI;
+  double* f = sp; sp += N;
+  double* colbuf = sp; sp += N;
+  double* invd = sp; sp += N;
+  double* X8 = sp; sp += 24;
+  double* Vc = sp; sp += P * Q;
+  double* Dc = sp; sp += P * Q;
+  double* Vo = sp; sp += p * Q;
+  double* qx = sp; sp += Q;
+  double* qw = sp; sp += Q;
+  double* wf = sp; sp += NFN;
+  double* flag = sp; sp += 4;
+  double* U = sp;                           // union region
+  // assembly view
+  double* T1 = U;
+  double* T2 = T1 + S::T1SZ;
+  double* Gu = T2 + S::T2SZ;                // [6][NQ] unit-coefficient mass weights
+  double* Ga = Gu + 6 * NQ;                 // [6][NQ] alpha-scaled
+  double* Gd = Ga + 6 * NQ;                 // [NQ]    beta-scaled divergence weights
+  double* Uq = Gd + NQ;                     // [3][NQ]
+  double* Wq = Uq + 3 * NQ;                 // [3][NQ]
+  double* VoVo = Wq + 3 * NQ;               // [p][p][Q]
+  // post-factorisation view
+  double* Y = U;                            // column-major packed lower, NB
+  double* YtY = U + S::TRIB;                // row-major packed lower, NB
+
+  const RefTables& rt = c_ref[K];
+  for (int i = tid; i < P * Q; i += NT) {
+    Vc[i] = rt.Vc[i / Q][i % Q];
+    Dc[i] = rt.Dc[i / Q][i % Q];
+  }
+  for (int i = tid; i < p * Q; i += NT) Vo[i] = rt.Vo[i / Q][i % Q];
+  for (int i = tid; i < Q; i += NT) { qx[i] = rt.qx[i]; qw[i] = rt.qw[i]; }
+  for (int i = tid; i < NFN; i += NT) wf[i] = rt.wf[i];
+  if (tid < 24) {
+    const int c = tid / 3, d = tid % 3;
+    const int64_t v = (ex + (c & 1)) + (int64_t)(args.nx + 1) * ((ey + ((c >> 1) & 1)) + (int64_t)(args.ny + 1) * (ez + (c >> 2)));
+    X8[tid] = args.vertices[3 * v + d];
+  }
+  __syncthreads();
+  for (int i = tid; i < p * p * Q; i += NT) {
+    const int q = i % Q, jl = (i / Q) % p, il = i / (Q * p);
+    VoVo[i] = Vo[il * Q + q] * Vo[jl * Q + q];
+  }
+
+  // ---- 1. geometry
+  const double alpha = args.alpha[e], beta = args.beta[e];
+  for (int q = tid; q < NQ; q += NT) {
+    const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
+    const double x0 = qx[q0], x1 = qx[q1], x2 = qx[q2];
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int s0 = c & 1, s1 = (c >> 1) & 1, s2 = c >> 2;
+      const double f0 = s0 ? x0 : 1.0 - x0, f1 = s1 ? x1 : 1.0 - x1, f2 = s2 ? x2 : 1.0 - x2;
+      const double g0 = s0 ? 1.0 : -1.0, g1 = s1 ? 1.0 : -1.0, g2 = s2 ? 1.0 : -1.0;
+      const double d0 = g0 * f1 * f2, d1 = f0 * g1 * f2, d2 = f0 * f1 * g2;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const double xv = X8[3 * c + r];
+        J[r][0] = fma(xv, d0, J[r][0]);
+        J[r][1] = fma(xv, d1, J[r][1]);
+        J[r][2] = fma(xv, d2, J[r][2]);
+      }
+    }
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    if (!(det > 0.0)) set_error(args.status, args.err_elem, HYB_ERR_MESH, e);
+    const double s = qw[q0] * qw[q1] * qw[q2] / det;
+    double g[6];
+    g[0] = J[0][0] * J[0][0] + J[1][0] * J[1][0] + J[2][0] * J[2][0];
+    g[1] = J[0][1] * J[0][1] + J[1][1] * J[1][1] + J[2][1] * J[2][1];
+    g[2] = J[0][2] * J[0][2] + J[1][2] * J[1][2] + J[2][2] * J[2][2];
+    g[3] = J[0][1] * J[0][0] + J[1][1] * J[1][0] + J[2][1] * J[2][0];
+    g[4] = J[0][2] * J[0][0] + J[1][2] * J[1][0] + J[2][2] * J[2][0];
+    g[5] = J[0][2] * J[0][1] + J[1][2] * J[1][1] + J[2][2] * J[2][1];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      Gu[t * NQ + q] = s * g[t];
+      Ga[t * NQ + q] = alpha * s * g[t];
+    }
+    Gd[q] = beta * s;
+  }
+  __syncthreads();
+
+  // ---- 2. A_T by sum factorisation (6 blocks, c >= cp)
+  const Tabs tb{Vc, Dc, Vo, qx, qw, wf};
+  assemble_block<K>(0, 0, tb, Ga, Gd, VoVo, T1, T2, A);
+  assemble_block<K>(1, 1, tb, Ga, Gd, VoVo, T1, T2, A);
+  assemble_block<K>(2, 2, tb, Ga, Gd, VoVo, T1, T2, A);
+  assemble_block<K>(1, 0, tb, Ga, Gd, VoVo, T1, T2, A);
+  assemble_block<K>(2, 0, tb, Ga, Gd, VoVo, T1, T2, A);
+  assemble_block<K>(2, 1, tb, Ga, Gd, VoVo, T1, T2, A);
+
+  // ---- 3. load f = M c (matrix-free): field components at the Gauss points, times w J^T J / det J, tested
+  const double* coef = args.load + e * (int64_t)N;
+  for (int t = tid; t < 3 * NQ; t += NT) {
+    const int c = t / NQ, q = t % NQ;
+    const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
+    double acc = 0.0;
+    for (int fi = 0; fi < S::NC; ++fi) {
+      int i0, i1, i2;
+      func_index<K>(c, fi, i0, i1, i2);
+      const double b0 = c == 0 ? Vc[i0 * Q + q0] : Vo[i0 * Q + q0];
+      const double b1 = c == 1 ? Vc[i1 * Q + q1] : Vo[i1 * Q + q1];
+      const double b2 = c == 2 ? Vc[i2 * Q + q2] : Vo[i2 * Q + q2];
+      acc = fma(coef[local_index<K>(c, i0, i1, i2)], b0 * b1 * b2, acc);
+    }
+    Uq[c * NQ + q] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < 3 * NQ; t += NT) {
+    const int c = t / NQ, q = t % NQ;
+    Wq[c * NQ + q] = Gu[gslot(c, 0) * NQ + q] * Uq[q] + Gu[gslot(c, 1) * NQ + q] * Uq[NQ + q] +
+                     Gu[gslot(c, 2) * NQ + q] * Uq[2 * NQ + q];
+  }
+  __syncthreads();
+  for (int t = tid; t < 3 * S::NC; t += NT) {
+    const int c = t / S::NC, fi = t % S::NC;
+    int i0, i1, i2;
+    func_index<K>(c, fi, i0, i1, i2);
+    double acc = 0.0;
+    for (int q = 0; q < NQ; ++q) {
+      const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
+      const double b0 = c == 0 ? Vc[i0 * Q + q0] : Vo[i0 * Q + q0];
+      const double b1 = c == 1 ? Vc[i1 * Q + q1] : Vo[i1 * Q + q1];
+      const double b2 = c == 2 ? Vc[i2 * Q + q2] : Vo[i2 * Q + q2];
+      acc = fma(b0 * b1 * b2, Wq[c * NQ + q], acc);
+    }
+    f[local_index<K>(c, i0, i1, i2)] = acc;
+  }
+  __syncthreads();
+
+  // ---- 4. essential dofs on boundary faces: f -= A_{:,e} u_e, then rows / columns -> identity
+  const int32_t* ef = args.elem_face + e * 6;
+  int bmask = 0;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) bmask |= (ef[a] < 0) << a;
+  if (bmask) {
+    const double* ue = args.ess ? args.ess + e * (int64_t)N : nullptr;
+    if (ue) {
+      for (int i = tid; i < N; i += NT) {
+        const bool ie = i >= NI && ((bmask >> ((i - NI) / NFN)) & 1);
+        if (ie) continue;
+        double acc = f[i];
+        for (int a = 0; a < 6; ++a) {
+          if (!((bmask >> a) & 1)) continue;
+          for (int m = 0; m < NFN; ++m) {
+            const int j = NI + a * NFN + m;
+            acc -= A[i >= j ? tri(i, j) : tri(j, i)] * ue[j];
+          }
+        }
+        colbuf[i] = acc;
+      }
+      __syncthreads();
+      for (int i = tid; i < N; i += NT) {
+        const bool ie = i >= NI && ((bmask >> ((i - NI) / NFN)) & 1);
+        f[i] = ie ? ue[i] : colbuf[i];
+      }
+    } else {
+      for (int i = tid; i < NB; i += NT)
+        if ((bmask >> (i / NFN)) & 1) f[NI + i] = 0.0;
+    }
+    __syncthreads();
+    // identity rows / columns
+    for (int a = 0; a < 6; ++a) {
+      if (!((bmask >> a) & 1)) continue;
+      for (int t = tid; t < NFN * N; t += NT) {
+        const int m = t / N, j = t % N;
+        const int i = NI + a * NFN + m;
+        const double v = (i == j) ? 1.0 : 0.0;
+        A[i >= j ? tri(i, j) : tri(j, i)] = v;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+
+  // ---- 5. Cholesky (right-looking, packed lower) fused with z = L^{-1} f
+  const int jend = MODE == MODE_SC ? NI : N;
+  if (tid == 0) {
+    const double d = jend > 0 ? A[0] : 1.0;
+    const double r = d > 0.0 ? sqrt(d) : 1.0;
+    flag[0] = d;
+    flag[1] = r;
+    flag[2] = 1.0 / r;
+  }
+  __syncthreads();
+  for (int j = 0; j < jend; ++j) {
+    const double d = flag[0];
+    if (!(d > 0.0) || !(d < INFINITY)) {
+      if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
+      return;                               // uniform: every thread read the same pivot
+    }
+    const double ljj = flag[1];
+    const double inv = flag[2];
+    for (int i = j + 1 + tid; i < N; i += NT) {
+      const double v = A[tri(i, j)] * inv;
+      A[tri(i, j)] = v;
+      colbuf[i] = v;
+    }
+    if (tid == 0) {
+      A[tri(j, j)] = ljj;
+      invd[j] = inv;
+      f[j] = f[j] * inv;                    // z_j
+    }
+    __syncthreads();
+    const double zj = f[j];
+    for (int i = j + 1 + warp; i < N; i += NW) {
+      const double lij = colbuf[i];
+      double* row = A + tri(i, 0);
+      for (int l = j + 1 + lane; l <= i; l += 32) row[l] = fma(-lij, colbuf[l], row[l]);
+      if (lane == 0) f[i] = fma(-lij, zj, f[i]);
+    }
+    __syncthreads();
+    if (tid == 0 && j + 1 < jend) {
+      const double dn = A[tri(j + 1, j + 1)];
+      const double r = dn > 0.0 ? sqrt(dn) : 1.0;
+      flag[0] = dn;
+      flag[1] = r;
+      flag[2] = 1.0 / r;
+    }
+    __syncthreads();
+  }
+
+  // ---- store z
+  double* zs = args.zstore + e * (int64_t)N;
+  for (int i = tid; i < N; i += NT) zs[i] = f[i];
+
+  // C_T = [0 D]: D_i = sign(face) * face weight on interior faces, 0 on boundary faces
+  const int32_t* bo_face = ef;
+  const int64_t* boff = args.blockoff + e * 36;
+
+  if (MODE == MODE_HYB) {
+    // ---- 6a. Y = L_bb^{-1} (column-major packed), row by row
+    auto yidx = [](int m, int i) { return i * NB - i * (i - 1) / 2 + (m - i); };   // m >= i
+    for (int i = 0; i < NB; ++i) {
+      const double* Li = A + tri(NI + i, NI);
+      const double di = invd[NI + i];
+      for (int jj = tid; jj <= i; jj += NT) {
+        double v;
+        if (jj == i) {
+          v = di;
+        } else {
+          double acc = 0.0;
+          for (int m = jj; m < i; ++m) acc = fma(Li[m], Y[yidx(m, jj)], acc);
+          v = -di * acc;
+        }
+        Y[yidx(i, jj)] = v;
+      }
+      __syncthreads();
+    }
+    // ---- 6b. Y^T Y (lower), g = D Y^T z_b
+    for (int t = tid; t < S::TRIB; t += NT) {
+      // decode t -> (i, jj), i >= jj, row-major packed
+      int i = (int)((sqrtf((float)(8 * t + 1)) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      while (i * (i + 1) / 2 > t) --i;
+      const int jj = t - i * (i + 1) / 2;
+      double acc = 0.0;
+      const double* yi = Y + yidx(i, i);
+      const double* yj = Y + yidx(i, jj);
+      for (int m = 0; m < NB - i; ++m) acc = fma(yi[m], yj[m], acc);
+      YtY[t] = acc;
+    }
+    __syncthreads();
+    // ---- 7. scatter S_T = D Y^T Y D and g_T
+    for (int t = tid; t < NB * NB; t += NT) {
+      const int ib = t / NB, jb = t % NB;
+      const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
+      if (bo_face[a] < 0 || bo_face[b] < 0) continue;
+      const double di = ((a & 1) ? 1.0 : -1.0) * wf[m1];
+      const double dj = ((b & 1) ? 1.0 : -1.0) * wf[m2];
+      const double v = di * dj * YtY[ib >= jb ? tri(ib, jb) : tri(jb, ib)];
+      const int64_t r0 = args.row_ptr[(int64_t)bo_face[a] * NFN];
+      const int64_t rl = args.row_ptr[(int64_t)bo_face[a] * NFN + 1] - r0;
+      const int64_t pos = boff[a * 6 + b] + m1 * rl + m2;
+      if (a == b && args.colour == 1) args.val[pos] += v;
+      else args.val[pos] = v;
+    }
+    for (int ib = tid; ib < NB; ib += NT) {
+      const int a = ib / NFN, m1 = ib % NFN;
+      if (bo_face[a] < 0) continue;
+      double acc = 0.0;
+      for (int m = ib; m < NB; ++m) acc = fma(Y[yidx(m, ib)], f[NI + m], acc);
+      const double v = ((a & 1) ? 1.0 : -1.0) * wf[m1] * acc;
+      const int64_t gi = (int64_t)bo_face[a] * NFN + m1;
+      if (args.colour == 1) args.rhs[gi] += v;
+      else args.rhs[gi] = v;
+    }
+    __syncthreads();
+    // ---- store the factor with Y in place of L_bb
+    double* Ls = args.Lstore + e * (int64_t)S::TRI;
+    if (S::A_SMEM) {
+      for (int64_t t = tid; t < S::TRI; t += NT) Ls[t] = A[t];
+      __syncthreads();
+    }
+    for (int t = tid; t < S::TRIB; t += NT) {
+      int i = (int)((sqrtf((float)(8 * t + 1)) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      while (i * (i + 1) / 2 > t) --i;
+      const int jj = t - i * (i + 1) / 2;
+      Ls[tri(NI + i, NI + jj)] = Y[yidx(i, jj)];
+    }
+  } else {
+    // ---- static condensation: scatter S_hat (trailing block) and rhs_b = f_b - L_bi z_i
+    for (int t = tid; t < NB * NB; t += NT) {
+      const int ib = t / NB, jb = t % NB;
+      const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
+      if (bo_face[a] < 0 || bo_face[b] < 0) continue;
+      const double v = A[ib >= jb ? tri(NI + ib, NI + jb) : tri(NI + jb, NI + ib)];
+      const int64_t r0 = args.row_ptr[(int64_t)bo_face[a] * NFN];
+      const int64_t rl = args.row_ptr[(int64_t)bo_face[a] * NFN + 1] - r0;
+      const int64_t pos = boff[a * 6 + b] + m1 * rl + m2;
+      if (a == b && args.colour == 1) args.val[pos] += v;
+      else args.val[pos] = v;
+    }
+    for (int ib = tid; ib < NB; ib += NT) {
+      const int a = ib / NFN, m1 = ib % NFN;
+      if (bo_face[a] < 0) continue;
+      const int64_t gi = (int64_t)bo_face[a] * NFN + m1;
+      if (args.colour == 1) args.rhs[gi] += f[NI + ib];
+      else args.rhs[gi] = f[NI + ib];
+    }
+    if (S::A_SMEM) {
+      double* Ls = args.Lstore + e * (int64_t)S::TRI;
+      for (int64_t t = tid; t < S::TRI; t += NT) Ls[t] = A[t];
+    }
+  }
+}
+
+// det J > 0 at the 8 corners and every Gauss point of every element.
+template <int K>
+__global__ void check_geometry_kernel(ElemArgs args) {
+  constexpr int Q = K + 2, NQ = Q * Q * Q;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= args.n_elem) return;
+  const int ex = (int)(e % args.nx), ey = (int)((e / args.nx) % args.ny), ez = (int)(e / ((int64_t)args.nx * args.ny));
+  double X[24];
+  for (int c = 0; c < 8; ++c) {
+    const int64_t v = (ex + (c & 1)) + (int64_t)(args.nx + 1) * ((ey + ((c >> 1) & 1)) + (int64_t)(args.ny + 1) * (ez + (c >> 2)));
+    for (int d = 0; d < 3; ++d) X[3 * c + d] = args.vertices[3 * v + d];
+  }
+  const RefTables& rt = c_ref[K];
+  bool ok = true;
+  for (int q = 0; q < NQ + 8; ++q) {
+    double x0, x1, x2;
+    if (q < NQ) {
+      x0 = rt.qx[q % Q]; x1 = rt.qx[(q / Q) % Q]; x2 = rt.qx[q / (Q * Q)];
+    } else {
+      const int c = q - NQ;
+      x0 = c & 1; x1 = (c >> 1) & 1; x2 = c >> 2;
+    }
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int c = 0; c < 8; ++c) {
+      const int s0 = c & 1, s1 = (c >> 1) & 1, s2 = c >> 2;
+      const double f0 = s0 ? x0 : 1.0 - x0, f1 = s1 ? x1 : 1.0 - x1, f2 = s2 ? x2 : 1.0 - x2;
+      const double d0 = (s0 ? 1.0 : -1.0) * f1 * f2, d1 = f0 * (s1 ? 1.0 : -1.0) * f2, d2 = f0 * f1 * (s2 ? 1.0 : -1.0);
+      for (int r = 0; r < 3; ++r) {
+        J[r][0] += X[3 * c + r] * d0;
+        J[r][1] += X[3 * c + r] * d1;
+        J[r][2] += X[3 * c + r] * d2;
+      }
+    }
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    ok = ok && (det > 0.0);
+  }
+  if (!ok) set_error(args.status, args.err_elem, HYB_ERR_MESH, e);
+}
+
+template <int K>
+cudaError_t launch_element_k(int mode, const ElemArgs& a, cudaStream_t s, Prof* prof) {
+  using S = EK<K>;
+  if (a.n_list == 0) return cudaSuccess;
+  const size_t smem = S::SMEM_BYTES;
+  cudaError_t err;
+  if (mode == MODE_HYB) {
+    err = cudaFuncSetAttribute(element_kernel<K, MODE_HYB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+    element_kernel<K, MODE_HYB><<<(unsigned)a.n_list, S::NT, smem, s>>>(a);
+    prof_end(prof, tok, s);
+  } else {
+    err = cudaFuncSetAttribute(element_kernel<K, MODE_SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+    element_kernel<K, MODE_SC><<<(unsigned)a.n_list, S::NT, smem, s>>>(a);
+    prof_end(prof, tok, s);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_element(int k, int mode, const ElemArgs& a, cudaStream_t s, Prof* prof) {
+  switch (k) {
+    case 0: return launch_element_k<0>(mode, a, s, prof);
+    case 1: return launch_element_k<1>(mode, a, s, prof);
+    case 2: return launch_element_k<2>(mode, a, s, prof);
+    case 3: return launch_element_k<3>(mode, a, s, prof);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_check_geometry(int k, const ElemArgs& a, cudaStream_t s, Prof* prof) {
+  const int nt = 128;
+  const unsigned nb = (unsigned)((a.n_elem + nt - 1) / nt);
+  if (nb == 0) return cudaSuccess;
+  const int tok = prof_begin(prof, HYB_K_SETUP, s);
+  switch (k) {
+    case 0: check_geometry_kernel<0><<<nb, nt, 0, s>>>(a); break;
+    case 1: check_geometry_kernel<1><<<nb, nt, 0, s>>>(a); break;
+    case 2: check_geometry_kernel<2><<<nb, nt, 0, s>>>(a); break;
+    case 3: check_geometry_kernel<3><<<nb, nt, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  prof_end(prof, tok, s);
+  return cudaGetLastError();
+}
+
+}  // namespace hyb

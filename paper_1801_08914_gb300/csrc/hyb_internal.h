@@ -1,0 +1,114 @@
+// Internal declarations shared by the translation units of libhyb.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hyb.h"
+
+namespace hyb {
+
+// Largest supported order and the table sizes it implies.
+constexpr int kMaxOrder = 3;
+constexpr int kMaxQ = kMaxOrder + 2;      // quadrature points per direction ((k+2)-point Gauss-Legendre)
+constexpr int kMaxClosed = kMaxOrder + 2; // Gauss-Lobatto nodes along a component
+constexpr int kMaxOpen = kMaxOrder + 1;   // Gauss-Legendre nodes across a component
+
+// 1-D reference tables of one order k, computed on the host (hyb_tables.cpp).
+struct RefTables {
+  double qx[kMaxQ], qw[kMaxQ];              // quadrature nodes / weights on [0,1]
+  double Vc[kMaxClosed][kMaxQ];             // closed Lagrange values at the quadrature nodes
+  double Dc[kMaxClosed][kMaxQ];             // their derivatives
+  double Vo[kMaxOpen][kMaxQ];               // open Lagrange values
+  double wf[kMaxOpen * kMaxOpen];           // face Gauss-Legendre weights (lower axis fastest)
+};
+
+// Element sizes for order k.
+struct Sizes {
+  int k, P, p, Q, NQ, nfn, ni, nb, n;
+  static Sizes of(int k) {
+    Sizes s;
+    s.k = k; s.P = k + 2; s.p = k + 1; s.Q = k + 2; s.NQ = s.Q * s.Q * s.Q;
+    s.nfn = s.p * s.p; s.ni = 3 * k * s.p * s.p; s.nb = 6 * s.nfn; s.n = s.ni + s.nb;
+    return s;
+  }
+};
+
+enum Mode { MODE_NONE = 0, MODE_HYB = 1, MODE_SC = 2 };
+
+// Device-side view of one problem, passed by value to kernels.
+struct ElemArgs {
+  int nx, ny, nz;
+  int64_t n_elem;
+  const double* vertices;
+  const double* alpha;
+  const double* beta;
+  const double* load;
+  const double* ess;          // may be null
+  const int32_t* elem_list;   // elements of the colour being processed
+  int64_t n_list;
+  int colour;                 // 0: store shared face blocks, 1: add to them
+  const int32_t* elem_face;   // E x 6 interior-face index, -1 on boundary faces
+  const int64_t* blockoff;    // E x 36 value offset of face block (a, b) for row node 0, -1 if absent
+  const int64_t* row_ptr;
+  double* val;                // CSR values of H or S
+  double* rhs;                // right-hand side
+  double* Lstore;             // E x n(n+1)/2 packed lower factor
+  double* zstore;             // E x n forward-substituted load
+  int* status;
+  long long* err_elem;
+};
+
+// Launch profile: CUDA events around each launch, accumulated per kernel class
+// after the owning call has synchronised (hyb_api.cpp).
+struct Prof;
+int prof_begin(Prof* p, int cls, cudaStream_t s);   // returns a token, -1 when off
+void prof_end(Prof* p, int token, cudaStream_t s);
+
+// status helpers
+__host__ __device__ inline int64_t tri_size(int n) { return (int64_t)n * (n + 1) / 2; }
+
+// Host-side table construction (hyb_tables.cpp).
+void build_ref_tables(int k, RefTables* t);
+
+// Kernel launchers (hyb_element.cu, hyb_solve.cu, hyb_recover.cu). Return a cudaError_t.
+cudaError_t upload_ref_tables(const RefTables* tabs, int count, cudaStream_t s);
+cudaError_t launch_check_geometry(int k, const ElemArgs& a, cudaStream_t s, Prof* prof);
+cudaError_t launch_element(int k, int mode, const ElemArgs& a, cudaStream_t s, Prof* prof);
+cudaError_t launch_expand_cols(const int64_t* row_ptr, const int32_t* adj, const int32_t* adj_count,
+                               int64_t n_faces, int nfn, int32_t* col, cudaStream_t s, Prof* prof);
+
+struct PcgArgs {
+  int64_t n;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+  const double* b;
+  double* x;
+  double* r;
+  double* p;
+  double* q;
+  double* dinv;
+  double* partial;           // per-block partial sums
+  double* scal;              // device scalars
+  int* flags;                // iteration count / converged / breakdown / ticket
+  int nblocks;               // grid size of every PCG kernel (partial holds 2*nblocks)
+  int nfn;                   // rows per face ((k+1)^2): rows of a face share their column list
+};
+cudaError_t pcg_init(const PcgArgs& a, cudaStream_t s, Prof* prof);
+cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_t s, Prof* prof);
+
+struct RecoverArgs {
+  int k;
+  int64_t n_elem;
+  int mode;
+  const int32_t* elem_face;
+  const double* lambda;       // multipliers (HB) or global face dofs (SC)
+  const double* Lstore;
+  const double* zstore;
+  double* u;
+  double wf[kMaxOpen * kMaxOpen];   // face Gauss weights of order k (C_T = [0 D])
+};
+cudaError_t launch_recover(const RecoverArgs& a, cudaStream_t s, Prof* prof);
+
+}  // namespace hyb

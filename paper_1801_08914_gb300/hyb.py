@@ -1,0 +1,226 @@
+"""Thin ctypes binding of libhyb.so (include/hyb.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Arrays are torch tensors on the CUDA device (float64, contiguous); the binding
+passes their data pointers and the current torch stream. There is no CPU
+fallback: importing this module without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhyb.so")
+
+HYB_OK = 0
+HYB_ERR_INVALID_ARG = -1
+HYB_ERR_UNSUPPORTED_ORDER = -2
+HYB_ERR_MESH = -3
+HYB_ERR_NOT_SPD = -4
+HYB_ERR_NOT_CONVERGED = -5
+HYB_ERR_BREAKDOWN = -6
+HYB_ERR_CUDA = -7
+HYB_ERR_OOM = -8
+HYB_ERR_TIMEOUT = -9
+HYB_FP64 = 0
+HYB_MIXED = 1
+KERNEL_CLASSES = {"element": 0, "spmv": 1, "pcg_vector": 2, "recover": 3, "setup": 4}
+
+EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recover",
+           "staticcond_assemble", "staticcond_recover", "hyb_get_reduced", "hyb_export_reduced", "hyb_get_sizes",
+           "hyb_set_profiling", "hyb_get_profile",
+           "hyb_last_error_element", "hyb_destroy", "hyb_status_string"]
+
+
+class HybError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("vertices", ctypes.c_void_p)]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhyb.so not built at {path}: run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    lib.hyb_setup.argtypes = [ctypes.POINTER(_Mesh), I, P, P, I, D, P, ctypes.POINTER(P)]
+    lib.hyb_assemble_reduced.argtypes = [P, P, P]
+    lib.staticcond_assemble.argtypes = [P, P, P]
+    lib.hyb_solve_reduced.argtypes = [P, D, I, P, ctypes.POINTER(I), ctypes.POINTER(D)]
+    lib.hyb_recover.argtypes = [P, P, P]
+    lib.staticcond_recover.argtypes = [P, P, P]
+    lib.hyb_get_reduced.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                    ctypes.POINTER(P), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.hyb_export_reduced.argtypes = [P, P, P, P, P]
+    lib.hyb_set_profiling.argtypes = [P, I]
+    lib.hyb_get_profile.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
+    lib.hyb_get_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I64),
+                                  ctypes.POINTER(I64)]
+    lib.hyb_last_error_element.argtypes = [P, ctypes.POINTER(I64)]
+    lib.hyb_destroy.argtypes = [P]
+    lib.hyb_destroy.restype = None
+    lib.hyb_status_string.argtypes = [I]
+    lib.hyb_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("hyb_destroy", "hyb_status_string"):
+            getattr(lib, name).restype = I
+    return lib
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().hyb_status_string(int(status)).decode()
+
+
+def _ptr(t, name, dtype=torch.float64):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(st: int, where: str, ok=(HYB_OK,)):
+    if st not in ok:
+        raise HybError(st, where)
+    return st
+
+
+class Context:
+    """Owns a hyb_ctx* and keeps the tensors the library holds pointers to alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def sizes(self):
+        E, L, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        n = ctypes.c_int()
+        _check(lib().hyb_get_sizes(self.handle, ctypes.byref(E), ctypes.byref(n), ctypes.byref(L),
+                                   ctypes.byref(nnz)), "hyb_get_sizes")
+        return dict(n_elem=E.value, n_loc=n.value, n_lambda=L.value, nnz=nnz.value)
+
+    def close(self):
+        if self.handle:
+            lib().hyb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hyb_setup(vertices, nx, ny, nz, order, alpha, beta, precision=HYB_FP64, contrast_threshold=0.0,
+              stream=None, check=True):
+    m = _Mesh(int(nx), int(ny), int(nz), _ptr(vertices, "vertices"))
+    h = ctypes.c_void_p()
+    st = lib().hyb_setup(ctypes.byref(m), int(order), _ptr(alpha, "alpha"), _ptr(beta, "beta"),
+                         int(precision), float(contrast_threshold), _stream(stream), ctypes.byref(h))
+    ctx = Context(h, (vertices, alpha, beta)) if h.value else None
+    if check:
+        _check(st, "hyb_setup")
+        return ctx
+    return ctx, st
+
+
+def hyb_assemble_reduced(ctx, load, ess=None, check=True):
+    st = lib().hyb_assemble_reduced(ctx.handle, _ptr(load, "load"), _ptr(ess, "ess"))
+    return _check(st, "hyb_assemble_reduced") if check else st
+
+
+def staticcond_assemble(ctx, load, ess=None, check=True):
+    st = lib().staticcond_assemble(ctx.handle, _ptr(load, "load"), _ptr(ess, "ess"))
+    return _check(st, "staticcond_assemble") if check else st
+
+
+def hyb_solve_reduced(ctx, rtol, maxit, lam, check=True):
+    """Returns (iterations, relative residual, status)."""
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = lib().hyb_solve_reduced(ctx.handle, float(rtol), int(maxit), _ptr(lam, "lambda"),
+                                 ctypes.byref(it), ctypes.byref(rr))
+    if check:
+        _check(st, "hyb_solve_reduced")
+    return it.value, rr.value, st
+
+
+def hyb_recover(ctx, lam, u, check=True):
+    st = lib().hyb_recover(ctx.handle, _ptr(lam, "lambda"), _ptr(u, "u"))
+    return _check(st, "hyb_recover") if check else st
+
+
+def staticcond_recover(ctx, u_face, u, check=True):
+    st = lib().staticcond_recover(ctx.handle, _ptr(u_face, "u_face"), _ptr(u, "u"))
+    return _check(st, "staticcond_recover") if check else st
+
+
+def hyb_get_reduced(ctx):
+    """Borrowed device pointers and sizes of the context's reduced system (ints)."""
+    P = ctypes.c_void_p
+    rp, cl, vl, rh = P(), P(), P(), P()
+    n, nnz = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().hyb_get_reduced(ctx.handle, ctypes.byref(rp), ctypes.byref(cl), ctypes.byref(vl),
+                                 ctypes.byref(rh), ctypes.byref(n), ctypes.byref(nnz)), "hyb_get_reduced")
+    return dict(row_ptr=rp.value, col=cl.value, val=vl.value, rhs=rh.value, n=n.value, nnz=nnz.value)
+
+
+def hyb_export_reduced(ctx):
+    """Copies of the reduced CSR system as CUDA tensors: row_ptr (int64), col (int32), val, rhs."""
+    sz = ctx.sizes()
+    n, nnz = sz["n_lambda"], sz["nnz"]
+    out = dict(row_ptr=torch.empty(n + 1, dtype=torch.int64, device="cuda"),
+               col=torch.empty(nnz, dtype=torch.int32, device="cuda"),
+               val=torch.empty(nnz, dtype=torch.float64, device="cuda"),
+               rhs=torch.empty(n, dtype=torch.float64, device="cuda"))
+    torch.cuda.current_stream().synchronize()
+    _check(lib().hyb_export_reduced(ctx.handle, _ptr(out["row_ptr"], "row_ptr", torch.int64),
+                                    _ptr(out["col"], "col", torch.int32), _ptr(out["val"], "val"),
+                                    _ptr(out["rhs"], "rhs")), "hyb_export_reduced")
+    return out
+
+
+def hyb_set_profiling(ctx, enable):
+    return _check(lib().hyb_set_profiling(ctx.handle, int(bool(enable))), "hyb_set_profiling")
+
+
+def hyb_get_profile(ctx):
+    """{kernel class: (total ms, launches)} since profiling was enabled."""
+    out = {}
+    for name, cls in KERNEL_CLASSES.items():
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(lib().hyb_get_profile(ctx.handle, cls, ctypes.byref(ms), ctypes.byref(n)), "hyb_get_profile")
+        out[name] = (ms.value, n.value)
+    return out
+
+
+def hyb_last_error_element(ctx):
+    e = ctypes.c_int64()
+    _check(lib().hyb_last_error_element(ctx.handle, ctypes.byref(e)), "hyb_last_error_element")
+    return e.value

@@ -1,0 +1,54 @@
+"""Shared drivers for the GPU parity tests: run the CUDA path through the C ABI and the CPU oracle
+on the same seeded inputs, and derive tolerances from the conditioning."""
+import numpy as np
+import scipy.sparse as sp
+
+EPS = np.finfo(np.float64).eps
+
+
+def dev(a, dtype=None):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def gpu_run(p, mode="hyb", rtol=1e-14, maxit=100000, solve=True):
+    """setup -> assemble -> export reduced system -> PCG -> recover, all through libhyb."""
+    import torch
+    from paper_1801_08914_gb300 import hyb
+    ctx = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta))
+    load = dev(p.load)
+    ess = None if p.ess is None else dev(p.ess)
+    if mode == "hyb":
+        hyb.hyb_assemble_reduced(ctx, load, ess)
+    else:
+        hyb.staticcond_assemble(ctx, load, ess)
+    red = {k: v.cpu().numpy() for k, v in hyb.hyb_export_reduced(ctx).items()}
+    sz = ctx.sizes()
+    out = dict(red=red, sizes=sz)
+    if solve:
+        lam = torch.zeros(sz["n_lambda"], dtype=torch.float64, device="cuda")
+        it, rr, st = hyb.hyb_solve_reduced(ctx, rtol, maxit, lam, check=False)
+        u = torch.zeros(sz["n_elem"], sz["n_loc"], dtype=torch.float64, device="cuda")
+        if mode == "hyb":
+            hyb.hyb_recover(ctx, lam, u)
+        else:
+            hyb.staticcond_recover(ctx, lam, u)
+        torch.cuda.synchronize()
+        out.update(lam=lam.cpu().numpy(), u=u.cpu().numpy(), it=it, rr=rr, status=st)
+    ctx.close()
+    return out
+
+
+def csr(red):
+    n = red["row_ptr"].size - 1
+    return sp.csr_matrix((red["val"], red["col"], red["row_ptr"]), shape=(n, n))
+
+
+def rel(a, b):
+    nb = np.linalg.norm(np.ravel(b))
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / (nb if nb > 0 else 1.0)
+
+
+def element_kappa(D, elements=None):
+    es = range(D.mesh.n_elem) if elements is None else elements
+    return max(np.linalg.cond(D.element(e)["A"]) for e in es)
