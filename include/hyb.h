@@ -177,6 +177,14 @@ int hyb_set_profiling(hyb_ctx* ctx, int enable);
  */
 int hyb_get_profile(const hyb_ctx* ctx, int kernel_class, double* total_ms, int64_t* launches);
 
+/*
+ * hyb_measure_fma_peak -- measured FMA throughput of the current device in TFLOP/s
+ *  (fp64 = 1: double, 0: float), from a grid of independent FMA chains timed with
+ *  CUDA events on cuda_stream (best of 3). Used as the roofline denominator for
+ *  kernels bound by arithmetic. Allocates and frees a small output buffer.
+ */
+int hyb_measure_fma_peak(int fp64, void* cuda_stream, double* tflops);
+
 /* hyb_get_sizes -- host outputs (any may be NULL): elements, n_loc, N_lambda, nnz. */
 int hyb_get_sizes(const hyb_ctx* ctx, int64_t* n_elem, int* n_loc, int64_t* n_lambda, int64_t* nnz);
 

@@ -244,7 +244,7 @@ cudaError_t pcg_init(const PcgArgs& a, cudaStream_t s, Prof* prof) {
   diag_inv_kernel<<<a.nblocks, kThreads, 0, s>>>(a);
   prof_end(prof, tok, s);
   tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
-  pcg_init_kernel<<<a.nblocks, kThreads, 0, s>>>(a);
+  pcg_init_kernel<<<a.nblocks / 4, kThreads, 0, s>>>(a);
   prof_end(prof, tok, s);
   return cudaGetLastError();
 }
@@ -252,22 +252,27 @@ cudaError_t pcg_init(const PcgArgs& a, cudaStream_t s, Prof* prof) {
 cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_t s, Prof* prof) {
   for (int it = 0; it < count; ++it) {
     int tok = prof_begin(prof, HYB_K_SPMV, s);
+    // FP64 is the scarce unit on this part (about 1.2 TFLOP/s): 4 lanes per face keep the
+    // cross-lane FP64 reduction small next to the nnz FMAs while each load instruction still
+    // covers whole 32-byte sectors (4 consecutive doubles of one row per face).
+    const int nbs = a.nblocks / 2, nbv = a.nblocks / 4;
     switch (a.nfn) {
-      case 1: spmv_face_kernel<1, 8><<<a.nblocks, kThreads, 0, s>>>(a); break;
-      case 4: spmv_face_kernel<4, 32><<<a.nblocks, kThreads, 0, s>>>(a); break;
-      case 9: spmv_face_kernel<9, 32><<<a.nblocks, kThreads, 0, s>>>(a); break;
-      case 16: spmv_face_kernel<16, 32><<<a.nblocks, kThreads, 0, s>>>(a); break;
+      case 1: spmv_face_kernel<1, 4><<<nbs, kThreads, 0, s>>>(a); break;
+      case 4: spmv_face_kernel<4, 4><<<nbs, kThreads, 0, s>>>(a); break;
+      case 9: spmv_face_kernel<9, 4><<<nbs, kThreads, 0, s>>>(a); break;
+      case 16: spmv_face_kernel<16, 4><<<nbs, kThreads, 0, s>>>(a); break;
       default: return cudaErrorInvalidValue;
     }
     prof_end(prof, tok, s);
     tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
-    pcg_update_kernel<<<a.nblocks, kThreads, 0, s>>>(a, rtol * rtol);
+    pcg_update_kernel<<<nbv, kThreads, 0, s>>>(a, rtol * rtol);
     prof_end(prof, tok, s);
     tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
-    pcg_direction_kernel<<<a.nblocks, kThreads, 0, s>>>(a);
+    pcg_direction_kernel<<<nbv, kThreads, 0, s>>>(a);
     prof_end(prof, tok, s);
   }
   return cudaGetLastError();
 }
 
 }  // namespace hyb
+

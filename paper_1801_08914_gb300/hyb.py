@@ -31,7 +31,7 @@ KERNEL_CLASSES = {"element": 0, "spmv": 1, "pcg_vector": 2, "recover": 3, "setup
 
 EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recover",
            "staticcond_assemble", "staticcond_recover", "hyb_get_reduced", "hyb_export_reduced", "hyb_get_sizes",
-           "hyb_set_profiling", "hyb_get_profile",
+           "hyb_set_profiling", "hyb_get_profile", "hyb_measure_fma_peak",
            "hyb_last_error_element", "hyb_destroy", "hyb_status_string"]
 
 
@@ -60,6 +60,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_get_reduced.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                     ctypes.POINTER(P), ctypes.POINTER(I64), ctypes.POINTER(I64)]
     lib.hyb_export_reduced.argtypes = [P, P, P, P, P]
+    lib.hyb_measure_fma_peak.argtypes = [I, P, ctypes.POINTER(D)]
     lib.hyb_set_profiling.argtypes = [P, I]
     lib.hyb_get_profile.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
     lib.hyb_get_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I64),
@@ -203,6 +204,13 @@ def hyb_export_reduced(ctx):
                                     _ptr(out["col"], "col", torch.int32), _ptr(out["val"], "val"),
                                     _ptr(out["rhs"], "rhs")), "hyb_export_reduced")
     return out
+
+
+def hyb_measure_fma_peak(fp64=True, stream=None):
+    """Measured FMA throughput of the current device, TFLOP/s."""
+    v = ctypes.c_double()
+    _check(lib().hyb_measure_fma_peak(int(bool(fp64)), _stream(stream), ctypes.byref(v)), "hyb_measure_fma_peak")
+    return v.value
 
 
 def hyb_set_profiling(ctx, enable):
