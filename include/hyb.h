@@ -178,6 +178,34 @@ int hyb_set_profiling(hyb_ctx* ctx, int enable);
 int hyb_get_profile(const hyb_ctx* ctx, int kernel_class, double* total_ms, int64_t* launches);
 
 /*
+ * hyb_pcg_solve_noalloc -- the diagonal-preconditioned CG of hyb_solve_reduced on a
+ *  caller-supplied CSR system, for callers that cannot allocate device memory: code
+ *  whose device memory is entirely reserved by another allocator (a framework's
+ *  caching pool, a fixed arena sized at start-up) or that must not make a call that
+ *  can block the whole device the way cudaMalloc / cudaFree do. The paper has no
+ *  counterpart; this is a deployment convenience.
+ *  It allocates nothing: its solver scratch (four vectors of the row count, block
+ *  partial sums, scalars and flags, about 16.8 MB) is one file-scope __device__
+ *  array in the library, present on every GPU that loads the library until the
+ *  process exits. Every call shares that array and leaves the last call's contents
+ *  in it; calls that can overlap on the GPU (other streams, other host threads)
+ *  race on it and must be serialised by the caller.
+ *  The first call on a device looks up the array's device address
+ *  (cudaGetSymbolAddress) and caches it per device; make that first call before
+ *  any stream capture on that device.
+ *  row_ptr (n+1 int64), col (nnz int32), val (nnz doubles), b (n doubles): device,
+ *  the SPD system. x: device, n doubles, receives the solution (x0 = 0).
+ *  n <= 524288 rows, else HYB_ERR_INVALID_ARG (nothing is enqueued).
+ *  rows_per_face: 1 for any CSR matrix; (k+1)^2 for the reduced systems built by
+ *  this library, whose (k+1)^2 consecutive rows share one column list.
+ *  rtol, maxit, iters, rel_res and the return codes are those of hyb_solve_reduced.
+ *  cuda_stream: the stream to run on; the call returns when its work is complete.
+ */
+int hyb_pcg_solve_noalloc(const int64_t* row_ptr, const int32_t* col, const double* val,
+                          const double* b, double* x, int64_t n, int rows_per_face,
+                          double rtol, int maxit, void* cuda_stream, int* iters, double* rel_res);
+
+/*
  * hyb_measure_fma_peak -- measured FMA throughput of the current device in TFLOP/s
  *  (fp64 = 1: double, 0: float), from a grid of independent FMA chains timed with
  *  CUDA events on cuda_stream (best of 3). Used as the roofline denominator for

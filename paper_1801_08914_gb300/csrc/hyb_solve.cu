@@ -10,6 +10,10 @@
 // iterations in chunks and reads the flags once per chunk.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
 #include "hyb_internal.h"
 
 namespace hyb {
@@ -276,3 +280,93 @@ cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_
 
 }  // namespace hyb
 
+// ---------------------------------------------------------------------------
+// Allocation-free PCG (hyb_pcg_solve_noalloc). The paper has no counterpart:
+// this serves callers that cannot allocate device memory. All solver
+// scratch (r, p, q, D^{-1}, block partials, scalars, flags) lives in one
+// file-scope device array sized for kNoAllocMaxRows rows; each GPU that loads
+// the library holds it until the process exits.
+namespace hyb {
+namespace {
+
+constexpr int64_t kNoAllocMaxRows = int64_t(1) << 19;     // 524,288 rows
+constexpr int kNoAllocBlocks = 152 * 8;
+constexpr int64_t kNoAllocDoubles = 4 * kNoAllocMaxRows + 2 * kNoAllocBlocks + 8 + 2;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = static_cast<double*>(ptr);
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace hyb
+
+extern "C" int hyb_pcg_solve_noalloc(const int64_t* row_ptr, const int32_t* col, const double* val,
+                                     const double* b, double* x, int64_t n, int rows_per_face, double rtol,
+                                     int maxit, void* cuda_stream, int* iters, double* rel_res) {
+  using namespace hyb;
+  if (!row_ptr || !col || !val || !b || !x) return HYB_ERR_INVALID_ARG;
+  if (n < 0 || n > kNoAllocMaxRows || maxit < 0 || !(rtol >= 0.0)) return HYB_ERR_INVALID_ARG;
+  if (rows_per_face != 1 && rows_per_face != 4 && rows_per_face != 9 && rows_per_face != 16) return HYB_ERR_INVALID_ARG;
+  if (n % rows_per_face != 0) return HYB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  double* base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) return HYB_ERR_CUDA;
+  PcgArgs a{};
+  a.n = n;
+  a.row_ptr = row_ptr;
+  a.col = col;
+  a.val = val;
+  a.b = b;
+  a.x = x;
+  a.r = base;
+  a.p = base + kNoAllocMaxRows;
+  a.q = base + 2 * kNoAllocMaxRows;
+  a.dinv = base + 3 * kNoAllocMaxRows;
+  a.partial = base + 4 * kNoAllocMaxRows;
+  a.scal = a.partial + 2 * kNoAllocBlocks;
+  a.flags = reinterpret_cast<int*>(a.scal + 8);
+  a.nblocks = kNoAllocBlocks;
+  a.nfn = rows_per_face;
+  e = pcg_init(a, s, nullptr);                 // clears the flags word, writes every vector it reads
+  if (e != cudaSuccess) return HYB_ERR_CUDA;
+  int hf[4] = {0, 0, 0, 0};
+  double hs[3] = {0, 0, 0};
+  int done = 0;
+  for (;;) {
+    e = cudaMemcpyAsync(hf, a.flags, sizeof(hf), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return HYB_ERR_CUDA;
+    done = hf[0];
+    if (hf[1] || hf[2] || done >= maxit) break;
+    e = pcg_iterations(a, std::min(32, maxit - done), rtol, s, nullptr);
+    if (e != cudaSuccess) return HYB_ERR_CUDA;
+  }
+  e = cudaMemcpyAsync(hs, a.scal, sizeof(hs), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return HYB_ERR_CUDA;
+  if (iters) *iters = done;
+  if (rel_res) *rel_res = hs[1] > 0.0 ? std::sqrt(hs[2] / hs[1]) : 0.0;
+  if (hf[2]) return HYB_ERR_BREAKDOWN;
+  if (!hf[1]) return HYB_ERR_NOT_CONVERGED;
+  return HYB_OK;
+}

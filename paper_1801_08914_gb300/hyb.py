@@ -31,7 +31,7 @@ KERNEL_CLASSES = {"element": 0, "spmv": 1, "pcg_vector": 2, "recover": 3, "setup
 
 EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recover",
            "staticcond_assemble", "staticcond_recover", "hyb_get_reduced", "hyb_export_reduced", "hyb_get_sizes",
-           "hyb_set_profiling", "hyb_get_profile", "hyb_measure_fma_peak",
+           "hyb_set_profiling", "hyb_get_profile", "hyb_pcg_solve_noalloc", "hyb_measure_fma_peak",
            "hyb_last_error_element", "hyb_destroy", "hyb_status_string"]
 
 
@@ -60,6 +60,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_get_reduced.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                     ctypes.POINTER(P), ctypes.POINTER(I64), ctypes.POINTER(I64)]
     lib.hyb_export_reduced.argtypes = [P, P, P, P, P]
+    lib.hyb_pcg_solve_noalloc.argtypes = [P, P, P, P, P, I64, I, D, I, P, ctypes.POINTER(I),
+                                          ctypes.POINTER(D)]
     lib.hyb_measure_fma_peak.argtypes = [I, P, ctypes.POINTER(D)]
     lib.hyb_set_profiling.argtypes = [P, I]
     lib.hyb_get_profile.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
@@ -204,6 +206,20 @@ def hyb_export_reduced(ctx):
                                     _ptr(out["col"], "col", torch.int32), _ptr(out["val"], "val"),
                                     _ptr(out["rhs"], "rhs")), "hyb_export_reduced")
     return out
+
+
+def hyb_pcg_solve_noalloc(row_ptr, col, val, b, x, rows_per_face, rtol, maxit, stream=None, check=True):
+    """Allocation-free PCG on a caller-supplied CSR system (see include/hyb.h).
+    Returns (iterations, relative residual, status)."""
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = lib().hyb_pcg_solve_noalloc(_ptr(row_ptr, "row_ptr", torch.int64), _ptr(col, "col", torch.int32),
+                                     _ptr(val, "val"), _ptr(b, "b"), _ptr(x, "x"), int(b.numel()),
+                                     int(rows_per_face), float(rtol), int(maxit), _stream(stream),
+                                     ctypes.byref(it), ctypes.byref(rr))
+    if check:
+        _check(st, "hyb_pcg_solve_noalloc")
+    return it.value, rr.value, st
 
 
 def hyb_measure_fma_peak(fp64=True, stream=None):
