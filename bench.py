@@ -44,6 +44,9 @@ def parse_args(argv=None):
     ap.add_argument("--maxit", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="mesh size override (parity / profiling runs)")
+    ap.add_argument("--config", default="2", help="workload: 2 (32^3 RT_1, default), 3 (96^3 RT_2), 5 (64^3 RT_3)")
+    ap.add_argument("--assembly-only", action="store_true",
+                    help="time only the element phase (assemble + recover with lambda = 0); per-config rates")
     return ap.parse_args(argv)
 
 
@@ -204,6 +207,30 @@ def spmv_bytes(n, nnz, nfn):
     return 8 * nnz + 4 * nnz // nfn + 16 * (n // nfn) + 8 * n + 8 * n
 
 
+def element_flops(k):
+    """Algorithmic FP64 flops of one element elimination (what the method needs, not what a
+    kernel issues): sum-factorised A_T (6 blocks, 3 stages, mass + divergence terms),
+    the load f = M c, Cholesky n^3/3, z = L^{-1} f, Y = L_bb^{-1} (n_b^3/3),
+    Y^T Y (n_b^3/3), g = Y^T z_b."""
+    P, p, Q = k + 2, k + 1, k + 2
+    nfn, ni = p * p, 3 * k * p * p
+    nb = 6 * nfn
+    n = ni + nb
+    nc = P * p * p
+    asm = 0
+    for diag in (True, True, True, False, False, False):
+        nja, njb = (P, p) if diag else (p, P)
+        st1 = Q * Q * P * nja * Q * 2 * 2
+        st2 = Q * P * nja * p * njb * Q * 2 * (1 if diag else 2)
+        st3 = P * nja * p * njb * p * p * Q * 2 // (2 if diag else 1)
+        asm += st1 + st2 + st3
+    load = 2 * 3 * 2 * (nc * Q + nc * Q + nc * Q)
+    chol = n ** 3 // 3 + n * n
+    inv = nb ** 3 // 3
+    gram = nb ** 3 // 3
+    return asm + load + chol + inv + gram + nb * nb
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -216,7 +243,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    p = inputs.make_config(2, n=args.n)
+    cfg = int(args.config)
+    p = inputs.make_config(cfg, n=args.n)
     tt = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     verts, alpha, beta, load = tt(p.vertices), tt(p.alpha), tt(p.beta), tt(p.load)
     ctx = hyb.hyb_setup(verts, p.nx, p.ny, p.nz, p.order, alpha, beta)
@@ -229,10 +257,13 @@ def run_ours(args):
 
     def step(load_dev):
         hyb.hyb_assemble_reduced(ctx, load_dev, None)
-        it, rr, st = hyb.hyb_solve_reduced(ctx, args.rtol, args.maxit, lam, check=False)
-        if st not in (hyb.HYB_OK,):
-            raise hyb.HybError(st, "hyb_solve_reduced")
-        iters.append(it)
+        if args.assembly_only:
+            iters.append(0)
+        else:
+            it, rr, st = hyb.hyb_solve_reduced(ctx, args.rtol, args.maxit, lam, check=False)
+            if st not in (hyb.HYB_OK,):
+                raise hyb.HybError(st, "hyb_solve_reduced")
+            iters.append(it)
         hyb.hyb_recover(ctx, lam, u)
 
     for _ in range(args.warmup):
@@ -291,7 +322,7 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    per_launch_ms = spmv_ms / max(1, it_total)            # no-op launches after convergence charged to real ones
+    per_launch_ms = spmv_ms / max(1, it_total) if it_total else float("nan")   # no-op launches charged to real ones
     nfn = (p.order + 1) ** 2
     gbs = spmv_bytes(N, nnz, nfn) / (per_launch_ms * 1e-3) / 1e9
     tflops = 2.0 * nnz / (per_launch_ms * 1e-3) / 1e12
@@ -309,20 +340,31 @@ def run_ours(args):
     launches = sum(v[1] for v in prof.values())
     phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
     elem_ms = prof["element"][0] / args.steps
+    elem_flops = element_flops(p.order)
+    elem_tflops = E * elem_flops / (elem_ms * 1e-3) / 1e12 if elem_ms > 0 else None
+    element_roofline = {"kernel": f"element_kernel<{p.order}> (FP64)", "bound": "alu",
+                        "achieved": elem_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                        "frac": elem_tflops / fp64_peak if elem_tflops else None,
+                        "algorithmic_flops_per_element": elem_flops}
+    workload = WORKLOAD if cfg == 2 else f"config {cfg}: {p.nx}^3 jittered hex mesh, RT_{p.order}, FP64"
+    if args.assembly_only:
+        workload += " (element phase only: assemble + recover)"
     line = {
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "elements": E, "order": p.order, "n_loc": n_loc, "n_lambda": N,
+        "config": {"workload": workload, "elements": E, "order": p.order, "n_loc": n_loc, "n_lambda": N,
                    "nnz": nnz, "pcg_rtol": args.rtol, "pcg_iterations": iters_timed[0] if iters_timed else None,
                    "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) before each step"},
         "e2e": {"value": e2e_value, "unit": "elements/s", "h2d_bytes_per_step": int(p.load.nbytes),
                 "d2h_bytes_per_step": int(E * n_loc * 8)},
         "gpu_launches": int(launches),
-        "roofline": roof,
+        "roofline": roof if not args.assembly_only else element_roofline,
+        "element_roofline": element_roofline,
         "phases": phases,
         "assembly_elements_per_s": E / (elem_ms * 1e-3) if elem_ms > 0 else None,
-        "reduced_dofs_per_s": N / (prof["spmv"][0] / args.steps * 1e-3 + prof["pcg_vector"][0] / args.steps * 1e-3),
+        "reduced_dofs_per_s": (N / ((prof["spmv"][0] + prof["pcg_vector"][0]) / args.steps * 1e-3)
+                               if prof["spmv"][0] > 0 else None),
         "clocks": ck,
         "wall_s": t_wall,
     }

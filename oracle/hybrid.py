@@ -112,6 +112,41 @@ class Discretization:
         d["L"] = L
         return d
 
+    def mixed_form_blocks(self, e):
+        """Blocks of the hybridized mixed form (Sec. 3.2, eq. 3.3-3.6) for element e.
+
+        With q = beta div u in Q_k (Lagrange basis l_a at the (k+1)^3 Gauss-Legendre nodes),
+        W_ab = sum_q w_q (beta / det J) l_a l_b and B_ai = sum_q w_q (beta / det J) l_a div_hat phi_i,
+        so that A_T = M_T + B^T W^{-1} B exactly (div_hat phi_i lies in Q_k) with M_T the
+        alpha-weighted mass. Returns M, B (restricted to free dofs), W and the element dict."""
+        d = self.element(e)
+        X8 = self.mesh.element_vertices(e)
+        integ = self.integ
+        M, _ = integ.matrices(X8, self.alpha[e], 0.0)
+        from .basis import lagrange
+        g, _ = gauss_legendre(self.k + 1)
+        Ls = [lagrange(g, integ.pts[:, dd])[0] for dd in range(3)]            # (nq, k+1) each
+        L = np.einsum("qa,qb,qc->qcba", Ls[0], Ls[1], Ls[2]).reshape(integ.pts.shape[0], -1)
+        J = np.einsum("ci,qcd->qid", X8, integ.dN)
+        wgt = integ.wts * self.beta[e] / np.linalg.det(J)
+        W = L.T @ (wgt[:, None] * L)
+        B = L.T @ (wgt[:, None] * integ.div)
+        free = d["free"]
+        return M[np.ix_(free, free)], B[:, free], W, d
+
+    def element_reduced_mixed(self, e):
+        """S_T and g_T from the mixed form: [C 0] [M B^T; B -W]^{-1} [C^T; 0] (Sec. 3.2, H = H~)."""
+        M, B, W, d = self.mixed_form_blocks(e)
+        nf, nq = M.shape[0], W.shape[0]
+        K = np.block([[M, B.T], [B, -W]])
+        rhs = np.zeros((nf + nq, d["C"].shape[0] + 1))
+        rhs[:nf, :-1] = d["C"].T
+        rhs[:nf, -1] = d["f"]
+        X = np.linalg.solve(K, rhs)[:nf]
+        d["S"] = d["C"] @ X[:, :-1]
+        d["g"] = d["C"] @ X[:, -1]
+        return d
+
     def hybridize(self, elements=None):
         """Assemble H and g (eq. 2.4); keeps per-element factors for the back substitution."""
         E = self.mesh.n_elem

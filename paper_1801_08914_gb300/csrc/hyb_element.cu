@@ -43,16 +43,16 @@ struct EK {
   static constexpr bool A_SMEM = K <= 2;
   static constexpr int TRI = N * (N + 1) / 2;
   static constexpr int TRIB = NB * (NB + 1) / 2;
-  // assembly scratch
+  // 1-D tables: Vc, Dc (P x Q), Vo (p x Q), products VcVc, DcDc (P P Q), VcVo, DcVo (P p Q), VoVo (p p Q)
+  static constexpr int TAB = 2 * P * Q + p * Q + 2 * P * P * Q + 2 * P * p * Q + p * p * Q + 2 * Q + NFN;
+  // assembly scratch: T1, T2, Gu[6], Ga[6], Gd; load scratch: 2 x 3 x (P P Q) buffers, U[3], W[3]
   static constexpr int T1SZ = 2 * Q * Q * P * P;
   static constexpr int T2SZ = Q * P * P * p * p;
-  static constexpr int GEO = 13 * NQ;                  // Gu[6], Ga[6], Gd
-  static constexpr int ASM = T1SZ + T2SZ + GEO + 6 * NQ + p * p * Q;   // + Uq, Wq, VoVo
-  static constexpr int POST = 2 * TRIB;                // Y (column-major packed), Y^T Y (row packed)
+  static constexpr int LBUF = 3 * P * P * Q;
+  static constexpr int ASM = T1SZ + T2SZ + 13 * NQ + 2 * LBUF + 6 * NQ;
+  static constexpr int POST = 2 * TRIB;                // Y, Y^T Y (row-major packed)
   static constexpr int UNION = ASM > POST ? ASM : POST;
-  // persistent: A (if in smem), f, colbuf, invdiag, X8, tables
-  static constexpr int TAB = 2 * P * Q + p * Q + 2 * Q + NFN;
-  static constexpr int SMEM_DOUBLES = (A_SMEM ? TRI : 0) + 3 * N + 24 + TAB + UNION + 4;
+  static constexpr int SMEM_DOUBLES = (A_SMEM ? TRI : 0) + 3 * N + 48 + TAB + UNION + 4;
   static constexpr size_t SMEM_BYTES = sizeof(double) * SMEM_DOUBLES;
 };
 
@@ -72,17 +72,6 @@ __device__ __forceinline__ int local_index(int c, int i0, int i1, int i2) {
   return NI + (2 * c + side) * NFN + t0 + p * t1;
 }
 
-// 1-D node indices of the f-th function of component c (first index fastest).
-template <int K>
-__device__ __forceinline__ void func_index(int c, int f, int& i0, int& i1, int& i2) {
-  constexpr int P = K + 2, p = K + 1;
-  const int n0 = c == 0 ? P : p, n1 = c == 1 ? P : p;
-  i0 = f % n0;
-  f /= n0;
-  i1 = f % n1;
-  i2 = f / n1;
-}
-
 // slot of the symmetric pair (a, b) in the 6-vector (00, 11, 22, 10, 20, 21)
 __device__ __forceinline__ int gslot(int a, int b) {
   if (a == b) return a;
@@ -90,19 +79,36 @@ __device__ __forceinline__ int gslot(int a, int b) {
   return hi == 1 ? 3 : (lo == 0 ? 4 : 5);
 }
 
+// Row index i of the packed lower-triangle position t (t = i(i+1)/2 + j, j <= i).
+__device__ __forceinline__ int tri_row(int t) {
+  int i = (int)((sqrtf((float)(8 * t + 1)) - 1.0f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  return i;
+}
+
+// 1 / sqrt(d) by Newton-Raphson on f(r) = r^-2 - d from a single-precision seed:
+// r <- r (3 - d r^2) / 2, two steps (23 -> 46 -> full FP64 bits). Falls back to the
+// library square root outside the single-precision range.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double r = (double)rsqrtf((float)d);
+  r = r * fma(-0.5 * d, r * r, 1.5);
+  r = r * fma(-0.5 * d, r * r, 1.5);
+  return r;
+}
+
 struct Tabs {
-  const double* Vc;   // [P][Q]
-  const double* Dc;   // [P][Q]
-  const double* Vo;   // [p][Q]
-  const double* qx;
-  const double* qw;
-  const double* wf;   // [NFN]
+  const double *Vc, *Dc, *Vo;                  // [P][Q], [P][Q], [p][Q]
+  const double *VcVc, *DcDc, *VcVo, *DcVo, *VoVo;   // [a][b][q] products
 };
 
 // Block (c, cp) of alpha M + beta K, c >= cp, written into the packed lower triangle of A.
+// Directions are contracted one at a time (sum factorisation); the mass and divergence
+// terms share every stage after the directions in which their 1-D factors differ.
 template <int K>
 __device__ void assemble_block(int c, int cp, const Tabs& tb, const double* Ga, const double* Gd,
-                               const double* VoVo, double* T1, double* T2, double* A) {
+                               double* T1, double* T2, double* A) {
   using S = EK<K>;
   constexpr int P = S::P, p = S::p, Q = S::Q, NT = S::NT;
   const int tid = threadIdx.x;
@@ -112,11 +118,13 @@ __device__ void assemble_block(int c, int cp, const Tabs& tb, const double* Ga, 
   const int dL = 3 - da - db;
   const int nia = P, nja = diag ? P : p;                   // along da (== c)
   const int nib = p, njb = diag ? p : P;                   // along db
-  const int niL = p, njL = p;                              // along dL (neither c nor cp)
+  constexpr int niL = p, njL = p;                          // along dL (neither c nor cp)
   const int sa = da == 0 ? 1 : da == 1 ? Q : Q * Q;
   const int sb = db == 0 ? 1 : db == 1 ? Q : Q * Q;
   const int sL = dL == 0 ? 1 : dL == 1 ? Q : Q * Q;
   const double* Gm = Ga + gslot(c, cp) * S::NQ;
+  const double* Pm = diag ? tb.VcVc : tb.VcVo;             // [ia][ja][q]
+  const double* Pd = diag ? tb.DcDc : tb.DcVo;
 
   // stage 1: contract q_a
   const int n1 = Q * Q * nia * nja;
@@ -126,16 +134,14 @@ __device__ void assemble_block(int c, int cp, const Tabs& tb, const double* Ga, 
     const int ia = r % nia; r /= nia;
     const int qL = r % Q;
     const int qb = r / Q;
+    const double* pm = Pm + (ia * nja + ja) * Q;
+    const double* pd = Pd + (ia * nja + ja) * Q;
     double accm = 0.0, accd = 0.0;
 #pragma unroll
     for (int qa = 0; qa < Q; ++qa) {
       const int q = qa * sa + qb * sb + qL * sL;
-      const double rm = tb.Vc[ia * Q + qa];
-      const double rd = tb.Dc[ia * Q + qa];
-      const double cm = diag ? tb.Vc[ja * Q + qa] : tb.Vo[ja * Q + qa];
-      const double cd = diag ? tb.Dc[ja * Q + qa] : tb.Vo[ja * Q + qa];
-      accm = fma(Gm[q] * rm, cm, accm);
-      accd = fma(Gd[q] * rd, cd, accd);
+      accm = fma(Gm[q], pm[qa], accm);
+      accd = fma(Gd[q], pd[qa], accd);
     }
     if (diag) {
       T1[idx] = accm + accd;
@@ -159,19 +165,21 @@ __device__ void assemble_block(int c, int cp, const Tabs& tb, const double* Ga, 
 #pragma unroll
     for (int qb = 0; qb < Q; ++qb) {
       const int t1 = ((qb * Q + qL) * nia + ia) * nja + ja;
-      const double ro = tb.Vo[ib * Q + qb];
       if (diag) {
-        acc = fma(T1[t1] * ro, tb.Vo[jb * Q + qb], acc);
+        acc = fma(T1[t1], tb.VoVo[(ib * p + jb) * Q + qb], acc);
       } else {
-        acc = fma(ro, fma(T1[t1], tb.Vc[jb * Q + qb], T1[n1 + t1] * tb.Dc[jb * Q + qb]), acc);
+        // rows: open in db; columns: closed value (mass) / closed derivative (div) in db == cp
+        acc = fma(T1[t1], tb.VcVo[(jb * p + ib) * Q + qb], acc);
+        acc = fma(T1[n1 + t1], tb.DcVo[(jb * p + ib) * Q + qb], acc);
       }
     }
     T2[idx] = acc;
   }
   __syncthreads();
 
-  // stage 3: contract q_L and write
+  // stage 3: contract q_L and write the lower triangle
   const int n3 = nia * nja * nib * njb * niL * njL;
+  const int s2 = nia * nja * nib * njb;
   for (int idx = tid; idx < n3; idx += NT) {
     int r = idx;
     const int jL = r % njL; r /= njL;
@@ -190,11 +198,100 @@ __device__ void assemble_block(int c, int cp, const Tabs& tb, const double* Ga, 
     const int ss = local_index<K>(cp, j0, j1, j2);
     if (diag && rr < ss) continue;
     const int t2 = (((ia * nja + ja) * nib + ib) * njb + jb);
+    const double* pv = tb.VoVo + (iL * p + jL) * Q;
     double acc = 0.0;
 #pragma unroll
-    for (int qL = 0; qL < Q; ++qL)
-      acc = fma(T2[qL * (nia * nja * nib * njb) + t2], VoVo[(iL * p + jL) * Q + qL], acc);
+    for (int qL = 0; qL < Q; ++qL) acc = fma(T2[qL * s2 + t2], pv[qL], acc);
     A[rr >= ss ? tri(rr, ss) : tri(ss, rr)] = acc;
+  }
+  __syncthreads();
+}
+
+// f = M c with M the unit-coefficient mass, by sum factorisation: interpolate the three
+// reference components of the coefficient field at the Gauss points, apply the weights
+// w J^T J / det J, test against the basis. B0, B1 hold 3 x (P P Q) doubles each.
+template <int K>
+__device__ void load_vector(const double* coef, const Tabs& tb, const double* Gu, double* B0, double* B1,
+                            double* U, double* W, double* f) {
+  using S = EK<K>;
+  constexpr int P = S::P, p = S::p, Q = S::Q, NQ = S::NQ, NT = S::NT, LB = P * P * Q;
+  const int tid = threadIdx.x;
+  auto nn = [](int c, int d) { return c == d ? P : p; };
+  auto tab = [&](int c, int d) { return c == d ? tb.Vc : tb.Vo; };
+  // Z1[c][i2][i1][q0] = sum_i0 coef * T0[i0][q0]
+  for (int t = tid; t < 3 * LB; t += NT) {
+    const int c = t / LB, r = t % LB;
+    const int n0 = nn(c, 0), n1 = nn(c, 1), n2 = nn(c, 2);
+    if (r >= n2 * n1 * Q) continue;
+    const int q0 = r % Q, i1 = (r / Q) % n1, i2 = r / (Q * n1);
+    const double* T = tab(c, 0);
+    double acc = 0.0;
+    for (int i0 = 0; i0 < n0; ++i0) acc = fma(coef[local_index<K>(c, i0, i1, i2)], T[i0 * Q + q0], acc);
+    B0[t] = acc;
+  }
+  __syncthreads();
+  // Z2[c][i2][q1][q0] = sum_i1 Z1 * T1[i1][q1]
+  for (int t = tid; t < 3 * LB; t += NT) {
+    const int c = t / LB, r = t % LB;
+    const int n1 = nn(c, 1), n2 = nn(c, 2);
+    if (r >= n2 * Q * Q) continue;
+    const int q0 = r % Q, q1 = (r / Q) % Q, i2 = r / (Q * Q);
+    const double* T = tab(c, 1);
+    double acc = 0.0;
+    for (int i1 = 0; i1 < n1; ++i1) acc = fma(B0[c * LB + (i2 * n1 + i1) * Q + q0], T[i1 * Q + q1], acc);
+    B1[t] = acc;
+  }
+  __syncthreads();
+  // U[c][q] = sum_i2 Z2 * T2[i2][q2]
+  for (int t = tid; t < 3 * NQ; t += NT) {
+    const int c = t / NQ, q = t % NQ;
+    const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
+    const int n2 = nn(c, 2);
+    const double* T = tab(c, 2);
+    double acc = 0.0;
+    for (int i2 = 0; i2 < n2; ++i2) acc = fma(B1[c * LB + (i2 * Q + q1) * Q + q0], T[i2 * Q + q2], acc);
+    U[t] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < 3 * NQ; t += NT) {
+    const int c = t / NQ, q = t % NQ;
+    W[t] = Gu[gslot(c, 0) * NQ + q] * U[q] + Gu[gslot(c, 1) * NQ + q] * U[NQ + q] +
+           Gu[gslot(c, 2) * NQ + q] * U[2 * NQ + q];
+  }
+  __syncthreads();
+  // Y1[c][q2][q1][i0] = sum_q0 W * T0[i0][q0]
+  for (int t = tid; t < 3 * LB; t += NT) {
+    const int c = t / LB, r = t % LB;
+    const int n0 = nn(c, 0);
+    if (r >= Q * Q * n0) continue;
+    const int i0 = r % n0, q1 = (r / n0) % Q, q2 = r / (n0 * Q);
+    const double* T = tab(c, 0);
+    double acc = 0.0;
+    for (int q0 = 0; q0 < Q; ++q0) acc = fma(W[c * NQ + (q2 * Q + q1) * Q + q0], T[i0 * Q + q0], acc);
+    B0[t] = acc;
+  }
+  __syncthreads();
+  // Y2[c][q2][i1][i0] = sum_q1 Y1 * T1[i1][q1]
+  for (int t = tid; t < 3 * LB; t += NT) {
+    const int c = t / LB, r = t % LB;
+    const int n0 = nn(c, 0), n1 = nn(c, 1);
+    if (r >= Q * n1 * n0) continue;
+    const int i0 = r % n0, i1 = (r / n0) % n1, q2 = r / (n0 * n1);
+    const double* T = tab(c, 1);
+    double acc = 0.0;
+    for (int q1 = 0; q1 < Q; ++q1) acc = fma(B0[c * LB + (q2 * Q + q1) * n0 + i0], T[i1 * Q + q1], acc);
+    B1[t] = acc;
+  }
+  __syncthreads();
+  // f[c][i2][i1][i0] = sum_q2 Y2 * T2[i2][q2]
+  for (int t = tid; t < 3 * S::NC; t += NT) {
+    const int c = t / S::NC, r = t % S::NC;
+    const int n0 = nn(c, 0), n1 = nn(c, 1);
+    const int i0 = r % n0, i1 = (r / n0) % n1, i2 = r / (n0 * n1);
+    const double* T = tab(c, 2);
+    double acc = 0.0;
+    for (int q2 = 0; q2 < Q; ++q2) acc = fma(B1[c * LB + (q2 * n1 + i1) * n0 + i0], T[i2 * Q + q2], acc);
+    f[local_index<K>(c, i0, i1, i2)] = acc;
   }
   __syncthreads();
 }
@@ -209,8 +306,6 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
   constexpr int P = S::P, p = S::p, Q = S::Q, NQ = S::NQ, NFN = S::NFN, NI = S::NI, NB = S::NB, N = S::N;
   constexpr int NT = S::NT;
   const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = NT / 32;
   extern __shared__ double smem[];
 
   const int64_t li = blockIdx.x;
@@ -226,26 +321,31 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
   double* colbuf = sp; sp += N;
   double* invd = sp; sp += N;
   double* X8 = sp; sp += 24;
+  double* Mc = sp; sp += 24;                // monomial coefficients of the trilinear map
   double* Vc = sp; sp += P * Q;
   double* Dc = sp; sp += P * Q;
   double* Vo = sp; sp += p * Q;
+  double* VcVc = sp; sp += P * P * Q;
+  double* DcDc = sp; sp += P * P * Q;
+  double* VcVo = sp; sp += P * p * Q;
+  double* DcVo = sp; sp += P * p * Q;
+  double* VoVo = sp; sp += p * p * Q;
   double* qx = sp; sp += Q;
   double* qw = sp; sp += Q;
   double* wf = sp; sp += NFN;
   double* flag = sp; sp += 4;
   double* U = sp;                           // union region
-  // assembly view
   double* T1 = U;
   double* T2 = T1 + S::T1SZ;
   double* Gu = T2 + S::T2SZ;                // [6][NQ] unit-coefficient mass weights
   double* Ga = Gu + 6 * NQ;                 // [6][NQ] alpha-scaled
   double* Gd = Ga + 6 * NQ;                 // [NQ]    beta-scaled divergence weights
-  double* Uq = Gd + NQ;                     // [3][NQ]
+  double* LB0 = Gd + NQ;                    // load scratch
+  double* LB1 = LB0 + S::LBUF;
+  double* Uq = LB1 + S::LBUF;               // [3][NQ]
   double* Wq = Uq + 3 * NQ;                 // [3][NQ]
-  double* VoVo = Wq + 3 * NQ;               // [p][p][Q]
-  // post-factorisation view
-  double* Y = U;                            // column-major packed lower, NB
-  double* YtY = U + S::TRIB;                // row-major packed lower, NB
+  double* Y = U;                            // after the factorisation: L_bb^{-1}, row-major packed
+  double* YtY = U + S::TRIB;
 
   const RefTables& rt = c_ref[K];
   for (int i = tid; i < P * Q; i += NT) {
@@ -261,99 +361,82 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
     X8[tid] = args.vertices[3 * v + d];
   }
   __syncthreads();
-  for (int i = tid; i < p * p * Q; i += NT) {
-    const int q = i % Q, jl = (i / Q) % p, il = i / (Q * p);
-    VoVo[i] = Vo[il * Q + q] * Vo[jl * Q + q];
+  for (int i = tid; i < P * P * Q; i += NT) {
+    const int q = i % Q, b = (i / Q) % P, a = i / (Q * P);
+    VcVc[i] = Vc[a * Q + q] * Vc[b * Q + q];
+    DcDc[i] = Dc[a * Q + q] * Dc[b * Q + q];
   }
+  for (int i = tid; i < P * p * Q; i += NT) {
+    const int q = i % Q, b = (i / Q) % p, a = i / (Q * p);
+    VcVo[i] = Vc[a * Q + q] * Vo[b * Q + q];
+    DcVo[i] = Dc[a * Q + q] * Vo[b * Q + q];
+  }
+  for (int i = tid; i < p * p * Q; i += NT) {
+    const int q = i % Q, b = (i / Q) % p, a = i / (Q * p);
+    VoVo[i] = Vo[a * Q + q] * Vo[b * Q + q];
+  }
+  // trilinear map x = m0 + m1 x0 + m2 x1 + m3 x2 + m4 x0 x1 + m5 x0 x2 + m6 x1 x2 + m7 x0 x1 x2
+  if (tid < 3) {
+    const int d = tid;
+    const double x0 = X8[d], x1 = X8[3 + d], x2 = X8[6 + d], x3 = X8[9 + d];
+    const double x4 = X8[12 + d], x5 = X8[15 + d], x6 = X8[18 + d], x7 = X8[21 + d];
+    Mc[d] = x0;
+    Mc[3 + d] = x1 - x0;
+    Mc[6 + d] = x2 - x0;
+    Mc[9 + d] = x4 - x0;
+    Mc[12 + d] = (x3 - x2) - (x1 - x0);
+    Mc[15 + d] = (x5 - x4) - (x1 - x0);
+    Mc[18 + d] = (x6 - x4) - (x2 - x0);
+    Mc[21 + d] = ((x7 - x6) - (x5 - x4)) - ((x3 - x2) - (x1 - x0));
+  }
+  __syncthreads();
 
-  // ---- 1. geometry
+  // ---- 1. geometry: J columns from the monomial form, w J^T J / det J and w / det J
   const double alpha = args.alpha[e], beta = args.beta[e];
   for (int q = tid; q < NQ; q += NT) {
     const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
     const double x0 = qx[q0], x1 = qx[q1], x2 = qx[q2];
-    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const double x12 = x1 * x2, x02 = x0 * x2, x01 = x0 * x1;
+    double J[3][3];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int s0 = c & 1, s1 = (c >> 1) & 1, s2 = c >> 2;
-      const double f0 = s0 ? x0 : 1.0 - x0, f1 = s1 ? x1 : 1.0 - x1, f2 = s2 ? x2 : 1.0 - x2;
-      const double g0 = s0 ? 1.0 : -1.0, g1 = s1 ? 1.0 : -1.0, g2 = s2 ? 1.0 : -1.0;
-      const double d0 = g0 * f1 * f2, d1 = f0 * g1 * f2, d2 = f0 * f1 * g2;
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const double xv = X8[3 * c + r];
-        J[r][0] = fma(xv, d0, J[r][0]);
-        J[r][1] = fma(xv, d1, J[r][1]);
-        J[r][2] = fma(xv, d2, J[r][2]);
-      }
+    for (int r = 0; r < 3; ++r) {
+      J[r][0] = fma(Mc[21 + r], x12, fma(Mc[15 + r], x2, fma(Mc[12 + r], x1, Mc[3 + r])));
+      J[r][1] = fma(Mc[21 + r], x02, fma(Mc[18 + r], x2, fma(Mc[12 + r], x0, Mc[6 + r])));
+      J[r][2] = fma(Mc[21 + r], x01, fma(Mc[18 + r], x1, fma(Mc[15 + r], x0, Mc[9 + r])));
     }
-    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    const double det = J[0][0] * fma(J[1][1], J[2][2], -J[1][2] * J[2][1]) -
+                       J[0][1] * fma(J[1][0], J[2][2], -J[1][2] * J[2][0]) +
+                       J[0][2] * fma(J[1][0], J[2][1], -J[1][1] * J[2][0]);
     if (!(det > 0.0)) set_error(args.status, args.err_elem, HYB_ERR_MESH, e);
     const double s = qw[q0] * qw[q1] * qw[q2] / det;
     double g[6];
-    g[0] = J[0][0] * J[0][0] + J[1][0] * J[1][0] + J[2][0] * J[2][0];
-    g[1] = J[0][1] * J[0][1] + J[1][1] * J[1][1] + J[2][1] * J[2][1];
-    g[2] = J[0][2] * J[0][2] + J[1][2] * J[1][2] + J[2][2] * J[2][2];
-    g[3] = J[0][1] * J[0][0] + J[1][1] * J[1][0] + J[2][1] * J[2][0];
-    g[4] = J[0][2] * J[0][0] + J[1][2] * J[1][0] + J[2][2] * J[2][0];
-    g[5] = J[0][2] * J[0][1] + J[1][2] * J[1][1] + J[2][2] * J[2][1];
+    g[0] = fma(J[0][0], J[0][0], fma(J[1][0], J[1][0], J[2][0] * J[2][0]));
+    g[1] = fma(J[0][1], J[0][1], fma(J[1][1], J[1][1], J[2][1] * J[2][1]));
+    g[2] = fma(J[0][2], J[0][2], fma(J[1][2], J[1][2], J[2][2] * J[2][2]));
+    g[3] = fma(J[0][1], J[0][0], fma(J[1][1], J[1][0], J[2][1] * J[2][0]));
+    g[4] = fma(J[0][2], J[0][0], fma(J[1][2], J[1][0], J[2][2] * J[2][0]));
+    g[5] = fma(J[0][2], J[0][1], fma(J[1][2], J[1][1], J[2][2] * J[2][1]));
+    const double as = alpha * s;
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
       Gu[t * NQ + q] = s * g[t];
-      Ga[t * NQ + q] = alpha * s * g[t];
+      Ga[t * NQ + q] = as * g[t];
     }
     Gd[q] = beta * s;
   }
   __syncthreads();
 
   // ---- 2. A_T by sum factorisation (6 blocks, c >= cp)
-  const Tabs tb{Vc, Dc, Vo, qx, qw, wf};
-  assemble_block<K>(0, 0, tb, Ga, Gd, VoVo, T1, T2, A);
-  assemble_block<K>(1, 1, tb, Ga, Gd, VoVo, T1, T2, A);
-  assemble_block<K>(2, 2, tb, Ga, Gd, VoVo, T1, T2, A);
-  assemble_block<K>(1, 0, tb, Ga, Gd, VoVo, T1, T2, A);
-  assemble_block<K>(2, 0, tb, Ga, Gd, VoVo, T1, T2, A);
-  assemble_block<K>(2, 1, tb, Ga, Gd, VoVo, T1, T2, A);
+  const Tabs tb{Vc, Dc, Vo, VcVc, DcDc, VcVo, DcVo, VoVo};
+  assemble_block<K>(0, 0, tb, Ga, Gd, T1, T2, A);
+  assemble_block<K>(1, 1, tb, Ga, Gd, T1, T2, A);
+  assemble_block<K>(2, 2, tb, Ga, Gd, T1, T2, A);
+  assemble_block<K>(1, 0, tb, Ga, Gd, T1, T2, A);
+  assemble_block<K>(2, 0, tb, Ga, Gd, T1, T2, A);
+  assemble_block<K>(2, 1, tb, Ga, Gd, T1, T2, A);
 
-  // ---- 3. load f = M c (matrix-free): field components at the Gauss points, times w J^T J / det J, tested
-  const double* coef = args.load + e * (int64_t)N;
-  for (int t = tid; t < 3 * NQ; t += NT) {
-    const int c = t / NQ, q = t % NQ;
-    const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
-    double acc = 0.0;
-    for (int fi = 0; fi < S::NC; ++fi) {
-      int i0, i1, i2;
-      func_index<K>(c, fi, i0, i1, i2);
-      const double b0 = c == 0 ? Vc[i0 * Q + q0] : Vo[i0 * Q + q0];
-      const double b1 = c == 1 ? Vc[i1 * Q + q1] : Vo[i1 * Q + q1];
-      const double b2 = c == 2 ? Vc[i2 * Q + q2] : Vo[i2 * Q + q2];
-      acc = fma(coef[local_index<K>(c, i0, i1, i2)], b0 * b1 * b2, acc);
-    }
-    Uq[c * NQ + q] = acc;
-  }
-  __syncthreads();
-  for (int t = tid; t < 3 * NQ; t += NT) {
-    const int c = t / NQ, q = t % NQ;
-    Wq[c * NQ + q] = Gu[gslot(c, 0) * NQ + q] * Uq[q] + Gu[gslot(c, 1) * NQ + q] * Uq[NQ + q] +
-                     Gu[gslot(c, 2) * NQ + q] * Uq[2 * NQ + q];
-  }
-  __syncthreads();
-  for (int t = tid; t < 3 * S::NC; t += NT) {
-    const int c = t / S::NC, fi = t % S::NC;
-    int i0, i1, i2;
-    func_index<K>(c, fi, i0, i1, i2);
-    double acc = 0.0;
-    for (int q = 0; q < NQ; ++q) {
-      const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
-      const double b0 = c == 0 ? Vc[i0 * Q + q0] : Vo[i0 * Q + q0];
-      const double b1 = c == 1 ? Vc[i1 * Q + q1] : Vo[i1 * Q + q1];
-      const double b2 = c == 2 ? Vc[i2 * Q + q2] : Vo[i2 * Q + q2];
-      acc = fma(b0 * b1 * b2, Wq[c * NQ + q], acc);
-    }
-    f[local_index<K>(c, i0, i1, i2)] = acc;
-  }
-  __syncthreads();
+  // ---- 3. load f = M c
+  load_vector<K>(args.load + e * (int64_t)N, tb, Gu, LB0, LB1, Uq, Wq, f);
 
   // ---- 4. essential dofs on boundary faces: f -= A_{:,e} u_e, then rows / columns -> identity
   const int32_t* ef = args.elem_face + e * 6;
@@ -371,7 +454,7 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
           if (!((bmask >> a) & 1)) continue;
           for (int m = 0; m < NFN; ++m) {
             const int j = NI + a * NFN + m;
-            acc -= A[i >= j ? tri(i, j) : tri(j, i)] * ue[j];
+            acc = fma(-A[i >= j ? tri(i, j) : tri(j, i)], ue[j], acc);
           }
         }
         colbuf[i] = acc;
@@ -386,28 +469,28 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
         if ((bmask >> (i / NFN)) & 1) f[NI + i] = 0.0;
     }
     __syncthreads();
-    // identity rows / columns
     for (int a = 0; a < 6; ++a) {
       if (!((bmask >> a) & 1)) continue;
       for (int t = tid; t < NFN * N; t += NT) {
         const int m = t / N, j = t % N;
         const int i = NI + a * NFN + m;
-        const double v = (i == j) ? 1.0 : 0.0;
-        A[i >= j ? tri(i, j) : tri(j, i)] = v;
+        A[i >= j ? tri(i, j) : tri(j, i)] = (i == j) ? 1.0 : 0.0;
       }
       __syncthreads();
     }
   }
   __syncthreads();
 
-  // ---- 5. Cholesky (right-looking, packed lower) fused with z = L^{-1} f
+  // ---- 5. Cholesky (right-looking, packed lower) fused with z = L^{-1} f. Every trailing
+  // update is spread over all threads (entry (i, l) of the trailing triangle, then f), and the
+  // thread that updates the next diagonal entry prepares the next pivot.
   const int jend = MODE == MODE_SC ? NI : N;
   if (tid == 0) {
     const double d = jend > 0 ? A[0] : 1.0;
-    const double r = d > 0.0 ? sqrt(d) : 1.0;
+    const double r = rsqrt_newton(d);
     flag[0] = d;
-    flag[1] = r;
-    flag[2] = 1.0 / r;
+    flag[1] = d * r;
+    flag[2] = r;
   }
   __syncthreads();
   for (int j = 0; j < jend; ++j) {
@@ -416,7 +499,6 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
       if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
       return;                               // uniform: every thread read the same pivot
     }
-    const double ljj = flag[1];
     const double inv = flag[2];
     for (int i = j + 1 + tid; i < N; i += NT) {
       const double v = A[tri(i, j)] * inv;
@@ -424,25 +506,30 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
       colbuf[i] = v;
     }
     if (tid == 0) {
-      A[tri(j, j)] = ljj;
+      A[tri(j, j)] = flag[1];
       invd[j] = inv;
       f[j] = f[j] * inv;                    // z_j
     }
     __syncthreads();
     const double zj = f[j];
-    for (int i = j + 1 + warp; i < N; i += NW) {
-      const double lij = colbuf[i];
-      double* row = A + tri(i, 0);
-      for (int l = j + 1 + lane; l <= i; l += 32) row[l] = fma(-lij, colbuf[l], row[l]);
-      if (lane == 0) f[i] = fma(-lij, zj, f[i]);
-    }
-    __syncthreads();
-    if (tid == 0 && j + 1 < jend) {
-      const double dn = A[tri(j + 1, j + 1)];
-      const double r = dn > 0.0 ? sqrt(dn) : 1.0;
-      flag[0] = dn;
-      flag[1] = r;
-      flag[2] = 1.0 / r;
+    const int m = N - 1 - j;
+    const int T = m * (m + 1) / 2;
+    for (int t = tid; t < T + m; t += NT) {
+      if (t < T) {
+        const int ii = tri_row(t), ll = t - ii * (ii + 1) / 2;
+        const int i = j + 1 + ii, l = j + 1 + ll;
+        const double v = fma(-colbuf[i], colbuf[l], A[tri(i, l)]);
+        A[tri(i, l)] = v;
+        if (t == 0 && j + 1 < jend) {        // next pivot, from its final value
+          const double r = rsqrt_newton(v);
+          flag[0] = v;
+          flag[1] = v * r;
+          flag[2] = r;
+        }
+      } else {
+        const int i = j + 1 + (t - T);
+        f[i] = fma(-colbuf[i], zj, f[i]);
+      }
     }
     __syncthreads();
   }
@@ -456,46 +543,35 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
   const int64_t* boff = args.blockoff + e * 36;
 
   if (MODE == MODE_HYB) {
-    // ---- 6a. Y = L_bb^{-1} (column-major packed), row by row
-    auto yidx = [](int m, int i) { return i * NB - i * (i - 1) / 2 + (m - i); };   // m >= i
-    for (int i = 0; i < NB; ++i) {
-      const double* Li = A + tri(NI + i, NI);
-      const double di = invd[NI + i];
-      for (int jj = tid; jj <= i; jj += NT) {
-        double v;
-        if (jj == i) {
-          v = di;
-        } else {
-          double acc = 0.0;
-          for (int m = jj; m < i; ++m) acc = fma(Li[m], Y[yidx(m, jj)], acc);
-          v = -di * acc;
-        }
-        Y[yidx(i, jj)] = v;
+    // ---- 6a. Y = L_bb^{-1} by right-looking forward elimination (row-major packed)
+    for (int t = tid; t < S::TRIB; t += NT) Y[t] = 0.0;
+    __syncthreads();
+    for (int m = 0; m < NB; ++m) {
+      const double im = invd[NI + m];
+      for (int jj = tid; jj <= m; jj += NT) Y[tri(m, jj)] = (jj == m) ? im : Y[tri(m, jj)] * im;
+      __syncthreads();
+      const int w = m + 1, cnt = (NB - 1 - m) * w;
+      for (int t = tid; t < cnt; t += NT) {
+        const int i = m + 1 + t / w, jj = t % w;
+        Y[tri(i, jj)] = fma(-A[tri(NI + i, NI + m)], Y[tri(m, jj)], Y[tri(i, jj)]);
       }
       __syncthreads();
     }
-    // ---- 6b. Y^T Y (lower), g = D Y^T z_b
+    // ---- 6b. Y^T Y (lower): (Y^T Y)_{i jj} = sum_{m >= i} Y_{m i} Y_{m jj}
     for (int t = tid; t < S::TRIB; t += NT) {
-      // decode t -> (i, jj), i >= jj, row-major packed
-      int i = (int)((sqrtf((float)(8 * t + 1)) - 1.0f) * 0.5f);
-      while ((i + 1) * (i + 2) / 2 <= t) ++i;
-      while (i * (i + 1) / 2 > t) --i;
-      const int jj = t - i * (i + 1) / 2;
+      const int i = tri_row(t), jj = t - i * (i + 1) / 2;
       double acc = 0.0;
-      const double* yi = Y + yidx(i, i);
-      const double* yj = Y + yidx(i, jj);
-      for (int m = 0; m < NB - i; ++m) acc = fma(yi[m], yj[m], acc);
+      for (int m = i; m < NB; ++m) acc = fma(Y[tri(m, i)], Y[tri(m, jj)], acc);
       YtY[t] = acc;
     }
     __syncthreads();
-    // ---- 7. scatter S_T = D Y^T Y D and g_T
+    // ---- 7. scatter S_T = D Y^T Y D and g_T = D Y^T z_b
     for (int t = tid; t < NB * NB; t += NT) {
       const int ib = t / NB, jb = t % NB;
       const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
       if (bo_face[a] < 0 || bo_face[b] < 0) continue;
-      const double di = ((a & 1) ? 1.0 : -1.0) * wf[m1];
-      const double dj = ((b & 1) ? 1.0 : -1.0) * wf[m2];
-      const double v = di * dj * YtY[ib >= jb ? tri(ib, jb) : tri(jb, ib)];
+      const double dd = (((a ^ b) & 1) ? -1.0 : 1.0) * wf[m1] * wf[m2];
+      const double v = dd * YtY[ib >= jb ? tri(ib, jb) : tri(jb, ib)];
       const int64_t r0 = args.row_ptr[(int64_t)bo_face[a] * NFN];
       const int64_t rl = args.row_ptr[(int64_t)bo_face[a] * NFN + 1] - r0;
       const int64_t pos = boff[a * 6 + b] + m1 * rl + m2;
@@ -506,7 +582,7 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
       const int a = ib / NFN, m1 = ib % NFN;
       if (bo_face[a] < 0) continue;
       double acc = 0.0;
-      for (int m = ib; m < NB; ++m) acc = fma(Y[yidx(m, ib)], f[NI + m], acc);
+      for (int m = ib; m < NB; ++m) acc = fma(Y[tri(m, ib)], f[NI + m], acc);
       const double v = ((a & 1) ? 1.0 : -1.0) * wf[m1] * acc;
       const int64_t gi = (int64_t)bo_face[a] * NFN + m1;
       if (args.colour == 1) args.rhs[gi] += v;
@@ -516,15 +592,12 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
     // ---- store the factor with Y in place of L_bb
     double* Ls = args.Lstore + e * (int64_t)S::TRI;
     if (S::A_SMEM) {
-      for (int64_t t = tid; t < S::TRI; t += NT) Ls[t] = A[t];
+      for (int t = tid; t < S::TRI; t += NT) Ls[t] = A[t];
       __syncthreads();
     }
     for (int t = tid; t < S::TRIB; t += NT) {
-      int i = (int)((sqrtf((float)(8 * t + 1)) - 1.0f) * 0.5f);
-      while ((i + 1) * (i + 2) / 2 <= t) ++i;
-      while (i * (i + 1) / 2 > t) --i;
-      const int jj = t - i * (i + 1) / 2;
-      Ls[tri(NI + i, NI + jj)] = Y[yidx(i, jj)];
+      const int i = tri_row(t), jj = t - i * (i + 1) / 2;
+      Ls[tri(NI + i, NI + jj)] = Y[t];
     }
   } else {
     // ---- static condensation: scatter S_hat (trailing block) and rhs_b = f_b - L_bi z_i
@@ -548,7 +621,7 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
     }
     if (S::A_SMEM) {
       double* Ls = args.Lstore + e * (int64_t)S::TRI;
-      for (int64_t t = tid; t < S::TRI; t += NT) Ls[t] = A[t];
+      for (int t = tid; t < S::TRI; t += NT) Ls[t] = A[t];
     }
   }
 }

@@ -47,17 +47,17 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// Ticket: returns true in exactly one (the last) block, after all partials are visible.
+// Ticket: returns true in exactly one (the last) block. Thread 0 wrote this block's partial;
+// it alone fences before taking a ticket, so the last block sees every partial in L2.
 __device__ __forceinline__ bool last_block(int* ticket, int nblocks) {
   __shared__ bool last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const int t = atomicAdd(ticket, 1);
     last = (t == nblocks - 1);
   }
   __syncthreads();
-  if (last) __threadfence();
   return last;
 }
 
@@ -65,7 +65,7 @@ __device__ __forceinline__ bool last_block(int* ticket, int nblocks) {
 // thread t adds entries t, t + 256, ... then the block tree. Result valid in thread 0.
 __device__ __forceinline__ double sum_partials(const double* part, int count, int stride, int off, double* sh) {
   double v = 0.0;
-  for (int b = threadIdx.x; b < count; b += kThreads) v += part[(int64_t)b * stride + off];
+  for (int b = threadIdx.x; b < count; b += kThreads) v += __ldcg(part + (int64_t)b * stride + off);
   return block_sum(v, sh);
 }
 
@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kThreads) spmv_face_kernel(PcgArgs a) {
       const int64_t r0 = f * NFN;
       const int64_t lo = a.row_ptr[r0];
       const int len = (int)(a.row_ptr[r0 + 1] - lo);
+#pragma unroll 4
       for (int t = gl; t < len; t += W) {
         const double pj = a.p[a.col[lo + t]];
 #pragma unroll
@@ -256,15 +257,15 @@ cudaError_t pcg_init(const PcgArgs& a, cudaStream_t s, Prof* prof) {
 cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_t s, Prof* prof) {
   for (int it = 0; it < count; ++it) {
     int tok = prof_begin(prof, HYB_K_SPMV, s);
-    // FP64 is the scarce unit on this part (about 1.2 TFLOP/s): 4 lanes per face keep the
-    // cross-lane FP64 reduction small next to the nnz FMAs while each load instruction still
-    // covers whole 32-byte sectors (4 consecutive doubles of one row per face).
+    // FP64 is the scarce unit on this part (about 1.2 TFLOP/s): 2 lanes per face keep the
+    // cross-lane FP64 reduction to one step per row while the 16 consecutive bytes a face
+    // gets per load instruction complete their 32-byte sector on the next iteration.
     const int nbs = a.nblocks / 2, nbv = a.nblocks / 4;
     switch (a.nfn) {
       case 1: spmv_face_kernel<1, 4><<<nbs, kThreads, 0, s>>>(a); break;
-      case 4: spmv_face_kernel<4, 4><<<nbs, kThreads, 0, s>>>(a); break;
-      case 9: spmv_face_kernel<9, 4><<<nbs, kThreads, 0, s>>>(a); break;
-      case 16: spmv_face_kernel<16, 4><<<nbs, kThreads, 0, s>>>(a); break;
+      case 4: spmv_face_kernel<4, 2><<<nbs, kThreads, 0, s>>>(a); break;
+      case 9: spmv_face_kernel<9, 2><<<nbs, kThreads, 0, s>>>(a); break;
+      case 16: spmv_face_kernel<16, 2><<<nbs, kThreads, 0, s>>>(a); break;
       default: return cudaErrorInvalidValue;
     }
     prof_end(prof, tok, s);

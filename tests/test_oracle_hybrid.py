@@ -231,3 +231,19 @@ def test_not_spd_detected():
     D = Discretization.from_problem(p)
     with pytest.raises(NotSPDError):
         D.hybridize()
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_mixed_form_gives_the_same_H(k):
+    """Sec. 3.2: H~ from the hybridized mixed form equals H (A = M + B^T W^{-1} B exactly);
+    also checks that identity on the element matrix itself."""
+    p = inputs.random_problem(2, k, 0.2, 61 + k, 1e-2, 1e2)
+    D = Discretization.from_problem(p)
+    for e in range(D.mesh.n_elem):
+        M, B, W, d = D.mixed_form_blocks(e)
+        A2 = M + B.T @ np.linalg.solve(W, B)
+        assert np.abs(A2 - d["A"]).max() < 1e-12 * np.abs(d["A"]).max()
+        tol = max(1e-12, np.linalg.cond(d["A"]) * 2.2e-16)
+        S1 = D.element_reduced(e)
+        S2 = D.element_reduced_mixed(e)
+        assert rel(S2["S"], S1["S"]) < tol and rel(S2["g"], S1["g"]) < tol
