@@ -44,7 +44,12 @@ def parse_args(argv=None):
     ap.add_argument("--maxit", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="mesh size override (parity / profiling runs)")
-    ap.add_argument("--config", default="2", help="workload: 2 (32^3 RT_1, default), 3 (96^3 RT_2), 5 (64^3 RT_3)")
+    ap.add_argument("--config", default="2",
+                    help="workload: 2 (32^3 RT_1, default), 3 (96^3 RT_2), 4 (256-problem batch), 5 (64^3 RT_3)")
+    ap.add_argument("--batch-count", type=int, default=256, help="problems in the batched workload")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="fp64, or mixed: FP32 mixed-form elimination below the contrast threshold")
+    ap.add_argument("--threshold", type=float, default=1e4, help="mixed: contrast above which elements stay FP64")
     ap.add_argument("--assembly-only", action="store_true",
                     help="time only the element phase (assemble + recover with lambda = 0); per-config rates")
     return ap.parse_args(argv)
@@ -191,7 +196,7 @@ def run_reference(args):
     v = E / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": args.gpus,
             "steps": K, "warmup": W, "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": f"{SAMPLE_N}^3 mesh of the same recipe", "parallelism": "none"},
             "cpu_baseline": {"value": v, "unit": "elements/s", "cores": 1, "kind": "oracle",
                              "sample": f"{SAMPLE_N}^3 mesh, full step per sample"},
@@ -231,6 +236,24 @@ def element_flops(k):
     return asm + load + chol + inv + gram + nb * nb
 
 
+def element_flops_mixed(k):
+    """Algorithmic FP32 flops of one element on the mixed path (hybridized mixed form):
+    alpha-mass by sum factorisation, G and G^{-1}, chol(M), Xd = L_M^{-1} D, Z = G^{-1} + Xd^T Xd,
+    chol(Z), Y = L_M,bb^{-1}, P = Xd_b^T Y, V = L_Z^{-1} P, S = Y^T Y - V^T V, two FP32 solves."""
+    P, p, Q = k + 2, k + 1, k + 2
+    nfn, ni = p * p, 3 * k * p * p
+    nb = 6 * nfn
+    n = ni + nb
+    nq = p ** 3
+    mass = 0
+    for diag in (True, True, True, False, False, False):
+        nja, njb = (P, p) if diag else (p, P)
+        mass += 2 * (Q * Q * P * nja * Q + Q * P * nja * p * njb * Q + P * nja * p * njb * p * p * Q // (2 if diag else 1))
+    g = 2 * (Q * Q * p * p * Q + Q * p ** 4 * Q + p ** 6 * Q) + 2 * nq ** 3
+    return (mass + g + n ** 3 // 3 + n * n * nq + nq * nq * n + nq ** 3 // 3 + nb ** 3 // 3 + nq * nb * nb
+            + nq * nq * nb + nb ** 3 // 3 + nb * nb * nq + 2 * 2 * (2 * n * n + 2 * n * nq + 2 * nq * nq))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -247,7 +270,11 @@ def run_ours(args):
     p = inputs.make_config(cfg, n=args.n)
     tt = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     verts, alpha, beta, load = tt(p.vertices), tt(p.alpha), tt(p.beta), tt(p.load)
-    ctx = hyb.hyb_setup(verts, p.nx, p.ny, p.nz, p.order, alpha, beta)
+    mixed = args.precision == "mixed"
+    ctx = hyb.hyb_setup(verts, p.nx, p.ny, p.nz, p.order, alpha, beta,
+                        precision=hyb.HYB_MIXED if mixed else hyb.HYB_FP64,
+                        contrast_threshold=args.threshold if mixed else 0.0)
+    n64, n32, theta = ctx.precision_split()
     sz = ctx.sizes()
     E, n_loc, N, nnz = sz["n_elem"], sz["n_loc"], sz["n_lambda"], sz["nnz"]
     lam = torch.zeros(N, dtype=torch.float64, device=dev)
@@ -341,18 +368,31 @@ def run_ours(args):
     phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
     elem_ms = prof["element"][0] / args.steps
     elem_flops = element_flops(p.order)
-    elem_tflops = E * elem_flops / (elem_ms * 1e-3) / 1e12 if elem_ms > 0 else None
-    element_roofline = {"kernel": f"element_kernel<{p.order}> (FP64)", "bound": "alu",
-                        "achieved": elem_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-                        "frac": elem_tflops / fp64_peak if elem_tflops else None,
-                        "algorithmic_flops_per_element": elem_flops}
+    if not mixed:
+        elem_tflops = E * elem_flops / (elem_ms * 1e-3) / 1e12 if elem_ms > 0 else None
+        element_roofline = {"kernel": f"element_kernel<{p.order}> (FP64)", "bound": "alu",
+                            "achieved": elem_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                            "frac": elem_tflops / fp64_peak if elem_tflops else None,
+                            "algorithmic_flops_per_element": elem_flops}
+    else:
+        f32 = element_flops_mixed(p.order)
+        # FP32 elements at the FP32 peak plus FP64 elements at the FP64 peak bound the phase from below
+        t_min = (n32 * f32 / (fp32_peak * 1e12) + n64 * elem_flops / (fp64_peak * 1e12))
+        element_roofline = {"kernel": f"element_mixed_kernel<{p.order}> (FP32) + element_kernel<{p.order}> (FP64)",
+                            "bound": "alu", "achieved": (n32 * f32 + n64 * elem_flops) / (elem_ms * 1e-3) / 1e12,
+                            "peak": (n32 * f32 + n64 * elem_flops) / t_min / 1e12 if t_min > 0 else None,
+                            "unit": "TFLOP/s", "frac": t_min / (elem_ms * 1e-3) if elem_ms > 0 else None,
+                            "algorithmic_flops_per_element_fp32": f32, "algorithmic_flops_per_element_fp64": elem_flops,
+                            "elements_fp64": n64, "elements_fp32": n32, "contrast_threshold": theta}
     workload = WORKLOAD if cfg == 2 else f"config {cfg}: {p.nx}^3 jittered hex mesh, RT_{p.order}, FP64"
+    if mixed:
+        workload = workload.replace("FP64", f"mixed FP32/FP64 (threshold {theta:g})")
     if args.assembly_only:
         workload += " (element phase only: assemble + recover)"
     line = {
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": workload, "elements": E, "order": p.order, "n_loc": n_loc, "n_lambda": N,
                    "nnz": nnz, "pcg_rtol": args.rtol, "pcg_iterations": iters_timed[0] if iters_timed else None,
                    "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) before each step"},
@@ -378,10 +418,97 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """The batched workload: 256 independent problems, n ~ U{6..24}, k ~ U{0..3}, one context."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    rank, local, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", 1)) > 1 else "gloo")
+    __graft_entry__.build()
+    from paper_1801_08914_gb300 import hyb, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    probs = inputs.batch_problems(count=args.batch_count)
+    tt = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    verts = [tt(p.vertices) for p in probs]
+    alphas = [tt(p.alpha) for p in probs]
+    betas = [tt(p.beta) for p in probs]
+    loads = [tt(p.load) for p in probs]
+    mixed = args.precision == "mixed"
+    t0 = time.perf_counter()
+    b = hyb.hyb_setup_batch([(v, p.nx, p.ny, p.nz) for v, p in zip(verts, probs)], [p.order for p in probs],
+                            alphas, betas, precision=hyb.HYB_MIXED if mixed else hyb.HYB_FP64,
+                            contrast_threshold=args.threshold if mixed else 0.0)
+    t_setup = time.perf_counter() - t0
+    sizes = [b.context(i).sizes() for i in range(len(probs))]
+    E = sum(s["n_elem"] for s in sizes)
+    N = sum(s["n_lambda"] for s in sizes)
+    lams = [torch.zeros(s["n_lambda"], dtype=torch.float64, device=dev) for s in sizes]
+    us = [torch.zeros(s["n_elem"], s["n_loc"], dtype=torch.float64, device=dev) for s in sizes]
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    iters = []
+
+    def step():
+        hyb.hyb_assemble_reduced_batch(b, loads)
+        if not args.assembly_only:
+            its, rr, st = hyb.hyb_solve_reduced_batch(b, args.rtol, args.maxit, lams, check=False)
+            if st != hyb.HYB_OK:
+                raise hyb.HybError(st, "hyb_solve_reduced_batch")
+            iters.append(max(its))
+        hyb.hyb_recover_batch(b, lams, us)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    hyb.hyb_batch_set_profiling(b, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters.clear()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    prof = hyb.hyb_batch_get_profile(b)
+    ms = sum(a.elapsed_time(c) for a, c in ev)
+    value, ms_max = aggregate(E * args.steps, ms, world, device=dev)
+    elem_ms = prof["element"][0] / args.steps
+    orders = [p.order for p in probs]
+    line = {
+        "metric": METRIC.replace("FP64 GPU path", "batched, " + ("mixed" if mixed else "FP64")),
+        "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"{len(probs)} independent problems, n ~ U{{6..24}}, k ~ U{{0..3}}, jitter 0.2h, "
+                               "contrast [1e-2, 1e4]" + (" (element phase only)" if args.assembly_only else ""),
+                   "elements": E, "n_lambda": N, "problems_per_order": [orders.count(k) for k in range(4)],
+                   "pcg_rtol": args.rtol, "pcg_iterations_max": iters[0] if iters else None,
+                   "setup_s": t_setup, "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) before each step"},
+        "gpu_launches": int(sum(v[1] for v in prof.values())),
+        "phases": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()},
+        "assembly_elements_per_s": E / (elem_ms * 1e-3) if elem_ms > 0 else None,
+        "clocks": ck,
+    }
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif str(args.config) == "4":
+        run_batch(args)
     else:
         run_ours(args)
     import torch.distributed as dist

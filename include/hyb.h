@@ -75,8 +75,13 @@ typedef struct hyb_ctx hyb_ctx;
  *  order      : k in 0..3.
  *  alpha,beta : device, nx*ny*nz doubles each, per-element mass and divergence
  *               coefficients (> 0); kept until hyb_destroy.
- *  precision  : HYB_FP64 (HYB_MIXED returns HYB_ERR_INVALID_ARG in this version).
- *  contrast_threshold : reserved for the mixed path; ignored for HYB_FP64.
+ *  precision  : HYB_FP64, or HYB_MIXED: elements whose contrast beta/alpha is at most
+ *               contrast_threshold are eliminated in FP32 through the hybridized mixed
+ *               form (Sec. 3.2: A^-1 = M^-1 - M^-1 D Z^-1 D^T M^-1, every factor well
+ *               conditioned), with the load term and the recovery refined against an FP64
+ *               residual; the others use the FP64 path. The reduced system, PCG and the
+ *               recovered u stay FP64. Static condensation needs an HYB_FP64 context.
+ *  contrast_threshold : HYB_MIXED only; <= 0 selects the default 1e4 (ignored for HYB_FP64).
  *  cuda_stream: cudaStream_t to enqueue on (NULL = legacy default stream).
  *  out        : host, receives the new context.
  *  Builds the CSR pattern of H (int64 row pointers, int32 columns), per-element
@@ -124,7 +129,7 @@ int hyb_recover(hyb_ctx* ctx, const double* lambda, double* u);
  * staticcond_assemble -- static condensation S_hat = A_bb - A_bi A_ii^-1 A_ib per
  *  element and S = [I;W]^T S_hat [I;W] (Sec. 3.1, eq. 3.1-3.2), assembled on the
  *  same CSR pattern as H with right-hand side f_b - A_bi A_ii^-1 f_i.
- *  load, ess : as for hyb_assemble_reduced.
+ *  load, ess : as for hyb_assemble_reduced. Returns HYB_ERR_INVALID_ARG on an HYB_MIXED context.
  */
 int staticcond_assemble(hyb_ctx* ctx, const double* load, const double* ess);
 
@@ -213,6 +218,10 @@ int hyb_pcg_solve_noalloc(const int64_t* row_ptr, const int32_t* col, const doub
  */
 int hyb_measure_fma_peak(int fp64, void* cuda_stream, double* tflops);
 
+/* hyb_get_precision_split -- host outputs (any may be NULL): elements on the FP64 and the
+ *  FP32 path and the contrast threshold in use (0 for HYB_FP64 contexts). */
+int hyb_get_precision_split(const hyb_ctx* ctx, int64_t* n_fp64, int64_t* n_fp32, double* threshold);
+
 /* hyb_get_sizes -- host outputs (any may be NULL): elements, n_loc, N_lambda, nnz. */
 int hyb_get_sizes(const hyb_ctx* ctx, int64_t* n_elem, int* n_loc, int64_t* n_lambda, int64_t* nnz);
 
@@ -224,6 +233,44 @@ void hyb_destroy(hyb_ctx* ctx);
 
 /* hyb_status_string -- static name of a status code. */
 const char* hyb_status_string(int status);
+
+/* ---------------------------------------------------------------------------------------
+ * Batches: many independent problems of uneven mesh size and order in one context. Each
+ * phase launches once per (order, colour, precision path) over all problems' elements, and
+ * the reduced solves of all problems run as one batched PCG (every problem keeps its own
+ * scalars and stopping test). Array-of-pointer arguments are HOST arrays of nprob DEVICE
+ * pointers; per-problem conventions are those of the single-problem calls above.
+ */
+typedef struct hyb_batch hyb_batch;
+
+/* hyb_setup_batch -- meshes, orders: host arrays of nprob; alphas, betas: host arrays of
+ *  device pointers (kept until hyb_destroy_batch). precision / contrast_threshold as for
+ *  hyb_setup. */
+int hyb_setup_batch(int nprob, const hyb_mesh* meshes, const int* orders, const double* const* alphas,
+                    const double* const* betas, int precision, double contrast_threshold, void* cuda_stream,
+                    hyb_batch** out);
+
+/* hyb_assemble_reduced_batch -- hyb_assemble_reduced for every problem (ess may be NULL). */
+int hyb_assemble_reduced_batch(hyb_batch* b, const double* const* loads, const double* const* ess);
+
+/* hyb_solve_reduced_batch -- diagonal PCG for every problem; iters, rel_res: host arrays of
+ *  nprob or NULL. Returns HYB_ERR_NOT_CONVERGED if any problem hit maxit. */
+int hyb_solve_reduced_batch(hyb_batch* b, double rtol, int maxit, double* const* lambdas, int* iters,
+                            double* rel_res);
+
+/* hyb_recover_batch -- hyb_recover for every problem. */
+int hyb_recover_batch(hyb_batch* b, const double* const* lambdas, double* const* us);
+
+/* hyb_batch_context -- the single-problem context of problem i (owned by the batch; do not
+ *  destroy), for sizes, exports and error queries. */
+int hyb_batch_context(hyb_batch* b, int problem, hyb_ctx** ctx);
+
+/* launch profile of the batch's own launches (see hyb_set_profiling / hyb_get_profile) */
+int hyb_batch_set_profiling(hyb_batch* b, int enable);
+int hyb_batch_get_profile(const hyb_batch* b, int kernel_class, double* total_ms, int64_t* launches);
+
+/* hyb_destroy_batch -- free the batch and every per-problem context; NULL is a no-op. */
+void hyb_destroy_batch(hyb_batch* b);
 
 #ifdef __cplusplus
 }

@@ -14,6 +14,7 @@
 //   * a two-colouring by (i + j + l) mod 2: the two neighbours of a face
 //     always differ in colour.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -95,6 +96,16 @@ struct hyb_ctx {
   int64_t* blockoff = nullptr;
   int32_t* colour_list[2] = {nullptr, nullptr};
   int64_t n_colour[2] = {0, 0};
+  // mixed precision: element lists by (colour, path) and per-precision recovery lists
+  int precision = HYB_FP64;
+  double theta = 0.0;                      // contrast beta/alpha above which an element stays FP64
+  int32_t* mlist[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [colour][0 = FP64, 1 = FP32]
+  int64_t n_mlist[2][2] = {{0, 0}, {0, 0}};
+  int32_t* plist[2] = {nullptr, nullptr};  // [path]: all elements of that path
+  int64_t n_path[2] = {0, 0};
+  int32_t* slot = nullptr;
+  float* Lstore32 = nullptr;
+  std::vector<int32_t> h_list[2][2];       // host copies: [colour][path] (path 0 = FP64, 1 = FP32)
   double* Lstore = nullptr;
   double* zstore = nullptr;
   int* status = nullptr;
@@ -195,7 +206,8 @@ ElemArgs elem_args(hyb_ctx* c, const double* load, const double* ess, int colour
   return a;
 }
 
-int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, const double* beta) {
+int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, const double* beta, int precision,
+               double theta) {
   c->nx = m->nx; c->ny = m->ny; c->nz = m->nz; c->k = order;
   c->sz = Sizes::of(order);
   c->vertices = m->vertices;
@@ -287,7 +299,50 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
     c->n_colour[t] = (int64_t)lists[t].size();
     if ((st = dalloc(c, &c->colour_list[t], lists[t].size()))) return st;
   }
-  if ((st = dalloc(c, &c->Lstore, (size_t)E * (size_t)tri_size(s.n)))) return st;
+  // precision paths: FP64 for every element, or (mixed) FP64 only above the contrast threshold
+  c->precision = precision;
+  c->theta = theta > 0.0 ? theta : 1e4;
+  std::vector<int32_t> slot_h(E, 0);
+  if (precision == HYB_MIXED) {
+    std::vector<double> ah(E), bh(E);
+    cudaError_t e0 = cudaMemcpy(ah.data(), alpha, E * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e0 == cudaSuccess) e0 = cudaMemcpy(bh.data(), beta, E * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e0 != cudaSuccess) return cuda_status(e0);
+    std::vector<int32_t> ml[2][2], pl[2];
+    for (int col = 0; col < 2; ++col)
+      for (int32_t el : lists[col]) {
+        const int path = (bh[el] / ah[el] > c->theta) ? 0 : 1;
+        slot_h[el] = (int32_t)pl[path].size();
+        pl[path].push_back(el);
+        ml[col][path].push_back(el);
+      }
+    for (int col = 0; col < 2; ++col)
+      for (int path = 0; path < 2; ++path) c->h_list[col][path] = ml[col][path];
+    for (int col = 0; col < 2; ++col)
+      for (int path = 0; path < 2; ++path) {
+        c->n_mlist[col][path] = (int64_t)ml[col][path].size();
+        if ((st = dalloc(c, &c->mlist[col][path], ml[col][path].size()))) return st;
+        if (!ml[col][path].empty() &&
+            cudaMemcpy(c->mlist[col][path], ml[col][path].data(), ml[col][path].size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+          return HYB_ERR_CUDA;
+      }
+    for (int path = 0; path < 2; ++path) {
+      c->n_path[path] = (int64_t)pl[path].size();
+      if ((st = dalloc(c, &c->plist[path], pl[path].size()))) return st;
+      if (!pl[path].empty() && cudaMemcpy(c->plist[path], pl[path].data(), pl[path].size() * sizeof(int32_t),
+                                          cudaMemcpyHostToDevice) != cudaSuccess)
+        return HYB_ERR_CUDA;
+    }
+    if ((st = dalloc(c, &c->slot, E))) return st;
+    if (cudaMemcpy(c->slot, slot_h.data(), E * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+      return HYB_ERR_CUDA;
+    if ((st = dalloc(c, &c->Lstore, (size_t)c->n_path[0] * (size_t)tri_size(s.n)))) return st;
+    if ((st = dalloc(c, &c->Lstore32, (size_t)c->n_path[1] * (size_t)mixed_store_floats(order)))) return st;
+  } else {
+    if ((st = dalloc(c, &c->Lstore, (size_t)E * (size_t)tri_size(s.n)))) return st;
+    for (int col = 0; col < 2; ++col) c->h_list[col][0] = lists[col];
+  }
   if ((st = dalloc(c, &c->zstore, (size_t)E * s.n))) return st;
   if ((st = dalloc(c, &c->status, 1))) return st;
   if ((st = dalloc(c, &c->err_elem, 1))) return st;
@@ -316,6 +371,7 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
   up(d_adjc, adj_count.data(), adj_count.size() * sizeof(int32_t));
   for (int t = 0; t <= kMaxOrder; ++t) build_ref_tables(t, &c->tabs[t]);
   if (e == cudaSuccess) e = upload_ref_tables(c->tabs, kMaxOrder + 1, S);
+  if (e == cudaSuccess) e = upload_ref_tables_mixed(c->tabs, kMaxOrder + 1, S);
   if (e == cudaSuccess) e = launch_expand_cols(c->row_ptr, d_adj, d_adjc, F, nfn, c->col, S, &c->prof);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S);   // host vectors die at return
   if (e != cudaSuccess) return cuda_status(e);
@@ -327,11 +383,26 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
 
 int assemble_impl(hyb_ctx* c, const double* load, const double* ess, int mode) {
   if (!c || !load) return HYB_ERR_INVALID_ARG;
+  if (c->precision == HYB_MIXED && mode == MODE_SC) return HYB_ERR_INVALID_ARG;
   int st = reset_status(c);
   if (st) return st;
   c->mode = MODE_NONE;
   for (int colour = 0; colour < 2; ++colour) {
     ElemArgs a = elem_args(c, load, ess, colour);
+    if (c->precision == HYB_MIXED) {
+      // colour 0 of both paths completes before colour 1 starts (stream order)
+      a.slot = c->slot;
+      a.elem_list = c->mlist[colour][0];
+      a.n_list = c->n_mlist[colour][0];
+      cudaError_t e = launch_element(c->k, mode, a, c->stream, &c->prof);
+      if (e != cudaSuccess) return cuda_status(e);
+      a.elem_list = c->mlist[colour][1];
+      a.n_list = c->n_mlist[colour][1];
+      a.Lstore32 = c->Lstore32;
+      e = launch_element_mixed(c->k, a, c->stream, &c->prof);
+      if (e != cudaSuccess) return cuda_status(e);
+      continue;
+    }
     cudaError_t e = launch_element(c->k, mode, a, c->stream, &c->prof);
     if (e != cudaSuccess) return cuda_status(e);
   }
@@ -353,8 +424,24 @@ int recover_impl(hyb_ctx* c, const double* lam, double* u, int mode) {
   a.zstore = c->zstore;
   a.u = u;
   std::memcpy(a.wf, c->tabs[c->k].wf, sizeof(a.wf));
+  if (c->precision == HYB_MIXED) {
+    a.elem_list = c->plist[0];
+    a.n_elem = c->n_path[0];
+    a.slot = c->slot;
+  }
+  int st = reset_status(c);
+  if (st) return st;
   cudaError_t e = launch_recover(a, c->stream, &c->prof);
   if (e != cudaSuccess) return cuda_status(e);
+  if (c->precision == HYB_MIXED) {
+    ElemArgs m = elem_args(c, nullptr, nullptr, 0);
+    m.elem_list = c->plist[1];
+    m.n_list = c->n_path[1];
+    m.slot = c->slot;
+    m.Lstore32 = c->Lstore32;
+    e = launch_recover_mixed(c->k, m, lam, u, c->stream, &c->prof);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   return finish_phase(c);
 }
 
@@ -364,20 +451,20 @@ extern "C" {
 
 int hyb_setup(const hyb_mesh* m, int order, const double* alpha, const double* beta, int precision,
               double contrast_threshold, void* cuda_stream, hyb_ctx** out) {
-  (void)contrast_threshold;
   if (!out) return HYB_ERR_INVALID_ARG;
   *out = nullptr;
   if (!m || !m->vertices || !alpha || !beta) return HYB_ERR_INVALID_ARG;
   if (m->nx < 1 || m->ny < 1 || m->nz < 1) return HYB_ERR_INVALID_ARG;
   if ((int64_t)m->nx * m->ny * m->nz > INT32_MAX) return HYB_ERR_INVALID_ARG;
   if (order < 0 || order > kMaxOrder) return HYB_ERR_UNSUPPORTED_ORDER;
-  if (precision != HYB_FP64) return HYB_ERR_INVALID_ARG;
+  if (precision != HYB_FP64 && precision != HYB_MIXED) return HYB_ERR_INVALID_ARG;
+  if (!(contrast_threshold >= 0.0)) return HYB_ERR_INVALID_ARG;
   hyb_ctx* c = new (std::nothrow) hyb_ctx();
   if (!c) return HYB_ERR_OOM;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   int st;
   try {
-    st = setup_impl(c, m, order, alpha, beta);
+    st = setup_impl(c, m, order, alpha, beta, precision, contrast_threshold);
   } catch (const std::bad_alloc&) {
     st = HYB_ERR_OOM;
   } catch (...) {
@@ -495,6 +582,15 @@ int hyb_get_profile(const hyb_ctx* c, int kernel_class, double* total_ms, int64_
   return HYB_OK;
 }
 
+int hyb_get_precision_split(const hyb_ctx* c, int64_t* n_fp64, int64_t* n_fp32, double* threshold) {
+  if (!c) return HYB_ERR_INVALID_ARG;
+  const bool mixed = c->precision == HYB_MIXED;
+  if (n_fp64) *n_fp64 = mixed ? c->n_path[0] : c->E;
+  if (n_fp32) *n_fp32 = mixed ? c->n_path[1] : 0;
+  if (threshold) *threshold = mixed ? c->theta : 0.0;
+  return HYB_OK;
+}
+
 int hyb_get_sizes(const hyb_ctx* c, int64_t* n_elem, int* n_loc, int64_t* n_lambda, int64_t* nnz) {
   if (!c) return HYB_ERR_INVALID_ARG;
   if (n_elem) *n_elem = c->E;
@@ -531,6 +627,354 @@ const char* hyb_status_string(int s) {
     case HYB_ERR_TIMEOUT: return "HYB_ERR_TIMEOUT";
   }
   return "HYB_ERR_UNKNOWN";
+}
+
+}  // extern "C"
+
+// ============================================================================================
+// Batched problems: many independent meshes of uneven size and order. Set-up reuses the
+// single-problem set-up per problem; every phase then launches once per (order, colour,
+// precision path) over (problem, element) work items with per-problem arguments read from
+// device arrays, and the reduced solves run as one batched PCG whose blocks are partitioned
+// by problem (each problem keeps its own scalars, so its iterates equal a solo solve's).
+struct hyb_batch {
+  int nprob = 0;
+  cudaStream_t stream = nullptr;
+  int precision = HYB_FP64;
+  std::vector<hyb_ctx*> ctx;
+  std::vector<int> order;
+  std::vector<ElemArgs> h_eargs;
+  std::vector<RecoverArgs> h_rargs;
+  std::vector<PcgArgs> h_pargs;
+  ElemArgs* d_eargs = nullptr;
+  RecoverArgs* d_rargs = nullptr;
+  PcgArgs* d_pargs = nullptr;
+  const double** d_lams = nullptr;
+  double** d_us = nullptr;
+  int2* items[kMaxOrder + 1][2][2] = {};    // [order][colour][path]
+  int64_t n_items[kMaxOrder + 1][2][2] = {};
+  int2* ritems[kMaxOrder + 1][2] = {};      // [order][path]
+  int64_t n_ritems[kMaxOrder + 1][2] = {};
+  int32_t *spmv_prob = nullptr, *spmv_first = nullptr, *spmv_count = nullptr;
+  int32_t *vec_prob = nullptr, *vec_first = nullptr, *vec_count = nullptr;
+  int n_spmv = 0, n_vec = 0;
+  int* flags_all = nullptr;
+  double* scal_all = nullptr;
+  int* status = nullptr;
+  std::vector<void*> allocs;
+  Prof prof;
+  int mode = MODE_NONE;
+};
+
+namespace {
+
+template <class T>
+int balloc(hyb_batch* b, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return HYB_ERR_OOM;
+  }
+  b->allocs.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return HYB_OK;
+}
+
+template <class T>
+int bupload(hyb_batch* b, T** dst, const std::vector<T>& src) {
+  int st = balloc(b, dst, src.size());
+  if (st) return st;
+  if (!src.empty() &&
+      cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return HYB_ERR_CUDA;
+  return HYB_OK;
+}
+
+int batch_finish(hyb_batch* b) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  b->prof.collect();
+  if (st != 0) {
+    // the failing element's id is recorded by its own problem
+    for (hyb_ctx* c : b->ctx) {
+      long long el = -1;
+      if (cudaMemcpy(&el, c->err_elem, sizeof(long long), cudaMemcpyDeviceToHost) == cudaSuccess && el >= 0)
+        c->last_err_elem = el;
+    }
+  }
+  return st;
+}
+
+int batch_reset(hyb_batch* b) {
+  cudaError_t e = cudaMemsetAsync(b->status, 0, sizeof(int), b->stream);
+  for (hyb_ctx* c : b->ctx)
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err_elem, 0xff, sizeof(long long), b->stream);
+  return cuda_status(e);
+}
+
+int setup_batch_impl(hyb_batch* b, const hyb_mesh* meshes, const int* orders, const double* const* alphas,
+                     const double* const* betas, double theta) {
+  int st;
+  std::vector<int2> items[kMaxOrder + 1][2][2], ritems[kMaxOrder + 1][2];
+  for (int p = 0; p < b->nprob; ++p) {
+    if (orders[p] < 0 || orders[p] > kMaxOrder) return HYB_ERR_UNSUPPORTED_ORDER;
+    hyb_ctx* c = new (std::nothrow) hyb_ctx();
+    if (!c) return HYB_ERR_OOM;
+    c->stream = b->stream;
+    b->ctx.push_back(c);
+    b->order.push_back(orders[p]);
+    if ((st = setup_impl(c, &meshes[p], orders[p], alphas[p], betas[p], b->precision, theta))) return st;
+    const int k = orders[p];
+    for (int col = 0; col < 2; ++col)
+      for (int path = 0; path < 2; ++path)
+        for (int32_t e : c->h_list[col][path]) {
+          items[k][col][path].push_back(make_int2(p, e));
+          ritems[k][path].push_back(make_int2(p, e));
+        }
+  }
+  if ((st = balloc(b, &b->status, 1))) return st;
+  if ((st = balloc(b, &b->flags_all, 4 * (size_t)b->nprob))) return st;
+  if ((st = balloc(b, &b->scal_all, 8 * (size_t)b->nprob))) return st;
+  for (int k = 0; k <= kMaxOrder; ++k)
+    for (int path = 0; path < 2; ++path) {
+      for (int col = 0; col < 2; ++col) {
+        b->n_items[k][col][path] = (int64_t)items[k][col][path].size();
+        if ((st = bupload(b, &b->items[k][col][path], items[k][col][path]))) return st;
+      }
+      b->n_ritems[k][path] = (int64_t)ritems[k][path].size();
+      if ((st = bupload(b, &b->ritems[k][path], ritems[k][path]))) return st;
+    }
+  // per-problem arguments (pointers that change per call are filled in by the phases)
+  std::vector<int32_t> sp, sf, sc, vp, vf, vc;
+  for (int p = 0; p < b->nprob; ++p) {
+    hyb_ctx* c = b->ctx[p];
+    ElemArgs a = elem_args(c, nullptr, nullptr, 0);
+    a.slot = c->slot;
+    a.Lstore32 = c->Lstore32;
+    a.status = b->status;
+    b->h_eargs.push_back(a);
+    RecoverArgs r{};
+    r.k = c->k;
+    r.mode = MODE_HYB;
+    r.elem_face = c->elem_face;
+    r.Lstore = c->Lstore;
+    r.zstore = c->zstore;
+    r.slot = c->slot;
+    std::memcpy(r.wf, c->tabs[c->k].wf, sizeof(r.wf));
+    b->h_rargs.push_back(r);
+    PcgArgs g{};
+    g.n = c->n_lambda;
+    g.row_ptr = c->row_ptr;
+    g.col = c->col;
+    g.val = c->val;
+    g.b = c->rhs;
+    g.r = c->r;
+    g.p = c->p;
+    g.q = c->q;
+    g.dinv = c->dinv;
+    g.partial = c->partial;
+    g.scal = b->scal_all + 8 * p;
+    g.flags = b->flags_all + 4 * p;
+    g.nblocks = c->nblocks;
+    g.nfn = c->sz.nfn;
+    b->h_pargs.push_back(g);
+    // problem-aligned block ranges: about 64k nonzeros per SpMV block, 8k rows per vector block
+    const int nbs = (int)std::max<int64_t>(1, std::min<int64_t>(c->nblocks * 5 / 8, (c->nnz + 65535) / 65536));
+    const int nbv = (int)std::max<int64_t>(1, std::min<int64_t>(c->nblocks / 4, (c->n_lambda + 8191) / 8192));
+    sf.push_back((int32_t)sp.size());
+    sc.push_back(nbs);
+    for (int i = 0; i < nbs; ++i) sp.push_back(p);
+    vf.push_back((int32_t)vp.size());
+    vc.push_back(nbv);
+    for (int i = 0; i < nbv; ++i) vp.push_back(p);
+  }
+  b->n_spmv = (int)sp.size();
+  b->n_vec = (int)vp.size();
+  if ((st = bupload(b, &b->spmv_prob, sp)) || (st = bupload(b, &b->spmv_first, sf)) ||
+      (st = bupload(b, &b->spmv_count, sc)) || (st = bupload(b, &b->vec_prob, vp)) ||
+      (st = bupload(b, &b->vec_first, vf)) || (st = bupload(b, &b->vec_count, vc)))
+    return st;
+  if ((st = bupload(b, &b->d_eargs, b->h_eargs)) || (st = bupload(b, &b->d_rargs, b->h_rargs)) ||
+      (st = bupload(b, &b->d_pargs, b->h_pargs)))
+    return st;
+  if ((st = balloc(b, &b->d_lams, b->nprob)) || (st = balloc(b, &b->d_us, b->nprob))) return st;
+  return cuda_status(cudaStreamSynchronize(b->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+int hyb_setup_batch(int nprob, const hyb_mesh* meshes, const int* orders, const double* const* alphas,
+                    const double* const* betas, int precision, double contrast_threshold, void* cuda_stream,
+                    hyb_batch** out) {
+  if (!out) return HYB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nprob < 1 || !meshes || !orders || !alphas || !betas) return HYB_ERR_INVALID_ARG;
+  if (precision != HYB_FP64 && precision != HYB_MIXED) return HYB_ERR_INVALID_ARG;
+  if (!(contrast_threshold >= 0.0)) return HYB_ERR_INVALID_ARG;
+  for (int p = 0; p < nprob; ++p) {
+    if (!meshes[p].vertices || !alphas[p] || !betas[p]) return HYB_ERR_INVALID_ARG;
+    if (meshes[p].nx < 1 || meshes[p].ny < 1 || meshes[p].nz < 1) return HYB_ERR_INVALID_ARG;
+  }
+  hyb_batch* b = new (std::nothrow) hyb_batch();
+  if (!b) return HYB_ERR_OOM;
+  b->nprob = nprob;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->precision = precision;
+  int st;
+  try {
+    st = setup_batch_impl(b, meshes, orders, alphas, betas, contrast_threshold);
+  } catch (const std::bad_alloc&) {
+    st = HYB_ERR_OOM;
+  } catch (...) {
+    st = HYB_ERR_CUDA;
+  }
+  if (st != HYB_OK) {
+    hyb_destroy_batch(b);
+    return st;
+  }
+  *out = b;
+  return HYB_OK;
+}
+
+int hyb_assemble_reduced_batch(hyb_batch* b, const double* const* loads, const double* const* ess) {
+  if (!b || !loads) return HYB_ERR_INVALID_ARG;
+  for (int p = 0; p < b->nprob; ++p) {
+    if (!loads[p]) return HYB_ERR_INVALID_ARG;
+    b->h_eargs[p].load = loads[p];
+    b->h_eargs[p].ess = ess ? ess[p] : nullptr;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_eargs, b->h_eargs.data(), b->h_eargs.size() * sizeof(ElemArgs),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = batch_reset(b);
+  if (st) return st;
+  b->mode = MODE_NONE;
+  for (int col = 0; col < 2; ++col)
+    for (int k = 0; k <= kMaxOrder; ++k) {
+      e = launch_element_batch(k, MODE_HYB, b->d_eargs, b->items[k][col][0], b->n_items[k][col][0], col, b->stream,
+                               &b->prof);
+      if (e == cudaSuccess && b->n_items[k][col][1])
+        e = launch_mixed_batch(k, b->d_eargs, b->items[k][col][1], b->n_items[k][col][1], col, false, nullptr,
+                               nullptr, b->stream, &b->prof);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  st = batch_finish(b);
+  if (st == HYB_OK) {
+    b->mode = MODE_HYB;
+    for (hyb_ctx* c : b->ctx) c->mode = MODE_HYB;
+  }
+  return st;
+}
+
+int hyb_solve_reduced_batch(hyb_batch* b, double rtol, int maxit, double* const* lambdas, int* iters,
+                            double* rel_res) {
+  if (!b || !lambdas || maxit < 0 || !(rtol >= 0.0)) return HYB_ERR_INVALID_ARG;
+  if (b->mode != MODE_HYB) return HYB_ERR_INVALID_ARG;
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < b->nprob && e == cudaSuccess; ++p) {
+    if (!lambdas[p]) return HYB_ERR_INVALID_ARG;
+    b->h_pargs[p].x = lambdas[p];
+    e = pcg_init(b->h_pargs[p], b->stream, &b->prof);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_pargs, b->h_pargs.data(), b->h_pargs.size() * sizeof(PcgArgs), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  PcgBatch pb{b->d_pargs, b->spmv_prob, b->spmv_first, b->spmv_count, b->vec_prob, b->vec_first, b->vec_count,
+              b->n_spmv, b->n_vec};
+  std::vector<int> hf(4 * (size_t)b->nprob);
+  int done = 0;
+  for (;;) {
+    e = cudaMemcpyAsync(hf.data(), b->flags_all, hf.size() * sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    b->prof.collect();
+    bool active = false;
+    done = 0;
+    for (int p = 0; p < b->nprob; ++p) {
+      done = std::max(done, hf[4 * p]);
+      if (!hf[4 * p + 1] && !hf[4 * p + 2]) active = true;
+    }
+    if (!active || done >= maxit) break;
+    e = pcg_iterations_batch(pb, std::min(32, maxit - done), rtol, b->stream, &b->prof);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  std::vector<double> hs(8 * (size_t)b->nprob);
+  e = cudaMemcpyAsync(hs.data(), b->scal_all, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = HYB_OK;
+  for (int p = 0; p < b->nprob; ++p) {
+    if (iters) iters[p] = hf[4 * p];
+    if (rel_res) rel_res[p] = hs[8 * p + 1] > 0.0 ? std::sqrt(hs[8 * p + 2] / hs[8 * p + 1]) : 0.0;
+    if (hf[4 * p + 2]) st = HYB_ERR_BREAKDOWN;
+    else if (!hf[4 * p + 1] && st == HYB_OK) st = HYB_ERR_NOT_CONVERGED;
+  }
+  return st;
+}
+
+int hyb_recover_batch(hyb_batch* b, const double* const* lambdas, double* const* us) {
+  if (!b || !lambdas || !us) return HYB_ERR_INVALID_ARG;
+  if (b->mode != MODE_HYB) return HYB_ERR_INVALID_ARG;
+  for (int p = 0; p < b->nprob; ++p) {
+    if (!lambdas[p] || !us[p]) return HYB_ERR_INVALID_ARG;
+    b->h_rargs[p].lambda = lambdas[p];
+    b->h_rargs[p].u = us[p];
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_rargs, b->h_rargs.data(), b->h_rargs.size() * sizeof(RecoverArgs),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_lams, lambdas, b->nprob * sizeof(double*), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_us, us, b->nprob * sizeof(double*), cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = batch_reset(b);
+  if (st) return st;
+  for (int k = 0; k <= kMaxOrder; ++k) {
+    e = launch_recover_batch(k, MODE_HYB, b->d_rargs, b->ritems[k][0], b->n_ritems[k][0], b->stream, &b->prof);
+    if (e == cudaSuccess && b->n_ritems[k][1])
+      e = launch_mixed_batch(k, b->d_eargs, b->ritems[k][1], b->n_ritems[k][1], 0, true, b->d_lams, b->d_us,
+                             b->stream, &b->prof);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return batch_finish(b);
+}
+
+int hyb_batch_context(hyb_batch* b, int problem, hyb_ctx** ctx) {
+  if (!b || !ctx || problem < 0 || problem >= b->nprob) return HYB_ERR_INVALID_ARG;
+  *ctx = b->ctx[problem];
+  return HYB_OK;
+}
+
+int hyb_batch_set_profiling(hyb_batch* b, int enable) {
+  if (!b) return HYB_ERR_INVALID_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  b->prof.collect();
+  b->prof.reset();
+  b->prof.on = enable != 0;
+  return HYB_OK;
+}
+
+int hyb_batch_get_profile(const hyb_batch* b, int kernel_class, double* total_ms, int64_t* launches) {
+  if (!b || kernel_class < 0 || kernel_class >= HYB_K_COUNT) return HYB_ERR_INVALID_ARG;
+  if (total_ms) *total_ms = b->prof.ms[kernel_class];
+  if (launches) *launches = b->prof.launches[kernel_class];
+  return HYB_OK;
+}
+
+void hyb_destroy_batch(hyb_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (hyb_ctx* c : b->ctx) hyb_destroy(c);
+  for (void* p : b->allocs) cudaFree(p);
+  delete b;
 }
 
 }  // extern "C"

@@ -20,6 +20,7 @@
 // the back substitution.
 #include <cuda_runtime.h>
 
+#include "hyb_device.h"
 #include "hyb_internal.h"
 
 namespace hyb {
@@ -32,7 +33,12 @@ cudaError_t upload_ref_tables(const RefTables* tabs, int count, cudaStream_t s) 
 
 namespace {
 
-__device__ __forceinline__ int64_t tri(int i, int j) { return (int64_t)i * (i + 1) / 2 + j; }
+using dev::tri;
+using dev::local_index;
+using dev::gslot;
+using dev::tri_row;
+using dev::rsqrt_newton;
+using dev::set_error;
 
 template <int K>
 struct EK {
@@ -55,48 +61,6 @@ struct EK {
   static constexpr int SMEM_DOUBLES = (A_SMEM ? TRI : 0) + 3 * N + 48 + TAB + UNION + 4;
   static constexpr size_t SMEM_BYTES = sizeof(double) * SMEM_DOUBLES;
 };
-
-// Local dof index of the component-c function with 1-D node indices (i0, i1, i2).
-template <int K>
-__device__ __forceinline__ int local_index(int c, int i0, int i1, int i2) {
-  constexpr int P = K + 2, p = K + 1, NI = 3 * K * p * p, NFN = p * p;
-  const int ic = c == 0 ? i0 : c == 1 ? i1 : i2;
-  if (ic > 0 && ic < P - 1) {
-    const int r0 = c == 0 ? K : p, r1 = c == 1 ? K : p;
-    const int j0 = i0 - (c == 0), j1 = i1 - (c == 1), j2 = i2 - (c == 2);
-    return c * K * p * p + j0 + r0 * (j1 + r1 * j2);
-  }
-  const int side = ic == 0 ? 0 : 1;
-  const int t0 = c == 0 ? i1 : i0;
-  const int t1 = c == 2 ? i1 : i2;
-  return NI + (2 * c + side) * NFN + t0 + p * t1;
-}
-
-// slot of the symmetric pair (a, b) in the 6-vector (00, 11, 22, 10, 20, 21)
-__device__ __forceinline__ int gslot(int a, int b) {
-  if (a == b) return a;
-  const int hi = a > b ? a : b, lo = a > b ? b : a;
-  return hi == 1 ? 3 : (lo == 0 ? 4 : 5);
-}
-
-// Row index i of the packed lower-triangle position t (t = i(i+1)/2 + j, j <= i).
-__device__ __forceinline__ int tri_row(int t) {
-  int i = (int)((sqrtf((float)(8 * t + 1)) - 1.0f) * 0.5f);
-  while ((i + 1) * (i + 2) / 2 <= t) ++i;
-  while (i * (i + 1) / 2 > t) --i;
-  return i;
-}
-
-// 1 / sqrt(d) by Newton-Raphson on f(r) = r^-2 - d from a single-precision seed:
-// r <- r (3 - d r^2) / 2, two steps (23 -> 46 -> full FP64 bits). Falls back to the
-// library square root outside the single-precision range.
-__device__ __forceinline__ double rsqrt_newton(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-  double r = (double)rsqrtf((float)d);
-  r = r * fma(-0.5 * d, r * r, 1.5);
-  r = r * fma(-0.5 * d, r * r, 1.5);
-  return r;
-}
 
 struct Tabs {
   const double *Vc, *Dc, *Vo;                  // [P][Q], [P][Q], [p][Q]
@@ -296,26 +260,18 @@ __device__ void load_vector(const double* coef, const Tabs& tb, const double* Gu
   __syncthreads();
 }
 
-__device__ __forceinline__ void set_error(int* status, long long* err_elem, int code, long long e) {
-  if (atomicCAS(status, 0, code) == 0) *err_elem = e;
-}
-
 template <int K, int MODE>
-__global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
+__device__ __forceinline__ void element_body(const ElemArgs& args, const int64_t e, double* smem) {
   using S = EK<K>;
   constexpr int P = S::P, p = S::p, Q = S::Q, NQ = S::NQ, NFN = S::NFN, NI = S::NI, NB = S::NB, N = S::N;
   constexpr int NT = S::NT;
   const int tid = threadIdx.x;
-  extern __shared__ double smem[];
-
-  const int64_t li = blockIdx.x;
-  if (li >= args.n_list) return;
-  const int64_t e = args.elem_list[li];
+  const int64_t es = args.slot ? args.slot[e] : e;       // index into the FP64 factor store
   const int ex = (int)(e % args.nx), ey = (int)((e / args.nx) % args.ny), ez = (int)(e / ((int64_t)args.nx * args.ny));
 
   // ---- shared memory carve-up
   double* sp = smem;
-  double* A = S::A_SMEM ? sp : args.Lstore + e * (int64_t)S::TRI;
+  double* A = S::A_SMEM ? sp : args.Lstore + es * (int64_t)S::TRI;
   if (S::A_SMEM) sp += S::TRI;
   double* f = sp; sp += N;
   double* colbuf = sp; sp += N;
@@ -590,7 +546,7 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
     }
     __syncthreads();
     // ---- store the factor with Y in place of L_bb
-    double* Ls = args.Lstore + e * (int64_t)S::TRI;
+    double* Ls = args.Lstore + es * (int64_t)S::TRI;
     if (S::A_SMEM) {
       for (int t = tid; t < S::TRI; t += NT) Ls[t] = A[t];
       __syncthreads();
@@ -620,10 +576,31 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
       else args.rhs[gi] = f[NI + ib];
     }
     if (S::A_SMEM) {
-      double* Ls = args.Lstore + e * (int64_t)S::TRI;
+      double* Ls = args.Lstore + es * (int64_t)S::TRI;
       for (int t = tid; t < S::TRI; t += NT) Ls[t] = A[t];
     }
   }
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
+  extern __shared__ double smem[];
+  const int64_t li = blockIdx.x;
+  if (li >= args.n_list) return;
+  element_body<K, MODE>(args, args.elem_list[li], smem);
+}
+
+// Many problems in one launch: work item (problem, element) with per-problem arguments.
+template <int K, int MODE>
+__global__ void __launch_bounds__(EK<K>::NT) element_kernel_batch(const ElemArgs* probs, const int2* items,
+                                                                  int64_t n_items, int colour) {
+  extern __shared__ double smem[];
+  const int64_t li = blockIdx.x;
+  if (li >= n_items) return;
+  const int2 it = items[li];
+  ElemArgs a = probs[it.x];
+  a.colour = colour;
+  element_body<K, MODE>(a, it.y, smem);
 }
 
 // det J > 0 at the 8 corners and every Gauss point of every element.
@@ -690,6 +667,38 @@ cudaError_t launch_element_k(int mode, const ElemArgs& a, cudaStream_t s, Prof* 
 }
 
 }  // namespace
+
+template <int K>
+cudaError_t launch_element_batch_k(int mode, const ElemArgs* probs, const int2* items, int64_t n, int colour,
+                                   cudaStream_t s, Prof* prof) {
+  using S = EK<K>;
+  if (n == 0) return cudaSuccess;
+  const size_t smem = S::SMEM_BYTES;
+  cudaError_t err;
+  const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+  if (mode == MODE_HYB) {
+    err = cudaFuncSetAttribute(element_kernel_batch<K, MODE_HYB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    element_kernel_batch<K, MODE_HYB><<<(unsigned)n, S::NT, smem, s>>>(probs, items, n, colour);
+  } else {
+    err = cudaFuncSetAttribute(element_kernel_batch<K, MODE_SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    element_kernel_batch<K, MODE_SC><<<(unsigned)n, S::NT, smem, s>>>(probs, items, n, colour);
+  }
+  prof_end(prof, tok, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_element_batch(int k, int mode, const ElemArgs* probs, const int2* items, int64_t n, int colour,
+                                 cudaStream_t s, Prof* prof) {
+  switch (k) {
+    case 0: return launch_element_batch_k<0>(mode, probs, items, n, colour, s, prof);
+    case 1: return launch_element_batch_k<1>(mode, probs, items, n, colour, s, prof);
+    case 2: return launch_element_batch_k<2>(mode, probs, items, n, colour, s, prof);
+    case 3: return launch_element_batch_k<3>(mode, probs, items, n, colour, s, prof);
+  }
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_element(int k, int mode, const ElemArgs& a, cudaStream_t s, Prof* prof) {
   switch (k) {

@@ -21,6 +21,7 @@ struct RefTables {
   double Dc[kMaxClosed][kMaxQ];             // their derivatives
   double Vo[kMaxOpen][kMaxQ];               // open Lagrange values
   double wf[kMaxOpen * kMaxOpen];           // face Gauss-Legendre weights (lower axis fastest)
+  double DcO[kMaxClosed][kMaxOpen];         // closed Lagrange derivatives at the open nodes (div into Q_k)
 };
 
 // Element sizes for order k.
@@ -53,8 +54,10 @@ struct ElemArgs {
   const int64_t* row_ptr;
   double* val;                // CSR values of H or S
   double* rhs;                // right-hand side
-  double* Lstore;             // E x n(n+1)/2 packed lower factor
-  double* zstore;             // E x n forward-substituted load
+  double* Lstore;             // packed lower factor, n(n+1)/2 per FP64 element
+  double* zstore;             // E x n forward-substituted load (FP64 path) / modified load (FP32 path)
+  const int32_t* slot;        // per element: index into its precision's factor store, or null (= e)
+  float* Lstore32;            // FP32 path: per element L_M | Xd | L_Z
   int* status;
   long long* err_elem;
 };
@@ -73,6 +76,11 @@ void build_ref_tables(int k, RefTables* t);
 
 // Kernel launchers (hyb_element.cu, hyb_solve.cu, hyb_recover.cu). Return a cudaError_t.
 cudaError_t upload_ref_tables(const RefTables* tabs, int count, cudaStream_t s);
+cudaError_t upload_ref_tables_mixed(const RefTables* tabs, int count, cudaStream_t s);
+int64_t mixed_store_floats(int k);
+cudaError_t launch_element_mixed(int k, const ElemArgs& a, cudaStream_t s, Prof* prof);
+cudaError_t launch_recover_mixed(int k, const ElemArgs& a, const double* lambda, double* u, cudaStream_t s,
+                                 Prof* prof);
 cudaError_t launch_check_geometry(int k, const ElemArgs& a, cudaStream_t s, Prof* prof);
 cudaError_t launch_element(int k, int mode, const ElemArgs& a, cudaStream_t s, Prof* prof);
 cudaError_t launch_expand_cols(const int64_t* row_ptr, const int32_t* adj, const int32_t* adj_count,
@@ -95,12 +103,22 @@ struct PcgArgs {
   int nblocks;               // grid size of every PCG kernel (partial holds 2*nblocks)
   int nfn;                   // rows per face ((k+1)^2): rows of a face share their column list
 };
+// Many independent PCG solves per launch: each problem owns a contiguous range of blocks.
+struct PcgBatch {
+  const PcgArgs* probs;                     // device, one per problem
+  const int32_t *spmv_prob, *spmv_first, *spmv_count;   // device, per SpMV block / per problem
+  const int32_t *vec_prob, *vec_first, *vec_count;      // device, per vector block / per problem
+  int n_spmv, n_vec;                        // grid sizes
+};
+cudaError_t pcg_iterations_batch(const PcgBatch& b, int count, double rtol, cudaStream_t s, Prof* prof);
 cudaError_t pcg_init(const PcgArgs& a, cudaStream_t s, Prof* prof);
 cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_t s, Prof* prof);
 
 struct RecoverArgs {
   int k;
-  int64_t n_elem;
+  int64_t n_elem;             // number of elements to recover (length of elem_list, or all)
+  const int32_t* elem_list;   // elements to recover, or null for 0..n_elem-1
+  const int32_t* slot;        // factor-store index per element, or null (= e)
   int mode;
   const int32_t* elem_face;
   const double* lambda;       // multipliers (HB) or global face dofs (SC)
@@ -110,5 +128,14 @@ struct RecoverArgs {
   double wf[kMaxOpen * kMaxOpen];   // face Gauss weights of order k (C_T = [0 D])
 };
 cudaError_t launch_recover(const RecoverArgs& a, cudaStream_t s, Prof* prof);
+
+// Batched forms: one launch over (problem, element) work items of one order, with the
+// per-problem arguments in device arrays.
+cudaError_t launch_element_batch(int k, int mode, const ElemArgs* probs, const int2* items, int64_t n, int colour,
+                                 cudaStream_t s, Prof* prof);
+cudaError_t launch_mixed_batch(int k, const ElemArgs* probs, const int2* items, int64_t n, int colour, bool recover,
+                               const double* const* lams, double* const* us, cudaStream_t s, Prof* prof);
+cudaError_t launch_recover_batch(int k, int mode, const RecoverArgs* probs, const int2* items, int64_t n,
+                                 cudaStream_t s, Prof* prof);
 
 }  // namespace hyb

@@ -17,7 +17,7 @@ namespace {
 __device__ __forceinline__ int64_t tri(int i, int j) { return (int64_t)i * (i + 1) / 2 + j; }
 
 template <int K, int MODE>
-__global__ void recover_kernel(RecoverArgs a) {
+__device__ __forceinline__ void recover_body(const RecoverArgs& a, const int64_t e) {
   constexpr int p = K + 1, NFN = p * p, NI = 3 * K * p * p, NB = 6 * NFN, N = NI + NB;
   constexpr int NT = K <= 1 ? 64 : K == 2 ? 128 : 256;
   constexpr int64_t TRI = (int64_t)N * (N + 1) / 2;
@@ -25,9 +25,8 @@ __global__ void recover_kernel(RecoverArgs a) {
   __shared__ double w[NB];
   __shared__ double rhs[NI > 0 ? NI : 1];
   const int tid = threadIdx.x;
-  const int64_t e = blockIdx.x;
-  if (e >= a.n_elem) return;
-  const double* L = a.Lstore + e * TRI;
+  const int64_t es = a.slot ? (int64_t)a.slot[e] : e;
+  const double* L = a.Lstore + es * TRI;
   const double* z = a.zstore + e * (int64_t)N;
   const int32_t* ef = a.elem_face + 6 * e;
 
@@ -86,6 +85,20 @@ __global__ void recover_kernel(RecoverArgs a) {
   for (int i = tid; i < N; i += NT) u[i] = x[i];
 }
 
+template <int K, int MODE>
+__global__ void recover_kernel(RecoverArgs a) {
+  if ((int64_t)blockIdx.x >= a.n_elem) return;
+  recover_body<K, MODE>(a, a.elem_list ? (int64_t)a.elem_list[blockIdx.x] : (int64_t)blockIdx.x);
+}
+
+template <int K, int MODE>
+__global__ void recover_kernel_batch(const RecoverArgs* probs, const int2* items, int64_t n_items) {
+  if ((int64_t)blockIdx.x >= n_items) return;
+  const int2 it = items[blockIdx.x];
+  const RecoverArgs a = probs[it.x];
+  recover_body<K, MODE>(a, it.y);
+}
+
 template <int K>
 cudaError_t launch_k(const RecoverArgs& a, cudaStream_t s, Prof* prof) {
   constexpr int NT = K <= 1 ? 64 : K == 2 ? 128 : 256;
@@ -98,6 +111,29 @@ cudaError_t launch_k(const RecoverArgs& a, cudaStream_t s, Prof* prof) {
 }
 
 }  // namespace
+
+template <int K>
+cudaError_t launch_batch_k(int mode, const RecoverArgs* probs, const int2* items, int64_t n, cudaStream_t s,
+                           Prof* prof) {
+  constexpr int NT = K <= 1 ? 64 : K == 2 ? 128 : 256;
+  if (n == 0) return cudaSuccess;
+  const int tok = prof_begin(prof, HYB_K_RECOVER, s);
+  if (mode == MODE_HYB) recover_kernel_batch<K, MODE_HYB><<<(unsigned)n, NT, 0, s>>>(probs, items, n);
+  else recover_kernel_batch<K, MODE_SC><<<(unsigned)n, NT, 0, s>>>(probs, items, n);
+  prof_end(prof, tok, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover_batch(int k, int mode, const RecoverArgs* probs, const int2* items, int64_t n,
+                                 cudaStream_t s, Prof* prof) {
+  switch (k) {
+    case 0: return launch_batch_k<0>(mode, probs, items, n, s, prof);
+    case 1: return launch_batch_k<1>(mode, probs, items, n, s, prof);
+    case 2: return launch_batch_k<2>(mode, probs, items, n, s, prof);
+    case 3: return launch_batch_k<3>(mode, probs, items, n, s, prof);
+  }
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_recover(const RecoverArgs& a, cudaStream_t s, Prof* prof) {
   switch (a.k) {

@@ -118,12 +118,11 @@ __global__ void pcg_init_kernel(PcgArgs a) {
 // loads a column index and the gathered p_j once and uses them for all NFN rows,
 // so the index stream costs 4 / NFN bytes per nonzero instead of 4.
 template <int NFN, int W>
-__global__ void __launch_bounds__(kThreads) spmv_face_kernel(PcgArgs a) {
+__device__ __forceinline__ void spmv_face_body(const PcgArgs& a, int vb, int nvb, double* sh) {
   if (a.flags[F_CONV] | a.flags[F_BRK]) return;
-  __shared__ double sh[32];
   constexpr int FPW = 32 / W;                              // faces per warp per step
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp = (vb * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)nvb * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int sub = lane / W, gl = lane % W;
   const int64_t nfaces = a.n / NFN;
@@ -161,9 +160,9 @@ __global__ void __launch_bounds__(kThreads) spmv_face_kernel(PcgArgs a) {
     }
   }
   pq = block_sum(pq, sh);
-  if (threadIdx.x == 0) a.partial[blockIdx.x] = pq;
-  if (last_block(&a.flags[F_TICKET], gridDim.x)) {
-    const double s = sum_partials(a.partial, gridDim.x, 1, 0, sh);
+  if (threadIdx.x == 0) a.partial[vb] = pq;
+  if (last_block(&a.flags[F_TICKET], nvb)) {
+    const double s = sum_partials(a.partial, nvb, 1, 0, sh);
     if (threadIdx.x == 0) {
       a.scal[S_PQ] = s;
       if (!(s > 0.0) || !(s < INFINITY)) a.flags[F_BRK] = 1;
@@ -173,30 +172,51 @@ __global__ void __launch_bounds__(kThreads) spmv_face_kernel(PcgArgs a) {
   }
 }
 
-// x += alpha p, r -= alpha q, z = D^{-1} r (into q); rz, rr; last block: beta, convergence
-__global__ void __launch_bounds__(kThreads) pcg_update_kernel(PcgArgs a, double rtol2) {
-  if (a.flags[F_CONV] | a.flags[F_BRK]) return;
+template <int NFN, int W>
+__global__ void __launch_bounds__(kThreads) spmv_face_kernel(PcgArgs a) {
   __shared__ double sh[32];
+  spmv_face_body<NFN, W>(a, blockIdx.x, gridDim.x, sh);
+}
+
+// x += alpha p, r -= alpha q, z = D^{-1} r (into q); rz, rr; last block: beta, convergence.
+// Four elements per thread per step with all loads issued first: the kernel is bound by
+// memory latency, so independent loads in flight matter more than occupancy.
+constexpr int kUnroll = 4;
+__device__ __forceinline__ void pcg_update_body(const PcgArgs& a, double rtol2, int vb, int nvb, double* sh) {
+  if (a.flags[F_CONV] | a.flags[F_BRK]) return;
   const double alpha = a.scal[S_ALPHA];
   double rz = 0.0, rr = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    a.x[i] = fma(alpha, a.p[i], a.x[i]);
-    const double r = fma(-alpha, a.q[i], a.r[i]);
-    a.r[i] = r;
-    const double z = a.dinv[i] * r;
-    a.q[i] = z;
-    rz = fma(r, z, rz);
-    rr = fma(r, r, rr);
+  const int64_t stride = (int64_t)nvb * blockDim.x;
+  for (int64_t base = vb * (int64_t)blockDim.x + threadIdx.x; base < a.n; base += kUnroll * stride) {
+    double xv[kUnroll], pv[kUnroll], rv[kUnroll], qv[kUnroll], dv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + u * stride;
+      if (i < a.n) { xv[u] = a.x[i]; pv[u] = a.p[i]; rv[u] = a.r[i]; qv[u] = a.q[i]; dv[u] = a.dinv[i]; }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + u * stride;
+      if (i < a.n) {
+        a.x[i] = fma(alpha, pv[u], xv[u]);
+        const double r = fma(-alpha, qv[u], rv[u]);
+        a.r[i] = r;
+        const double z = dv[u] * r;
+        a.q[i] = z;
+        rz = fma(r, z, rz);
+        rr = fma(r, r, rr);
+      }
+    }
   }
   rz = block_sum(rz, sh);
   rr = block_sum(rr, sh);
   if (threadIdx.x == 0) {
-    a.partial[2 * blockIdx.x] = rz;
-    a.partial[2 * blockIdx.x + 1] = rr;
+    a.partial[2 * vb] = rz;
+    a.partial[2 * vb + 1] = rr;
   }
-  if (last_block(&a.flags[F_TICKET], gridDim.x)) {
-    const double s0 = sum_partials(a.partial, gridDim.x, 2, 0, sh);
-    const double s1 = sum_partials(a.partial, gridDim.x, 2, 1, sh);
+  if (last_block(&a.flags[F_TICKET], nvb)) {
+    const double s0 = sum_partials(a.partial, nvb, 2, 0, sh);
+    const double s1 = sum_partials(a.partial, nvb, 2, 1, sh);
     if (threadIdx.x == 0) {
       a.scal[S_BETA] = s0 / a.scal[S_RZ];
       a.scal[S_RZ] = s0;
@@ -209,12 +229,63 @@ __global__ void __launch_bounds__(kThreads) pcg_update_kernel(PcgArgs a, double 
   }
 }
 
+__global__ void __launch_bounds__(kThreads) pcg_update_kernel(PcgArgs a, double rtol2) {
+  __shared__ double sh[32];
+  pcg_update_body(a, rtol2, blockIdx.x, gridDim.x, sh);
+}
+
 // p = z + beta p
-__global__ void __launch_bounds__(kThreads) pcg_direction_kernel(PcgArgs a) {
+__device__ __forceinline__ void pcg_direction_body(const PcgArgs& a, int vb, int nvb) {
   if (a.flags[F_CONV] | a.flags[F_BRK]) return;
   const double beta = a.scal[S_BETA];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
-    a.p[i] = fma(beta, a.p[i], a.q[i]);
+  const int64_t stride = (int64_t)nvb * blockDim.x;
+  for (int64_t base = vb * (int64_t)blockDim.x + threadIdx.x; base < a.n; base += kUnroll * stride) {
+    double pv[kUnroll], zv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + u * stride;
+      if (i < a.n) { pv[u] = a.p[i]; zv[u] = a.q[i]; }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + u * stride;
+      if (i < a.n) a.p[i] = fma(beta, pv[u], zv[u]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) pcg_direction_kernel(PcgArgs a) {
+  pcg_direction_body(a, blockIdx.x, gridDim.x);
+}
+
+// ---- batched forms: block b works for problem blk_prob[b] as its block b - blk_first[that problem]
+// of blk_count[that problem]; every problem keeps its own scalars, tickets and flags.
+__global__ void __launch_bounds__(kThreads) spmv_batch_kernel(const PcgArgs* probs, const int32_t* blk_prob,
+                                                              const int32_t* blk_first, const int32_t* blk_count) {
+  __shared__ double sh[32];
+  const int pb = blk_prob[blockIdx.x];
+  const PcgArgs a = probs[pb];
+  const int vb = blockIdx.x - blk_first[pb], nvb = blk_count[pb];
+  switch (a.nfn) {
+    case 1: spmv_face_body<1, 4>(a, vb, nvb, sh); break;
+    case 4: spmv_face_body<4, 2>(a, vb, nvb, sh); break;
+    case 9: spmv_face_body<9, 2>(a, vb, nvb, sh); break;
+    default: spmv_face_body<16, 2>(a, vb, nvb, sh); break;
+  }
+}
+__global__ void __launch_bounds__(kThreads) update_batch_kernel(const PcgArgs* probs, const int32_t* blk_prob,
+                                                                const int32_t* blk_first, const int32_t* blk_count,
+                                                                double rtol2) {
+  __shared__ double sh[32];
+  const int pb = blk_prob[blockIdx.x];
+  const PcgArgs a = probs[pb];
+  pcg_update_body(a, rtol2, blockIdx.x - blk_first[pb], blk_count[pb], sh);
+}
+__global__ void __launch_bounds__(kThreads) direction_batch_kernel(const PcgArgs* probs, const int32_t* blk_prob,
+                                                                   const int32_t* blk_first, const int32_t* blk_count) {
+  const int pb = blk_prob[blockIdx.x];
+  const PcgArgs a = probs[pb];
+  pcg_direction_body(a, blockIdx.x - blk_first[pb], blk_count[pb]);
 }
 
 __global__ void expand_cols_kernel(const int64_t* row_ptr, const int32_t* adj, const int32_t* adj_count,
@@ -260,7 +331,7 @@ cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_
     // FP64 is the scarce unit on this part (about 1.2 TFLOP/s): 2 lanes per face keep the
     // cross-lane FP64 reduction to one step per row while the 16 consecutive bytes a face
     // gets per load instruction complete their 32-byte sector on the next iteration.
-    const int nbs = a.nblocks / 2, nbv = a.nblocks / 4;
+    const int nbs = a.nblocks * 5 / 8, nbv = a.nblocks / 4;
     switch (a.nfn) {
       case 1: spmv_face_kernel<1, 4><<<nbs, kThreads, 0, s>>>(a); break;
       case 4: spmv_face_kernel<4, 2><<<nbs, kThreads, 0, s>>>(a); break;
@@ -274,6 +345,21 @@ cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_
     prof_end(prof, tok, s);
     tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
     pcg_direction_kernel<<<nbv, kThreads, 0, s>>>(a);
+    prof_end(prof, tok, s);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t pcg_iterations_batch(const PcgBatch& b, int count, double rtol, cudaStream_t s, Prof* prof) {
+  for (int it = 0; it < count; ++it) {
+    int tok = prof_begin(prof, HYB_K_SPMV, s);
+    spmv_batch_kernel<<<b.n_spmv, kThreads, 0, s>>>(b.probs, b.spmv_prob, b.spmv_first, b.spmv_count);
+    prof_end(prof, tok, s);
+    tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
+    update_batch_kernel<<<b.n_vec, kThreads, 0, s>>>(b.probs, b.vec_prob, b.vec_first, b.vec_count, rtol * rtol);
+    prof_end(prof, tok, s);
+    tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
+    direction_batch_kernel<<<b.n_vec, kThreads, 0, s>>>(b.probs, b.vec_prob, b.vec_first, b.vec_count);
     prof_end(prof, tok, s);
   }
   return cudaGetLastError();

@@ -100,6 +100,13 @@ void build_ref_tables(int k, RefTables* t) {
     }
   for (int s1 = 0; s1 < p; ++s1)
     for (int s0 = 0; s0 < p; ++s0) t->wf[s0 + p * s1] = ow[s0] * ow[s1];
+  // div_hat of an RT_k basis function lies in Q_k; its value at the open node a along the
+  // component's own axis is the closed-Lagrange derivative there (Kronecker across).
+  for (int a = 0; a < P; ++a)
+    for (int b = 0; b < p; ++b) {
+      double v;
+      lagrange_at(closed, P, a, open[b], &v, &t->DcO[a][b]);
+    }
 }
 
 }  // namespace hyb

@@ -32,6 +32,9 @@ KERNEL_CLASSES = {"element": 0, "spmv": 1, "pcg_vector": 2, "recover": 3, "setup
 EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recover",
            "staticcond_assemble", "staticcond_recover", "hyb_get_reduced", "hyb_export_reduced", "hyb_get_sizes",
            "hyb_set_profiling", "hyb_get_profile", "hyb_pcg_solve_noalloc", "hyb_measure_fma_peak",
+           "hyb_get_precision_split", "hyb_setup_batch", "hyb_assemble_reduced_batch", "hyb_solve_reduced_batch",
+           "hyb_recover_batch", "hyb_batch_context", "hyb_batch_set_profiling", "hyb_batch_get_profile",
+           "hyb_destroy_batch",
            "hyb_last_error_element", "hyb_destroy", "hyb_status_string"]
 
 
@@ -63,6 +66,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_pcg_solve_noalloc.argtypes = [P, P, P, P, P, I64, I, D, I, P, ctypes.POINTER(I),
                                           ctypes.POINTER(D)]
     lib.hyb_measure_fma_peak.argtypes = [I, P, ctypes.POINTER(D)]
+    lib.hyb_get_precision_split.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(D)]
+    PP = ctypes.POINTER(P)
+    lib.hyb_setup_batch.argtypes = [I, ctypes.POINTER(_Mesh), ctypes.POINTER(I), PP, PP, I, D, P, ctypes.POINTER(P)]
+    lib.hyb_assemble_reduced_batch.argtypes = [P, PP, PP]
+    lib.hyb_solve_reduced_batch.argtypes = [P, D, I, PP, ctypes.POINTER(I), ctypes.POINTER(D)]
+    lib.hyb_recover_batch.argtypes = [P, PP, PP]
+    lib.hyb_batch_context.argtypes = [P, I, ctypes.POINTER(P)]
+    lib.hyb_batch_set_profiling.argtypes = [P, I]
+    lib.hyb_batch_get_profile.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
+    lib.hyb_destroy_batch.argtypes = [P]
+    lib.hyb_destroy_batch.restype = None
     lib.hyb_set_profiling.argtypes = [P, I]
     lib.hyb_get_profile.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
     lib.hyb_get_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I64),
@@ -73,7 +87,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_status_string.argtypes = [I]
     lib.hyb_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("hyb_destroy", "hyb_status_string"):
+        if name not in ("hyb_destroy", "hyb_status_string", "hyb_destroy_batch"):
             getattr(lib, name).restype = I
     return lib
 
@@ -126,6 +140,13 @@ class Context:
         _check(lib().hyb_get_sizes(self.handle, ctypes.byref(E), ctypes.byref(n), ctypes.byref(L),
                                    ctypes.byref(nnz)), "hyb_get_sizes")
         return dict(n_elem=E.value, n_loc=n.value, n_lambda=L.value, nnz=nnz.value)
+
+    def precision_split(self):
+        """(elements on the FP64 path, elements on the FP32 path, contrast threshold)."""
+        a, b, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().hyb_get_precision_split(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t)),
+               "hyb_get_precision_split")
+        return a.value, b.value, t.value
 
     def close(self):
         if self.handle:
@@ -248,3 +269,91 @@ def hyb_last_error_element(ctx):
     e = ctypes.c_int64()
     _check(lib().hyb_last_error_element(ctx.handle, ctypes.byref(e)), "hyb_last_error_element")
     return e.value
+
+
+# ---------------------------------------------------------------- batches
+def _ptr_array(tensors, name, allow_none=False):
+    if tensors is None:
+        if allow_none:
+            return None
+        raise TypeError(f"{name} required")
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        p = _ptr(t, f"{name}[{i}]")
+        arr[i] = p.value if p is not None else None
+    return arr
+
+
+class Batch:
+    """Owns a hyb_batch* (many problems); keeps the tensors it points to alive."""
+
+    def __init__(self, handle, n, keep):
+        self.handle = handle
+        self.n = n
+        self._keep = keep
+
+    def context(self, i):
+        """Borrowed single-problem context of problem i (owned by the batch)."""
+        h = ctypes.c_void_p()
+        _check(lib().hyb_batch_context(self.handle, int(i), ctypes.byref(h)), "hyb_batch_context")
+        c = Context(h, None)
+        c.close = lambda: None           # owned by the batch
+        return c
+
+    def close(self):
+        if self.handle:
+            lib().hyb_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hyb_setup_batch(meshes, orders, alphas, betas, precision=HYB_FP64, contrast_threshold=0.0, stream=None):
+    """meshes: list of (vertices tensor, nx, ny, nz); orders: ints; alphas, betas: lists of tensors."""
+    n = len(meshes)
+    ms = (_Mesh * n)(*[_Mesh(int(nx), int(ny), int(nz), _ptr(v, "vertices")) for v, nx, ny, nz in meshes])
+    ords = (ctypes.c_int * n)(*[int(k) for k in orders])
+    h = ctypes.c_void_p()
+    st = lib().hyb_setup_batch(n, ms, ords, _ptr_array(alphas, "alphas"), _ptr_array(betas, "betas"),
+                               int(precision), float(contrast_threshold), _stream(stream), ctypes.byref(h))
+    _check(st, "hyb_setup_batch")
+    return Batch(h, n, (meshes, alphas, betas))
+
+
+def hyb_assemble_reduced_batch(batch, loads, ess=None, check=True):
+    st = lib().hyb_assemble_reduced_batch(batch.handle, _ptr_array(loads, "loads"), _ptr_array(ess, "ess", True))
+    return _check(st, "hyb_assemble_reduced_batch") if check else st
+
+
+def hyb_solve_reduced_batch(batch, rtol, maxit, lambdas, check=True):
+    """Returns (iterations per problem, relative residual per problem, status)."""
+    its = (ctypes.c_int * batch.n)()
+    rr = (ctypes.c_double * batch.n)()
+    st = lib().hyb_solve_reduced_batch(batch.handle, float(rtol), int(maxit), _ptr_array(lambdas, "lambdas"), its, rr)
+    if check:
+        _check(st, "hyb_solve_reduced_batch")
+    return list(its), list(rr), st
+
+
+def hyb_recover_batch(batch, lambdas, us, check=True):
+    st = lib().hyb_recover_batch(batch.handle, _ptr_array(lambdas, "lambdas"), _ptr_array(us, "us"))
+    return _check(st, "hyb_recover_batch") if check else st
+
+
+def hyb_batch_set_profiling(batch, enable):
+    return _check(lib().hyb_batch_set_profiling(batch.handle, int(bool(enable))), "hyb_batch_set_profiling")
+
+
+def hyb_batch_get_profile(batch):
+    out = {}
+    for name, cls in KERNEL_CLASSES.items():
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(lib().hyb_batch_get_profile(batch.handle, cls, ctypes.byref(ms), ctypes.byref(n)),
+               "hyb_batch_get_profile")
+        out[name] = (ms.value, n.value)
+    return out

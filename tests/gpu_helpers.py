@@ -11,11 +11,12 @@ def dev(a, dtype=None):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
 
 
-def gpu_run(p, mode="hyb", rtol=1e-14, maxit=100000, solve=True):
+def gpu_run(p, mode="hyb", rtol=1e-14, maxit=100000, solve=True, precision=0, threshold=0.0):
     """setup -> assemble -> export reduced system -> PCG -> recover, all through libhyb."""
     import torch
     from paper_1801_08914_gb300 import hyb
-    ctx = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta))
+    ctx = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta),
+                        precision=precision, contrast_threshold=threshold)
     load = dev(p.load)
     ess = None if p.ess is None else dev(p.ess)
     if mode == "hyb":
@@ -24,7 +25,7 @@ def gpu_run(p, mode="hyb", rtol=1e-14, maxit=100000, solve=True):
         hyb.staticcond_assemble(ctx, load, ess)
     red = {k: v.cpu().numpy() for k, v in hyb.hyb_export_reduced(ctx).items()}
     sz = ctx.sizes()
-    out = dict(red=red, sizes=sz)
+    out = dict(red=red, sizes=sz, split=ctx.precision_split())
     if solve:
         lam = torch.zeros(sz["n_lambda"], dtype=torch.float64, device="cuda")
         it, rr, st = hyb.hyb_solve_reduced(ctx, rtol, maxit, lam, check=False)

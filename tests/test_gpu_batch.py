@@ -1,0 +1,55 @@
+"""Batched problems (uneven sizes and orders in one context) against solo contexts and the oracle.
+
+The element phase of a batch runs the same element code as a solo context, so its reduced
+systems must be bitwise identical; the batched PCG partitions its blocks per problem, so its
+iterates differ from a solo solve only by the order of the reductions (compared at the
+conditioning-derived bound of the parity tests)."""
+import numpy as np
+import pytest
+
+from gpu_helpers import EPS, dev, element_kappa, gpu_run, rel
+from oracle.hybrid import Discretization, solve_dense
+from paper_1801_08914_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(specs):
+    return [inputs.random_problem(n, k, 0.2, 700 + i, 1e-2, 1e4, name=f"b{i}") for i, (n, k) in enumerate(specs)]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_solo_and_oracle(precision):
+    import torch
+    from paper_1801_08914_gb300 import hyb
+    specs = [(3, 0), (4, 1), (2, 2), (3, 3), (5, 0), (2, 1)]
+    probs = make_batch(specs)
+    verts = [dev(p.vertices) for p in probs]
+    alphas = [dev(p.alpha) for p in probs]
+    betas = [dev(p.beta) for p in probs]
+    b = hyb.hyb_setup_batch([(v, p.nx, p.ny, p.nz) for v, p in zip(verts, probs)], [p.order for p in probs],
+                            alphas, betas, precision=precision, contrast_threshold=1e4)
+    loads = [dev(p.load) for p in probs]
+    hyb.hyb_assemble_reduced_batch(b, loads)
+    sizes = [b.context(i).sizes() for i in range(len(probs))]
+    lams = [torch.zeros(s["n_lambda"], dtype=torch.float64, device="cuda") for s in sizes]
+    us = [torch.zeros(s["n_elem"], s["n_loc"], dtype=torch.float64, device="cuda") for s in sizes]
+    its, rrs, st = hyb.hyb_solve_reduced_batch(b, 1e-14, 20000, lams)
+    hyb.hyb_recover_batch(b, lams, us)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        red = {k: v.cpu().numpy() for k, v in hyb.hyb_export_reduced(b.context(i)).items()}
+        solo = gpu_run(p, rtol=1e-14, maxit=20000, precision=precision, threshold=1e4)
+        assert np.array_equal(red["val"], solo["red"]["val"]) and np.array_equal(red["rhs"], solo["red"]["rhs"])
+        D = Discretization.from_problem(p)
+        H, g = D.hybridize()
+        ev = np.linalg.eigvalsh(H.toarray())
+        kH = ev[-1] / ev[0]
+        el = rel(lams[i].cpu().numpy(), solo["lam"])
+        eu = rel(us[i].cpu().numpy(), solo["u"])
+        print(f"batch problem {i} (n={p.nx}, k={p.order}, prec={precision}): {its[i]} it, batch vs solo lam {el:.1e} u {eu:.1e}")
+        assert el <= max(1e-12, kH * 100 * EPS) and eu <= max(1e-12, kH * 100 * EPS)
+        if precision == 0:
+            lam_o = solve_dense(H, g)
+            assert rel(lams[i].cpu().numpy(), lam_o) <= max(1e-12, max(kH, element_kappa(D)) * EPS)
+    b.close()

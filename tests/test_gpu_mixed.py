@@ -1,0 +1,84 @@
+"""Mixed precision (HYB_MIXED) against the FP64 oracle and the FP64 GPU path.
+
+Elements with contrast beta/alpha up to the threshold are eliminated in FP32 through the
+hybridized mixed form (Sec. 3.2, H = H~): every factored matrix there (the alpha mass M,
+Z = G^{-1} + D^T M^{-1} D) is well conditioned, so S_T carries an error of order
+kappa(M, Z) u_32 ~ 1e-6 whatever the contrast below the threshold; elements above it stay
+FP64. The load term g_T and the recovery are refined in the mixed variables against FP64
+residuals, so g_T carries FP64-level error (bounded like the FP64 path, kappa eps_64). The
+bounds asserted: S (CSR values) <= 100 u_32 kappa_w with kappa_w the largest kappa(M) or
+kappa(Z) over the elements; lambda and u <= kappa(H) times the S bound. The measured numbers
+are printed.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import EPS, csr, element_kappa, gpu_run, rel
+from oracle.hybrid import Discretization, solve_dense
+from paper_1801_08914_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+U32 = np.finfo(np.float32).eps / 2
+
+
+def kappa_w(D):
+    """Largest condition number of M and Z = W^{-1} (W + B M^{-1} B^T) W^{-1} over the elements."""
+    out = 1.0
+    for e in range(D.mesh.n_elem):
+        M, B, W, _ = D.mixed_form_blocks(e)
+        Wi = np.linalg.inv(W)
+        Z = Wi @ (W + B @ np.linalg.solve(M, B.T)) @ Wi
+        out = max(out, np.linalg.cond(M), np.linalg.cond(Z))
+    return out
+
+
+def test_threshold_below_every_contrast_is_the_fp64_path():
+    p = inputs.random_problem(4, 1, 0.2, 401, 1e-2, 1e4, name="mixed64")
+    a = gpu_run(p, rtol=1e-13, maxit=20000)
+    b = gpu_run(p, rtol=1e-13, maxit=20000, precision=1, threshold=1e-300)
+    assert b["split"][1] == 0
+    for key in ("val", "rhs"):
+        assert np.array_equal(a["red"][key], b["red"][key])
+    assert np.array_equal(a["lam"], b["lam"]) and np.array_equal(a["u"], b["u"])
+
+
+@pytest.mark.parametrize("k,n", [(0, 5), (1, 4), (2, 3), (3, 3)])
+def test_mixed_fp32_path_against_oracle(k, n):
+    """All elements on the FP32 path (contrast <= 1e4 = threshold)."""
+    p = inputs.random_problem(n, k, 0.2, 410 + k, 1e-2, 1e4, name="mixed32")
+    D = Discretization.from_problem(p)
+    H, g = D.hybridize()
+    lam = solve_dense(H, g)
+    u = D.recover(lam)
+    r = gpu_run(p, rtol=1e-14, maxit=20000, precision=1, threshold=1e4)
+    assert r["split"] == (0, p.n_elem, 1e4)
+    kw = kappa_w(D)
+    ev = np.linalg.eigvalsh(H.toarray())
+    kH = ev[-1] / ev[0]
+    tol_S = 100 * U32 * kw
+    eS, eg = rel(r["red"]["val"], H.data), rel(r["red"]["rhs"], g)
+    el, eu = rel(r["lam"], lam), rel(r["u"], u)
+    print(f"mixed k={k}: kappa_w={kw:.1e} kappa_H={kH:.1e} S {eS:.1e} g {eg:.1e} lam {el:.1e} u {eu:.1e} "
+          f"(tol S {tol_S:.1e}, lam/u {kH * tol_S:.1e})")
+    assert eS <= tol_S
+    assert eg <= max(1e-12, max(kH, element_kappa(D)) * EPS)   # refined against the FP64 residual
+    assert el <= kH * tol_S and eu <= kH * tol_S
+    Hg = csr(r["red"])
+    assert abs(Hg - Hg.T).max() == 0.0
+
+
+def test_mixed_split_paths():
+    """Contrast up to 1e6 with threshold 1e4: both paths in one assembly and one recovery."""
+    p = inputs.random_problem(4, 1, 0.2, 420, 1e-2, 1e6, name="mixedsplit")
+    D = Discretization.from_problem(p)
+    H, g = D.hybridize()
+    lam = solve_dense(H, g)
+    u = D.recover(lam)
+    r = gpu_run(p, rtol=1e-14, maxit=50000, precision=1, threshold=1e4)
+    n64, n32, _ = r["split"]
+    assert n64 > 0 and n32 > 0 and n64 + n32 == p.n_elem
+    eS, el, eu = rel(r["red"]["val"], H.data), rel(r["lam"], lam), rel(r["u"], u)
+    print(f"mixed split: {n64} FP64 + {n32} FP32 elements: S {eS:.1e} lam {el:.1e} u {eu:.1e}")
+    kw = kappa_w(D)
+    ev = np.linalg.eigvalsh(H.toarray())
+    assert eS <= 100 * U32 * kw and eu <= (ev[-1] / ev[0]) * 100 * U32 * kw
