@@ -303,6 +303,95 @@ __device__ bool chol32(float* A, int n, int ld, float* colbuf, float* invd, floa
   return true;
 }
 
+// Register-resident Cholesky of the packed lower triangle A (n = N) fused with X <- L^{-1} X
+// (N x M, row-major), for matrices whose entries fit in the registers of the CTA: thread t owns
+// packed entries t, t + NT, ... and right-hand-side entries t, t + NT, ..., with their (row,
+// column) precomputed, so each column step is two predicated passes over registers:
+//   B: scale column j by 1/sqrt(pivot) and publish it (and row j of X) to shared memory;
+//   C: rank-1 update of the entries right of column j; the owner of (j+1, j+1) publishes the
+//      next pivot.
+// Results are written back to A and X. Returns false (in every thread) on a bad pivot.
+template <int N, int M, int NT>
+__device__ bool chol32_reg(float* A, float* X, float* colbuf, float* xrow, float* invd, float* piv) {
+  constexpr int TRI = N * (N + 1) / 2, ST = (TRI + NT - 1) / NT, SX = (N * M + NT - 1) / NT;
+  const int tid = threadIdx.x;
+  float av[ST], xv[SX];
+  int ak[ST], xk[SX];                              // (row << 16) | column, packed
+#pragma unroll
+  for (int s = 0; s < ST; ++s) {
+    const int t = tid + s * NT;
+    if (t < TRI) {
+      const int i = tri_row(t);
+      ak[s] = (i << 16) | (t - i * (i + 1) / 2);
+      av[s] = A[t];
+    } else {
+      ak[s] = 0xffff;                                // row 0, column 65535: never active
+      av[s] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < SX; ++s) {
+    const int u = tid + s * NT;
+    if (u < N * M) {
+      xk[s] = ((u / M) << 16) | (u % M);
+      xv[s] = X[u];
+    } else {
+      xk[s] = -1;                                    // row -1: never active
+      xv[s] = 0.f;
+    }
+  }
+  if (tid == 0) piv[0] = A[0];
+  __syncthreads();
+  bool ok = true;
+  for (int j = 0; j < N; ++j) {
+    const float d = piv[0];
+    if (!(d > 0.0f) || !(d < INFINITY)) { ok = false; break; }
+    const float r = dev::rsqrt_newton(d);
+#pragma unroll
+    for (int s = 0; s < ST; ++s) {
+      const int i = ak[s] >> 16, l = ak[s] & 0xffff;
+      if (l == j) {
+        if (i == j) {
+          av[s] = d * r;
+          invd[j] = r;
+        } else {
+          av[s] *= r;
+          colbuf[i] = av[s];
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < SX; ++s)
+      if ((xk[s] >> 16) == j) {
+        xv[s] *= r;
+        xrow[xk[s] & 0xffff] = xv[s];
+      }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < ST; ++s) {
+      const int i = ak[s] >> 16, l = ak[s] & 0xffff;
+      if (l > j && l < N) {
+        av[s] = fmaf(-colbuf[i], colbuf[l], av[s]);
+        if (l == j + 1 && i == j + 1) piv[0] = av[s];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < SX; ++s) {
+      const int i = xk[s] >> 16;
+      if (i > j) xv[s] = fmaf(-colbuf[i], xrow[xk[s] & 0xffff], xv[s]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < ST; ++s)
+    if (tid + s * NT < TRI) A[tid + s * NT] = av[s];
+#pragma unroll
+  for (int s = 0; s < SX; ++s)
+    if (tid + s * NT < N * M) X[tid + s * NT] = xv[s];
+  __syncthreads();
+  return ok;
+}
+
 // Single-warp triangular solves with a packed lower factor L (invd = 1 / diag):
 // forward L y = v in place, and backward L^T x = y in place.
 __device__ void warp_fwd(const float* L, const float* invd, float* v, int n) {
@@ -716,7 +805,10 @@ __device__ __forceinline__ void element_mixed_body(const ElemArgs& args, const i
     Xd[t] = v;
   }
   __syncthreads();
-  if (!chol32<NT>(LM, N, -1, colbuf, invd, flag, Xd, NQK)) {
+  bool spd;
+  if constexpr (S::BIG_SMEM) spd = chol32_reg<N, NQK, NT>(LM, Xd, colbuf, vec, invd, flag);
+  else spd = chol32<NT>(LM, N, -1, colbuf, invd, flag, Xd, NQK);
+  if (!spd) {
     if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
     return;
   }
