@@ -50,6 +50,11 @@ def parse_args(argv=None):
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="fp64, or mixed: FP32 mixed-form elimination below the contrast threshold")
     ap.add_argument("--threshold", type=float, default=1e4, help="mixed: contrast above which elements stay FP64")
+    ap.add_argument("--refine", type=int, default=0,
+                    help="FP64 refinement steps after the solve (hyb_refine; for --precision mixed)")
+    ap.add_argument("--refine-rtol", type=float, default=1e-6, help="inner PCG tolerance of a refinement step")
+    ap.add_argument("--pcg", choices=["fused", "split"], default="fused",
+                    help="PCG launch form: one cooperative launch per 64 iterations, or 3 launches per iteration")
     ap.add_argument("--assembly-only", action="store_true",
                     help="time only the element phase (assemble + recover with lambda = 0); per-config rates")
     return ap.parse_args(argv)
@@ -212,6 +217,18 @@ def spmv_bytes(n, nnz, nfn):
     return 8 * nnz + 4 * nnz // nfn + 16 * (n // nfn) + 8 * n + 8 * n
 
 
+def pcg_iteration_flops(n, nnz):
+    """FP64 flops of one PCG iteration: SpMV (2 per nonzero), p^T q (2n), x and r updates (4n),
+    z = D^-1 r (n), r^T z and r^T r (4n), p = z + beta p (2n)."""
+    return 2 * nnz + 13 * n
+
+
+def pcg_iteration_bytes(n, nnz, nfn):
+    """Algorithmic bytes of one PCG iteration: the SpMV's, then x, p, r, q, D^-1 read and x, r, z
+    written by the update, p and z read and p written by the direction update."""
+    return spmv_bytes(n, nnz, nfn) + 8 * 8 * n + 3 * 8 * n
+
+
 def element_flops(k):
     """Algorithmic FP64 flops of one element elimination (what the method needs, not what a
     kernel issues): sum-factorised A_T (6 blocks, 3 stages, mass + divergence terms),
@@ -274,6 +291,7 @@ def run_ours(args):
     ctx = hyb.hyb_setup(verts, p.nx, p.ny, p.nz, p.order, alpha, beta,
                         precision=hyb.HYB_MIXED if mixed else hyb.HYB_FP64,
                         contrast_threshold=args.threshold if mixed else 0.0)
+    hyb.hyb_set_pcg_fused(ctx, args.pcg == "fused")
     n64, n32, theta = ctx.precision_split()
     sz = ctx.sizes()
     E, n_loc, N, nnz = sz["n_elem"], sz["n_loc"], sz["n_lambda"], sz["nnz"]
@@ -281,6 +299,7 @@ def run_ours(args):
     u = torch.zeros(E, n_loc, dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     iters = []
+    jumps = []
 
     def step(load_dev):
         hyb.hyb_assemble_reduced(ctx, load_dev, None)
@@ -292,6 +311,9 @@ def run_ours(args):
                 raise hyb.HybError(st, "hyb_solve_reduced")
             iters.append(it)
         hyb.hyb_recover(ctx, lam, u)
+        if args.refine and not args.assembly_only:
+            j, _ = hyb.hyb_refine(ctx, args.refine, args.refine_rtol, args.maxit, lam, u)
+            jumps.append(j)
 
     for _ in range(args.warmup):
         step(load)
@@ -342,6 +364,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel class
     spmv_ms, spmv_launches = prof["spmv"]
+    fused_ms, fused_launches = prof["pcg_fused"]
     dominant = max(prof, key=lambda k: prof[k][0])
     peaks = {}
     try:
@@ -349,7 +372,7 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    per_launch_ms = spmv_ms / max(1, it_total) if it_total else float("nan")   # no-op launches charged to real ones
+    per_launch_ms = spmv_ms / it_total if it_total and spmv_ms > 0 else float("nan")   # no-op launches charged to real ones
     nfn = (p.order + 1) ** 2
     gbs = spmv_bytes(N, nnz, nfn) / (per_launch_ms * 1e-3) / 1e9
     tflops = 2.0 * nnz / (per_launch_ms * 1e-3) / 1e12
@@ -364,6 +387,22 @@ def run_ours(args):
             "hbm_peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
             "avg_launch_ms": per_launch_ms, "dominant_class": dominant,
             "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak}
+    if fused_ms > 0 and it_total:
+        # one unit = one PCG iteration (SpMV + p^T q, the x/r/z update with r^T z and r^T r,
+        # the direction update); a launch runs up to 64 of them
+        it_ms = fused_ms / it_total
+        flops_it, bytes_it = pcg_iteration_flops(N, nnz), pcg_iteration_bytes(N, nnz, nfn)
+        tf, gb = flops_it / (it_ms * 1e-3) / 1e12, bytes_it / (it_ms * 1e-3) / 1e9
+        roof = {"kernel": "pcg_fused_kernel (cooperative: SpMV + p^T H p, updates, reductions)", "bound": "alu",
+                "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf / fp64_peak,
+                "peak_source": "FP64 FMA throughput measured in this run (hyb_measure_fma_peak)",
+                "traffic": None, "unit_of_work": "one PCG iteration",
+                "iterations_per_launch": it_total / max(1, fused_launches),
+                "algorithmic_flops_per_iteration": flops_it, "algorithmic_bytes_per_iteration": bytes_it,
+                "achieved_gbs": gb, "hbm_peak_gbs": hbm_peak, "hbm_frac": gb / hbm_peak,
+                "hbm_peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+                "avg_launch_ms": fused_ms / max(1, fused_launches), "avg_iteration_ms": it_ms,
+                "dominant_class": dominant, "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak}
     launches = sum(v[1] for v in prof.values())
     phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
     elem_ms = prof["element"][0] / args.steps
@@ -387,6 +426,8 @@ def run_ours(args):
     workload = WORKLOAD if cfg == 2 else f"config {cfg}: {p.nx}^3 jittered hex mesh, RT_{p.order}, FP64"
     if mixed:
         workload = workload.replace("FP64", f"mixed FP32/FP64 (threshold {theta:g})")
+    if args.refine and not args.assembly_only:
+        workload += f", {args.refine} FP64 refinement steps"
     if args.assembly_only:
         workload += " (element phase only: assemble + recover)"
     line = {
@@ -403,11 +444,15 @@ def run_ours(args):
         "element_roofline": element_roofline,
         "phases": phases,
         "assembly_elements_per_s": E / (elem_ms * 1e-3) if elem_ms > 0 else None,
-        "reduced_dofs_per_s": (N / ((prof["spmv"][0] + prof["pcg_vector"][0]) / args.steps * 1e-3)
-                               if prof["spmv"][0] > 0 else None),
+        "pcg_ms_per_iteration": ((prof["spmv"][0] + prof["pcg_vector"][0] + prof["pcg_fused"][0]) / it_total
+                                 if it_total else None),
         "clocks": ck,
         "wall_s": t_wall,
     }
+    if args.refine and jumps:
+        line["refinement"] = {"steps": args.refine, "inner_rtol": args.refine_rtol,
+                              "jump_per_step": jumps[-1],
+                              "note": "||C u|| / ||g|| before each FP64 refinement step and after the last"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline()

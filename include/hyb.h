@@ -112,7 +112,15 @@ int hyb_assemble_reduced(hyb_ctx* ctx, const double* load, const double* ess);
  *  stopping when ||r||_2 <= rtol ||r_0||_2 (the paper's criterion, Sec. 6.1).
  *  lambda : device, N_lambda doubles, receives the solution.
  *  iters, rel_res : host, may be NULL.
- *  Returns HYB_ERR_NOT_CONVERGED after maxit iterations (lambda still written).
+ *  By default the iterations run 64 at a time in one cooperative launch (grid-wide
+ *  barriers between SpMV, update and direction; the reductions are summed in a fixed
+ *  block order, so the result is reproducible); hyb_set_pcg_fused(ctx, 0) selects
+ *  three launches per iteration instead. Both give the same iterates up to rounding
+ *  of the reductions.
+ *  Returns HYB_ERR_NOT_CONVERGED after maxit iterations (lambda still written),
+ *  HYB_ERR_BREAKDOWN when p^T H p <= 0 or a residual is not finite, and
+ *  HYB_ERR_TIMEOUT when a grid barrier waited longer than about a second (the
+ *  kernel then returns; the context stays usable).
  */
 int hyb_solve_reduced(hyb_ctx* ctx, double rtol, int maxit, double* lambda,
                       int* iters, double* rel_res);
@@ -157,6 +165,49 @@ int hyb_get_reduced(hyb_ctx* ctx, const int64_t** row_ptr, const int32_t** col,
  */
 int hyb_export_reduced(hyb_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val, double* rhs);
 
+/*
+ * hyb_refine -- FP64 iterative refinement of a solved hybridized system. It matters for
+ *  mixed-precision contexts, where H was assembled from FP32 element eliminations
+ *  (Sec. 3.2's mixed form): the correction equation is eq. 2.4 with the residual as its
+ *  right-hand side. Each step
+ *    rho = C u                       normal jump of the current flux, FP64 (eq. 2.3's constraint)
+ *    H dlambda = rho                 diagonal PCG on the assembled H to inner_rtol
+ *    lambda += dlambda, u = hyb_recover(lambda)
+ *  For u = A^-1 (f - C^T lambda), which hyb_recover forms with FP64 residual refinement,
+ *  the jump C u equals g - H lambda with the exact H, so each step contracts the error of
+ *  lambda by about ||I - H_assembled^-1 H|| and u follows.
+ *  lambda, u : device, on entry the output of hyb_solve_reduced and hyb_recover; updated.
+ *  jump      : host, steps + 1 doubles or NULL; receives ||C u|| / ||g|| before each
+ *              step and after the last.
+ *  Only after hyb_assemble_reduced (HYB_ERR_INVALID_ARG after static condensation).
+ *  Allocates two N_lambda vectors on first use (kept by the context).
+ *  An inner solve that stops at maxit is not an error (the next step corrects it).
+ */
+int hyb_refine(hyb_ctx* ctx, int steps, double inner_rtol, int maxit, double* lambda, double* u,
+               double* jump);
+
+/*
+ * hyb_set_pcg_fused -- choose the PCG launch form used by hyb_solve_reduced:
+ *  1 (default) one cooperative launch per 64 iterations, 0 three launches per
+ *  iteration. Implementation choice with no counterpart in the paper.
+ *  HYB_ERR_INVALID_ARG for other values or when the device cannot launch
+ *  cooperative kernels.
+ */
+int hyb_set_pcg_fused(hyb_ctx* ctx, int on);
+
+/*
+ * hyb_barrier_selftest -- exercise the grid barrier of the fused PCG kernel.
+ *  Runs `rounds` barrier-and-reduce steps over a cooperative grid (one block per
+ *  free slot of every SM) and checks the reduced sums. `absent` arrivals are
+ *  counted as missing, so absent > 0 makes the first wait run out: every block
+ *  then gives up after about a second and the kernel returns. Implementation
+ *  check with no counterpart in the paper. Allocates and frees ~20 KB; synchronises
+ *  `cuda_stream`.
+ *  Returns HYB_OK, HYB_ERR_TIMEOUT (a wait ran out), HYB_ERR_BREAKDOWN (a wrong
+ *  sum) or HYB_ERR_INVALID_ARG (absent outside 0..1024, rounds < 0).
+ */
+int hyb_barrier_selftest(int absent, int rounds, void* cuda_stream);
+
 /* Kernel classes for the launch profile. */
 enum {
   HYB_K_ELEMENT = 0,     /* element elimination (assemble / static condensation) */
@@ -164,7 +215,8 @@ enum {
   HYB_K_PCG_VECTOR = 2,  /* PCG vector updates, reductions, initialisation */
   HYB_K_RECOVER = 3,     /* back substitution */
   HYB_K_SETUP = 4,       /* set-up kernels (column expansion, geometry check) */
-  HYB_K_COUNT = 5
+  HYB_K_PCG_FUSED = 5,   /* fused PCG iterations: SpMV, updates and reductions in one launch */
+  HYB_K_COUNT = 6
 };
 
 /*

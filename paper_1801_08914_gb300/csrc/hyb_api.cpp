@@ -110,8 +110,15 @@ struct hyb_ctx {
   double* zstore = nullptr;
   int* status = nullptr;
   long long* err_elem = nullptr;
-  double *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *partial = nullptr, *scal = nullptr;
+  double *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *z = nullptr, *partial = nullptr,
+         *scal = nullptr;
   int* flags = nullptr;
+  int32_t* face_dof = nullptr;             // per interior face: 6 e + a of its low, then high side
+  double* rho = nullptr;                   // refinement: normal jump C u, then the correction
+  double* dlam = nullptr;
+  double* rnorm = nullptr;                 // 2 doubles: ||rho||^2, ||g||^2
+  unsigned long long* gridbar = nullptr;   // arrival counter of the fused PCG kernel's grid barrier
+  int fused = 1;                           // PCG: one cooperative launch per chunk (1) or 3 launches/iteration (0)
   int nblocks = 0;
   int mode = MODE_NONE;
   int64_t last_err_elem = -1;
@@ -241,10 +248,14 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
   const int64_t F = c->n_ifaces;
   std::vector<int32_t> adj(11 * F, -1), adj_count(F, 0);
   std::vector<int64_t> nb(2 * F, -1);                 // low / high neighbour element
+  std::vector<int32_t> face_dof(2 * F, 0);            // the same, as 6 e + local face
   for (int64_t e = 0; e < E; ++e)
     for (int a = 0; a < 6; ++a) {
       const int32_t f = elem_face[6 * e + a];
-      if (f >= 0) nb[2 * f + (a & 1 ? 0 : 1)] = e;   // face at x_hat = 1 of e: e is the low side
+      if (f >= 0) {
+        nb[2 * f + (a & 1 ? 0 : 1)] = e;   // face at x_hat = 1 of e: e is the low side
+        face_dof[2 * f + (a & 1 ? 0 : 1)] = (int32_t)(6 * e + a);
+      }
     }
   for (int64_t f = 0; f < F; ++f) {
     int32_t tmp[12];
@@ -353,9 +364,13 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
   if ((st = dalloc(c, &c->p, c->n_lambda))) return st;
   if ((st = dalloc(c, &c->q, c->n_lambda))) return st;
   if ((st = dalloc(c, &c->dinv, c->n_lambda))) return st;
+  if ((st = dalloc(c, &c->z, c->n_lambda))) return st;
   if ((st = dalloc(c, &c->partial, 2 * c->nblocks))) return st;
   if ((st = dalloc(c, &c->scal, 8))) return st;
   if ((st = dalloc(c, &c->flags, 4))) return st;
+  if ((st = dalloc(c, &c->gridbar, 2))) return st;
+  if ((st = dalloc(c, &c->face_dof, 2 * F))) return st;
+  if ((st = dalloc(c, &c->rnorm, 2))) return st;
 
   cudaStream_t S = c->stream;
   cudaError_t e = cudaSuccess;
@@ -364,6 +379,7 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
   };
   up(c->row_ptr, row_ptr.data(), row_ptr.size() * sizeof(int64_t));
   up(c->elem_face, elem_face.data(), elem_face.size() * sizeof(int32_t));
+  up(c->face_dof, face_dof.data(), face_dof.size() * sizeof(int32_t));
   up(c->blockoff, blockoff.data(), blockoff.size() * sizeof(int64_t));
   up(c->colour_list[0], lists[0].data(), lists[0].size() * sizeof(int32_t));
   up(c->colour_list[1], lists[1].data(), lists[1].size() * sizeof(int32_t));
@@ -486,31 +502,34 @@ int staticcond_assemble(hyb_ctx* ctx, const double* load, const double* ess) {
   return assemble_impl(ctx, load, ess, MODE_SC);
 }
 
-int hyb_solve_reduced(hyb_ctx* c, double rtol, int maxit, double* lambda, int* iters, double* rel_res) {
-  if (!c || !lambda || maxit < 0 || !(rtol >= 0.0)) return HYB_ERR_INVALID_ARG;
-  if (c->mode == MODE_NONE) return HYB_ERR_INVALID_ARG;
+namespace {
+
+// Diagonal PCG on the assembled H (or S) with right-hand side b, x0 = 0.
+int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lambda, int* iters, double* rel_res) {
   PcgArgs a{};
   a.n = c->n_lambda;
   a.row_ptr = c->row_ptr;
   a.col = c->col;
   a.val = c->val;
-  a.b = c->rhs;
+  a.b = b;
   a.x = lambda;
   a.r = c->r;
   a.p = c->p;
   a.q = c->q;
   a.dinv = c->dinv;
+  a.z = c->fused ? c->z : nullptr;
   a.partial = c->partial;
   a.scal = c->scal;
   a.flags = c->flags;
   a.nblocks = c->nblocks;
   a.nfn = c->sz.nfn;
   cudaError_t e = pcg_init(a, c->stream, &c->prof);
+  if (e == cudaSuccess && c->fused) e = cudaMemsetAsync(c->gridbar, 0, 2 * sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return cuda_status(e);
   int hf[4] = {0, 0, 0, 0};
   double hs[8] = {0};
   int done = 0;
-  const int chunk = 32;
+  const int chunk = c->fused ? 64 : 32;
   for (;;) {
     e = cudaMemcpyAsync(hf, c->flags, sizeof(hf), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -519,7 +538,8 @@ int hyb_solve_reduced(hyb_ctx* c, double rtol, int maxit, double* lambda, int* i
     done = hf[0];
     if (hf[1] || hf[2] || done >= maxit) break;
     const int n = std::min(chunk, maxit - done);
-    e = pcg_iterations(a, n, rtol, c->stream, &c->prof);
+    e = c->fused ? pcg_iterations_fused(a, n, rtol, c->gridbar, c->stream, &c->prof)
+                 : pcg_iterations(a, n, rtol, c->stream, &c->prof);
     if (e != cudaSuccess) return cuda_status(e);
   }
   e = cudaMemcpyAsync(hs, c->scal, sizeof(hs), cudaMemcpyDeviceToHost, c->stream);
@@ -527,8 +547,76 @@ int hyb_solve_reduced(hyb_ctx* c, double rtol, int maxit, double* lambda, int* i
   if (e != cudaSuccess) return cuda_status(e);
   if (iters) *iters = done;
   if (rel_res) *rel_res = hs[1] > 0.0 ? std::sqrt(hs[2] / hs[1]) : 0.0;
+  if (hf[2] == 2) return HYB_ERR_TIMEOUT;
   if (hf[2]) return HYB_ERR_BREAKDOWN;
   if (!hf[1]) return HYB_ERR_NOT_CONVERGED;
+  return HYB_OK;
+}
+
+}  // namespace
+
+int hyb_solve_reduced(hyb_ctx* c, double rtol, int maxit, double* lambda, int* iters, double* rel_res) {
+  if (!c || !lambda || maxit < 0 || !(rtol >= 0.0)) return HYB_ERR_INVALID_ARG;
+  if (c->mode == MODE_NONE) return HYB_ERR_INVALID_ARG;
+  return solve_impl(c, c->rhs, rtol, maxit, lambda, iters, rel_res);
+}
+
+int hyb_refine(hyb_ctx* c, int steps, double inner_rtol, int maxit, double* lambda, double* u, double* jump) {
+  if (!c || !lambda || !u || steps < 0 || maxit < 0 || !(inner_rtol >= 0.0)) return HYB_ERR_INVALID_ARG;
+  if (c->mode != MODE_HYB) return HYB_ERR_INVALID_ARG;
+  int st;
+  if (!c->rho) {
+    if ((st = dalloc(c, &c->rho, c->n_lambda))) return st;
+    if ((st = dalloc(c, &c->dlam, c->n_lambda))) return st;
+  }
+  JumpArgs j{};
+  j.n_faces = c->n_ifaces;
+  j.nfn = c->sz.nfn;
+  j.n_loc = c->sz.n;
+  j.ni = c->sz.ni;
+  j.face_dof = c->face_dof;
+  j.u = u;
+  j.rho = c->rho;
+  j.partial = c->partial;
+  j.norm2 = c->rnorm;
+  j.ticket = &c->flags[3];
+  j.nblocks = c->nblocks;
+  std::memcpy(j.wf, c->tabs[c->k].wf, sizeof(j.wf));
+  cudaError_t e = launch_norm2(c->n_lambda, c->rhs, c->partial, c->nblocks, c->rnorm + 1, &c->flags[3], c->stream,
+                               &c->prof);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int s = 0; s <= steps; ++s) {
+    e = launch_face_jump(j, c->stream, &c->prof);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (jump) {
+      double hn[2] = {0, 0};
+      e = cudaMemcpyAsync(hn, c->rnorm, sizeof(hn), cudaMemcpyDeviceToHost, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) return cuda_status(e);
+      jump[s] = hn[1] > 0.0 ? std::sqrt(hn[0] / hn[1]) : std::sqrt(hn[0]);
+    }
+    if (s == steps) break;
+    st = solve_impl(c, c->rho, inner_rtol, maxit, c->dlam, nullptr, nullptr);
+    if (st != HYB_OK && st != HYB_ERR_NOT_CONVERGED) return st;
+    e = launch_axpy(c->n_lambda, c->dlam, lambda, c->stream, &c->prof);
+    if (e != cudaSuccess) return cuda_status(e);
+    st = recover_impl(c, lambda, u, MODE_HYB);
+    if (st != HYB_OK) return st;
+  }
+  e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? HYB_OK : cuda_status(e);
+}
+
+int hyb_set_pcg_fused(hyb_ctx* c, int on) {
+  if (!c || (on != 0 && on != 1)) return HYB_ERR_INVALID_ARG;
+  if (on) {
+    int dev = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!coop) return HYB_ERR_INVALID_ARG;
+  }
+  c->fused = on;
   return HYB_OK;
 }
 

@@ -97,6 +97,7 @@ struct PcgArgs {
   double* p;
   double* q;
   double* dinv;
+  double* z;                 // preconditioned residual (fused form only; NULL otherwise)
   double* partial;           // per-block partial sums
   double* scal;              // device scalars
   int* flags;                // iteration count / converged / breakdown / ticket
@@ -112,7 +113,34 @@ struct PcgBatch {
 };
 cudaError_t pcg_iterations_batch(const PcgBatch& b, int count, double rtol, cudaStream_t s, Prof* prof);
 cudaError_t pcg_init(const PcgArgs& a, cudaStream_t s, Prof* prof);
+// Up to `count` iterations in one cooperative launch (grid barriers between the phases).
+// bar: 16 bytes, zeroed at the start of every solve; a.z must be set (pcg_init fills it).
+// Stops at convergence or breakdown; a barrier that waits too long sets flags[3rd] = 2
+// (reported as HYB_ERR_TIMEOUT).
+cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void* bar, cudaStream_t s, Prof* prof);
 cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_t s, Prof* prof);
+
+// Normal jump of a broken flux: rho = C u (eq. 2.3's constraint), row (f, m) =
+// w_m (u of the low-side element - u of the high-side element) at face node m. For the
+// locally exact u(lambda) = A^-1 (f - C^T lambda) this is g - H lambda (eq. 2.4).
+struct JumpArgs {
+  int64_t n_faces;
+  int nfn, n_loc, ni;
+  const int32_t* face_dof;   // per interior face: 6 e + a of the low side, then of the high side
+  const double* u;           // E x n_loc
+  double* rho;               // n_faces * nfn
+  double* partial;           // >= nblocks doubles
+  double* norm2;             // out: rho^T rho
+  int* ticket;               // zero on entry, zero on exit
+  int nblocks;
+  double wf[16];
+};
+cudaError_t launch_face_jump(const JumpArgs& a, cudaStream_t s, Prof* prof);
+// out = v^T v (fixed-order block sums; ticket zero on entry and exit, partial >= nblocks)
+cudaError_t launch_norm2(int64_t n, const double* v, double* partial, int nblocks, double* out, int* ticket,
+                         cudaStream_t s, Prof* prof);
+// y += x
+cudaError_t launch_axpy(int64_t n, const double* x, double* y, cudaStream_t s, Prof* prof);
 
 struct RecoverArgs {
   int k;

@@ -47,6 +47,23 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// Block-wide sum to thread 0 through shared memory (sh: kThreads doubles): the values are
+// stored, then warp 0 adds 8 of them per lane and finishes with one shuffle tree. Far fewer
+// FP64 instructions than a shuffle tree in every warp, which matters where the FP64 pipe is
+// the bound and every warp instruction occupies it whatever its active lanes.
+__device__ __forceinline__ double block_sum_smem(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[threadIdx.x + 32 * k];
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  return t;
+}
+
 // Ticket: returns true in exactly one (the last) block. Thread 0 wrote this block's partial;
 // it alone fences before taking a ticket, so the last block sees every partial in L2.
 __device__ __forceinline__ bool last_block(int* ticket, int nblocks) {
@@ -88,6 +105,7 @@ __global__ void pcg_init_kernel(PcgArgs a) {
     a.x[i] = 0.0;
     a.r[i] = r;
     a.p[i] = z;
+    if (a.z) a.z[i] = z;
     rz = fma(r, z, rz);
     rr = fma(r, r, rr);
   }
@@ -104,6 +122,7 @@ __global__ void pcg_init_kernel(PcgArgs a) {
       a.scal[S_RZ] = s0;
       a.scal[S_RR0] = s1;
       a.scal[S_RR] = s1;
+      a.scal[S_BETA] = 0.0;
       a.flags[F_IT] = 0;
       a.flags[F_CONV] = (s1 == 0.0);
       a.flags[F_BRK] = 0;
@@ -182,6 +201,7 @@ __global__ void __launch_bounds__(kThreads) spmv_face_kernel(PcgArgs a) {
 // Four elements per thread per step with all loads issued first: the kernel is bound by
 // memory latency, so independent loads in flight matter more than occupancy.
 constexpr int kUnroll = 4;
+
 __device__ __forceinline__ void pcg_update_body(const PcgArgs& a, double rtol2, int vb, int nvb, double* sh) {
   if (a.flags[F_CONV] | a.flags[F_BRK]) return;
   const double alpha = a.scal[S_ALPHA];
@@ -256,6 +276,323 @@ __device__ __forceinline__ void pcg_direction_body(const PcgArgs& a, int vb, int
 
 __global__ void __launch_bounds__(kThreads) pcg_direction_kernel(PcgArgs a) {
   pcg_direction_body(a, blockIdx.x, gridDim.x);
+}
+
+// ---- fused iterations: one cooperative launch runs up to `count` iterations.
+//
+// Grid-wide synchronisation is a monotonic arrival counter (64-bit, zeroed at the start of a
+// solve): barrier number B completes when the counter reaches (B + 1) * gridDim.x. Before
+// arriving, thread 0 of each block stores the block's partial sums in one of two buffers
+// (alternating with B); after the barrier every block sums all partials itself in block order,
+// so every block obtains bitwise the same totals without a serial reduction step. A buffer is
+// rewritten two barriers later, after every block has passed the barrier in between and so
+// has finished reading it. Waits are bounded: a block that waits longer than a second sets
+// flags[F_BRK] = 2, and every block leaves at its next barrier.
+constexpr unsigned long long kBarrierNs = 1000000000ull;  // a barrier gives up after 1 s
+constexpr long long kBarrierSpins = 1ll << 26;            // and after this many polls in any case
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Every thread of every block calls this; thread 0 has already stored the block's partials.
+// Returns false in all threads of the block if the wait ran out (here or in another block).
+// The arrival is a release add and the poll an acquire load (gpu scope): after
+// __syncthreads the block's earlier stores are ordered before thread 0's release, and the
+// acquire that observes the final count orders every other block's stores before this
+// block's later loads (the second __syncthreads extends that to all its threads).
+__device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned long long target, int* flags) {
+  __shared__ int brk;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(count), "l"(1ull) : "memory");
+    long long spins = 0;
+    const unsigned long long t0 = global_ns();
+    while ((long long)(ld_acquire(count) - target) < 0) {
+      if (++spins > kBarrierSpins || global_ns() - t0 > kBarrierNs) {
+        atomicExch(&flags[F_BRK], 2);
+        break;
+      }
+      if ((spins & 1023) == 0 && ld_relaxed(&flags[F_BRK]) == 2) break;   // another block gave up
+      __nanosleep(20);
+    }
+    brk = ld_relaxed(&flags[F_BRK]) == 2;
+  }
+  __syncthreads();
+  return !brk;
+}
+
+// Totals of the 2 * nblk partials in `part` (pairs), fixed order; valid in thread 0.
+__device__ __forceinline__ void sum_pairs(const double* part, int nblk, double* sh, double& s0, double& s1) {
+  double a0 = 0.0, a1 = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += kThreads) {
+    a0 += __ldcg(part + 2 * b);
+    a1 += __ldcg(part + 2 * b + 1);
+  }
+  s0 = block_sum_smem(a0, sh);
+  s1 = block_sum_smem(a1, sh);
+}
+
+struct GridBar {
+  unsigned long long count;
+  unsigned long long pad;
+};
+
+// Fused iteration in two phases separated by the two reductions of CG:
+//   S: w = H z;  p = z + beta p;  q = w + beta q  (= H p by linearity);  p^T q
+//   U: x += alpha p;  r -= alpha q;  z = D^{-1} r;  r^T z, r^T r
+// The SpMV reads z, which the previous U phase finished before its barrier, so the direction
+// update rides along with the SpMV instead of needing a third barrier and pass. In exact
+// arithmetic the iterates are those of the three-launch form; q is carried by the recursion.
+// On the first iteration after initialisation (flags[F_IT] == 0) beta = 0 and q is not read.
+//
+// W lanes share a face (their partial sums of the NFN rows). Where W divides NFN they
+// reduce-scatter: at each of the log2(W) levels a lane keeps half of its current values,
+// sends the other half to its partner and adds what it receives, so lane gl ends with the
+// full sums of NFN / W rows after NFN (1 - 1/W) adds (instead of NFN log2(W)) and updates
+// exactly those rows; otherwise every lane reduces every row and lane m % W updates row m.
+template <int NFN, int W>
+__device__ __forceinline__ int scatter_row(int j, int gl) {
+  int row = j, S = NFN;
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    if (gl & o) row += S / 2;
+    S >>= 1;
+  }
+  return row;
+}
+
+template <int NFN, int W>
+__global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
+    pcg_fused_kernel(PcgArgs a, int count, double rtol2, GridBar* bar) {
+  constexpr bool kScatter = NFN % W == 0;
+  __shared__ double sh[kThreads];
+  __shared__ double bc[3];
+  if (a.flags[F_CONV] | a.flags[F_BRK]) return;
+  const int it0 = a.flags[F_IT];                          // no block changes it before all have read it
+  const double rr0 = a.scal[S_RR0];
+  double rz = a.scal[S_RZ];
+  double beta = a.scal[S_BETA];
+  bool first = it0 == 0;
+  const int vb = blockIdx.x, nvb = gridDim.x;
+  constexpr int FPW = 32 / W;
+  const int64_t warp = (vb * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)nvb * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31, sub = lane / W, gl = lane % W;
+  const int64_t nfaces = a.n / NFN;
+  double* part0 = a.partial;                              // barrier 2i   (p^T q)
+  double* part1 = a.partial + 2 * nvb;                    // barrier 2i+1 (r^T z, r^T r)
+  for (int it = 0; it < count; ++it) {
+    const unsigned long long B = 2ull * (unsigned long long)(it0 + it);
+    // ---- S phase
+    double pq = 0.0;
+    for (int64_t base = warp * FPW; base < nfaces; base += nwarps * FPW) {
+      const int64_t f = base + sub;
+      double acc[NFN];
+#pragma unroll
+      for (int m = 0; m < NFN; ++m) acc[m] = 0.0;
+      if (f < nfaces) {
+        const int64_t r0 = f * NFN;
+        const int64_t lo = __ldcs(a.row_ptr + r0);
+        const int len = (int)(__ldcs(a.row_ptr + r0 + 1) - lo);
+#pragma unroll 4
+        for (int t = gl; t < len; t += W) {
+          const double zj = __ldcg(a.z + __ldcs(a.col + lo + t));
+#pragma unroll
+          for (int m = 0; m < NFN; ++m) acc[m] = fma(__ldcs(a.val + lo + (int64_t)m * len + t), zj, acc[m]);
+        }
+      }
+      if constexpr (kScatter) {
+#pragma unroll
+        for (int o = W / 2, S = NFN; o > 0; o >>= 1, S >>= 1) {
+          const bool hi = gl & o;
+#pragma unroll
+          for (int j = 0; j < S / 2; ++j) {
+            const double keep = hi ? acc[j + S / 2] : acc[j];
+            const double send = hi ? acc[j] : acc[j + S / 2];
+            acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o, W);
+          }
+        }
+        if (f < nfaces) {
+#pragma unroll
+          for (int j = 0; j < NFN / W; ++j) {
+            const int64_t i = f * NFN + scatter_row<NFN, W>(j, gl);
+            const double zi = __ldcg(a.z + i);
+            const double pi = first ? zi : fma(beta, a.p[i], zi);
+            const double qi = first ? acc[j] : fma(beta, a.q[i], acc[j]);
+            a.p[i] = pi;
+            a.q[i] = qi;
+            pq = fma(pi, qi, pq);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < NFN; ++m) {
+#pragma unroll
+          for (int o = W / 2; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o, W);
+        }
+        if (f < nfaces) {
+#pragma unroll
+          for (int m = 0; m < NFN; ++m)
+            if (gl == m % W) {
+              const int64_t i = f * NFN + m;
+              const double zi = __ldcg(a.z + i);
+              const double pi = first ? zi : fma(beta, a.p[i], zi);
+              const double qi = first ? acc[m] : fma(beta, a.q[i], acc[m]);
+              a.p[i] = pi;
+              a.q[i] = qi;
+              pq = fma(pi, qi, pq);
+            }
+        }
+      }
+    }
+    first = false;
+    pq = block_sum_smem(pq, sh);
+    if (threadIdx.x == 0) {
+      part0[2 * vb] = pq;
+      part0[2 * vb + 1] = 0.0;
+    }
+    if (!grid_barrier(&bar->count, (B + 1) * nvb, a.flags)) return;
+    {
+      double tpq, unused;
+      sum_pairs(part0, nvb, sh, tpq, unused);
+      if (threadIdx.x == 0) {
+        bc[0] = tpq;
+        bc[1] = rz / tpq;
+      }
+      __syncthreads();
+    }
+    const double tpq = bc[0], alpha = bc[1];
+    if (!(tpq > 0.0) || !(tpq < INFINITY)) {
+      if (vb == 0 && threadIdx.x == 0) { a.flags[F_BRK] = 1; a.scal[S_PQ] = tpq; }
+      return;
+    }
+    // ---- U phase
+    double rzl = 0.0, rrl = 0.0;
+    {
+      const int64_t stride = (int64_t)nvb * blockDim.x;
+      for (int64_t i = vb * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        a.x[i] = fma(alpha, a.p[i], a.x[i]);
+        const double r = fma(-alpha, a.q[i], a.r[i]);
+        a.r[i] = r;
+        const double z = a.dinv[i] * r;
+        a.z[i] = z;
+        rzl = fma(r, z, rzl);
+        rrl = fma(r, r, rrl);
+      }
+    }
+    rzl = block_sum_smem(rzl, sh);
+    rrl = block_sum_smem(rrl, sh);
+    if (threadIdx.x == 0) {
+      part1[2 * vb] = rzl;
+      part1[2 * vb + 1] = rrl;
+    }
+    if (!grid_barrier(&bar->count, (B + 2) * nvb, a.flags)) return;
+    {
+      double rzn, rrn;
+      sum_pairs(part1, nvb, sh, rzn, rrn);
+      if (threadIdx.x == 0) {
+        bc[0] = rzn;
+        bc[1] = rrn;
+        bc[2] = rzn / rz;
+      }
+      __syncthreads();
+    }
+    const double rzn = bc[0], rrn = bc[1];
+    beta = bc[2];
+    rz = rzn;
+    const bool conv = rrn <= rtol2 * rr0;
+    if (vb == 0 && threadIdx.x == 0) {
+      a.scal[S_ALPHA] = alpha;
+      a.scal[S_BETA] = beta;
+      a.scal[S_RZ] = rzn;
+      a.scal[S_RR] = rrn;
+      a.flags[F_IT] += 1;
+      if (conv) a.flags[F_CONV] = 1;
+      if (!(rrn < INFINITY)) a.flags[F_BRK] = 1;
+    }
+    if (conv || !(rrn < INFINITY)) return;
+  }
+}
+
+// Barrier self-test: `rounds` barriers over a cooperative grid, each checking the fixed-order
+// totals of per-block partials; `absent` arrivals are counted as missing (the counter starts
+// at -absent), so absent > 0 makes every wait run out.
+__global__ void __launch_bounds__(kThreads) barrier_selftest_kernel(int rounds, GridBar* bar, double* part,
+                                                                    int* flags) {
+  __shared__ double sh[kThreads];
+  const int nvb = gridDim.x;
+  for (int r = 0; r < rounds; ++r) {
+    double* pb = part + (r & 1) * 2 * nvb;
+    if (threadIdx.x == 0) {
+      pb[2 * blockIdx.x] = 1.0;
+      pb[2 * blockIdx.x + 1] = (double)blockIdx.x;
+    }
+    if (!grid_barrier(&bar->count, (unsigned long long)(r + 1) * nvb, flags)) return;
+    double s0, s1;
+    sum_pairs(pb, nvb, sh, s0, s1);
+    if (threadIdx.x == 0 && (s0 != (double)nvb || s1 != 0.5 * nvb * (nvb - 1.0))) flags[F_BRK] = 1;
+  }
+}
+
+// ---- refinement helpers
+__global__ void __launch_bounds__(kThreads) face_jump_kernel(JumpArgs a) {
+  __shared__ double sh[32];
+  const int64_t n = a.n_faces * a.nfn;
+  double ss = 0.0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = r / a.nfn;
+    const int m = (int)(r - f * a.nfn);
+    const int lo = a.face_dof[2 * f], hi = a.face_dof[2 * f + 1];
+    const double ul = a.u[(int64_t)(lo / 6) * a.n_loc + a.ni + (lo % 6) * a.nfn + m];
+    const double uh = a.u[(int64_t)(hi / 6) * a.n_loc + a.ni + (hi % 6) * a.nfn + m];
+    const double v = a.wf[m] * (ul - uh);
+    a.rho[r] = v;
+    ss = fma(v, v, ss);
+  }
+  ss = block_sum(ss, sh);
+  if (threadIdx.x == 0) a.partial[blockIdx.x] = ss;
+  if (last_block(a.ticket, gridDim.x)) {
+    const double t = sum_partials(a.partial, gridDim.x, 1, 0, sh);
+    if (threadIdx.x == 0) {
+      *a.norm2 = t;
+      *a.ticket = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) norm2_kernel(int64_t n, const double* v, double* partial, double* out,
+                                                          int* ticket) {
+  __shared__ double sh[32];
+  double ss = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    ss = fma(v[i], v[i], ss);
+  ss = block_sum(ss, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = ss;
+  if (last_block(ticket, gridDim.x)) {
+    const double t = sum_partials(partial, gridDim.x, 1, 0, sh);
+    if (threadIdx.x == 0) {
+      *out = t;
+      *ticket = 0;
+    }
+  }
+}
+
+__global__ void axpy_kernel(int64_t n, const double* x, double* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
 }
 
 // ---- batched forms: block b works for problem blk_prob[b] as its block b - blk_first[that problem]
@@ -348,6 +685,91 @@ cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_
     prof_end(prof, tok, s);
   }
   return cudaGetLastError();
+}
+
+template <int NFN, int W>
+cudaError_t launch_fused(const PcgArgs& a, int count, double rtol, void* bar, cudaStream_t s) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_fused_kernel<NFN, W>, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  int grid = sms * per_sm;
+  if (grid > a.nblocks / 2) grid = a.nblocks / 2;         // two buffers of pairs: 4 * grid <= 2 * nblocks
+  if (grid < 1) return cudaErrorInvalidConfiguration;
+  PcgArgs aa = a;
+  double rtol2 = rtol * rtol;
+  GridBar* gb = static_cast<GridBar*>(bar);
+  void* params[] = {&aa, &count, &rtol2, &gb};
+  return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<NFN, W>, grid, kThreads, params, 0, s);
+}
+
+cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void* bar, cudaStream_t s, Prof* prof) {
+  const int tok = prof_begin(prof, HYB_K_PCG_FUSED, s);
+  cudaError_t e;
+  switch (a.nfn) {
+    case 1: e = launch_fused<1, 4>(a, count, rtol, bar, s); break;
+    case 4: e = launch_fused<4, 4>(a, count, rtol, bar, s); break;
+    case 9: e = launch_fused<9, 2>(a, count, rtol, bar, s); break;
+    case 16: e = launch_fused<16, 4>(a, count, rtol, bar, s); break;
+    default: e = cudaErrorInvalidValue;
+  }
+  prof_end(prof, tok, s);
+  return e;
+}
+
+cudaError_t launch_face_jump(const JumpArgs& a, cudaStream_t s, Prof* prof) {
+  const int tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
+  face_jump_kernel<<<a.nblocks, kThreads, 0, s>>>(a);
+  prof_end(prof, tok, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(int64_t n, const double* v, double* partial, int nblocks, double* out, int* ticket,
+                         cudaStream_t s, Prof* prof) {
+  const int tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
+  norm2_kernel<<<nblocks, kThreads, 0, s>>>(n, v, partial, out, ticket);
+  prof_end(prof, tok, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(int64_t n, const double* x, double* y, cudaStream_t s, Prof* prof) {
+  const int tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
+  axpy_kernel<<<152 * 4, kThreads, 0, s>>>(n, x, y);
+  prof_end(prof, tok, s);
+  return cudaGetLastError();
+}
+
+cudaError_t barrier_selftest(int absent, int rounds, cudaStream_t s, int* result) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, barrier_selftest_kernel, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  int grid = sms * per_sm;
+  if (grid < 1) return cudaErrorInvalidConfiguration;
+  // layout: bar (16 bytes) | flags (4 ints) | partials (two buffers of pairs)
+  char* buf = nullptr;
+  const size_t bytes = 16 + 16 + 4 * sizeof(double) * (size_t)grid;
+  e = cudaMalloc(&buf, bytes);
+  if (e != cudaSuccess) return e;
+  GridBar* bar = reinterpret_cast<GridBar*>(buf);
+  int* flags = reinterpret_cast<int*>(buf + 16);
+  double* part = reinterpret_cast<double*>(buf + 32);
+  const GridBar init{static_cast<unsigned long long>(-(long long)absent), 0ull};
+  int hf[4] = {0, 0, 0, 0};
+  e = cudaMemsetAsync(buf, 0, bytes, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bar, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    void* params[] = {&rounds, &bar, &part, &flags};
+    e = cudaLaunchCooperativeKernel((const void*)barrier_selftest_kernel, grid, kThreads, params, 0, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaError_t ef = cudaFree(buf);
+  if (e == cudaSuccess) e = ef;
+  *result = hf[F_BRK];
+  return e;
 }
 
 cudaError_t pcg_iterations_batch(const PcgBatch& b, int count, double rtol, cudaStream_t s, Prof* prof) {
@@ -455,5 +877,16 @@ extern "C" int hyb_pcg_solve_noalloc(const int64_t* row_ptr, const int32_t* col,
   if (rel_res) *rel_res = hs[1] > 0.0 ? std::sqrt(hs[2] / hs[1]) : 0.0;
   if (hf[2]) return HYB_ERR_BREAKDOWN;
   if (!hf[1]) return HYB_ERR_NOT_CONVERGED;
+  return HYB_OK;
+}
+
+extern "C" int hyb_barrier_selftest(int absent, int rounds, void* cuda_stream) {
+  using namespace hyb;
+  if (absent < 0 || absent > 1024 || rounds < 0) return HYB_ERR_INVALID_ARG;
+  int result = 0;
+  cudaError_t e = barrier_selftest(absent, rounds, static_cast<cudaStream_t>(cuda_stream), &result);
+  if (e != cudaSuccess) return HYB_ERR_CUDA;
+  if (result == 2) return HYB_ERR_TIMEOUT;
+  if (result != 0) return HYB_ERR_BREAKDOWN;
   return HYB_OK;
 }

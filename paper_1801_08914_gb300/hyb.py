@@ -27,7 +27,7 @@ HYB_ERR_OOM = -8
 HYB_ERR_TIMEOUT = -9
 HYB_FP64 = 0
 HYB_MIXED = 1
-KERNEL_CLASSES = {"element": 0, "spmv": 1, "pcg_vector": 2, "recover": 3, "setup": 4}
+KERNEL_CLASSES = {"element": 0, "spmv": 1, "pcg_vector": 2, "recover": 3, "setup": 4, "pcg_fused": 5}
 
 EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recover",
            "staticcond_assemble", "staticcond_recover", "hyb_get_reduced", "hyb_export_reduced", "hyb_get_sizes",
@@ -78,6 +78,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_destroy_batch.argtypes = [P]
     lib.hyb_destroy_batch.restype = None
     lib.hyb_set_profiling.argtypes = [P, I]
+    lib.hyb_set_pcg_fused.argtypes = [P, I]
+    lib.hyb_refine.argtypes = [P, I, D, I, P, P, ctypes.POINTER(D)]
+    lib.hyb_barrier_selftest.argtypes = [I, I, P]
     lib.hyb_get_profile.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
     lib.hyb_get_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I64),
                                   ctypes.POINTER(I64)]
@@ -248,6 +251,26 @@ def hyb_measure_fma_peak(fp64=True, stream=None):
     v = ctypes.c_double()
     _check(lib().hyb_measure_fma_peak(int(bool(fp64)), _stream(stream), ctypes.byref(v)), "hyb_measure_fma_peak")
     return v.value
+
+
+def hyb_refine(ctx, steps, inner_rtol, maxit, lam, u, check=True):
+    """FP64 refinement steps on (lambda, u); returns (||C u|| / ||g|| per step, status)."""
+    jump = (ctypes.c_double * (int(steps) + 1))()
+    st = lib().hyb_refine(ctx.handle, int(steps), float(inner_rtol), int(maxit), _ptr(lam, "lambda"),
+                          _ptr(u, "u"), jump)
+    if check:
+        _check(st, "hyb_refine")
+    return list(jump), st
+
+
+def hyb_set_pcg_fused(ctx, on):
+    """PCG launch form: True = one cooperative launch per 64 iterations, False = 3 per iteration."""
+    return _check(lib().hyb_set_pcg_fused(ctx.handle, int(bool(on))), "hyb_set_pcg_fused")
+
+
+def hyb_barrier_selftest(absent, rounds, stream=None):
+    """Status of the grid-barrier self-test (HYB_OK, or HYB_ERR_TIMEOUT when absent > 0)."""
+    return lib().hyb_barrier_selftest(int(absent), int(rounds), _stream(stream))
 
 
 def hyb_set_profiling(ctx, enable):
