@@ -217,6 +217,11 @@ def spmv_bytes(n, nnz, nfn):
     return 8 * nnz + 4 * nnz // nfn + 16 * (n // nfn) + 8 * n + 8 * n
 
 
+# DRAM bytes per PCG iteration of pcg_fused_kernel from one ncu capture of the unchanged kernel,
+# keyed by (config, mesh size, order); remove an entry when the kernel changes.
+FUSED_TRAFFIC = {(2, 32, 1): 163.0e6}
+
+
 def pcg_iteration_flops(n, nnz):
     """FP64 flops of one PCG iteration: SpMV (2 per nonzero), p^T q (2n), x and r updates (4n),
     z = D^-1 r (n), r^T z and r^T r (4n), p = z + beta p (2n)."""
@@ -396,7 +401,10 @@ def run_ours(args):
         roof = {"kernel": "pcg_fused_kernel (cooperative: SpMV + p^T H p, updates, reductions)", "bound": "alu",
                 "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf / fp64_peak,
                 "peak_source": "FP64 FMA throughput measured in this run (hyb_measure_fma_peak)",
-                "traffic": None, "unit_of_work": "one PCG iteration",
+                "traffic": FUSED_TRAFFIC.get((cfg, p.nx, p.order)), "unit_of_work": "one PCG iteration",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 64-iteration launch / 64 "
+                                  "(profiles/pcg_fused_kernel_32cube_rt1.md)" if (cfg, p.nx, p.order) in FUSED_TRAFFIC
+                                  else None,
                 "iterations_per_launch": it_total / max(1, fused_launches),
                 "algorithmic_flops_per_iteration": flops_it, "algorithmic_bytes_per_iteration": bytes_it,
                 "achieved_gbs": gb, "hbm_peak_gbs": hbm_peak, "hbm_frac": gb / hbm_peak,
