@@ -1023,12 +1023,33 @@ __global__ void __launch_bounds__(MX<K>::NT) recover_mixed_kernel_batch(const El
   recover_mixed_body<K>(a, it.y, lams[it.x], us[it.x], smem);
 }
 
+#include "hyb_mixed_tiled.cuh"
+
 template <int K>
 cudaError_t launch_mixed_batch_k(const ElemArgs* probs, const int2* items, int64_t n, int colour, bool recover,
                                  const double* const* lams, double* const* us, cudaStream_t s, Prof* prof) {
-  using S = MX<K>;
   if (n == 0) return cudaSuccess;
   cudaError_t err;
+  if constexpr (K >= 2) {
+    using S = MT<K>;
+    if (!recover) {
+      err = cudaFuncSetAttribute(element_tiled_kernel_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)S::SMEM);
+      if (err != cudaSuccess) return err;
+      const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+      element_tiled_kernel_batch<K><<<(unsigned)n, S::NT, S::SMEM, s>>>(probs, items, n, colour);
+      prof_end(prof, tok, s);
+    } else {
+      err = cudaFuncSetAttribute(recover_tiled_kernel_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)S::SMEM);
+      if (err != cudaSuccess) return err;
+      const int tok = prof_begin(prof, HYB_K_RECOVER, s);
+      recover_tiled_kernel_batch<K><<<(unsigned)n, S::NT, S::SMEM, s>>>(probs, lams, us, items, n);
+      prof_end(prof, tok, s);
+    }
+    return cudaGetLastError();
+  } else {
+  using S = MX<K>;
   if (!recover) {
     err = cudaFuncSetAttribute(element_mixed_kernel_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     if (err != cudaSuccess) return err;
@@ -1043,14 +1064,32 @@ cudaError_t launch_mixed_batch_k(const ElemArgs* probs, const int2* items, int64
     prof_end(prof, tok, s);
   }
   return cudaGetLastError();
+  }
 }
 
 template <int K>
 cudaError_t launch_mixed_k(const ElemArgs& a, cudaStream_t s, Prof* prof, bool recover, const double* lambda,
                            double* u) {
-  using S = MX<K>;
   if (a.n_list == 0) return cudaSuccess;
   cudaError_t err;
+  if constexpr (K >= 2) {
+    using S = MT<K>;
+    if (!recover) {
+      err = cudaFuncSetAttribute(element_tiled_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+      if (err != cudaSuccess) return err;
+      const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+      element_tiled_kernel<K><<<(unsigned)a.n_list, S::NT, S::SMEM, s>>>(a);
+      prof_end(prof, tok, s);
+    } else {
+      err = cudaFuncSetAttribute(recover_tiled_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+      if (err != cudaSuccess) return err;
+      const int tok = prof_begin(prof, HYB_K_RECOVER, s);
+      recover_tiled_kernel<K><<<(unsigned)a.n_list, S::NT, S::SMEM, s>>>(a, lambda, u);
+      prof_end(prof, tok, s);
+    }
+    return cudaGetLastError();
+  } else {
+  using S = MX<K>;
   if (!recover) {
     err = cudaFuncSetAttribute(element_mixed_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     if (err != cudaSuccess) return err;
@@ -1065,16 +1104,19 @@ cudaError_t launch_mixed_k(const ElemArgs& a, cudaStream_t s, Prof* prof, bool r
     prof_end(prof, tok, s);
   }
   return cudaGetLastError();
+  }
 }
 
 }  // namespace
 
+// FP32-path store per element: the untiled kernels keep L_M | Xd | L_Z | G^{-1} for the
+// recovery; the tiled kernels (RT_2, RT_3) recompute the factors and keep only G^{-1}.
 int64_t mixed_store_floats(int k) {
   switch (k) {
     case 0: return MX<0>::STORE;
     case 1: return MX<1>::STORE;
-    case 2: return MX<2>::STORE;
-    case 3: return MX<3>::STORE;
+    case 2: return (int64_t)MT<2>::NQK * MT<2>::NQK;
+    case 3: return (int64_t)MT<3>::NQK * MT<3>::NQK;
   }
   return 0;
 }

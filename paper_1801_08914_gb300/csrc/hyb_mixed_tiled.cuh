@@ -1,0 +1,908 @@
+// Tiled FP32 element elimination of the hybridized mixed form for RT_2 and RT_3
+// (arXiv:1801.08914, Sec. 3.2; the factorisation of Sec. 3.1 applied to the alpha mass M).
+// Included by hyb_mixed.cu inside namespace hyb { namespace { ... } }; it uses that
+// translation unit's FP64 helpers (geometry64, load_element64, apply_A64/D64/Dt64/G64) and
+// its constant tables.
+//
+// The same algebra as the untiled kernel:
+//    L_M = chol(M), Xd = L_M^{-1} D, L_Z = chol(G^{-1} + Xd^T Xd),
+//    Y = L_M,bb^{-1}, P = Xd_b^T Y, V = L_Z^{-1} P,  (A^{-1})_bb = Y^T Y - V^T V,
+// with the matrices held as TB x TB tiles in shared memory so that every step is a short
+// sequence of CTA-wide passes:
+//  * L_M and L_Z: packed lower tiles, column of tiles after column of tiles (tile (I, J),
+//    I >= J, at J T - J (J - 1) / 2 + I - J), column-major inside a tile. After the
+//    factorisation a diagonal tile holds the inverse of its triangle, which is what the
+//    panel step, the triangular solves and the inverse Y use.
+//  * Cholesky: right-looking by tile columns; per column one warp factors and inverts the
+//    diagonal tile, the CTA scales the panel (and the matching rows of the fused right-hand
+//    sides), and the CTA applies the rank-TB update to the trailing tiles with MR x MC
+//    register micro-tiles: three barriers per tile column.
+//  * Triangular solves with one right-hand side (the refinement): two barriers per tile.
+// TB divides both the interior and the face block of the local ordering (interior dofs
+// first), so the face block is a trailing square of whole tiles. The recovery recomputes the
+// factorisation instead of reading stored factors: that is fewer bytes than the factors
+// themselves (which would be ~200 KB per RT_3 element), and the element work is the cheap
+// part of this path.
+
+template <int K>
+struct TileShape;
+template <>
+struct TileShape<2> {
+  static constexpr int TB = 18, MR = 3, MC = 6, NT = 256;
+};
+template <>
+struct TileShape<3> {
+  static constexpr int TB = 16, MR = 4, MC = 4, NT = 512;
+};
+
+template <int K>
+struct MT {
+  using TS = TileShape<K>;
+  static constexpr int TB = TS::TB, MR = TS::MR, MC = TS::MC, NT = TS::NT;
+  static constexpr int P = K + 2, p = K + 1, Q = K + 2, NQ = Q * Q * Q;
+  static constexpr int NFN = p * p, NI = 3 * K * p * p, NB = 6 * NFN, N = NI + NB, NC = P * p * p;
+  static constexpr int NQK = p * p * p;
+  static constexpr int T = N / TB, TI = NI / TB, TQ = (NQK + TB - 1) / TB, NQP = TQ * TB;
+  static constexpr int TT = TB * TB;
+  static constexpr int LT = T * (T + 1) / 2 * TT;          // L_M tiles
+  static constexpr int ZTS = TQ * (TQ + 1) / 2 * TT;       // L_Z tiles
+  static constexpr int XD = N * NQP;                       // Xd, row-major, columns >= NQK zero
+  static constexpr int LT_INTERIOR = (TI * T - TI * (TI - 1) / 2) * TT;   // tile columns J < TI
+  static constexpr int YPS = 2 * NB * NB + NQP * NB;       // Y | S | P (= V) after the refinement
+  static constexpr bool YPS_IN_LT = YPS <= LT_INTERIOR;
+  static constexpr int TMP64 = P * Q * Q;
+  static constexpr int D64 = 24 + 24 + 2 * P * Q + p * Q + 2 * Q + NFN + 7 * NQ /*g6 gd*/ + 4 * N /*f x r ut*/ +
+                             3 * NQ /*U*/ + 3 * NQ /*Wv*/ + NQ /*Dv*/ + NC /*xc*/ + 2 * TMP64 + 8 + NQK /*qv*/ +
+                             (N > NQ ? N : NQ) /*rq*/ + P * p /*DcO64*/;
+  static constexpr int TABF = 2 * P * Q + p * Q + P * P * Q + P * p * Q + p * p * Q + P * p;
+  static constexpr int F32 = TABF + LT + XD + ZTS + N /*vec*/ + 2 * NQP /*tq tmpq*/ + 32 /*ybuf*/ + 8 /*flag*/ +
+                             (YPS_IN_LT ? 0 : YPS);
+  static constexpr size_t SMEM = sizeof(double) * D64 + sizeof(float) * F32 + sizeof(int) * N;
+  static_assert(N % TB == 0 && NI % TB == 0, "tiles must split the interior and face blocks");
+  static_assert(TB % MR == 0 && TB % MC == 0 && NQP % MC == 0 && NB % MC == 0, "micro-tile shape");
+  static_assert(TB <= 32, "one warp per diagonal tile");
+  // scratch before the factorisation (in the L_M region): G, its tiles, the G^{-1} solve,
+  // the sum-factorisation temporaries
+  static constexpr int GSCR = NQK * NQK + ZTS + NQP * NQP + Q * Q * p * p + Q * p * p * p * p + NQ;
+  static_assert(GSCR <= LT, "G scratch fits in the L_M region");
+  static constexpr int MSCR = 6 * NQ + Q * Q * P * P + Q * P * P * p * p;   // mass assembly temporaries
+  static_assert(MSCR <= XD, "mass scratch fits in the Xd region");
+};
+
+__device__ __forceinline__ int tcol(int I, int J, int T) { return J * T - J * (J - 1) / 2 + (I - J); }
+
+// ---- one warp: Cholesky of the lower triangle of a TB x TB column-major tile in place,
+// then replace it by the inverse of the factor (strict upper part zero). flag[0] = 1 on a bad
+// pivot (every lane leaves at the same step).
+template <int TB>
+__device__ void diag_factor_invert(float* D, float* rinv, float* flag) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < TB; ++k) {
+    const float d = D[k + k * TB];
+    if (!(d > 0.0f) || !(d < INFINITY)) {
+      if (lane == 0) flag[0] = 1.0f;
+      __syncwarp();
+      return;
+    }
+    const float r = dev::rsqrt_newton(d);
+    __syncwarp();
+    if (lane > k && lane < TB) D[lane + k * TB] *= r;
+    if (lane == k) {
+      D[k + k * TB] = d * r;
+      rinv[k] = r;                                   // 1 / L_kk
+    }
+    __syncwarp();
+    constexpr int W = TB;                            // trailing entries (i, l), k < l <= i
+    const int m = TB - k - 1;
+    for (int e = lane; e < m * m; e += 32) {
+      const int i = k + 1 + e / m, l = k + 1 + e % m;
+      if (l <= i) D[i + l * W] = fmaf(-D[i + k * W], D[l + k * W], D[i + l * W]);
+    }
+    __syncwarp();
+  }
+  // column c of L^{-1} in lane c (forward substitution on e_c)
+  float col[TB];
+  if (lane < TB) {
+#pragma unroll
+    for (int i = 0; i < TB; ++i) {
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < i; ++k) s = fmaf(D[i + k * TB], col[k], s);
+      col[i] = i < lane ? 0.0f : (i == lane ? rinv[i] : -s * rinv[i]);
+    }
+  }
+  __syncwarp();
+  if (lane < TB) {
+#pragma unroll
+    for (int i = 0; i < TB; ++i) D[i + lane * TB] = col[i];
+  }
+  __syncwarp();
+}
+
+// ---- CTA: X_J <- Dinv_J X_J (rows J TB .. of X, row-major with ld MX), one thread per column.
+template <int TB, int NT>
+__device__ __forceinline__ void scale_rows_item(const float* Dv, float* XJ, int MX, int cx) {
+  float x[TB];
+#pragma unroll
+  for (int k = 0; k < TB; ++k) x[k] = XJ[k * MX + cx];
+#pragma unroll
+  for (int r = 0; r < TB; ++r) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k <= r; ++k) s = fmaf(Dv[r + k * TB], x[k], s);
+    XJ[r * MX + cx] = s;
+  }
+}
+
+// ---- micro-tile: C (MR x MC block at r0, c0) -= A(rows r0..) * B(rows c0..)^T, K dim TB,
+// A and B column-major TB x TB tiles; C column-major with leading dimension TB.
+template <int TB, int MR, int MC>
+__device__ __forceinline__ void syrk_micro(const float* A, const float* B, float* C, int r0, int c0) {
+  float acc[MR][MC];
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
+#pragma unroll 2
+  for (int k = 0; k < TB; ++k) {
+    float a[MR], b[MC];
+#pragma unroll
+    for (int i = 0; i < MR; ++i) a[i] = A[r0 + i + k * TB];
+#pragma unroll
+    for (int j = 0; j < MC; ++j) b[j] = B[c0 + j + k * TB];
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+      for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int j = 0; j < MC; ++j) C[(r0 + i) + (c0 + j) * TB] -= acc[i][j];
+}
+
+// ---- micro-tile: XI (MR x MC block at r0, c0; row-major, ld MX) -= A(rows r0..) * XJ, K dim TB
+template <int TB, int MR, int MC>
+__device__ __forceinline__ void gemm_x_micro(const float* A, const float* XJ, float* XI, int MX, int r0, int c0) {
+  float acc[MR][MC];
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
+#pragma unroll 2
+  for (int k = 0; k < TB; ++k) {
+    float a[MR], b[MC];
+#pragma unroll
+    for (int i = 0; i < MR; ++i) a[i] = A[r0 + i + k * TB];
+#pragma unroll
+    for (int j = 0; j < MC; ++j) b[j] = XJ[k * MX + c0 + j];
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+      for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int j = 0; j < MC; ++j) XI[(r0 + i) * MX + c0 + j] -= acc[i][j];
+}
+
+// ---- CTA: blocked Cholesky of T x T tiles (packed by tile columns) fused with
+// X <- L^{-1} X (T TB rows, ld MX; X may be null). Returns false in every thread on a bad pivot.
+template <int TB, int MR, int MC, int NT>
+__device__ bool tile_chol(float* Lt, int T, float* X, int MX, float* rinv, float* flag) {
+  constexpr int TT = TB * TB;
+  const int tid = threadIdx.x;
+  if (tid == 0) flag[0] = 0.0f;
+  __syncthreads();
+  for (int J = 0; J < T; ++J) {
+    float* Dv = Lt + tcol(J, J, T) * TT;
+    if (tid < 32) diag_factor_invert<TB>(Dv, rinv, flag);
+    __syncthreads();
+    if (flag[0] != 0.0f) return false;
+    // panel: A_IJ <- A_IJ Dinv^T (one thread per row), X_J <- Dinv X_J (one thread per column)
+    const int nrows = (T - J - 1) * TB, ncols = X ? MX : 0;
+    for (int it = tid; it < nrows + ncols; it += NT) {
+      if (it < nrows) {
+        float* A = Lt + tcol(J + 1 + it / TB, J, T) * TT;
+        const int r = it % TB;
+        float a[TB];
+#pragma unroll
+        for (int k = 0; k < TB; ++k) a[k] = A[r + k * TB];
+#pragma unroll
+        for (int c = 0; c < TB; ++c) {
+          float s = 0.0f;
+#pragma unroll
+          for (int k = 0; k <= c; ++k) s = fmaf(a[k], Dv[c + k * TB], s);
+          A[r + c * TB] = s;
+        }
+      } else {
+        scale_rows_item<TB, NT>(Dv, X + J * TB * MX, MX, it - nrows);
+      }
+    }
+    __syncthreads();
+    // trailing update of the tiles (I, K2), J < K2 <= I, and of the rows I > J of X
+    const int m = T - J - 1;
+    constexpr int PM = (TB / MR) * (TB / MC);
+    const int npair = m * (m + 1) / 2 * PM;
+    const int xm = (TB / MR) * (MX / MC);
+    const int nx = X ? m * xm : 0;
+    for (int it = tid; it < npair + nx; it += NT) {
+      if (it < npair) {
+        const int q = it / PM, u = it % PM;
+        int ip = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
+        while ((ip + 1) * (ip + 2) / 2 <= q) ++ip;
+        while (ip * (ip + 1) / 2 > q) --ip;
+        const int kp = q - ip * (ip + 1) / 2;
+        const int I = J + 1 + ip, K2 = J + 1 + kp;
+        syrk_micro<TB, MR, MC>(Lt + tcol(I, J, T) * TT, Lt + tcol(K2, J, T) * TT, Lt + tcol(I, K2, T) * TT,
+                               (u / (TB / MC)) * MR, (u % (TB / MC)) * MC);
+      } else {
+        const int it2 = it - npair, ti = it2 / xm, u = it2 % xm;
+        const int I = J + 1 + ti;
+        gemm_x_micro<TB, MR, MC>(Lt + tcol(I, J, T) * TT, X + J * TB * MX, X + I * TB * MX, MX,
+                                 (u / (MX / MC)) * MR, (u % (MX / MC)) * MC);
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// ---- CTA: X <- L^{-1} X for the tiles J0..T-1 of a factored L (diagonal tiles inverted);
+// X holds the rows of those tiles ((J - J0) TB + r), ld MX.
+template <int TB, int MR, int MC, int NT>
+__device__ void tile_fwd_mat(const float* Lt, int T, int J0, float* X, int MX) {
+  constexpr int TT = TB * TB;
+  const int tid = threadIdx.x;
+  for (int J = J0; J < T; ++J) {
+    const float* Dv = Lt + tcol(J, J, T) * TT;
+    float* XJ = X + (J - J0) * TB * MX;
+    for (int cx = tid; cx < MX; cx += NT) scale_rows_item<TB, NT>(Dv, XJ, MX, cx);
+    __syncthreads();
+    const int m = T - J - 1, xm = (TB / MR) * (MX / MC);
+    for (int it = tid; it < m * xm; it += NT) {
+      const int ti = it / xm, u = it % xm;
+      const int I = J + 1 + ti;
+      gemm_x_micro<TB, MR, MC>(Lt + tcol(I, J, T) * TT, XJ, X + (I - J0) * TB * MX, MX, (u / (MX / MC)) * MR,
+                               (u % (MX / MC)) * MC);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- CTA: X <- L^{-T} X (all T tiles), X row-major with ld MX (small systems: G^{-1}).
+template <int TB, int NT>
+__device__ void tile_bwd_mat(const float* Lt, int T, float* X, int MX) {
+  constexpr int TT = TB * TB;
+  const int tid = threadIdx.x;
+  for (int J = T - 1; J >= 0; --J) {
+    const float* Dv = Lt + tcol(J, J, T) * TT;
+    float* XJ = X + J * TB * MX;
+    for (int cx = tid; cx < MX; cx += NT) {          // X_J <- Dinv^T X_J
+      float x[TB];
+#pragma unroll
+      for (int k = 0; k < TB; ++k) x[k] = XJ[k * MX + cx];
+#pragma unroll
+      for (int c = 0; c < TB; ++c) {
+        float s = 0.0f;
+#pragma unroll
+        for (int r = c; r < TB; ++r) s = fmaf(Dv[r + c * TB], x[r], s);
+        XJ[c * MX + cx] = s;
+      }
+    }
+    __syncthreads();
+    for (int it = tid; it < J * TB * MX; it += NT) {   // X_K2 -= L_J,K2^T X_J
+      const int row = it / MX, cx = it % MX;
+      const int K2 = row / TB, c = row % TB;
+      const float* L = Lt + tcol(J, K2, T) * TT;
+      float s = 0.0f;
+#pragma unroll
+      for (int r = 0; r < TB; ++r) s = fmaf(L[r + c * TB], XJ[r * MX + cx], s);
+      X[row * MX + cx] -= s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- CTA: v <- L^{-1} v (one right-hand side, T TB entries)
+template <int TB, int NT>
+__device__ void tile_fwd_vec(const float* Lt, int T, float* v) {
+  constexpr int TT = TB * TB;
+  const int tid = threadIdx.x;
+  for (int J = 0; J < T; ++J) {
+    const float* Dv = Lt + tcol(J, J, T) * TT;
+    float* vJ = v + J * TB;
+    if (tid < 32) {
+      float y = 0.0f;
+      if (tid < TB) {
+#pragma unroll
+        for (int k = 0; k < TB; ++k)
+          if (k <= tid) y = fmaf(Dv[tid + k * TB], vJ[k], y);
+      }
+      __syncwarp();
+      if (tid < TB) vJ[tid] = y;
+    }
+    __syncthreads();
+    for (int i = tid; i < (T - J - 1) * TB; i += NT) {
+      const int I = J + 1 + i / TB, r = i % TB;
+      const float* L = Lt + tcol(I, J, T) * TT;
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < TB; ++k) s = fmaf(L[r + k * TB], vJ[k], s);
+      v[I * TB + r] -= s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- CTA: v <- L^{-T} v
+template <int TB, int NT>
+__device__ void tile_bwd_vec(const float* Lt, int T, float* v) {
+  constexpr int TT = TB * TB;
+  const int tid = threadIdx.x;
+  for (int J = T - 1; J >= 0; --J) {
+    const float* Dv = Lt + tcol(J, J, T) * TT;
+    float* vJ = v + J * TB;
+    if (tid < 32) {
+      float x = 0.0f;
+      if (tid < TB) {
+#pragma unroll
+        for (int r = 0; r < TB; ++r)
+          if (r >= tid) x = fmaf(Dv[r + tid * TB], vJ[r], x);
+      }
+      __syncwarp();
+      if (tid < TB) vJ[tid] = x;
+    }
+    __syncthreads();
+    for (int i = tid; i < J * TB; i += NT) {          // v_K2 -= L_J,K2^T x_J
+      const int K2 = i / TB, c = i % TB;
+      const float* L = Lt + tcol(J, K2, T) * TT;
+      float s = 0.0f;
+#pragma unroll
+      for (int t = 0; t < TB; ++t) {
+        const int r = (c + t) % TB;                  // rotated start: no bank conflicts across c
+        s = fmaf(L[r + c * TB], vJ[r], s);
+      }
+      v[i] -= s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- CTA: one FP32 solve of the mixed-form saddle system with the tiled factors.
+// In: v = r1 (N), t = rho (NQK, padded to NQP with zeros). Out: v = dx, t = dq, where
+//   y = L_M^{-1} r1,  dq = Z^{-1} (G^{-1} rho + Xd^T y),  dx = L_M^{-T} (y - Xd dq).
+template <int K>
+__device__ void mixed_solve_tiled(const float* Lt, const float* Xd, const float* Zt, const float* Gi, float* v,
+                                  float* t, float* tmp) {
+  using S = MT<K>;
+  constexpr int N = S::N, NQK = S::NQK, NQP = S::NQP, NT = S::NT;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  tile_fwd_vec<S::TB, NT>(Lt, S::T, v);
+  for (int a = warp; a < NQP; a += NT / 32) {
+    float acc = 0.0f;
+    if (a < NQK) {
+      for (int b = lane; b < NQK; b += 32) acc = fmaf(Gi[a * NQK + b], t[b], acc);
+      for (int i = lane; i < N; i += 32) acc = fmaf(Xd[i * NQP + a], v[i], acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) tmp[a] = acc;
+  }
+  __syncthreads();
+  for (int a = tid; a < NQP; a += NT) t[a] = tmp[a];
+  __syncthreads();
+  tile_fwd_vec<S::TB, NT>(Zt, S::TQ, t);
+  tile_bwd_vec<S::TB, NT>(Zt, S::TQ, t);
+  for (int i = tid; i < N; i += NT) {
+    float acc = v[i];
+    for (int a = 0; a < NQK; ++a) acc = fmaf(-Xd[i * NQP + a], t[a], acc);
+    v[i] = acc;
+  }
+  __syncthreads();
+  tile_bwd_vec<S::TB, NT>(Lt, S::T, v);
+}
+
+// ---- refinement of the element solve in the mixed variables (x, q = G D^T x) against FP64
+// residuals, as in the untiled kernel, with the tiled FP32 solve.
+template <int K>
+__device__ void refine_tiled(const double* f, double* x, double* q, int steps, double alpha, double beta, int bmask,
+                             const double* g6, const double* gd, const double* Vc, const double* Dc, const double* Vo,
+                             const double* DcO64, const int* dofcode, const float* Lt, const float* Xd,
+                             const float* Zt, const float* Gi, double* r, double* ut, double* rq, double* U,
+                             double* Wv, double* Dv, double* xc, double* t1, double* t2, float* vec, float* tq,
+                             float* tmp) {
+  using S = MT<K>;
+  constexpr int NI = S::NI, NFN = S::NFN, N = S::N, NQK = S::NQK, NQP = S::NQP, NT = S::NT;
+  const int tid = threadIdx.x;
+  auto is_e = [&](int i) { return i >= NI && ((bmask >> ((i - NI) / NFN)) & 1); };
+  for (int i = tid; i < N; i += NT) x[i] = 0.0;
+  for (int a = tid; a < NQK; a += NT) q[a] = 0.0;
+  __syncthreads();
+  for (int it = 0; it <= steps; ++it) {
+    for (int i = tid; i < N; i += NT) ut[i] = is_e(i) ? 0.0 : x[i];
+    __syncthreads();
+    apply_A64<K, NT>(ut, r, alpha, 0.0, false, g6, gd, Vc, Dc, Vo, U, Wv, Dv, xc, t1, t2);
+    apply_D64<K, NT>(q, rq, dofcode, DcO64, bmask);
+    for (int i = tid; i < N; i += NT) vec[i] = (float)(is_e(i) ? f[i] - x[i] : f[i] - r[i] - rq[i]);
+    __syncthreads();
+    apply_Dt64<K, NT>(ut, rq, DcO64, bmask);
+    apply_G64<K, NT>(rq, r, beta, gd, Vo, U, t1, t2);
+    for (int a = tid; a < NQP; a += NT) tq[a] = a < NQK ? (float)(r[a] - q[a]) : 0.0f;
+    __syncthreads();
+    mixed_solve_tiled<K>(Lt, Xd, Zt, Gi, vec, tq, tmp);
+    for (int i = tid; i < N; i += NT) x[i] += (double)vec[i];
+    for (int a = tid; a < NQK; a += NT) q[a] += (double)tq[a];
+    __syncthreads();
+  }
+}
+
+// ---- the element: factorisation (both modes), then either S_T / g_T (assembly) or the
+// recovery u_T = A^{-1}(f_T - C_T^T lambda).
+template <int K, bool RECOVER>
+__device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double* smem, const double* lambda,
+                                   double* u_out) {
+  using S = MT<K>;
+  constexpr int P = S::P, p = S::p, Q = S::Q, NQ = S::NQ, NFN = S::NFN, NI = S::NI, NB = S::NB, N = S::N;
+  constexpr int NQK = S::NQK, NQP = S::NQP, NT = S::NT, NC = S::NC, TB = S::TB, MR = S::MR, MC = S::MC;
+  constexpr int T = S::T, TQ = S::TQ, TT = S::TT;
+  const int tid = threadIdx.x;
+  const int64_t slot = args.slot ? args.slot[e] : e;
+  float* Gi = args.Lstore32 + slot * (int64_t)(NQK * NQK);      // G^{-1}, global scratch of this element
+
+  // ---- shared memory
+  double* d = smem;
+  double* X8 = d; d += 24;
+  double* Mc = d; d += 24;
+  double* Vc = d; d += P * Q;
+  double* Dc = d; d += P * Q;
+  double* Vo = d; d += p * Q;
+  double* qx = d; d += Q;
+  double* qw = d; d += Q;
+  double* wf = d; d += NFN;
+  double* g6 = d; d += 6 * NQ;
+  double* gd = d; d += NQ;
+  double* f = d; d += N;
+  double* x = d; d += N;
+  double* r = d; d += N;
+  double* ut = d; d += N;
+  double* U = d; d += 3 * NQ;
+  double* Wv = d; d += 3 * NQ;
+  double* Dv = d; d += NQ;
+  double* xc = d; d += NC;
+  double* t1 = d; d += S::TMP64;
+  double* t2 = d; d += S::TMP64;
+  d += 8;
+  double* qv = d; d += NQK;
+  double* rq = d; d += (N > NQ ? N : NQ);
+  double* DcO64 = d; d += P * p;
+  float* fl = reinterpret_cast<float*>(d);
+  float* Vcf = fl; fl += P * Q;
+  float* Dcf = fl; fl += P * Q;
+  float* Vof = fl; fl += p * Q;
+  float* VcVc = fl; fl += P * P * Q;
+  float* VcVo = fl; fl += P * p * Q;
+  float* VoVo = fl; fl += p * p * Q;
+  float* DcO = fl; fl += P * p;
+  float* Lt = fl; fl += S::LT;
+  float* Xd = fl; fl += S::XD;
+  float* Zt = fl; fl += S::ZTS;
+  float* vec = fl; fl += N;
+  float* tq = fl; fl += NQP;
+  float* tmpq = fl; fl += NQP;
+  float* rinv = fl; fl += 32;
+  float* flag = fl; fl += 8;
+  float* yps = S::YPS_IN_LT ? Lt : fl;
+  if (!S::YPS_IN_LT) fl += S::YPS;
+  int* dofcode = reinterpret_cast<int*>(fl);
+
+  load_element64<K, NT>(args, e, X8, Mc, Vc, Dc, Vo, qx, qw, wf);
+  const RefTables& rt = c_refm[K];
+  for (int i = tid; i < P * p; i += NT) DcO64[i] = rt.DcO[i / p][i % p];
+  for (int i = tid; i < P * Q; i += NT) { Vcf[i] = (float)Vc[i]; Dcf[i] = (float)Dc[i]; }
+  for (int i = tid; i < p * Q; i += NT) Vof[i] = (float)Vo[i];
+  for (int i = tid; i < P * p; i += NT) DcO[i] = (float)rt.DcO[i / p][i % p];
+  for (int t = tid; t < 3 * NC; t += NT) {
+    const int c = t / NC, fi = t % NC;
+    const int n0 = c == 0 ? P : p, n1 = c == 1 ? P : p;
+    const int i0 = fi % n0, i1 = (fi / n0) % n1, i2 = fi / (n0 * n1);
+    dofcode[local_index<K>(c, i0, i1, i2)] = c | (i0 << 2) | (i1 << 8) | (i2 << 14);
+  }
+  __syncthreads();
+  for (int i = tid; i < P * P * Q; i += NT) {
+    const int q = i % Q, b = (i / Q) % P, a = i / (Q * P);
+    VcVc[i] = Vcf[a * Q + q] * Vcf[b * Q + q];
+  }
+  for (int i = tid; i < P * p * Q; i += NT) {
+    const int q = i % Q, b = (i / Q) % p, a = i / (Q * p);
+    VcVo[i] = Vcf[a * Q + q] * Vof[b * Q + q];
+  }
+  for (int i = tid; i < p * p * Q; i += NT) {
+    const int q = i % Q, b = (i / Q) % p, a = i / (Q * p);
+    VoVo[i] = Vof[a * Q + q] * Vof[b * Q + q];
+  }
+  geometry64<K, NT>(Mc, qx, qw, g6, gd, args.status, args.err_elem, e);
+  const double alpha = args.alpha[e], beta = args.beta[e];
+  const int32_t* ef = args.elem_face + e * 6;
+  int bmask = 0;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) bmask |= (ef[a] < 0) << a;
+  auto is_e = [&](int i) { return i >= NI && ((bmask >> ((i - NI) / NFN)) & 1); };
+
+  // ---- FP64 right-hand side: assembly forms f = M c (essential values folded in) and keeps
+  // it for the recovery; the recovery reads it back and subtracts C^T lambda
+  double* fs = args.zstore + e * (int64_t)N;
+  if (!RECOVER) {
+    const double* coef = args.load + e * (int64_t)N;
+    for (int i = tid; i < N; i += NT) ut[i] = coef[i];
+    __syncthreads();
+    apply_A64<K, NT>(ut, f, 1.0, 0.0, false, g6, gd, Vc, Dc, Vo, U, Wv, Dv, xc, t1, t2);
+    if (bmask) {
+      const double* ue = args.ess ? args.ess + e * (int64_t)N : nullptr;
+      if (ue) {
+        for (int i = tid; i < N; i += NT) ut[i] = is_e(i) ? ue[i] : 0.0;
+        __syncthreads();
+        apply_A64<K, NT>(ut, r, alpha, beta, true, g6, gd, Vc, Dc, Vo, U, Wv, Dv, xc, t1, t2);
+        for (int i = tid; i < N; i += NT) f[i] = is_e(i) ? ue[i] : f[i] - r[i];
+      } else {
+        for (int i = tid; i < N; i += NT)
+          if (is_e(i)) f[i] = 0.0;
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < N; i += NT) fs[i] = f[i];
+  } else {
+    for (int i = tid; i < N; i += NT) {
+      double v = fs[i];
+      if (i >= NI) {
+        const int a = (i - NI) / NFN, m = (i - NI) % NFN;
+        if (ef[a] >= 0) v -= ((a & 1) ? 1.0 : -1.0) * wf[m] * lambda[(int64_t)ef[a] * NFN + m];
+      }
+      f[i] = v;                                  // f_T - C_T^T lambda
+    }
+  }
+
+  // ---- G (Q_k mass weighted by beta / det J), its tiled Cholesky, G^{-1} -> global scratch.
+  // Scratch in the L_M region, which is free until the mass assembly.
+  {
+    float* Gf = Lt;                               // [NQK][NQK]
+    float* Gt = Gf + NQK * NQK;                   // tiles of the padded G
+    float* Xg = Gt + S::ZTS;                      // [NQP][NQP]: identity -> L^{-1} -> G^{-1}
+    float* T1 = Xg + NQP * NQP;                   // [Q][Q][p][p]
+    float* T2 = T1 + Q * Q * p * p;               // [Q][p^4]
+    float* Gd32 = T2 + Q * p * p * p * p;         // [NQ]
+    for (int q = tid; q < NQ; q += NT) Gd32[q] = (float)(beta * gd[q]);
+    __syncthreads();
+    for (int t = tid; t < Q * Q * p * p; t += NT) {
+      const int b0 = t % p, a0 = (t / p) % p, q1 = (t / (p * p)) % Q, q2 = t / (p * p * Q);
+      float acc = 0.f;
+      for (int q0 = 0; q0 < Q; ++q0) acc = fmaf(Gd32[(q2 * Q + q1) * Q + q0], VoVo[(a0 * p + b0) * Q + q0], acc);
+      T1[t] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < Q * p * p * p * p; t += NT) {
+      const int b0 = t % p, a0 = (t / p) % p, b1 = (t / (p * p)) % p, a1 = (t / (p * p * p)) % p, q2 = t / (p * p * p * p);
+      float acc = 0.f;
+      for (int q1 = 0; q1 < Q; ++q1) acc = fmaf(T1[((q2 * Q + q1) * p + a0) * p + b0], VoVo[(a1 * p + b1) * Q + q1], acc);
+      T2[t] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < NQK * NQK; t += NT) {
+      const int a = t / NQK, b = t % NQK;
+      const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
+      const int b0 = b % p, b1 = (b / p) % p, b2 = b / (p * p);
+      float acc = 0.f;
+      for (int q2 = 0; q2 < Q; ++q2)
+        acc = fmaf(T2[(((q2 * p + a1) * p + b1) * p + a0) * p + b0], VoVo[(a2 * p + b2) * Q + q2], acc);
+      Gf[t] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < S::ZTS; t += NT) {      // pack the lower tiles of [[G, 0], [0, I]]
+      const int tile = t / TT, w = t % TT, rr = w % TB, cc = w / TB;
+      int J = 0, rem = tile;
+      while (rem >= TQ - J) { rem -= TQ - J; ++J; }
+      const int I = J + rem, i = I * TB + rr, j = J * TB + cc;
+      Gt[t] = (i < NQK && j < NQK) ? Gf[i * NQK + j] : (i == j ? 1.0f : 0.0f);
+    }
+    for (int t = tid; t < NQP * NQP; t += NT) Xg[t] = (t / NQP == t % NQP) ? 1.0f : 0.0f;
+    __syncthreads();
+    if (!tile_chol<TB, MR, MC, NT>(Gt, TQ, Xg, NQP, rinv, flag)) {
+      if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
+      return;
+    }
+    tile_bwd_mat<TB, NT>(Gt, TQ, Xg, NQP);
+    for (int t = tid; t < NQK * NQK; t += NT) Gi[t] = Xg[(t / NQK) * NQP + t % NQK];
+    __syncthreads();
+  }
+
+  // ---- FP32 alpha-mass M into the L_M tiles (lower triangle), essential rows -> identity.
+  // Temporaries in the Xd region, which is free until D' is written.
+  for (int t = tid; t < S::LT; t += NT) Lt[t] = 0.0f;
+  __syncthreads();
+  {
+    float* Ga32 = Xd;                             // [6][NQ]
+    float* T1 = Xd + 6 * NQ;
+    float* T2 = T1 + Q * Q * P * P;
+    for (int t = tid; t < 6 * NQ; t += NT) Ga32[t] = (float)(alpha * g6[t]);
+    __syncthreads();
+    for (int blk = 0; blk < 6; ++blk) {
+      const int c = blk < 3 ? blk : (blk == 3 ? 1 : 2);
+      const int cp = blk < 3 ? blk : (blk == 5 ? 1 : 0);
+      const bool diag = c == cp;
+      const int da = c, db = diag ? (c + 1) % 3 : cp, dL = 3 - da - db;
+      const int nia = P, nja = diag ? P : p, nib = p, njb = diag ? p : P;
+      const int sa = da == 0 ? 1 : da == 1 ? Q : Q * Q;
+      const int sb = db == 0 ? 1 : db == 1 ? Q : Q * Q;
+      const int sL = dL == 0 ? 1 : dL == 1 ? Q : Q * Q;
+      const float* Gm = Ga32 + gslot(c, cp) * NQ;
+      const float* Pm = diag ? VcVc : VcVo;
+      const int n1 = Q * Q * nia * nja;
+      for (int idx = tid; idx < n1; idx += NT) {
+        int rr = idx;
+        const int ja = rr % nja; rr /= nja;
+        const int ia = rr % nia; rr /= nia;
+        const int qL = rr % Q, qb = rr / Q;
+        float acc = 0.f;
+        for (int qa = 0; qa < Q; ++qa) acc = fmaf(Gm[qa * sa + qb * sb + qL * sL], Pm[(ia * nja + ja) * Q + qa], acc);
+        T1[idx] = acc;
+      }
+      __syncthreads();
+      const int n2 = Q * nia * nja * nib * njb;
+      for (int idx = tid; idx < n2; idx += NT) {
+        int rr = idx;
+        const int jb = rr % njb; rr /= njb;
+        const int ib = rr % nib; rr /= nib;
+        const int ja = rr % nja; rr /= nja;
+        const int ia = rr % nia, qL = rr / nia;
+        float acc = 0.f;
+        for (int qb = 0; qb < Q; ++qb) {
+          const float tv = T1[((qb * Q + qL) * nia + ia) * nja + ja];
+          acc = fmaf(tv, diag ? VoVo[(ib * p + jb) * Q + qb] : VcVo[(jb * p + ib) * Q + qb], acc);
+        }
+        T2[idx] = acc;
+      }
+      __syncthreads();
+      const int s2 = nia * nja * nib * njb;
+      for (int idx = tid; idx < s2 * p * p; idx += NT) {
+        int rr = idx;
+        const int jL = rr % p; rr /= p;
+        const int iL = rr % p; rr /= p;
+        const int jb = rr % njb; rr /= njb;
+        const int ib = rr % nib; rr /= nib;
+        const int ja = rr % nja, ia = rr / nja;
+        const int i0 = da == 0 ? ia : db == 0 ? ib : iL, i1 = da == 1 ? ia : db == 1 ? ib : iL;
+        const int i2 = da == 2 ? ia : db == 2 ? ib : iL;
+        const int j0 = da == 0 ? ja : db == 0 ? jb : jL, j1 = da == 1 ? ja : db == 1 ? jb : jL;
+        const int j2 = da == 2 ? ja : db == 2 ? jb : jL;
+        const int ra = local_index<K>(c, i0, i1, i2), sa2 = local_index<K>(cp, j0, j1, j2);
+        if (diag && ra < sa2) continue;
+        const int tt = ((ia * nja + ja) * nib + ib) * njb + jb;
+        float acc = 0.f;
+        for (int qL = 0; qL < Q; ++qL) acc = fmaf(T2[qL * s2 + tt], VoVo[(iL * p + jL) * Q + qL], acc);
+        const int gi = ra >= sa2 ? ra : sa2, gj = ra >= sa2 ? sa2 : ra;
+        Lt[tcol(gi / TB, gj / TB, T) * TT + (gi % TB) + (gj % TB) * TB] = acc;
+      }
+      __syncthreads();
+    }
+    if (bmask) {
+      for (int t = tid; t < NB * N; t += NT) {   // essential rows and columns -> identity
+        const int i = NI + t / N, j = t % N;
+        if (!is_e(i)) continue;
+        const int gi = i >= j ? i : j, gj = i >= j ? j : i;
+        Lt[tcol(gi / TB, gj / TB, T) * TT + (gi % TB) + (gj % TB) * TB] = (i == j) ? 1.f : 0.f;
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- D' (zero rows on essential dofs, zero columns beyond NQK) into Xd, then the tiled
+  // Cholesky of M fused with Xd <- L_M^{-1} D'
+  for (int t = tid; t < N * NQP; t += NT) {
+    const int i = t / NQP, a = t % NQP;
+    float v = 0.f;
+    if (a < NQK && !is_e(i)) {
+      const int code = dofcode[i];
+      const int c = code & 3, i0 = (code >> 2) & 63, i1 = (code >> 8) & 63, i2 = (code >> 14) & 63;
+      const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
+      const bool match = (c == 0 || i0 == a0) && (c == 1 || i1 == a1) && (c == 2 || i2 == a2);
+      if (match) v = DcO[(c == 0 ? i0 : c == 1 ? i1 : i2) * p + (c == 0 ? a0 : c == 1 ? a1 : a2)];
+    }
+    Xd[t] = v;
+  }
+  __syncthreads();
+  if (!tile_chol<TB, MR, MC, NT>(Lt, T, Xd, NQP, rinv, flag)) {
+    if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
+    return;
+  }
+  // ---- Z = G^{-1} + Xd^T Xd (padded with the identity) into the L_Z tiles, then its Cholesky
+  {
+    constexpr int PM = (TB / MR) * (TB / MC);
+    constexpr int NP = TQ * (TQ + 1) / 2;
+    for (int it = tid; it < NP * PM; it += NT) {
+      const int tile = it / PM, u = it % PM;
+      int J = 0, rem = tile;
+      while (rem >= TQ - J) { rem -= TQ - J; ++J; }
+      const int I = J + rem;
+      const int r0 = (u / (TB / MC)) * MR, c0 = (u % (TB / MC)) * MC;
+      float acc[MR][MC];
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
+      for (int k = 0; k < N; ++k) {
+        float a[MR], b[MC];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) a[i] = Xd[k * NQP + I * TB + r0 + i];
+#pragma unroll
+        for (int j = 0; j < MC; ++j) b[j] = Xd[k * NQP + J * TB + c0 + j];
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+          for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      float* Zq = Zt + tile * TT;
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MC; ++j) {
+          const int gi = I * TB + r0 + i, gj = J * TB + c0 + j;
+          const float g = (gi < NQK && gj < NQK) ? Gi[gi * NQK + gj] : (gi == gj ? 1.0f : 0.0f);
+          Zq[(r0 + i) + (c0 + j) * TB] = acc[i][j] + g;
+        }
+    }
+    __syncthreads();
+    if (!tile_chol<TB, MR, MC, NT>(Zt, TQ, nullptr, 0, rinv, flag)) {
+      if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
+      return;
+    }
+  }
+
+  // ---- the refined element solve: g_T (assembly) or u_T (recovery)
+  refine_tiled<K>(f, x, qv, 3, alpha, beta, bmask, g6, gd, Vc, Dc, Vo, DcO64, dofcode, Lt, Xd, Zt, Gi, r, ut, rq,
+                  U, Wv, Dv, xc, t1, t2, vec, tq, tmpq);
+  if (RECOVER) {
+    double* ue = u_out + e * (int64_t)N;
+    for (int i = tid; i < N; i += NT) ue[i] = x[i];
+    return;
+  }
+  for (int ib = tid; ib < NB; ib += NT) {
+    const int a = ib / NFN, m1 = ib % NFN;
+    if (ef[a] < 0) continue;
+    const double v = ((a & 1) ? 1.0 : -1.0) * wf[m1] * x[NI + ib];
+    const int64_t gi = (int64_t)ef[a] * NFN + m1;
+    if (args.colour == 1) args.rhs[gi] += v;
+    else args.rhs[gi] = v;
+  }
+
+  // ---- Y = L_M,bb^{-1}, P = Xd_b^T Y, V = L_Z^{-1} P, S = Y^T Y - V^T V. The buffers take the
+  // interior tile columns of L_M (no longer needed) where they fit.
+  float* Y = yps;                                 // [NB][NB]
+  float* Sb = Y + NB * NB;                        // [NB][NB]
+  float* Pv = Sb + NB * NB;                       // [NQP][NB]
+  __syncthreads();
+  for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0f : 0.0f;
+  __syncthreads();
+  tile_fwd_mat<TB, MR, MC, NT>(Lt, T, S::TI, Y, NB);
+  {
+    constexpr int RM = NQP / MR, CM = NB / MC;
+    for (int it = tid; it < RM * CM; it += NT) {  // P[a][j] = sum_i Xd[NI + i][a] Y[i][j]
+      const int a0 = (it / CM) * MR, j0 = (it % CM) * MC;
+      float acc[MR][MC];
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
+      for (int k = 0; k < NB; ++k) {
+        float a[MR], b[MC];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) a[i] = Xd[(NI + k) * NQP + a0 + i];
+#pragma unroll
+        for (int j = 0; j < MC; ++j) b[j] = Y[k * NB + j0 + j];
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+          for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MC; ++j) Pv[(a0 + i) * NB + j0 + j] = acc[i][j];
+    }
+  }
+  __syncthreads();
+  tile_fwd_mat<TB, MR, MC, NT>(Zt, TQ, 0, Pv, NB);
+  {
+    constexpr int RM = NB / MR, CM = NB / MC;
+    for (int it = tid; it < RM * CM; it += NT) {  // S[i][j] = sum_m Y[m][i] Y[m][j] - sum_a V[a][i] V[a][j]
+      const int i0 = (it / CM) * MR, j0 = (it % CM) * MC;
+      float acc[MR][MC];
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
+      for (int k = 0; k < NB; ++k) {
+        float a[MR], b[MC];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) a[i] = Y[k * NB + i0 + i];
+#pragma unroll
+        for (int j = 0; j < MC; ++j) b[j] = Y[k * NB + j0 + j];
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+          for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      for (int k = 0; k < NQK; ++k) {
+        float a[MR], b[MC];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) a[i] = Pv[k * NB + i0 + i];
+#pragma unroll
+        for (int j = 0; j < MC; ++j) b[j] = Pv[k * NB + j0 + j];
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+          for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(-a[i], b[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MC; ++j) Sb[(i0 + i) * NB + j0 + j] = acc[i][j];
+    }
+  }
+  __syncthreads();
+  // ---- scatter S_T = D_c S D_c into the FP64 CSR values (the lower triangle of S mirrored,
+  // so both face blocks of a pair carry bitwise transposed values)
+  const int64_t* boff = args.blockoff + e * 36;
+  for (int t = tid; t < NB * NB; t += NT) {
+    const int ib = t / NB, jb = t % NB;
+    const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
+    if (ef[a] < 0 || ef[b] < 0) continue;
+    const double dd = (((a ^ b) & 1) ? -1.0 : 1.0) * wf[m1] * wf[m2];
+    const double v = dd * (double)(ib >= jb ? Sb[ib * NB + jb] : Sb[jb * NB + ib]);
+    const int64_t r0 = args.row_ptr[(int64_t)ef[a] * NFN];
+    const int64_t rl = args.row_ptr[(int64_t)ef[a] * NFN + 1] - r0;
+    const int64_t pos = boff[a * 6 + b] + m1 * rl + m2;
+    if (a == b && args.colour == 1) args.val[pos] += v;
+    else args.val[pos] = v;
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(MT<K>::NT) element_tiled_kernel(ElemArgs args) {
+  extern __shared__ double smem[];
+  const int64_t li = blockIdx.x;
+  if (li >= args.n_list) return;
+  element_tiled_body<K, false>(args, args.elem_list[li], smem, nullptr, nullptr);
+}
+
+template <int K>
+__global__ void __launch_bounds__(MT<K>::NT) element_tiled_kernel_batch(const ElemArgs* probs, const int2* items,
+                                                                        int64_t n_items, int colour) {
+  extern __shared__ double smem[];
+  const int64_t li = blockIdx.x;
+  if (li >= n_items) return;
+  const int2 it = items[li];
+  ElemArgs a = probs[it.x];
+  a.colour = colour;
+  element_tiled_body<K, false>(a, it.y, smem, nullptr, nullptr);
+}
+
+template <int K>
+__global__ void __launch_bounds__(MT<K>::NT) recover_tiled_kernel(ElemArgs args, const double* lambda, double* u) {
+  extern __shared__ double smem[];
+  const int64_t li = blockIdx.x;
+  if (li >= args.n_list) return;
+  element_tiled_body<K, true>(args, args.elem_list[li], smem, lambda, u);
+}
+
+template <int K>
+__global__ void __launch_bounds__(MT<K>::NT) recover_tiled_kernel_batch(const ElemArgs* probs,
+                                                                        const double* const* lams, double* const* us,
+                                                                        const int2* items, int64_t n_items) {
+  extern __shared__ double smem[];
+  const int64_t li = blockIdx.x;
+  if (li >= n_items) return;
+  const int2 it = items[li];
+  const ElemArgs a = probs[it.x];
+  element_tiled_body<K, true>(a, it.y, smem, lams[it.x], us[it.x]);
+}
