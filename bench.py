@@ -49,7 +49,8 @@ def parse_args(argv=None):
     ap.add_argument("--batch-count", type=int, default=256, help="problems in the batched workload")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="fp64, or mixed: FP32 mixed-form elimination below the contrast threshold")
-    ap.add_argument("--threshold", type=float, default=1e4, help="mixed: contrast above which elements stay FP64")
+    ap.add_argument("--threshold", type=float, default=0.0,
+                    help="mixed: contrast above which elements stay FP64 (0: autotuned by the library)")
     ap.add_argument("--refine", type=int, default=0,
                     help="FP64 refinement steps after the solve (hyb_refine; for --precision mixed)")
     ap.add_argument("--refine-rtol", type=float, default=1e-6, help="inner PCG tolerance of a refinement step")
@@ -433,7 +434,8 @@ def run_ours(args):
                             "elements_fp64": n64, "elements_fp32": n32, "contrast_threshold": theta}
     workload = WORKLOAD if cfg == 2 else f"config {cfg}: {p.nx}^3 jittered hex mesh, RT_{p.order}, FP64"
     if mixed:
-        workload = workload.replace("FP64", f"mixed FP32/FP64 (threshold {theta:g})")
+        how = "autotuned " if args.threshold == 0 else ""
+        workload = workload.replace("FP64", f"mixed FP32/FP64 ({how}threshold {theta:g}: {n32} FP32 + {n64} FP64 elements)")
     if args.refine and not args.assembly_only:
         workload += f", {args.refine} FP64 refinement steps"
     if args.assembly_only:

@@ -81,7 +81,13 @@ typedef struct hyb_ctx hyb_ctx;
  *               conditioned), with the load term and the recovery refined against an FP64
  *               residual; the others use the FP64 path. The reduced system, PCG and the
  *               recovered u stay FP64. Static condensation needs an HYB_FP64 context.
- *  contrast_threshold : HYB_MIXED only; <= 0 selects the default 1e4 (ignored for HYB_FP64).
+ *  contrast_threshold : HYB_MIXED only (ignored for HYB_FP64); > 0 as given, 0 = autotuned:
+ *               the FP32 elimination's error bound does not grow with beta/alpha, so the
+ *               threshold only trades speed. The first HYB_MIXED set-up of each order on
+ *               a device times both element kernels on a 16^3 (RT_3: 12^3) unit-cube mesh
+ *               and puts every element on the faster path (threshold 1e300 or 0); the
+ *               choice is cached for the process. hyb_get_precision_split reports it.
+ *               Negative values: HYB_ERR_INVALID_ARG.
  *  cuda_stream: cudaStream_t to enqueue on (NULL = legacy default stream).
  *  out        : host, receives the new context.
  *  Builds the CSR pattern of H (int64 row pointers, int32 columns), per-element

@@ -17,7 +17,10 @@
 #include <cstdint>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -213,6 +216,8 @@ ElemArgs elem_args(hyb_ctx* c, const double* load, const double* ess, int colour
   return a;
 }
 
+int autotune_theta(int order, cudaStream_t s, double* theta);
+
 int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, const double* beta, int precision,
                double theta) {
   c->nx = m->nx; c->ny = m->ny; c->nz = m->nz; c->k = order;
@@ -311,8 +316,12 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
     if ((st = dalloc(c, &c->colour_list[t], lists[t].size()))) return st;
   }
   // precision paths: FP64 for every element, or (mixed) FP64 only above the contrast threshold
+  // (threshold 0: chosen by autotune_theta for this order on this device)
   c->precision = precision;
-  c->theta = theta > 0.0 ? theta : 1e4;
+  if (precision == HYB_MIXED && !(theta > 0.0)) {
+    if ((st = autotune_theta(order, c->stream, &theta))) return st;
+  }
+  c->theta = theta;
   std::vector<int32_t> slot_h(E, 0);
   if (precision == HYB_MIXED) {
     std::vector<double> ah(E), bh(E);
@@ -425,6 +434,72 @@ int assemble_impl(hyb_ctx* c, const double* load, const double* ess, int mode) {
   st = finish_phase(c);
   if (st == HYB_OK) c->mode = mode;
   return st;
+}
+
+// ---- contrast-threshold autotuner. The mixed-form FP32 elimination keeps its error (about
+// kappa(M, Z) u_32, bounds independent of beta / alpha) at every contrast, so the threshold
+// only trades speed: both element paths are timed on a unit-cube mesh of the same order
+// (alpha = beta = 1, zero load; the element work does not depend on the values), and every
+// element goes to the faster one: threshold 1e300 (all FP32) or 0 (all FP64). Measured once
+// per order and device, then cached for the process.
+std::mutex g_tune_mutex;
+std::map<std::pair<int, int>, double> g_tuned;
+
+int autotune_theta(int order, cudaStream_t s, double* theta) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HYB_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  const auto key = std::make_pair(dev, order);
+  const auto it = g_tuned.find(key);
+  if (it != g_tuned.end()) {
+    *theta = it->second;
+    return HYB_OK;
+  }
+  const int n = order >= 3 ? 12 : 16;
+  const int64_t E = (int64_t)n * n * n, nv = (int64_t)(n + 1) * (n + 1) * (n + 1);
+  const int nloc = Sizes::of(order).n;
+  std::vector<double> vh(3 * nv);
+  for (int l = 0; l <= n; ++l)
+    for (int j = 0; j <= n; ++j)
+      for (int i = 0; i <= n; ++i) {
+        const int64_t v = i + (int64_t)(n + 1) * (j + (int64_t)(n + 1) * l);
+        vh[3 * v] = (double)i / n;
+        vh[3 * v + 1] = (double)j / n;
+        vh[3 * v + 2] = (double)l / n;
+      }
+  std::vector<double> ones(E, 1.0);
+  double* buf = nullptr;
+  const size_t nd = 3 * nv + 2 * E + E * nloc;
+  if (cudaMalloc(&buf, nd * sizeof(double)) != cudaSuccess) return HYB_ERR_OOM;
+  double *verts = buf, *alpha = buf + 3 * nv, *beta = alpha + E, *load = beta + E;
+  cudaError_t e = cudaMemcpyAsync(verts, vh.data(), vh.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(alpha, ones.data(), E * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(beta, ones.data(), E * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(load, 0, (size_t)E * nloc * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int st = e == cudaSuccess ? HYB_OK : cuda_status(e);
+  double ms[2] = {0.0, 0.0};
+  hyb_mesh mesh{n, n, n, verts};
+  for (int path = 0; path < 2 && st == HYB_OK; ++path) {
+    hyb_ctx* t = new (std::nothrow) hyb_ctx();
+    if (!t) { st = HYB_ERR_OOM; break; }
+    t->stream = s;
+    st = setup_impl(t, &mesh, order, alpha, beta, path ? HYB_MIXED : HYB_FP64, 1e300);
+    if (st == HYB_OK) st = assemble_impl(t, load, nullptr, MODE_HYB);       // warm-up
+    if (st == HYB_OK) {
+      t->prof.reset();
+      t->prof.on = true;
+      for (int r = 0; r < 2 && st == HYB_OK; ++r) st = assemble_impl(t, load, nullptr, MODE_HYB);
+      t->prof.collect();
+      ms[path] = t->prof.ms[HYB_K_ELEMENT];
+    }
+    hyb_destroy(t);
+  }
+  cudaFree(buf);
+  if (st != HYB_OK) return st;
+  *theta = ms[1] < ms[0] ? 1e300 : 0.0;
+  g_tuned[key] = *theta;
+  return HYB_OK;
 }
 
 int recover_impl(hyb_ctx* c, const double* lam, double* u, int mode) {

@@ -1109,14 +1109,14 @@ cudaError_t launch_mixed_k(const ElemArgs& a, cudaStream_t s, Prof* prof, bool r
 
 }  // namespace
 
-// FP32-path store per element: the untiled kernels keep L_M | Xd | L_Z | G^{-1} for the
-// recovery; the tiled kernels (RT_2, RT_3) recompute the factors and keep only G^{-1}.
+// FP32-path store per element: L_M | Xd | L_Z | G^{-1} for the recovery (packed triangles
+// for RT_0 and RT_1, tiles for RT_2 and RT_3).
 int64_t mixed_store_floats(int k) {
   switch (k) {
     case 0: return MX<0>::STORE;
     case 1: return MX<1>::STORE;
-    case 2: return (int64_t)MT<2>::NQK * MT<2>::NQK;
-    case 3: return (int64_t)MT<3>::NQK * MT<3>::NQK;
+    case 2: return MT<2>::STORE;
+    case 3: return MT<3>::STORE;
   }
   return 0;
 }

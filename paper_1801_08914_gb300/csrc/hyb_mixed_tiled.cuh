@@ -19,10 +19,9 @@
 //    register micro-tiles: three barriers per tile column.
 //  * Triangular solves with one right-hand side (the refinement): two barriers per tile.
 // TB divides both the interior and the face block of the local ordering (interior dofs
-// first), so the face block is a trailing square of whole tiles. The recovery recomputes the
-// factorisation instead of reading stored factors: that is fewer bytes than the factors
-// themselves (which would be ~200 KB per RT_3 element), and the element work is the cheap
-// part of this path.
+// first), so the face block is a trailing square of whole tiles. The assembly stores the
+// tiles of L_M and L_Z, Xd and G^{-1} per element (211 KB at RT_3, 50 KB at RT_2); the
+// recovery copies them back into shared memory and runs only the refined solve.
 
 template <int K>
 struct TileShape;
@@ -54,7 +53,8 @@ struct MT {
   static constexpr int D64 = 24 + 24 + 2 * P * Q + p * Q + 2 * Q + NFN + 7 * NQ /*g6 gd*/ + 4 * N /*f x r ut*/ +
                              3 * NQ /*U*/ + 3 * NQ /*Wv*/ + NQ /*Dv*/ + NC /*xc*/ + 2 * TMP64 + 8 + NQK /*qv*/ +
                              (N > NQ ? N : NQ) /*rq*/ + P * p /*DcO64*/;
-  static constexpr int TABF = 2 * P * Q + p * Q + P * P * Q + P * p * Q + p * p * Q + P * p;
+  static constexpr int TABF = (2 * P * Q + p * Q + P * P * Q + P * p * Q + p * p * Q + P * p + 3) / 4 * 4;
+  static constexpr int64_t STORE = ((int64_t)LT + XD + ZTS + NQK * NQK + 3) / 4 * 4;   // L_M | Xd | L_Z | G^{-1}
   static constexpr int F32 = TABF + LT + XD + ZTS + N /*vec*/ + 2 * NQP /*tq tmpq*/ + 32 /*ybuf*/ + 8 /*flag*/ +
                              (YPS_IN_LT ? 0 : YPS);
   static constexpr size_t SMEM = sizeof(double) * D64 + sizeof(float) * F32 + sizeof(int) * N;
@@ -67,6 +67,7 @@ struct MT {
   static_assert(GSCR <= LT, "G scratch fits in the L_M region");
   static constexpr int MSCR = 6 * NQ + Q * Q * P * P + Q * P * P * p * p;   // mass assembly temporaries
   static_assert(MSCR <= XD, "mass scratch fits in the Xd region");
+  static_assert(LT % 4 == 0 && XD % 4 == 0 && ZTS % 4 == 0 && (D64 * 2) % 4 == 0, "16-byte aligned tile blocks");
 };
 
 __device__ __forceinline__ int tcol(int I, int J, int T) { return J * T - J * (J - 1) / 2 + (I - J); }
@@ -449,7 +450,8 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   constexpr int T = S::T, TQ = S::TQ, TT = S::TT;
   const int tid = threadIdx.x;
   const int64_t slot = args.slot ? args.slot[e] : e;
-  float* Gi = args.Lstore32 + slot * (int64_t)(NQK * NQK);      // G^{-1}, global scratch of this element
+  float* store = args.Lstore32 + slot * S::STORE;                // this element's factors (global)
+  float* Gi = store + S::LT + S::XD + S::ZTS;                     // G^{-1}
 
   // ---- shared memory
   double* d = smem;
@@ -484,7 +486,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   float* VcVc = fl; fl += P * P * Q;
   float* VcVo = fl; fl += P * p * Q;
   float* VoVo = fl; fl += p * p * Q;
-  float* DcO = fl; fl += P * p;
+  float* DcO = fl; fl += S::TABF - (2 * P * Q + p * Q + P * P * Q + P * p * Q + p * p * Q);
   float* Lt = fl; fl += S::LT;
   float* Xd = fl; fl += S::XD;
   float* Zt = fl; fl += S::ZTS;
@@ -563,6 +565,14 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     }
   }
 
+  if (RECOVER) {
+    // ---- the stored factors back into shared memory
+    const float4* src = reinterpret_cast<const float4*>(store);
+    float4* dst = reinterpret_cast<float4*>(Lt);
+    constexpr int NV = (S::LT + S::XD + S::ZTS) / 4;           // Lt | Xd | Zt are contiguous
+    for (int t = tid; t < NV; t += NT) dst[t] = __ldcs(src + t);
+    __syncthreads();
+  } else {
   // ---- G (Q_k mass weighted by beta / det J), its tiled Cholesky, G^{-1} -> global scratch.
   // Scratch in the L_M region, which is free until the mass assembly.
   {
@@ -756,6 +766,14 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
       if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
       return;
     }
+  }
+  {
+    // ---- keep the factors for the recovery
+    const float4* src = reinterpret_cast<const float4*>(Lt);
+    float4* dst = reinterpret_cast<float4*>(store);
+    constexpr int NV = (S::LT + S::XD + S::ZTS) / 4;
+    for (int t = tid; t < NV; t += NT) __stcs(dst + t, src[t]);
+  }
   }
 
   // ---- the refined element solve: g_T (assembly) or u_T (recovery)

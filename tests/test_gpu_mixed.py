@@ -82,3 +82,47 @@ def test_mixed_split_paths():
     kw = kappa_w(D)
     ev = np.linalg.eigvalsh(H.toarray())
     assert eS <= 100 * U32 * kw and eu <= (ev[-1] / ev[0]) * 100 * U32 * kw
+
+
+@pytest.mark.parametrize("k,n", [(1, 4), (2, 3), (3, 3)])
+def test_mixed_fp32_path_at_contrast_1e6(k, n):
+    """Every element on the FP32 path at contrast up to 1e6: the bound on S is the same
+    kappa(M, Z) u_32 bound as at low contrast (the mixed form does not see beta / alpha)."""
+    p = inputs.random_problem(n, k, 0.2, 430 + k, 1e-2, 1e6, name="mixed32hc")
+    D = Discretization.from_problem(p)
+    H, g = D.hybridize()
+    lam = solve_dense(H, g)
+    u = D.recover(lam)
+    r = gpu_run(p, rtol=1e-14, maxit=50000, precision=1, threshold=1e300)
+    assert r["split"][1] == p.n_elem
+    kw = kappa_w(D)
+    ev = np.linalg.eigvalsh(H.toarray())
+    kH = ev[-1] / ev[0]
+    eS, el, eu = rel(r["red"]["val"], H.data), rel(r["lam"], lam), rel(r["u"], u)
+    print(f"mixed FP32 k={k} contrast<=1e6: kappa_w={kw:.1e} kappa_H={kH:.1e} S {eS:.1e} lam {el:.1e} u {eu:.1e}")
+    assert eS <= 100 * U32 * kw
+    assert el <= kH * 100 * U32 * kw and eu <= kH * 100 * U32 * kw
+
+
+def test_threshold_autotune():
+    """threshold 0 picks the faster element path for the order (all FP32 or all FP64) and
+    reports it; a second set-up of the same order reuses the measurement."""
+    import time
+    from paper_1801_08914_gb300 import hyb
+    from gpu_helpers import dev
+    for k in (1, 2, 3):
+        p = inputs.random_problem(3, k, 0.2, 440 + k, 1e-2, 1e6)
+        ctx = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta),
+                            precision=hyb.HYB_MIXED, contrast_threshold=0.0)
+        n64, n32, theta = ctx.precision_split()
+        ctx.close()
+        assert theta in (0.0, 1e300) and n64 + n32 == p.n_elem
+        assert (n32 == p.n_elem) if theta == 1e300 else (n64 == p.n_elem)
+        t = time.perf_counter()
+        ctx = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta),
+                            precision=hyb.HYB_MIXED, contrast_threshold=0.0)
+        again = ctx.precision_split()[2]
+        ctx.close()
+        print(f"k={k}: autotuned threshold {theta:g} ({n32} FP32, {n64} FP64), cached set-up "
+              f"{1e3 * (time.perf_counter() - t):.1f} ms")
+        assert again == theta
