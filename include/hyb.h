@@ -323,6 +323,14 @@ int hyb_recover_batch(hyb_batch* b, const double* const* lambdas, double* const*
  *  destroy), for sizes, exports and error queries. */
 int hyb_batch_context(hyb_batch* b, int problem, hyb_ctx** ctx);
 
+/*
+ * hyb_batch_set_graphs -- 1 (default): hyb_solve_reduced_batch replays its 32-iteration
+ *  chunk of batched PCG (96 launches) as one CUDA graph (captured on the first solve, and
+ *  again when rtol changes; profiled as one HYB_K_PCG_FUSED launch); 0: direct launches.
+ *  Implementation choice with no counterpart in the paper.
+ */
+int hyb_batch_set_graphs(hyb_batch* b, int on);
+
 /* launch profile of the batch's own launches (see hyb_set_profiling / hyb_get_profile) */
 int hyb_batch_set_profiling(hyb_batch* b, int enable);
 int hyb_batch_get_profile(const hyb_batch* b, int kernel_class, double* total_ms, int64_t* launches);

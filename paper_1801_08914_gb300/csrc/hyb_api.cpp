@@ -827,6 +827,13 @@ struct hyb_batch {
   std::vector<void*> allocs;
   Prof prof;
   int mode = MODE_NONE;
+  // the 32-iteration chunk of the batched PCG as a CUDA graph (captured on a private stream,
+  // launched on `stream`); re-captured when rtol changes
+  bool use_graph = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  double graph_rtol = -1.0;
 };
 
 namespace {
@@ -1066,7 +1073,30 @@ int hyb_solve_reduced_batch(hyb_batch* b, double rtol, int maxit, double* const*
       if (!hf[4 * p + 1] && !hf[4 * p + 2]) active = true;
     }
     if (!active || done >= maxit) break;
-    e = pcg_iterations_batch(pb, std::min(32, maxit - done), rtol, b->stream, &b->prof);
+    const int n = std::min(32, maxit - done);
+    if (b->use_graph && n == 32) {
+      if (!b->graph_exec || b->graph_rtol != rtol) {
+        if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->graph_exec = nullptr;
+        b->graph = nullptr;
+        if (!b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          const cudaError_t el = pcg_iterations_batch(pb, 32, rtol, b->cap_stream, nullptr);
+          e = cudaStreamEndCapture(b->cap_stream, &b->graph);
+          if (e == cudaSuccess) e = el;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph_exec, b->graph, 0);
+        if (e != cudaSuccess) return cuda_status(e);
+        b->graph_rtol = rtol;
+      }
+      const int tok = prof_begin(&b->prof, HYB_K_PCG_FUSED, b->stream);
+      e = cudaGraphLaunch(b->graph_exec, b->stream);
+      prof_end(&b->prof, tok, b->stream);
+    } else {
+      e = pcg_iterations_batch(pb, n, rtol, b->stream, &b->prof);
+    }
     if (e != cudaSuccess) return cuda_status(e);
   }
   std::vector<double> hs(8 * (size_t)b->nprob);
@@ -1132,9 +1162,18 @@ int hyb_batch_get_profile(const hyb_batch* b, int kernel_class, double* total_ms
   return HYB_OK;
 }
 
+int hyb_batch_set_graphs(hyb_batch* b, int on) {
+  if (!b || (on != 0 && on != 1)) return HYB_ERR_INVALID_ARG;
+  b->use_graph = on != 0;
+  return HYB_OK;
+}
+
 void hyb_destroy_batch(hyb_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (hyb_ctx* c : b->ctx) hyb_destroy(c);
   for (void* p : b->allocs) cudaFree(p);
   delete b;

@@ -1033,14 +1033,18 @@ cudaError_t launch_mixed_batch_k(const ElemArgs* probs, const int2* items, int64
   if constexpr (K >= 2) {
     using S = MT<K>;
     if (!recover) {
-      err = cudaFuncSetAttribute(element_tiled_kernel_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      err = cudaFuncSetAttribute(element_tiled_kernel_batch<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (err == cudaSuccess) err = cudaFuncSetAttribute(element_tiled_kernel_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)S::SMEM);
       if (err != cudaSuccess) return err;
       const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
       element_tiled_kernel_batch<K><<<(unsigned)n, S::NT, S::SMEM, s>>>(probs, items, n, colour);
       prof_end(prof, tok, s);
     } else {
-      err = cudaFuncSetAttribute(recover_tiled_kernel_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      err = cudaFuncSetAttribute(recover_tiled_kernel_batch<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (err == cudaSuccess) err = cudaFuncSetAttribute(recover_tiled_kernel_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)S::SMEM);
       if (err != cudaSuccess) return err;
       const int tok = prof_begin(prof, HYB_K_RECOVER, s);
@@ -1075,13 +1079,17 @@ cudaError_t launch_mixed_k(const ElemArgs& a, cudaStream_t s, Prof* prof, bool r
   if constexpr (K >= 2) {
     using S = MT<K>;
     if (!recover) {
-      err = cudaFuncSetAttribute(element_tiled_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+      err = cudaFuncSetAttribute(element_tiled_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (err == cudaSuccess) err = cudaFuncSetAttribute(element_tiled_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
       if (err != cudaSuccess) return err;
       const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
       element_tiled_kernel<K><<<(unsigned)a.n_list, S::NT, S::SMEM, s>>>(a);
       prof_end(prof, tok, s);
     } else {
-      err = cudaFuncSetAttribute(recover_tiled_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+      err = cudaFuncSetAttribute(recover_tiled_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (err == cudaSuccess) err = cudaFuncSetAttribute(recover_tiled_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
       if (err != cudaSuccess) return err;
       const int tok = prof_begin(prof, HYB_K_RECOVER, s);
       recover_tiled_kernel<K><<<(unsigned)a.n_list, S::NT, S::SMEM, s>>>(a, lambda, u);

@@ -27,17 +27,17 @@ template <int K>
 struct TileShape;
 template <>
 struct TileShape<2> {
-  static constexpr int TB = 18, MR = 3, MC = 6, NT = 256;
+  static constexpr int TB = 18, MR = 3, MC = 6, NT = 256, MINB = 3;   // 3 CTAs per SM (63 KB each)
 };
 template <>
 struct TileShape<3> {
-  static constexpr int TB = 16, MR = 4, MC = 4, NT = 512;
+  static constexpr int TB = 16, MR = 4, MC = 4, NT = 512, MINB = 1;   // 227 KB of shared memory
 };
 
 template <int K>
 struct MT {
   using TS = TileShape<K>;
-  static constexpr int TB = TS::TB, MR = TS::MR, MC = TS::MC, NT = TS::NT;
+  static constexpr int TB = TS::TB, MR = TS::MR, MC = TS::MC, NT = TS::NT, MINB = TS::MINB;
   static constexpr int P = K + 2, p = K + 1, Q = K + 2, NQ = Q * Q * Q;
   static constexpr int NFN = p * p, NI = 3 * K * p * p, NB = 6 * NFN, N = NI + NB, NC = P * p * p;
   static constexpr int NQK = p * p * p;
@@ -47,7 +47,7 @@ struct MT {
   static constexpr int ZTS = TQ * (TQ + 1) / 2 * TT;       // L_Z tiles
   static constexpr int XD = N * NQP;                       // Xd, row-major, columns >= NQK zero
   static constexpr int LT_INTERIOR = (TI * T - TI * (TI - 1) / 2) * TT;   // tile columns J < TI
-  static constexpr int YPS = 2 * NB * NB + NQP * NB;       // Y | S | P (= V) after the refinement
+  static constexpr int YPS = NB * NB + NQP * NB;           // Y | P (= V) after the refinement
   static constexpr bool YPS_IN_LT = YPS <= LT_INTERIOR;
   static constexpr int TMP64 = P * Q * Q;
   static constexpr int D64 = 24 + 24 + 2 * P * Q + p * Q + 2 * Q + NFN + 7 * NQ /*g6 gd*/ + 4 * N /*f x r ut*/ +
@@ -70,49 +70,56 @@ struct MT {
   static_assert(LT % 4 == 0 && XD % 4 == 0 && ZTS % 4 == 0 && (D64 * 2) % 4 == 0, "16-byte aligned tile blocks");
 };
 
+// Refinement steps of each element solve: every step multiplies the error by about
+// kappa(M, Z) u_32 <= 5e-5, so two steps take the FP32 solve (1e-7) below FP64 rounding.
+constexpr int kRefineSteps = 2;
+
 __device__ __forceinline__ int tcol(int I, int J, int T) { return J * T - J * (J - 1) / 2 + (I - J); }
 
 // ---- one warp: Cholesky of the lower triangle of a TB x TB column-major tile in place,
-// then replace it by the inverse of the factor (strict upper part zero). flag[0] = 1 on a bad
-// pivot (every lane leaves at the same step).
+// then replace it by the inverse of the factor (strict upper part zero). Lane i holds row i
+// in registers and the columns travel by shuffles, so there is no shared-memory round trip or
+// index arithmetic inside the elimination. flag[0] = 1 on a bad pivot (every lane leaves at
+// the same step: the pivot is broadcast).
 template <int TB>
-__device__ void diag_factor_invert(float* D, float* rinv, float* flag) {
+__device__ void diag_factor_invert(float* D, float* flag) {
   const int lane = threadIdx.x & 31;
+  constexpr unsigned FULL = 0xffffffffu;
+  float row[TB], rv[TB];
+#pragma unroll
+  for (int l = 0; l < TB; ++l) row[l] = (lane < TB && l <= lane) ? D[lane + l * TB] : 0.0f;
+  bool ok = true;
+#pragma unroll
   for (int k = 0; k < TB; ++k) {
-    const float d = D[k + k * TB];
+    const float d = __shfl_sync(FULL, row[k], k);          // pivot, after the previous updates
     if (!(d > 0.0f) || !(d < INFINITY)) {
-      if (lane == 0) flag[0] = 1.0f;
-      __syncwarp();
-      return;
+      ok = false;
+      break;
     }
     const float r = dev::rsqrt_newton(d);
-    __syncwarp();
-    if (lane > k && lane < TB) D[lane + k * TB] *= r;
-    if (lane == k) {
-      D[k + k * TB] = d * r;
-      rinv[k] = r;                                   // 1 / L_kk
+    rv[k] = r;                                             // 1 / L_kk, in every lane
+    row[k] = lane == k ? d * r : row[k] * r;               // column k of L (rows > k, and the pivot)
+#pragma unroll
+    for (int l = k + 1; l < TB; ++l) {                     // row_i[l] -= L_ik L_lk, k < l <= i
+      const float lk = __shfl_sync(FULL, row[k], l);
+      if (lane >= l) row[l] = fmaf(-row[k], lk, row[l]);
     }
-    __syncwarp();
-    constexpr int W = TB;                            // trailing entries (i, l), k < l <= i
-    const int m = TB - k - 1;
-    for (int e = lane; e < m * m; e += 32) {
-      const int i = k + 1 + e / m, l = k + 1 + e % m;
-      if (l <= i) D[i + l * W] = fmaf(-D[i + k * W], D[l + k * W], D[i + l * W]);
-    }
-    __syncwarp();
   }
-  // column c of L^{-1} in lane c (forward substitution on e_c)
+  if (!ok) {
+    if (lane == 0) flag[0] = 1.0f;
+    __syncwarp();
+    return;
+  }
+  // column c of L^{-1} in lane c: col_i = -(sum_{c <= k < i} L_ik col_k) / L_ii, col_c = 1 / L_cc;
+  // L_ik comes from lane i by shuffle
   float col[TB];
-  if (lane < TB) {
 #pragma unroll
-    for (int i = 0; i < TB; ++i) {
-      float s = 0.0f;
+  for (int i = 0; i < TB; ++i) {
+    float s = 0.0f;
 #pragma unroll
-      for (int k = 0; k < i; ++k) s = fmaf(D[i + k * TB], col[k], s);
-      col[i] = i < lane ? 0.0f : (i == lane ? rinv[i] : -s * rinv[i]);
-    }
+    for (int k = 0; k < i; ++k) s = fmaf(__shfl_sync(FULL, row[k], i), col[k], s);
+    col[i] = i < lane ? 0.0f : (i == lane ? rv[i] : -s * rv[i]);
   }
-  __syncwarp();
   if (lane < TB) {
 #pragma unroll
     for (int i = 0; i < TB; ++i) D[i + lane * TB] = col[i];
@@ -191,14 +198,14 @@ __device__ __forceinline__ void gemm_x_micro(const float* A, const float* XJ, fl
 // ---- CTA: blocked Cholesky of T x T tiles (packed by tile columns) fused with
 // X <- L^{-1} X (T TB rows, ld MX; X may be null). Returns false in every thread on a bad pivot.
 template <int TB, int MR, int MC, int NT>
-__device__ bool tile_chol(float* Lt, int T, float* X, int MX, float* rinv, float* flag) {
+__device__ bool tile_chol(float* Lt, int T, float* X, int MX, float* flag) {
   constexpr int TT = TB * TB;
   const int tid = threadIdx.x;
   if (tid == 0) flag[0] = 0.0f;
   __syncthreads();
   for (int J = 0; J < T; ++J) {
     float* Dv = Lt + tcol(J, J, T) * TT;
-    if (tid < 32) diag_factor_invert<TB>(Dv, rinv, flag);
+    if (tid < 32) diag_factor_invert<TB>(Dv, flag);
     __syncthreads();
     if (flag[0] != 0.0f) return false;
     // panel: A_IJ <- A_IJ Dinv^T (one thread per row), X_J <- Dinv X_J (one thread per column)
@@ -493,7 +500,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   float* vec = fl; fl += N;
   float* tq = fl; fl += NQP;
   float* tmpq = fl; fl += NQP;
-  float* rinv = fl; fl += 32;
+  fl += 32;                                       // spare
   float* flag = fl; fl += 8;
   float* yps = S::YPS_IN_LT ? Lt : fl;
   if (!S::YPS_IN_LT) fl += S::YPS;
@@ -617,7 +624,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     }
     for (int t = tid; t < NQP * NQP; t += NT) Xg[t] = (t / NQP == t % NQP) ? 1.0f : 0.0f;
     __syncthreads();
-    if (!tile_chol<TB, MR, MC, NT>(Gt, TQ, Xg, NQP, rinv, flag)) {
+    if (!tile_chol<TB, MR, MC, NT>(Gt, TQ, Xg, NQP, flag)) {
       if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
       return;
     }
@@ -721,7 +728,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     Xd[t] = v;
   }
   __syncthreads();
-  if (!tile_chol<TB, MR, MC, NT>(Lt, T, Xd, NQP, rinv, flag)) {
+  if (!tile_chol<TB, MR, MC, NT>(Lt, T, Xd, NQP, flag)) {
     if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
     return;
   }
@@ -762,7 +769,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
         }
     }
     __syncthreads();
-    if (!tile_chol<TB, MR, MC, NT>(Zt, TQ, nullptr, 0, rinv, flag)) {
+    if (!tile_chol<TB, MR, MC, NT>(Zt, TQ, nullptr, 0, flag)) {
       if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
       return;
     }
@@ -777,7 +784,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   }
 
   // ---- the refined element solve: g_T (assembly) or u_T (recovery)
-  refine_tiled<K>(f, x, qv, 3, alpha, beta, bmask, g6, gd, Vc, Dc, Vo, DcO64, dofcode, Lt, Xd, Zt, Gi, r, ut, rq,
+  refine_tiled<K>(f, x, qv, kRefineSteps, alpha, beta, bmask, g6, gd, Vc, Dc, Vo, DcO64, dofcode, Lt, Xd, Zt, Gi, r, ut, rq,
                   U, Wv, Dv, xc, t1, t2, vec, tq, tmpq);
   if (RECOVER) {
     double* ue = u_out + e * (int64_t)N;
@@ -796,8 +803,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   // ---- Y = L_M,bb^{-1}, P = Xd_b^T Y, V = L_Z^{-1} P, S = Y^T Y - V^T V. The buffers take the
   // interior tile columns of L_M (no longer needed) where they fit.
   float* Y = yps;                                 // [NB][NB]
-  float* Sb = Y + NB * NB;                        // [NB][NB]
-  float* Pv = Sb + NB * NB;                       // [NQP][NB]
+  float* Pv = Y + NB * NB;                        // [NQP][NB]
   __syncthreads();
   for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0f : 0.0f;
   __syncthreads();
@@ -830,10 +836,32 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   }
   __syncthreads();
   tile_fwd_mat<TB, MR, MC, NT>(Zt, TQ, 0, Pv, NB);
+  // ---- S[i][j] = sum_m Y[m][i] Y[m][j] - sum_a V[a][i] V[a][j] for i >= j, in register
+  // micro-tiles, scattered as S_T = D_c S D_c straight into the FP64 CSR values: entry (i, j)
+  // and its mirror (j, i) get the same value, so both face blocks of a pair are bitwise
+  // transposed.
+  __shared__ int64_t s_row0[6];
+  __shared__ int s_rlen[6];
+  if (tid < 6) {
+    const int64_t r0 = ef[tid] >= 0 ? args.row_ptr[(int64_t)ef[tid] * NFN] : 0;
+    s_row0[tid] = r0;
+    s_rlen[tid] = ef[tid] >= 0 ? (int)(args.row_ptr[(int64_t)ef[tid] * NFN + 1] - r0) : 0;
+  }
+  __syncthreads();
+  const int64_t* boff = args.blockoff + e * 36;
+  auto put = [&](int ib, int jb, float sv) {
+    const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
+    if (ef[a] < 0 || ef[b] < 0) return;
+    const double v = (((a ^ b) & 1) ? -1.0 : 1.0) * wf[m1] * wf[m2] * (double)sv;
+    const int64_t pos = boff[a * 6 + b] + m1 * (int64_t)s_rlen[a] + m2;
+    if (a == b && args.colour == 1) args.val[pos] += v;
+    else args.val[pos] = v;
+  };
   {
     constexpr int RM = NB / MR, CM = NB / MC;
-    for (int it = tid; it < RM * CM; it += NT) {  // S[i][j] = sum_m Y[m][i] Y[m][j] - sum_a V[a][i] V[a][j]
+    for (int it = tid; it < RM * CM; it += NT) {
       const int i0 = (it / CM) * MR, j0 = (it % CM) * MC;
+      if (i0 + MR - 1 < j0) continue;             // strictly above the diagonal
       float acc[MR][MC];
 #pragma unroll
       for (int i = 0; i < MR; ++i)
@@ -864,29 +892,18 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
 #pragma unroll
       for (int i = 0; i < MR; ++i)
 #pragma unroll
-        for (int j = 0; j < MC; ++j) Sb[(i0 + i) * NB + j0 + j] = acc[i][j];
+        for (int j = 0; j < MC; ++j) {
+          const int ib = i0 + i, jb = j0 + j;
+          if (ib < jb) continue;
+          put(ib, jb, acc[i][j]);
+          if (ib != jb) put(jb, ib, acc[i][j]);
+        }
     }
-  }
-  __syncthreads();
-  // ---- scatter S_T = D_c S D_c into the FP64 CSR values (the lower triangle of S mirrored,
-  // so both face blocks of a pair carry bitwise transposed values)
-  const int64_t* boff = args.blockoff + e * 36;
-  for (int t = tid; t < NB * NB; t += NT) {
-    const int ib = t / NB, jb = t % NB;
-    const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
-    if (ef[a] < 0 || ef[b] < 0) continue;
-    const double dd = (((a ^ b) & 1) ? -1.0 : 1.0) * wf[m1] * wf[m2];
-    const double v = dd * (double)(ib >= jb ? Sb[ib * NB + jb] : Sb[jb * NB + ib]);
-    const int64_t r0 = args.row_ptr[(int64_t)ef[a] * NFN];
-    const int64_t rl = args.row_ptr[(int64_t)ef[a] * NFN + 1] - r0;
-    const int64_t pos = boff[a * 6 + b] + m1 * rl + m2;
-    if (a == b && args.colour == 1) args.val[pos] += v;
-    else args.val[pos] = v;
   }
 }
 
 template <int K>
-__global__ void __launch_bounds__(MT<K>::NT) element_tiled_kernel(ElemArgs args) {
+__global__ void __launch_bounds__(MT<K>::NT, MT<K>::MINB) element_tiled_kernel(ElemArgs args) {
   extern __shared__ double smem[];
   const int64_t li = blockIdx.x;
   if (li >= args.n_list) return;
@@ -894,7 +911,7 @@ __global__ void __launch_bounds__(MT<K>::NT) element_tiled_kernel(ElemArgs args)
 }
 
 template <int K>
-__global__ void __launch_bounds__(MT<K>::NT) element_tiled_kernel_batch(const ElemArgs* probs, const int2* items,
+__global__ void __launch_bounds__(MT<K>::NT, MT<K>::MINB) element_tiled_kernel_batch(const ElemArgs* probs, const int2* items,
                                                                         int64_t n_items, int colour) {
   extern __shared__ double smem[];
   const int64_t li = blockIdx.x;
@@ -906,7 +923,7 @@ __global__ void __launch_bounds__(MT<K>::NT) element_tiled_kernel_batch(const El
 }
 
 template <int K>
-__global__ void __launch_bounds__(MT<K>::NT) recover_tiled_kernel(ElemArgs args, const double* lambda, double* u) {
+__global__ void __launch_bounds__(MT<K>::NT, MT<K>::MINB) recover_tiled_kernel(ElemArgs args, const double* lambda, double* u) {
   extern __shared__ double smem[];
   const int64_t li = blockIdx.x;
   if (li >= args.n_list) return;
@@ -914,7 +931,7 @@ __global__ void __launch_bounds__(MT<K>::NT) recover_tiled_kernel(ElemArgs args,
 }
 
 template <int K>
-__global__ void __launch_bounds__(MT<K>::NT) recover_tiled_kernel_batch(const ElemArgs* probs,
+__global__ void __launch_bounds__(MT<K>::NT, MT<K>::MINB) recover_tiled_kernel_batch(const ElemArgs* probs,
                                                                         const double* const* lams, double* const* us,
                                                                         const int2* items, int64_t n_items) {
   extern __shared__ double smem[];

@@ -64,6 +64,44 @@ __device__ __forceinline__ double block_sum_smem(double v, double* sh) {
   return t;
 }
 
+// Row sums of a face shared by W lanes (each lane holds partial sums of the NFN rows).
+// Where W divides NFN they reduce-scatter: at each of the log2(W) levels a lane keeps half of
+// its current values, sends the other half to its partner and adds what it receives, so lane
+// gl ends with the full sums of NFN / W rows, acc[j] being row scatter_row(j, gl), after
+// NFN (1 - 1/W) adds instead of NFN log2(W); otherwise every lane reduces every row.
+template <int NFN, int W>
+__device__ __forceinline__ int scatter_row(int j, int gl) {
+  int row = j, S = NFN;
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    if (gl & o) row += S / 2;
+    S >>= 1;
+  }
+  return row;
+}
+
+template <int NFN, int W>
+__device__ __forceinline__ void face_reduce(double (&acc)[NFN], int gl) {
+  if constexpr (NFN % W == 0) {
+#pragma unroll
+    for (int o = W / 2, S = NFN; o > 0; o >>= 1, S >>= 1) {
+      const bool hi = gl & o;
+#pragma unroll
+      for (int j = 0; j < S / 2; ++j) {
+        const double keep = hi ? acc[j + S / 2] : acc[j];
+        const double send = hi ? acc[j] : acc[j + S / 2];
+        acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o, W);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < NFN; ++m) {
+#pragma unroll
+      for (int o = W / 2; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o, W);
+    }
+  }
+}
+
 // Ticket: returns true in exactly one (the last) block. Thread 0 wrote this block's partial;
 // it alone fences before taking a ticket, so the last block sees every partial in L2.
 __device__ __forceinline__ bool last_block(int* ticket, int nblocks) {
@@ -162,23 +200,28 @@ __device__ __forceinline__ void spmv_face_body(const PcgArgs& a, int vb, int nvb
         for (int m = 0; m < NFN; ++m) acc[m] = fma(a.val[lo + (int64_t)m * len + t], pj, acc[m]);
       }
     }
-#pragma unroll
-    for (int m = 0; m < NFN; ++m) {
-#pragma unroll
-      for (int o = W / 2; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o, W);
-    }
+    face_reduce<NFN, W>(acc, gl);
     if (f < nfaces) {
+      if constexpr (NFN % W == 0) {
 #pragma unroll
-      for (int m = 0; m < NFN; ++m) {
-        if (gl == m % W) {
-          const int64_t i = f * NFN + m;
-          a.q[i] = acc[m];
-          pq = fma(a.p[i], acc[m], pq);
+        for (int j = 0; j < NFN / W; ++j) {
+          const int64_t i = f * NFN + scatter_row<NFN, W>(j, gl);
+          a.q[i] = acc[j];
+          pq = fma(a.p[i], acc[j], pq);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < NFN; ++m) {
+          if (gl == m % W) {
+            const int64_t i = f * NFN + m;
+            a.q[i] = acc[m];
+            pq = fma(a.p[i], acc[m], pq);
+          }
         }
       }
     }
   }
-  pq = block_sum(pq, sh);
+  pq = block_sum_smem(pq, sh);
   if (threadIdx.x == 0) a.partial[vb] = pq;
   if (last_block(&a.flags[F_TICKET], nvb)) {
     const double s = sum_partials(a.partial, nvb, 1, 0, sh);
@@ -193,7 +236,7 @@ __device__ __forceinline__ void spmv_face_body(const PcgArgs& a, int vb, int nvb
 
 template <int NFN, int W>
 __global__ void __launch_bounds__(kThreads) spmv_face_kernel(PcgArgs a) {
-  __shared__ double sh[32];
+  __shared__ double sh[kThreads];
   spmv_face_body<NFN, W>(a, blockIdx.x, gridDim.x, sh);
 }
 
@@ -357,23 +400,7 @@ struct GridBar {
 // update rides along with the SpMV instead of needing a third barrier and pass. In exact
 // arithmetic the iterates are those of the three-launch form; q is carried by the recursion.
 // On the first iteration after initialisation (flags[F_IT] == 0) beta = 0 and q is not read.
-//
-// W lanes share a face (their partial sums of the NFN rows). Where W divides NFN they
-// reduce-scatter: at each of the log2(W) levels a lane keeps half of its current values,
-// sends the other half to its partner and adds what it receives, so lane gl ends with the
-// full sums of NFN / W rows after NFN (1 - 1/W) adds (instead of NFN log2(W)) and updates
-// exactly those rows; otherwise every lane reduces every row and lane m % W updates row m.
-template <int NFN, int W>
-__device__ __forceinline__ int scatter_row(int j, int gl) {
-  int row = j, S = NFN;
-#pragma unroll
-  for (int o = W / 2; o > 0; o >>= 1) {
-    if (gl & o) row += S / 2;
-    S >>= 1;
-  }
-  return row;
-}
-
+// W lanes share a face (face_reduce); each lane then updates the rows it holds.
 template <int NFN, int W>
 __global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
     pcg_fused_kernel(PcgArgs a, int count, double rtol2, GridBar* bar) {
@@ -414,17 +441,8 @@ __global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
           for (int m = 0; m < NFN; ++m) acc[m] = fma(__ldcs(a.val + lo + (int64_t)m * len + t), zj, acc[m]);
         }
       }
+      face_reduce<NFN, W>(acc, gl);
       if constexpr (kScatter) {
-#pragma unroll
-        for (int o = W / 2, S = NFN; o > 0; o >>= 1, S >>= 1) {
-          const bool hi = gl & o;
-#pragma unroll
-          for (int j = 0; j < S / 2; ++j) {
-            const double keep = hi ? acc[j + S / 2] : acc[j];
-            const double send = hi ? acc[j] : acc[j + S / 2];
-            acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o, W);
-          }
-        }
         if (f < nfaces) {
 #pragma unroll
           for (int j = 0; j < NFN / W; ++j) {
@@ -438,11 +456,6 @@ __global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
           }
         }
       } else {
-#pragma unroll
-        for (int m = 0; m < NFN; ++m) {
-#pragma unroll
-          for (int o = W / 2; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o, W);
-        }
         if (f < nfaces) {
 #pragma unroll
           for (int m = 0; m < NFN; ++m)
@@ -599,15 +612,15 @@ __global__ void axpy_kernel(int64_t n, const double* x, double* y) {
 // of blk_count[that problem]; every problem keeps its own scalars, tickets and flags.
 __global__ void __launch_bounds__(kThreads) spmv_batch_kernel(const PcgArgs* probs, const int32_t* blk_prob,
                                                               const int32_t* blk_first, const int32_t* blk_count) {
-  __shared__ double sh[32];
+  __shared__ double sh[kThreads];
   const int pb = blk_prob[blockIdx.x];
   const PcgArgs a = probs[pb];
   const int vb = blockIdx.x - blk_first[pb], nvb = blk_count[pb];
   switch (a.nfn) {
     case 1: spmv_face_body<1, 4>(a, vb, nvb, sh); break;
-    case 4: spmv_face_body<4, 2>(a, vb, nvb, sh); break;
+    case 4: spmv_face_body<4, 4>(a, vb, nvb, sh); break;
     case 9: spmv_face_body<9, 2>(a, vb, nvb, sh); break;
-    default: spmv_face_body<16, 2>(a, vb, nvb, sh); break;
+    default: spmv_face_body<16, 4>(a, vb, nvb, sh); break;
   }
 }
 __global__ void __launch_bounds__(kThreads) update_batch_kernel(const PcgArgs* probs, const int32_t* blk_prob,
@@ -671,9 +684,9 @@ cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_
     const int nbs = a.nblocks * 5 / 8, nbv = a.nblocks / 4;
     switch (a.nfn) {
       case 1: spmv_face_kernel<1, 4><<<nbs, kThreads, 0, s>>>(a); break;
-      case 4: spmv_face_kernel<4, 2><<<nbs, kThreads, 0, s>>>(a); break;
+      case 4: spmv_face_kernel<4, 4><<<nbs, kThreads, 0, s>>>(a); break;
       case 9: spmv_face_kernel<9, 2><<<nbs, kThreads, 0, s>>>(a); break;
-      case 16: spmv_face_kernel<16, 2><<<nbs, kThreads, 0, s>>>(a); break;
+      case 16: spmv_face_kernel<16, 4><<<nbs, kThreads, 0, s>>>(a); break;
       default: return cudaErrorInvalidValue;
     }
     prof_end(prof, tok, s);

@@ -53,3 +53,28 @@ def test_batch_matches_solo_and_oracle(precision):
             lam_o = solve_dense(H, g)
             assert rel(lams[i].cpu().numpy(), lam_o) <= max(1e-12, max(kH, element_kappa(D)) * EPS)
     b.close()
+
+
+def test_batch_graph_replay_matches_direct_launches():
+    """The CUDA-graph replay of a PCG chunk runs the same kernels in the same order as the
+    direct launches: iterates and counts are bitwise identical (also across an rtol change,
+    which re-captures the graph)."""
+    import torch
+    from paper_1801_08914_gb300 import hyb
+    probs = make_batch([(4, 1), (3, 2), (5, 0), (3, 3)])
+    verts = [dev(p.vertices) for p in probs]
+    b = hyb.hyb_setup_batch([(v, p.nx, p.ny, p.nz) for v, p in zip(verts, probs)], [p.order for p in probs],
+                            [dev(p.alpha) for p in probs], [dev(p.beta) for p in probs], precision=0)
+    hyb.hyb_assemble_reduced_batch(b, [dev(p.load) for p in probs])
+    sizes = [b.context(i).sizes() for i in range(len(probs))]
+    for rtol in (1e-12, 1e-10):
+        res = []
+        for graphs in (True, False):
+            hyb.hyb_batch_set_graphs(b, graphs)
+            lams = [torch.zeros(s["n_lambda"], dtype=torch.float64, device="cuda") for s in sizes]
+            its, rrs, st = hyb.hyb_solve_reduced_batch(b, rtol, 20000, lams)
+            assert st == hyb.HYB_OK
+            res.append((list(its), [l.clone() for l in lams]))
+        assert res[0][0] == res[1][0] and max(res[0][0]) > 32
+        assert all(torch.equal(x, y) for x, y in zip(res[0][1], res[1][1]))
+    b.close()
