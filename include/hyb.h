@@ -324,8 +324,21 @@ int hyb_recover_batch(hyb_batch* b, const double* const* lambdas, double* const*
 int hyb_batch_context(hyb_batch* b, int problem, hyb_ctx** ctx);
 
 /*
- * hyb_batch_set_graphs -- 1 (default): hyb_solve_reduced_batch replays its 32-iteration
- *  chunk of batched PCG (96 launches) as one CUDA graph (captured on the first solve, and
+ * hyb_batch_set_pcg_fused -- 1: hyb_solve_reduced_batch runs the fused PCG of
+ *  hyb_solve_reduced on teams of blocks, one team per unconverged problem: per chunk of 64
+ *  iterations the problems, sorted by size, go in groups to cooperative launches whose grid
+ *  is split in proportion to their nonzeros. 0 (default): three launches per iteration over
+ *  all problems (hyb_batch_set_graphs applies); on large batches those launches are big
+ *  enough that launch and barrier costs do not matter, and non-cooperative blocks share the
+ *  GPU among the problems better (256-problem benchmark: 5.3 s against 8.1 s).
+ *  Implementation choice with no counterpart in the paper.
+ */
+int hyb_batch_set_pcg_fused(hyb_batch* b, int on);
+
+/*
+ * hyb_batch_set_graphs -- 1 (default): with the three-launch form (the default of
+ *  hyb_batch_set_pcg_fused), hyb_solve_reduced_batch replays its 32-iteration chunk of batched PCG (96 launches)
+ *  as one CUDA graph (captured on the first solve, and
  *  again when rtol changes; profiled as one HYB_K_PCG_FUSED launch); 0: direct launches.
  *  Implementation choice with no counterpart in the paper.
  */

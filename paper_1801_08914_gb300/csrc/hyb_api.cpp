@@ -599,7 +599,6 @@ int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lamb
   a.nblocks = c->nblocks;
   a.nfn = c->sz.nfn;
   cudaError_t e = pcg_init(a, c->stream, &c->prof);
-  if (e == cudaSuccess && c->fused) e = cudaMemsetAsync(c->gridbar, 0, 2 * sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return cuda_status(e);
   int hf[4] = {0, 0, 0, 0};
   double hs[8] = {0};
@@ -613,8 +612,12 @@ int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lamb
     done = hf[0];
     if (hf[1] || hf[2] || done >= maxit) break;
     const int n = std::min(chunk, maxit - done);
-    e = c->fused ? pcg_iterations_fused(a, n, rtol, c->gridbar, c->stream, &c->prof)
-                 : pcg_iterations(a, n, rtol, c->stream, &c->prof);
+    if (c->fused) {
+      e = cudaMemsetAsync(c->gridbar, 0, 2 * sizeof(unsigned long long), c->stream);
+      if (e == cudaSuccess) e = pcg_iterations_fused(a, n, rtol, c->gridbar, c->stream, &c->prof);
+    } else {
+      e = pcg_iterations(a, n, rtol, c->stream, &c->prof);
+    }
     if (e != cudaSuccess) return cuda_status(e);
   }
   e = cudaMemcpyAsync(hs, c->scal, sizeof(hs), cudaMemcpyDeviceToHost, c->stream);
@@ -829,6 +832,9 @@ struct hyb_batch {
   int mode = MODE_NONE;
   // the 32-iteration chunk of the batched PCG as a CUDA graph (captured on a private stream,
   // launched on `stream`); re-captured when rtol changes
+  bool use_fused = false;                  // team-fused cooperative PCG, or three launches per iteration (default)
+  int4* d_team = nullptr;                  // per-launch block tables of the team-fused form
+  int team_cap = 0;
   bool use_graph = true;
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -947,6 +953,8 @@ int setup_batch_impl(hyb_batch* b, const hyb_mesh* meshes, const int* orders, co
     g.p = c->p;
     g.q = c->q;
     g.dinv = c->dinv;
+    g.z = c->z;                            // the team-fused form keeps z and a barrier counter per problem
+    g.bar = c->gridbar;
     g.partial = c->partial;
     g.scal = b->scal_all + 8 * p;
     g.flags = b->flags_all + 4 * p;
@@ -974,6 +982,83 @@ int setup_batch_impl(hyb_batch* b, const hyb_mesh* meshes, const int* orders, co
     return st;
   if ((st = balloc(b, &b->d_lams, b->nprob)) || (st = balloc(b, &b->d_us, b->nprob))) return st;
   return cuda_status(cudaStreamSynchronize(b->stream));
+}
+
+// Batched PCG in the team-fused form: between chunks of 64 iterations the host reads every
+// problem's flags, sorts the unconverged problems by size and runs them in groups of at most
+// an eighth as many problems as the cooperative grid has blocks, one launch per group, the
+// grid split in proportion to their nonzeros (at least one block each: with few problems per
+// launch that floor costs little, and problems of similar size share a launch). The last,
+// largest problems get the whole GPU.
+int solve_batch_team(hyb_batch* b, double rtol, int maxit, int* iters, double* rel_res) {
+  cudaError_t e = cudaSuccess;
+  int st;
+  constexpr int kSlots = 8;                        // block tables in flight per chunk
+  if (!b->d_team) {
+    if ((e = pcg_team_capacity(&b->team_cap)) != cudaSuccess) return cuda_status(e);
+    if (b->team_cap < 1) return HYB_ERR_CUDA;
+    if ((st = balloc(b, &b->d_team, (size_t)kSlots * b->team_cap))) return st;
+  }
+  const int cap = b->team_cap;
+  std::vector<int> hf(4 * (size_t)b->nprob);
+  std::vector<int4> table;
+  for (;;) {
+    e = cudaMemcpyAsync(hf.data(), b->flags_all, hf.size() * sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    b->prof.collect();
+    int done = 0;
+    std::vector<int> L;
+    for (int p = 0; p < b->nprob; ++p) {
+      done = std::max(done, hf[4 * p]);
+      if (!hf[4 * p + 1] && !hf[4 * p + 2]) L.push_back(p);
+    }
+    if (L.empty() || done >= maxit) break;
+    const int n = std::min(64, maxit - done);
+    if ((e = pcg_zero_bars(b->d_pargs, b->nprob, b->stream)) != cudaSuccess) return cuda_status(e);
+    std::sort(L.begin(), L.end(), [&](int x, int y) { return b->ctx[x]->nnz > b->ctx[y]->nnz; });
+    int slot = 0;
+    const size_t per_launch = (size_t)std::max(1, cap / 8);
+    for (size_t g0 = 0; g0 < L.size(); g0 += per_launch) {
+      const size_t g1 = std::min(L.size(), g0 + per_launch);
+      const int m = (int)(g1 - g0);
+      double wsum = 0.0;
+      for (size_t i = g0; i < g1; ++i) wsum += (double)b->ctx[L[i]]->nnz;
+      std::vector<int> nb(m, 1);
+      int used = m;
+      for (int i = 0; i < m; ++i) {                // one block each, the rest in proportion to nnz
+        const int extra = (int)((double)(cap - m) * (double)b->ctx[L[g0 + i]]->nnz / wsum);
+        nb[i] += extra;
+        used += extra;
+      }
+      for (int i = 0; used < cap && i < m; ++i, ++used) nb[i] += 1;
+      table.clear();
+      for (int i = 0; i < m; ++i)
+        for (int v = 0; v < nb[i]; ++v) table.push_back(make_int4(L[g0 + i], v, nb[i], 0));
+      if (slot == kSlots) {                        // every table in use: let the launches drain
+        if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return cuda_status(e);
+        slot = 0;
+      }
+      int4* dt = b->d_team + (size_t)slot * cap;
+      ++slot;
+      e = cudaMemcpyAsync(dt, table.data(), table.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+      if (e == cudaSuccess) e = pcg_iterations_team(b->d_pargs, dt, (int)table.size(), n, rtol, b->stream, &b->prof);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  }
+  std::vector<double> hs(8 * (size_t)b->nprob);
+  e = cudaMemcpyAsync(hs.data(), b->scal_all, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  st = HYB_OK;
+  for (int p = 0; p < b->nprob; ++p) {
+    if (iters) iters[p] = hf[4 * p];
+    if (rel_res) rel_res[p] = hs[8 * p + 1] > 0.0 ? std::sqrt(hs[8 * p + 2] / hs[8 * p + 1]) : 0.0;
+    if (hf[4 * p + 2] == 2) st = HYB_ERR_TIMEOUT;
+    else if (hf[4 * p + 2] && st == HYB_OK) st = HYB_ERR_BREAKDOWN;
+    else if (!hf[4 * p + 1] && st == HYB_OK) st = HYB_ERR_NOT_CONVERGED;
+  }
+  return st;
 }
 
 }  // namespace
@@ -1051,7 +1136,15 @@ int hyb_solve_reduced_batch(hyb_batch* b, double rtol, int maxit, double* const*
   for (int p = 0; p < b->nprob && e == cudaSuccess; ++p) {
     if (!lambdas[p]) return HYB_ERR_INVALID_ARG;
     b->h_pargs[p].x = lambdas[p];
-    e = pcg_init(b->h_pargs[p], b->stream, &b->prof);
+    PcgArgs a = b->h_pargs[p];
+    if (!b->use_fused) a.z = nullptr;
+    e = pcg_init(a, b->stream, &b->prof);
+  }
+  if (b->use_fused && e == cudaSuccess) {
+    e = cudaMemcpyAsync(b->d_pargs, b->h_pargs.data(), b->h_pargs.size() * sizeof(PcgArgs), cudaMemcpyHostToDevice,
+                        b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return solve_batch_team(b, rtol, maxit, iters, rel_res);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_pargs, b->h_pargs.data(), b->h_pargs.size() * sizeof(PcgArgs), cudaMemcpyHostToDevice,
@@ -1159,6 +1252,12 @@ int hyb_batch_get_profile(const hyb_batch* b, int kernel_class, double* total_ms
   if (!b || kernel_class < 0 || kernel_class >= HYB_K_COUNT) return HYB_ERR_INVALID_ARG;
   if (total_ms) *total_ms = b->prof.ms[kernel_class];
   if (launches) *launches = b->prof.launches[kernel_class];
+  return HYB_OK;
+}
+
+int hyb_batch_set_pcg_fused(hyb_batch* b, int on) {
+  if (!b || (on != 0 && on != 1)) return HYB_ERR_INVALID_ARG;
+  b->use_fused = on != 0;
   return HYB_OK;
 }
 

@@ -98,6 +98,7 @@ struct PcgArgs {
   double* q;
   double* dinv;
   double* z;                 // preconditioned residual (fused form only; NULL otherwise)
+  unsigned long long* bar;   // fused form in a batch: this problem's barrier counter (16 bytes, zeroed per launch)
   double* partial;           // per-block partial sums
   double* scal;              // device scalars
   int* flags;                // iteration count / converged / breakdown / ticket
@@ -114,10 +115,18 @@ struct PcgBatch {
 cudaError_t pcg_iterations_batch(const PcgBatch& b, int count, double rtol, cudaStream_t s, Prof* prof);
 cudaError_t pcg_init(const PcgArgs& a, cudaStream_t s, Prof* prof);
 // Up to `count` iterations in one cooperative launch (grid barriers between the phases).
-// bar: 16 bytes, zeroed at the start of every solve; a.z must be set (pcg_init fills it).
+// bar: 16 bytes, zeroed before every launch; a.z must be set (pcg_init fills it).
 // Stops at convergence or breakdown; a barrier that waits too long sets flags[3rd] = 2
 // (reported as HYB_ERR_TIMEOUT).
 cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void* bar, cudaStream_t s, Prof* prof);
+// Batch form: one cooperative launch runs up to `count` fused iterations for several problems
+// (any orders), each on its own team of blocks: block b works for problem team[b].x as block
+// team[b].y of team[b].z (device table). nblocks <= pcg_team_capacity.
+cudaError_t pcg_iterations_team(const PcgArgs* probs, const int4* team, int nblocks, int count, double rtol,
+                                cudaStream_t s, Prof* prof);
+cudaError_t pcg_team_capacity(int* blocks);
+// zero every problem's barrier counter (before each team launch)
+cudaError_t pcg_zero_bars(const PcgArgs* probs, int n, cudaStream_t s);
 cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_t s, Prof* prof);
 
 // Normal jump of a broken flux: rho = C u (eq. 2.3's constraint), row (f, m) =

@@ -323,8 +323,9 @@ __global__ void __launch_bounds__(kThreads) pcg_direction_kernel(PcgArgs a) {
 
 // ---- fused iterations: one cooperative launch runs up to `count` iterations.
 //
-// Grid-wide synchronisation is a monotonic arrival counter (64-bit, zeroed at the start of a
-// solve): barrier number B completes when the counter reaches (B + 1) * gridDim.x. Before
+// Grid-wide synchronisation is a monotonic arrival counter (64-bit, zeroed before every
+// launch, so a team may change size between launches): barrier number B of the launch
+// completes when the counter reaches (B + 1) * (blocks in the team). Before
 // arriving, thread 0 of each block stores the block's partial sums in one of two buffers
 // (alternating with B); after the barrier every block sums all partials itself in block order,
 // so every block obtains bitwise the same totals without a serial reduction step. A buffer is
@@ -401,19 +402,19 @@ struct GridBar {
 // arithmetic the iterates are those of the three-launch form; q is carried by the recursion.
 // On the first iteration after initialisation (flags[F_IT] == 0) beta = 0 and q is not read.
 // W lanes share a face (face_reduce); each lane then updates the rows it holds.
+// The iteration loop of one problem run by nvb cooperating blocks (vb = this block's index
+// among them); `bar` is their arrival counter. The single-problem kernel runs it with the
+// whole grid, the batch kernel with a team of blocks per problem.
 template <int NFN, int W>
-__global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
-    pcg_fused_kernel(PcgArgs a, int count, double rtol2, GridBar* bar) {
+__device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, double rtol2, GridBar* bar, int vb,
+                                               int nvb, double* sh, double* bc) {
   constexpr bool kScatter = NFN % W == 0;
-  __shared__ double sh[kThreads];
-  __shared__ double bc[3];
   if (a.flags[F_CONV] | a.flags[F_BRK]) return;
   const int it0 = a.flags[F_IT];                          // no block changes it before all have read it
   const double rr0 = a.scal[S_RR0];
   double rz = a.scal[S_RZ];
   double beta = a.scal[S_BETA];
   bool first = it0 == 0;
-  const int vb = blockIdx.x, nvb = gridDim.x;
   constexpr int FPW = 32 / W;
   const int64_t warp = (vb * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)nvb * blockDim.x) >> 5;
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
   double* part0 = a.partial;                              // barrier 2i   (p^T q)
   double* part1 = a.partial + 2 * nvb;                    // barrier 2i+1 (r^T z, r^T r)
   for (int it = 0; it < count; ++it) {
-    const unsigned long long B = 2ull * (unsigned long long)(it0 + it);
+    const unsigned long long B = 2ull * (unsigned long long)it;   // the counter is zeroed before every launch
     // ---- S phase
     double pq = 0.0;
     for (int64_t base = warp * FPW; base < nfaces; base += nwarps * FPW) {
@@ -537,6 +538,32 @@ __global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
       if (!(rrn < INFINITY)) a.flags[F_BRK] = 1;
     }
     if (conv || !(rrn < INFINITY)) return;
+  }
+}
+
+template <int NFN, int W>
+__global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
+    pcg_fused_kernel(PcgArgs a, int count, double rtol2, GridBar* bar) {
+  __shared__ double sh[kThreads];
+  __shared__ double bc[3];
+  pcg_fused_body<NFN, W>(a, count, rtol2, bar, blockIdx.x, gridDim.x, sh, bc);
+}
+
+// Batch: block b works for problem team[b].x as block team[b].y of team[b].z, with that
+// problem's order (rows per face) and its own barrier counter (PcgArgs::bar): the teams of all
+// orders share one launch at two blocks per SM.
+__global__ void __launch_bounds__(kThreads, 2)
+    pcg_team_kernel(const PcgArgs* __restrict__ probs, const int4* __restrict__ team, int count, double rtol2) {
+  __shared__ double sh[kThreads];
+  __shared__ double bc[3];
+  const int4 t = team[blockIdx.x];
+  const PcgArgs& a = probs[t.x];
+  GridBar* bar = reinterpret_cast<GridBar*>(a.bar);
+  switch (a.nfn) {
+    case 1: pcg_fused_body<1, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
+    case 4: pcg_fused_body<4, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
+    case 9: pcg_fused_body<9, 2>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
+    default: pcg_fused_body<16, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
   }
 }
 
@@ -715,6 +742,37 @@ cudaError_t launch_fused(const PcgArgs& a, int count, double rtol, void* bar, cu
   GridBar* gb = static_cast<GridBar*>(bar);
   void* params[] = {&aa, &count, &rtol2, &gb};
   return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<NFN, W>, grid, kThreads, params, 0, s);
+}
+
+__global__ void zero_bars_kernel(const PcgArgs* probs, int n) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    probs[p].bar[0] = 0ull;
+    probs[p].bar[1] = 0ull;
+  }
+}
+
+cudaError_t pcg_zero_bars(const PcgArgs* probs, int n, cudaStream_t s) {
+  zero_bars_kernel<<<(n + 255) / 256, 256, 0, s>>>(probs, n);
+  return cudaGetLastError();
+}
+
+cudaError_t pcg_team_capacity(int* blocks) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_team_kernel, kThreads, 0);
+  *blocks = sms * per_sm;
+  return e;
+}
+
+cudaError_t pcg_iterations_team(const PcgArgs* probs, const int4* team, int nblocks, int count, double rtol,
+                                cudaStream_t s, Prof* prof) {
+  const int tok = prof_begin(prof, HYB_K_PCG_FUSED, s);
+  double rtol2 = rtol * rtol;
+  void* params[] = {&probs, &team, &count, &rtol2};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_team_kernel, nblocks, kThreads, params, 0, s);
+  prof_end(prof, tok, s);
+  return e;
 }
 
 cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void* bar, cudaStream_t s, Prof* prof) {

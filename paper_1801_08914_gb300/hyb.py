@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_batch_context.argtypes = [P, I, ctypes.POINTER(P)]
     lib.hyb_batch_set_profiling.argtypes = [P, I]
     lib.hyb_batch_set_graphs.argtypes = [P, I]
+    lib.hyb_batch_set_pcg_fused.argtypes = [P, I]
     lib.hyb_batch_get_profile.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
     lib.hyb_destroy_batch.argtypes = [P]
     lib.hyb_destroy_batch.restype = None
@@ -366,6 +367,11 @@ def hyb_solve_reduced_batch(batch, rtol, maxit, lambdas, check=True):
 def hyb_recover_batch(batch, lambdas, us, check=True):
     st = lib().hyb_recover_batch(batch.handle, _ptr_array(lambdas, "lambdas"), _ptr_array(us, "us"))
     return _check(st, "hyb_recover_batch") if check else st
+
+
+def hyb_batch_set_pcg_fused(batch, on):
+    """True (default): team-fused cooperative PCG per order; False: three launches per iteration."""
+    return _check(lib().hyb_batch_set_pcg_fused(batch.handle, int(bool(on))), "hyb_batch_set_pcg_fused")
 
 
 def hyb_batch_set_graphs(batch, on):

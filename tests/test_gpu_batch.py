@@ -66,6 +66,7 @@ def test_batch_graph_replay_matches_direct_launches():
     b = hyb.hyb_setup_batch([(v, p.nx, p.ny, p.nz) for v, p in zip(verts, probs)], [p.order for p in probs],
                             [dev(p.alpha) for p in probs], [dev(p.beta) for p in probs], precision=0)
     hyb.hyb_assemble_reduced_batch(b, [dev(p.load) for p in probs])
+    hyb.hyb_batch_set_pcg_fused(b, False)              # the default; graphs apply to this form
     sizes = [b.context(i).sizes() for i in range(len(probs))]
     for rtol in (1e-12, 1e-10):
         res = []
@@ -77,4 +78,38 @@ def test_batch_graph_replay_matches_direct_launches():
             res.append((list(its), [l.clone() for l in lams]))
         assert res[0][0] == res[1][0] and max(res[0][0]) > 32
         assert all(torch.equal(x, y) for x, y in zip(res[0][1], res[1][1]))
+    b.close()
+
+
+def test_batch_team_fused_pcg():
+    """The team-fused batched PCG against the three-launch form and solo fused solves: the
+    same CG iterates up to the rounding of the reductions (iteration counts within 2, the
+    solutions within the kappa(H) rtol bound), bitwise reproducible, and per-problem
+    iteration counts (problems converge and leave their teams at different chunks)."""
+    import torch
+    from paper_1801_08914_gb300 import hyb
+    probs = make_batch([(6, 1), (3, 2), (8, 0), (4, 3), (2, 1), (5, 2)])
+    verts = [dev(p.vertices) for p in probs]
+    b = hyb.hyb_setup_batch([(v, p.nx, p.ny, p.nz) for v, p in zip(verts, probs)], [p.order for p in probs],
+                            [dev(p.alpha) for p in probs], [dev(p.beta) for p in probs], precision=0)
+    hyb.hyb_assemble_reduced_batch(b, [dev(p.load) for p in probs])
+    sizes = [b.context(i).sizes() for i in range(len(probs))]
+
+    def run(fused):
+        hyb.hyb_batch_set_pcg_fused(b, fused)
+        lams = [torch.zeros(s["n_lambda"], dtype=torch.float64, device="cuda") for s in sizes]
+        its, rrs, st = hyb.hyb_solve_reduced_batch(b, 1e-12, 20000, lams)
+        assert st == hyb.HYB_OK and max(rrs) <= 1e-12
+        return list(its), lams
+
+    itf, lf = run(True)
+    itf2, lf2 = run(True)
+    itu, lu = run(False)
+    assert itf == itf2 and all(torch.equal(x, y) for x, y in zip(lf, lf2))
+    assert len(set(itf)) > 1
+    for i, p in enumerate(probs):
+        assert abs(itf[i] - itu[i]) <= 2, (i, itf[i], itu[i])
+        d = rel(lf[i].cpu().numpy(), lu[i].cpu().numpy())
+        print(f"team-fused problem {i} (n={p.nx}, k={p.order}): {itf[i]} it (three-launch {itu[i]}), rel diff {d:.1e}")
+        assert d <= 1e-8
     b.close()
