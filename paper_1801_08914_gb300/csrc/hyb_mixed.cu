@@ -1030,7 +1030,7 @@ cudaError_t launch_mixed_batch_k(const ElemArgs* probs, const int2* items, int64
                                  const double* const* lams, double* const* us, cudaStream_t s, Prof* prof) {
   if (n == 0) return cudaSuccess;
   cudaError_t err;
-  if constexpr (K >= 2) {
+  if constexpr (K >= 1) {
     using S = MT<K>;
     if (!recover) {
       err = cudaFuncSetAttribute(element_tiled_kernel_batch<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1076,7 +1076,7 @@ cudaError_t launch_mixed_k(const ElemArgs& a, cudaStream_t s, Prof* prof, bool r
                            double* u) {
   if (a.n_list == 0) return cudaSuccess;
   cudaError_t err;
-  if constexpr (K >= 2) {
+  if constexpr (K >= 1) {
     using S = MT<K>;
     if (!recover) {
       err = cudaFuncSetAttribute(element_tiled_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1118,11 +1118,11 @@ cudaError_t launch_mixed_k(const ElemArgs& a, cudaStream_t s, Prof* prof, bool r
 }  // namespace
 
 // FP32-path store per element: L_M | Xd | L_Z | G^{-1} for the recovery (packed triangles
-// for RT_0 and RT_1, tiles for RT_2 and RT_3).
+// for RT_0, tiles for RT_1 to RT_3).
 int64_t mixed_store_floats(int k) {
   switch (k) {
     case 0: return MX<0>::STORE;
-    case 1: return MX<1>::STORE;
+    case 1: return MT<1>::STORE;
     case 2: return MT<2>::STORE;
     case 3: return MT<3>::STORE;
   }

@@ -1,4 +1,4 @@
-// Tiled FP32 element elimination of the hybridized mixed form for RT_2 and RT_3
+// Tiled FP32 element elimination of the hybridized mixed form for RT_1, RT_2 and RT_3
 // (arXiv:1801.08914, Sec. 3.2; the factorisation of Sec. 3.1 applied to the alpha mass M).
 // Included by hyb_mixed.cu inside namespace hyb { namespace { ... } }; it uses that
 // translation unit's FP64 helpers (geometry64, load_element64, apply_A64/D64/Dt64/G64) and
@@ -25,6 +25,10 @@
 
 template <int K>
 struct TileShape;
+template <>
+struct TileShape<1> {
+  static constexpr int TB = 12, MR = 3, MC = 4, NT = 128, MINB = 4;
+};
 template <>
 struct TileShape<2> {
   static constexpr int TB = 18, MR = 3, MC = 6, NT = 256, MINB = 3;   // 3 CTAs per SM (63 KB each)
