@@ -51,6 +51,8 @@ def parse_args(argv=None):
                     help="fp64, or mixed: FP32 mixed-form elimination below the contrast threshold")
     ap.add_argument("--threshold", type=float, default=0.0,
                     help="mixed: contrast above which elements stay FP64 (0: autotuned by the library)")
+    ap.add_argument("--mode", choices=["hyb", "sc"], default="hyb",
+                    help="hybridization, or static condensation of the interior dofs (FP64 only)")
     ap.add_argument("--refine", type=int, default=0,
                     help="FP64 refinement steps after the solve (hyb_refine; for --precision mixed)")
     ap.add_argument("--refine-rtol", type=float, default=1e-6, help="inner PCG tolerance of a refinement step")
@@ -307,8 +309,12 @@ def run_ours(args):
     iters = []
     jumps = []
 
+    sc = args.mode == "sc"
+    if sc and mixed:
+        raise SystemExit("static condensation runs in FP64 contexts only")
+
     def step(load_dev):
-        hyb.hyb_assemble_reduced(ctx, load_dev, None)
+        (hyb.staticcond_assemble if sc else hyb.hyb_assemble_reduced)(ctx, load_dev, None)
         if args.assembly_only:
             iters.append(0)
         else:
@@ -316,7 +322,7 @@ def run_ours(args):
             if st not in (hyb.HYB_OK,):
                 raise hyb.HybError(st, "hyb_solve_reduced")
             iters.append(it)
-        hyb.hyb_recover(ctx, lam, u)
+        (hyb.staticcond_recover if sc else hyb.hyb_recover)(ctx, lam, u)
         if args.refine and not args.assembly_only:
             j, _ = hyb.hyb_refine(ctx, args.refine, args.refine_rtol, args.maxit, lam, u)
             jumps.append(j)
@@ -438,10 +444,14 @@ def run_ours(args):
         workload = workload.replace("FP64", f"mixed FP32/FP64 ({how}threshold {theta:g}: {n32} FP32 + {n64} FP64 elements)")
     if args.refine and not args.assembly_only:
         workload += f", {args.refine} FP64 refinement steps"
+    if sc:
+        workload = workload.replace("hybridization", "static condensation").replace("FP64", "FP64 static condensation")
     if args.assembly_only:
         workload += " (element phase only: assemble + recover)"
     line = {
-        "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+        "metric": (METRIC.replace("hybridized", "statically condensed") if sc else
+                   METRIC.replace("FP64 GPU path", "mixed FP32/FP64 GPU path") if mixed else METRIC),
+        "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": workload, "elements": E, "order": p.order, "n_loc": n_loc, "n_lambda": N,
@@ -456,6 +466,8 @@ def run_ours(args):
         "assembly_elements_per_s": E / (elem_ms * 1e-3) if elem_ms > 0 else None,
         "pcg_ms_per_iteration": ((prof["spmv"][0] + prof["pcg_vector"][0] + prof["pcg_fused"][0]) / it_total
                                  if it_total else None),
+        "reduced_dofs_per_s": (N * args.steps / ((prof["spmv"][0] + prof["pcg_vector"][0] + prof["pcg_fused"][0]) * 1e-3)
+                               if it_total else None),
         "clocks": ck,
         "wall_s": t_wall,
     }

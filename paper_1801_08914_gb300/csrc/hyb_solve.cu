@@ -69,6 +69,11 @@ __device__ __forceinline__ double block_sum_smem(double v, double* sh) {
 // its current values, sends the other half to its partner and adds what it receives, so lane
 // gl ends with the full sums of NFN / W rows, acc[j] being row scatter_row(j, gl), after
 // NFN (1 - 1/W) adds instead of NFN log2(W); otherwise every lane reduces every row.
+// Row sums per lane padded up to a multiple of W, so that the reduce-scatter applies to any
+// number of rows per face (9 rows on 4 lanes: 12 sums, the last 3 always zero).
+template <int NFN, int W>
+__host__ __device__ constexpr int padded_rows() { return (NFN + W - 1) / W * W; }
+
 template <int NFN, int W>
 __device__ __forceinline__ int scatter_row(int j, int gl) {
   int row = j, S = NFN;
@@ -184,11 +189,12 @@ __device__ __forceinline__ void spmv_face_body(const PcgArgs& a, int vb, int nvb
   const int sub = lane / W, gl = lane % W;
   const int64_t nfaces = a.n / NFN;
   double pq = 0.0;
+  constexpr int NP = padded_rows<NFN, W>();
   for (int64_t base = warp * FPW; base < nfaces; base += nwarps * FPW) {
     const int64_t f = base + sub;
-    double acc[NFN];
+    double acc[NP];
 #pragma unroll
-    for (int m = 0; m < NFN; ++m) acc[m] = 0.0;
+    for (int m = 0; m < NP; ++m) acc[m] = 0.0;
     if (f < nfaces) {
       const int64_t r0 = f * NFN;
       const int64_t lo = a.row_ptr[r0];
@@ -200,12 +206,14 @@ __device__ __forceinline__ void spmv_face_body(const PcgArgs& a, int vb, int nvb
         for (int m = 0; m < NFN; ++m) acc[m] = fma(a.val[lo + (int64_t)m * len + t], pj, acc[m]);
       }
     }
-    face_reduce<NFN, W>(acc, gl);
+    face_reduce<NP, W>(acc, gl);
     if (f < nfaces) {
-      if constexpr (NFN % W == 0) {
+      if constexpr (NP % W == 0) {
 #pragma unroll
-        for (int j = 0; j < NFN / W; ++j) {
-          const int64_t i = f * NFN + scatter_row<NFN, W>(j, gl);
+        for (int j = 0; j < NP / W; ++j) {
+          const int row = scatter_row<NP, W>(j, gl);
+          if (row >= NFN) continue;
+          const int64_t i = f * NFN + row;
           a.q[i] = acc[j];
           pq = fma(a.p[i], acc[j], pq);
         }
@@ -408,7 +416,8 @@ struct GridBar {
 template <int NFN, int W>
 __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, double rtol2, GridBar* bar, int vb,
                                                int nvb, double* sh, double* bc) {
-  constexpr bool kScatter = NFN % W == 0;
+  constexpr int NP = padded_rows<NFN, W>();
+  constexpr bool kScatter = NP % W == 0;
   if (a.flags[F_CONV] | a.flags[F_BRK]) return;
   const int it0 = a.flags[F_IT];                          // no block changes it before all have read it
   const double rr0 = a.scal[S_RR0];
@@ -428,9 +437,9 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
     double pq = 0.0;
     for (int64_t base = warp * FPW; base < nfaces; base += nwarps * FPW) {
       const int64_t f = base + sub;
-      double acc[NFN];
+      double acc[NP];
 #pragma unroll
-      for (int m = 0; m < NFN; ++m) acc[m] = 0.0;
+      for (int m = 0; m < NP; ++m) acc[m] = 0.0;
       if (f < nfaces) {
         const int64_t r0 = f * NFN;
         const int64_t lo = __ldcs(a.row_ptr + r0);
@@ -442,12 +451,14 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
           for (int m = 0; m < NFN; ++m) acc[m] = fma(__ldcs(a.val + lo + (int64_t)m * len + t), zj, acc[m]);
         }
       }
-      face_reduce<NFN, W>(acc, gl);
+      face_reduce<NP, W>(acc, gl);
       if constexpr (kScatter) {
         if (f < nfaces) {
 #pragma unroll
-          for (int j = 0; j < NFN / W; ++j) {
-            const int64_t i = f * NFN + scatter_row<NFN, W>(j, gl);
+          for (int j = 0; j < NP / W; ++j) {
+            const int row = scatter_row<NP, W>(j, gl);
+            if (row >= NFN) continue;
+            const int64_t i = f * NFN + row;
             const double zi = __ldcg(a.z + i);
             const double pi = first ? zi : fma(beta, a.p[i], zi);
             const double qi = first ? acc[j] : fma(beta, a.q[i], acc[j]);
@@ -562,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   switch (a.nfn) {
     case 1: pcg_fused_body<1, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
     case 4: pcg_fused_body<4, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
-    case 9: pcg_fused_body<9, 2>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
+    case 9: pcg_fused_body<9, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
     default: pcg_fused_body<16, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
   }
 }
@@ -646,7 +657,7 @@ __global__ void __launch_bounds__(kThreads) spmv_batch_kernel(const PcgArgs* pro
   switch (a.nfn) {
     case 1: spmv_face_body<1, 4>(a, vb, nvb, sh); break;
     case 4: spmv_face_body<4, 4>(a, vb, nvb, sh); break;
-    case 9: spmv_face_body<9, 2>(a, vb, nvb, sh); break;
+    case 9: spmv_face_body<9, 4>(a, vb, nvb, sh); break;
     default: spmv_face_body<16, 4>(a, vb, nvb, sh); break;
   }
 }
@@ -712,7 +723,7 @@ cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_
     switch (a.nfn) {
       case 1: spmv_face_kernel<1, 4><<<nbs, kThreads, 0, s>>>(a); break;
       case 4: spmv_face_kernel<4, 4><<<nbs, kThreads, 0, s>>>(a); break;
-      case 9: spmv_face_kernel<9, 2><<<nbs, kThreads, 0, s>>>(a); break;
+      case 9: spmv_face_kernel<9, 4><<<nbs, kThreads, 0, s>>>(a); break;
       case 16: spmv_face_kernel<16, 4><<<nbs, kThreads, 0, s>>>(a); break;
       default: return cudaErrorInvalidValue;
     }
@@ -781,7 +792,7 @@ cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void*
   switch (a.nfn) {
     case 1: e = launch_fused<1, 4>(a, count, rtol, bar, s); break;
     case 4: e = launch_fused<4, 4>(a, count, rtol, bar, s); break;
-    case 9: e = launch_fused<9, 2>(a, count, rtol, bar, s); break;
+    case 9: e = launch_fused<9, 4>(a, count, rtol, bar, s); break;
     case 16: e = launch_fused<16, 4>(a, count, rtol, bar, s); break;
     default: e = cudaErrorInvalidValue;
   }
