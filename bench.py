@@ -204,7 +204,7 @@ def run_reference(args):
     v = E / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": args.gpus,
             "steps": K, "warmup": W, "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": f"{SAMPLE_N}^3 mesh of the same recipe", "parallelism": "none"},
             "cpu_baseline": {"value": v, "unit": "elements/s", "cores": 1, "kind": "oracle",
                              "sample": f"{SAMPLE_N}^3 mesh, full step per sample"},
