@@ -57,7 +57,7 @@ struct ElemArgs {
   double* Lstore;             // packed lower factor, n(n+1)/2 per FP64 element
   double* zstore;             // E x n forward-substituted load (FP64 path) / modified load (FP32 path)
   const int32_t* slot;        // per element: index into its precision's factor store, or null (= e)
-  float* Lstore32;            // FP32 path: per element L_M | Xd | L_Z
+  float* Lstore32;            // FP32 path: per element the tiles of L_M | Xd | L_Z | G^{-1}
   int* status;
   long long* err_elem;
 };

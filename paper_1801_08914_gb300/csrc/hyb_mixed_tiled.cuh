@@ -1,4 +1,4 @@
-// Tiled FP32 element elimination of the hybridized mixed form for RT_1, RT_2 and RT_3
+// Tiled FP32 element elimination of the hybridized mixed form (RT_0 to RT_3)
 // (arXiv:1801.08914, Sec. 3.2; the factorisation of Sec. 3.1 applied to the alpha mass M).
 // Included by hyb_mixed.cu inside namespace hyb { namespace { ... } }; it uses that
 // translation unit's FP64 helpers (geometry64, load_element64, apply_A64/D64/Dt64/G64) and
@@ -25,6 +25,10 @@
 
 template <int K>
 struct TileShape;
+template <>
+struct TileShape<0> {
+  static constexpr int TB = 6, MR = 3, MC = 3, NT = 64, MINB = 8;
+};
 template <>
 struct TileShape<1> {
   static constexpr int TB = 12, MR = 3, MC = 4, NT = 128, MINB = 4;
@@ -58,20 +62,20 @@ struct MT {
                              3 * NQ /*U*/ + 3 * NQ /*Wv*/ + NQ /*Dv*/ + NC /*xc*/ + 2 * TMP64 + 8 + NQK /*qv*/ +
                              (N > NQ ? N : NQ) /*rq*/ + P * p /*DcO64*/;
   static constexpr int TABF = (2 * P * Q + p * Q + P * P * Q + P * p * Q + p * p * Q + P * p + 3) / 4 * 4;
-  static constexpr int64_t STORE = ((int64_t)LT + XD + ZTS + NQK * NQK + 3) / 4 * 4;   // L_M | Xd | L_Z | G^{-1}
-  static constexpr int F32 = TABF + LT + XD + ZTS + N /*vec*/ + 2 * NQP /*tq tmpq*/ + 32 /*ybuf*/ + 8 /*flag*/ +
+  // scratch before the factorisation (in the L_M region): G, its tiles, the G^{-1} solve,
+  // the sum-factorisation temporaries; mass-assembly temporaries (in the Xd region)
+  static constexpr int GSCR = NQK * NQK + ZTS + NQP * NQP + Q * Q * p * p + Q * p * p * p * p + NQ;
+  static constexpr int MSCR = 6 * NQ + Q * Q * P * P + Q * P * P * p * p;
+  static constexpr int LTA = ((LT > GSCR ? LT : GSCR) + 3) / 4 * 4;   // L_M region (only RT_0 needs the padding)
+  static constexpr int XDA = ((XD > MSCR ? XD : MSCR) + 3) / 4 * 4;   // Xd region
+  static constexpr int64_t STORE = ((int64_t)LTA + XDA + ZTS + NQK * NQK + 3) / 4 * 4;   // L_M | Xd | L_Z | G^{-1}
+  static constexpr int F32 = TABF + LTA + XDA + ZTS + N /*vec*/ + 2 * NQP /*tq tmpq*/ + 32 /*ybuf*/ + 8 /*flag*/ +
                              (YPS_IN_LT ? 0 : YPS);
   static constexpr size_t SMEM = sizeof(double) * D64 + sizeof(float) * F32 + sizeof(int) * N;
   static_assert(N % TB == 0 && NI % TB == 0, "tiles must split the interior and face blocks");
   static_assert(TB % MR == 0 && TB % MC == 0 && NQP % MC == 0 && NB % MC == 0, "micro-tile shape");
   static_assert(TB <= 32, "one warp per diagonal tile");
-  // scratch before the factorisation (in the L_M region): G, its tiles, the G^{-1} solve,
-  // the sum-factorisation temporaries
-  static constexpr int GSCR = NQK * NQK + ZTS + NQP * NQP + Q * Q * p * p + Q * p * p * p * p + NQ;
-  static_assert(GSCR <= LT, "G scratch fits in the L_M region");
-  static constexpr int MSCR = 6 * NQ + Q * Q * P * P + Q * P * P * p * p;   // mass assembly temporaries
-  static_assert(MSCR <= XD, "mass scratch fits in the Xd region");
-  static_assert(LT % 4 == 0 && XD % 4 == 0 && ZTS % 4 == 0 && (D64 * 2) % 4 == 0, "16-byte aligned tile blocks");
+  static_assert(ZTS % 4 == 0 && (D64 * 2) % 4 == 0, "16-byte aligned tile blocks");
 };
 
 // Refinement steps of each element solve: every step multiplies the error by about
@@ -462,7 +466,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   const int tid = threadIdx.x;
   const int64_t slot = args.slot ? args.slot[e] : e;
   float* store = args.Lstore32 + slot * S::STORE;                // this element's factors (global)
-  float* Gi = store + S::LT + S::XD + S::ZTS;                     // G^{-1}
+  float* Gi = store + S::LTA + S::XDA + S::ZTS;                   // G^{-1}
 
   // ---- shared memory
   double* d = smem;
@@ -498,8 +502,8 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   float* VcVo = fl; fl += P * p * Q;
   float* VoVo = fl; fl += p * p * Q;
   float* DcO = fl; fl += S::TABF - (2 * P * Q + p * Q + P * P * Q + P * p * Q + p * p * Q);
-  float* Lt = fl; fl += S::LT;
-  float* Xd = fl; fl += S::XD;
+  float* Lt = fl; fl += S::LTA;
+  float* Xd = fl; fl += S::XDA;
   float* Zt = fl; fl += S::ZTS;
   float* vec = fl; fl += N;
   float* tq = fl; fl += NQP;
@@ -580,7 +584,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     // ---- the stored factors back into shared memory
     const float4* src = reinterpret_cast<const float4*>(store);
     float4* dst = reinterpret_cast<float4*>(Lt);
-    constexpr int NV = (S::LT + S::XD + S::ZTS) / 4;           // Lt | Xd | Zt are contiguous
+    constexpr int NV = (S::LTA + S::XDA + S::ZTS) / 4;         // Lt | Xd | Zt are contiguous
     for (int t = tid; t < NV; t += NT) dst[t] = __ldcs(src + t);
     __syncthreads();
   } else {
@@ -782,7 +786,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     // ---- keep the factors for the recovery
     const float4* src = reinterpret_cast<const float4*>(Lt);
     float4* dst = reinterpret_cast<float4*>(store);
-    constexpr int NV = (S::LT + S::XD + S::ZTS) / 4;
+    constexpr int NV = (S::LTA + S::XDA + S::ZTS) / 4;
     for (int t = tid; t < NV; t += NT) __stcs(dst + t, src[t]);
   }
   }
@@ -790,118 +794,118 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   // ---- the refined element solve: g_T (assembly) or u_T (recovery)
   refine_tiled<K>(f, x, qv, kRefineSteps, alpha, beta, bmask, g6, gd, Vc, Dc, Vo, DcO64, dofcode, Lt, Xd, Zt, Gi, r, ut, rq,
                   U, Wv, Dv, xc, t1, t2, vec, tq, tmpq);
-  if (RECOVER) {
+  if constexpr (RECOVER) {
     double* ue = u_out + e * (int64_t)N;
     for (int i = tid; i < N; i += NT) ue[i] = x[i];
-    return;
-  }
-  for (int ib = tid; ib < NB; ib += NT) {
-    const int a = ib / NFN, m1 = ib % NFN;
-    if (ef[a] < 0) continue;
-    const double v = ((a & 1) ? 1.0 : -1.0) * wf[m1] * x[NI + ib];
-    const int64_t gi = (int64_t)ef[a] * NFN + m1;
-    if (args.colour == 1) args.rhs[gi] += v;
-    else args.rhs[gi] = v;
-  }
-
-  // ---- Y = L_M,bb^{-1}, P = Xd_b^T Y, V = L_Z^{-1} P, S = Y^T Y - V^T V. The buffers take the
-  // interior tile columns of L_M (no longer needed) where they fit.
-  float* Y = yps;                                 // [NB][NB]
-  float* Pv = Y + NB * NB;                        // [NQP][NB]
-  __syncthreads();
-  for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0f : 0.0f;
-  __syncthreads();
-  tile_fwd_mat<TB, MR, MC, NT>(Lt, T, S::TI, Y, NB);
-  {
-    constexpr int RM = NQP / MR, CM = NB / MC;
-    for (int it = tid; it < RM * CM; it += NT) {  // P[a][j] = sum_i Xd[NI + i][a] Y[i][j]
-      const int a0 = (it / CM) * MR, j0 = (it % CM) * MC;
-      float acc[MR][MC];
-#pragma unroll
-      for (int i = 0; i < MR; ++i)
-#pragma unroll
-        for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
-      for (int k = 0; k < NB; ++k) {
-        float a[MR], b[MC];
-#pragma unroll
-        for (int i = 0; i < MR; ++i) a[i] = Xd[(NI + k) * NQP + a0 + i];
-#pragma unroll
-        for (int j = 0; j < MC; ++j) b[j] = Y[k * NB + j0 + j];
-#pragma unroll
-        for (int i = 0; i < MR; ++i)
-#pragma unroll
-          for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-      }
-#pragma unroll
-      for (int i = 0; i < MR; ++i)
-#pragma unroll
-        for (int j = 0; j < MC; ++j) Pv[(a0 + i) * NB + j0 + j] = acc[i][j];
+  } else {
+    for (int ib = tid; ib < NB; ib += NT) {
+      const int a = ib / NFN, m1 = ib % NFN;
+      if (ef[a] < 0) continue;
+      const double v = ((a & 1) ? 1.0 : -1.0) * wf[m1] * x[NI + ib];
+      const int64_t gi = (int64_t)ef[a] * NFN + m1;
+      if (args.colour == 1) args.rhs[gi] += v;
+      else args.rhs[gi] = v;
     }
-  }
-  __syncthreads();
-  tile_fwd_mat<TB, MR, MC, NT>(Zt, TQ, 0, Pv, NB);
-  // ---- S[i][j] = sum_m Y[m][i] Y[m][j] - sum_a V[a][i] V[a][j] for i >= j, in register
-  // micro-tiles, scattered as S_T = D_c S D_c straight into the FP64 CSR values: entry (i, j)
-  // and its mirror (j, i) get the same value, so both face blocks of a pair are bitwise
-  // transposed.
-  __shared__ int64_t s_row0[6];
-  __shared__ int s_rlen[6];
-  if (tid < 6) {
-    const int64_t r0 = ef[tid] >= 0 ? args.row_ptr[(int64_t)ef[tid] * NFN] : 0;
-    s_row0[tid] = r0;
-    s_rlen[tid] = ef[tid] >= 0 ? (int)(args.row_ptr[(int64_t)ef[tid] * NFN + 1] - r0) : 0;
-  }
-  __syncthreads();
-  const int64_t* boff = args.blockoff + e * 36;
-  auto put = [&](int ib, int jb, float sv) {
-    const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
-    if (ef[a] < 0 || ef[b] < 0) return;
-    const double v = (((a ^ b) & 1) ? -1.0 : 1.0) * wf[m1] * wf[m2] * (double)sv;
-    const int64_t pos = boff[a * 6 + b] + m1 * (int64_t)s_rlen[a] + m2;
-    if (a == b && args.colour == 1) args.val[pos] += v;
-    else args.val[pos] = v;
-  };
-  {
-    constexpr int RM = NB / MR, CM = NB / MC;
-    for (int it = tid; it < RM * CM; it += NT) {
-      const int i0 = (it / CM) * MR, j0 = (it % CM) * MC;
-      if (i0 + MR - 1 < j0) continue;             // strictly above the diagonal
-      float acc[MR][MC];
-#pragma unroll
-      for (int i = 0; i < MR; ++i)
-#pragma unroll
-        for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
-      for (int k = 0; k < NB; ++k) {
-        float a[MR], b[MC];
-#pragma unroll
-        for (int i = 0; i < MR; ++i) a[i] = Y[k * NB + i0 + i];
-#pragma unroll
-        for (int j = 0; j < MC; ++j) b[j] = Y[k * NB + j0 + j];
-#pragma unroll
+
+    // ---- Y = L_M,bb^{-1}, P = Xd_b^T Y, V = L_Z^{-1} P, S = Y^T Y - V^T V. The buffers take the
+    // interior tile columns of L_M (no longer needed) where they fit.
+    float* Y = yps;                                 // [NB][NB]
+    float* Pv = Y + NB * NB;                        // [NQP][NB]
+    __syncthreads();
+    for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0f : 0.0f;
+    __syncthreads();
+    tile_fwd_mat<TB, MR, MC, NT>(Lt, T, S::TI, Y, NB);
+    {
+      constexpr int RM = NQP / MR, CM = NB / MC;
+      for (int it = tid; it < RM * CM; it += NT) {  // P[a][j] = sum_i Xd[NI + i][a] Y[i][j]
+        const int a0 = (it / CM) * MR, j0 = (it % CM) * MC;
+        float acc[MR][MC];
+  #pragma unroll
         for (int i = 0; i < MR; ++i)
-#pragma unroll
-          for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-      }
-      for (int k = 0; k < NQK; ++k) {
-        float a[MR], b[MC];
-#pragma unroll
-        for (int i = 0; i < MR; ++i) a[i] = Pv[k * NB + i0 + i];
-#pragma unroll
-        for (int j = 0; j < MC; ++j) b[j] = Pv[k * NB + j0 + j];
-#pragma unroll
-        for (int i = 0; i < MR; ++i)
-#pragma unroll
-          for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(-a[i], b[j], acc[i][j]);
-      }
-#pragma unroll
-      for (int i = 0; i < MR; ++i)
-#pragma unroll
-        for (int j = 0; j < MC; ++j) {
-          const int ib = i0 + i, jb = j0 + j;
-          if (ib < jb) continue;
-          put(ib, jb, acc[i][j]);
-          if (ib != jb) put(jb, ib, acc[i][j]);
+  #pragma unroll
+          for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
+        for (int k = 0; k < NB; ++k) {
+          float a[MR], b[MC];
+  #pragma unroll
+          for (int i = 0; i < MR; ++i) a[i] = Xd[(NI + k) * NQP + a0 + i];
+  #pragma unroll
+          for (int j = 0; j < MC; ++j) b[j] = Y[k * NB + j0 + j];
+  #pragma unroll
+          for (int i = 0; i < MR; ++i)
+  #pragma unroll
+            for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
+  #pragma unroll
+        for (int i = 0; i < MR; ++i)
+  #pragma unroll
+          for (int j = 0; j < MC; ++j) Pv[(a0 + i) * NB + j0 + j] = acc[i][j];
+      }
+    }
+    __syncthreads();
+    tile_fwd_mat<TB, MR, MC, NT>(Zt, TQ, 0, Pv, NB);
+    // ---- S[i][j] = sum_m Y[m][i] Y[m][j] - sum_a V[a][i] V[a][j] for i >= j, in register
+    // micro-tiles, scattered as S_T = D_c S D_c straight into the FP64 CSR values: entry (i, j)
+    // and its mirror (j, i) get the same value, so both face blocks of a pair are bitwise
+    // transposed.
+    __shared__ int64_t s_row0[6];
+    __shared__ int s_rlen[6];
+    if (tid < 6) {
+      const int64_t r0 = ef[tid] >= 0 ? args.row_ptr[(int64_t)ef[tid] * NFN] : 0;
+      s_row0[tid] = r0;
+      s_rlen[tid] = ef[tid] >= 0 ? (int)(args.row_ptr[(int64_t)ef[tid] * NFN + 1] - r0) : 0;
+    }
+    __syncthreads();
+    const int64_t* boff = args.blockoff + e * 36;
+    auto put = [&](int ib, int jb, float sv) {
+      const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
+      if (ef[a] < 0 || ef[b] < 0) return;
+      const double v = (((a ^ b) & 1) ? -1.0 : 1.0) * wf[m1] * wf[m2] * (double)sv;
+      const int64_t pos = boff[a * 6 + b] + m1 * (int64_t)s_rlen[a] + m2;
+      if (a == b && args.colour == 1) args.val[pos] += v;
+      else args.val[pos] = v;
+    };
+    {
+      constexpr int RM = NB / MR, CM = NB / MC;
+      for (int it = tid; it < RM * CM; it += NT) {
+        const int i0 = (it / CM) * MR, j0 = (it % CM) * MC;
+        if (i0 + MR - 1 < j0) continue;             // strictly above the diagonal
+        float acc[MR][MC];
+  #pragma unroll
+        for (int i = 0; i < MR; ++i)
+  #pragma unroll
+          for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
+        for (int k = 0; k < NB; ++k) {
+          float a[MR], b[MC];
+  #pragma unroll
+          for (int i = 0; i < MR; ++i) a[i] = Y[k * NB + i0 + i];
+  #pragma unroll
+          for (int j = 0; j < MC; ++j) b[j] = Y[k * NB + j0 + j];
+  #pragma unroll
+          for (int i = 0; i < MR; ++i)
+  #pragma unroll
+            for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        for (int k = 0; k < NQK; ++k) {
+          float a[MR], b[MC];
+  #pragma unroll
+          for (int i = 0; i < MR; ++i) a[i] = Pv[k * NB + i0 + i];
+  #pragma unroll
+          for (int j = 0; j < MC; ++j) b[j] = Pv[k * NB + j0 + j];
+  #pragma unroll
+          for (int i = 0; i < MR; ++i)
+  #pragma unroll
+            for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(-a[i], b[j], acc[i][j]);
+        }
+  #pragma unroll
+        for (int i = 0; i < MR; ++i)
+  #pragma unroll
+          for (int j = 0; j < MC; ++j) {
+            const int ib = i0 + i, jb = j0 + j;
+            if (ib < jb) continue;
+            put(ib, jb, acc[i][j]);
+            if (ib != jb) put(jb, ib, acc[i][j]);
+          }
+      }
     }
   }
 }
