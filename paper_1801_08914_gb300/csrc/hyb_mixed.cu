@@ -182,6 +182,106 @@ __device__ void apply_A64(const double* x, double* y, double alpha, double beta,
   }
 }
 
+// y = alpha M x (the Piola-mapped mass, no boundary conditions), FP64, by sum factorisation
+// with the three components in every pass: interpolation to the Gauss points in three
+// contractions, the 3 x 3 geometric factor, testing in three contractions; 7 barriers.
+// t1, t2: 3 P Q Q doubles each.
+template <int K, int NT>
+__device__ void apply_mass64(const double* x, double* y, double alpha, const double* g6, const double* Vc,
+                             const double* Vo, double* U, double* Wv, double* t1, double* t2) {
+  constexpr int P = K + 2, p = K + 1, Q = K + 2, NQ = Q * Q * Q;
+  // component c has n0 x n1 x n2 dofs: P along its own axis, p across
+  constexpr int S1 = Q * p * p, S1B = Q * P * p;              // stage-1 items of c = 0, of c = 1, 2
+  constexpr int S2A = Q * Q * p, S2B = Q * Q * P;             // stage-2 items of c = 0, 1 and of c = 2
+  const int tid = threadIdx.x;
+  auto nd = [](int c, int d) { return c == d ? P : p; };
+  auto tab = [&](int c, int d) { return c == d ? Vc : Vo; };
+  // forward stage 1: t1[c][i2][i1][o0] = sum_i0 x[c](i0, i1, i2) T(i0, o0)
+  for (int t = tid; t < S1 + 2 * S1B; t += NT) {
+    const int c = t < S1 ? 0 : (t < S1 + S1B ? 1 : 2);
+    const int l = t - (c == 0 ? 0 : (c == 1 ? S1 : S1 + S1B));
+    const int n0 = nd(c, 0), n1 = nd(c, 1);
+    const int o0 = l % Q, i1 = (l / Q) % n1, i2 = l / (Q * n1);
+    const double* A = tab(c, 0);
+    double acc = 0.0;
+    for (int i0 = 0; i0 < n0; ++i0) acc = fma(x[local_index<K>(c, i0, i1, i2)], A[i0 * Q + o0], acc);
+    t1[t] = acc;
+  }
+  __syncthreads();
+  // forward stage 2: t2[c][i2][o1][o0] = sum_i1 t1[c][i2][i1][o0] T(i1, o1)
+  for (int t = tid; t < 2 * S2A + S2B; t += NT) {
+    const int c = t < S2A ? 0 : (t < 2 * S2A ? 1 : 2);
+    const int l = t - c * S2A;
+    const int n1 = nd(c, 1);
+    const int o0 = l % Q, o1 = (l / Q) % Q, i2 = l / (Q * Q);
+    const double* A = tab(c, 1);
+    const double* src = t1 + (c == 0 ? 0 : (c == 1 ? S1 : S1 + S1B));
+    double acc = 0.0;
+    for (int i1 = 0; i1 < n1; ++i1) acc = fma(src[(i2 * n1 + i1) * Q + o0], A[i1 * Q + o1], acc);
+    t2[t] = acc;
+  }
+  __syncthreads();
+  // forward stage 3: U[c][o2][o1][o0] = sum_i2 t2[c][i2][o1][o0] T(i2, o2)
+  for (int t = tid; t < 3 * NQ; t += NT) {
+    const int c = t / NQ, l = t % NQ;
+    const int n2 = nd(c, 2);
+    const int o01 = l % (Q * Q), o2 = l / (Q * Q);
+    const double* A = tab(c, 2);
+    const double* src = t2 + c * S2A;
+    double acc = 0.0;
+    for (int i2 = 0; i2 < n2; ++i2) acc = fma(src[i2 * Q * Q + o01], A[i2 * Q + o2], acc);
+    U[t] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < 3 * NQ; t += NT) {
+    const int c = t / NQ, q = t % NQ;
+    Wv[t] = alpha * (g6[gslot(c, 0) * NQ + q] * U[q] + g6[gslot(c, 1) * NQ + q] * U[NQ + q] +
+                     g6[gslot(c, 2) * NQ + q] * U[2 * NQ + q]);
+  }
+  __syncthreads();
+  // test stage 1: t1[c][q2][q1][i0] = sum_q0 Wv[c][q2][q1][q0] T(i0, q0)
+  constexpr int B1A = p * Q * Q, B1B = P * Q * Q;             // items of c = 0 (P) and c = 1, 2 (p)
+  for (int t = tid; t < B1B + 2 * B1A; t += NT) {
+    const int c = t < B1B ? 0 : (t < B1B + B1A ? 1 : 2);
+    const int l = t - (c == 0 ? 0 : (c == 1 ? B1B : B1B + B1A));
+    const int n0 = nd(c, 0);
+    const int i0 = l % n0, q1 = (l / n0) % Q, q2 = l / (n0 * Q);
+    const double* A = tab(c, 0);
+    const double* src = Wv + c * NQ + (q2 * Q + q1) * Q;
+    double acc = 0.0;
+    for (int q0 = 0; q0 < Q; ++q0) acc = fma(src[q0], A[i0 * Q + q0], acc);
+    t1[t] = acc;
+  }
+  __syncthreads();
+  // test stage 2: t2[c][q2][i1][i0] = sum_q1 t1[c][q2][q1][i0] T(i1, q1)
+  constexpr int B2A = P * p * Q, B2B = p * p * Q;             // items of c = 0, 1 (n0 n1 = P p) and c = 2 (p p)
+  for (int t = tid; t < 2 * B2A + B2B; t += NT) {
+    const int c = t < B2A ? 0 : (t < 2 * B2A ? 1 : 2);
+    const int l = t - c * B2A;
+    const int n0 = nd(c, 0), n1 = nd(c, 1);
+    const int i0 = l % n0, i1 = (l / n0) % n1, q2 = l / (n0 * n1);
+    const double* A = tab(c, 1);
+    const double* src = t1 + (c == 0 ? 0 : (c == 1 ? B1B : B1B + B1A));
+    double acc = 0.0;
+    for (int q1 = 0; q1 < Q; ++q1) acc = fma(src[(q2 * Q + q1) * n0 + i0], A[i1 * Q + q1], acc);
+    t2[t] = acc;
+  }
+  __syncthreads();
+  // test stage 3: y[c](i0, i1, i2) = sum_q2 t2[c][q2][i1][i0] T(i2, q2)
+  constexpr int NC = P * p * p;
+  for (int t = tid; t < 3 * NC; t += NT) {
+    const int c = t / NC, l = t % NC;
+    const int n0 = nd(c, 0), n1 = nd(c, 1);
+    const int i0 = l % n0, i1 = (l / n0) % n1, i2 = l / (n0 * n1);
+    const double* A = tab(c, 2);
+    const double* src = t2 + c * B2A;
+    double acc = 0.0;
+    for (int q2 = 0; q2 < Q; ++q2) acc = fma(src[(q2 * n1 + i1) * n0 + i0], A[i2 * Q + q2], acc);
+    y[local_index<K>(c, i0, i1, i2)] = acc;
+  }
+  __syncthreads();
+}
+
 // y = D' q (D' the divergence coefficients with zero rows on essential dofs), FP64.
 template <int K, int NT>
 __device__ void apply_D64(const double* q, double* y, const int* dofcode, const double* DcO, int bmask) {

@@ -1,7 +1,7 @@
 // Tiled FP32 element elimination of the hybridized mixed form (RT_0 to RT_3)
 // (arXiv:1801.08914, Sec. 3.2; the factorisation of Sec. 3.1 applied to the alpha mass M).
 // Included by hyb_mixed.cu inside namespace hyb { namespace { ... } }; it uses that
-// translation unit's FP64 helpers (geometry64, load_element64, apply_A64/D64/Dt64/G64) and
+// translation unit's FP64 helpers (geometry64, load_element64, apply_mass64/A64/D64/Dt64/G64) and
 // its constant tables.
 //
 // The same algebra as the untiled kernel:
@@ -57,7 +57,7 @@ struct MT {
   static constexpr int LT_INTERIOR = (TI * T - TI * (TI - 1) / 2) * TT;   // tile columns J < TI
   static constexpr int YPS = NB * NB + NQP * NB;           // Y | P (= V) after the refinement
   static constexpr bool YPS_IN_LT = YPS <= LT_INTERIOR;
-  static constexpr int TMP64 = P * Q * Q;
+  static constexpr int TMP64 = 3 * P * Q * Q;             // apply_mass64 scratch (all three components)
   static constexpr int D64 = 24 + 24 + 2 * P * Q + p * Q + 2 * Q + NFN + 7 * NQ /*g6 gd*/ + 4 * N /*f x r ut*/ +
                              3 * NQ /*U*/ + 3 * NQ /*Wv*/ + NQ /*Dv*/ + NC /*xc*/ + 2 * TMP64 + 8 + NQK /*qv*/ +
                              (N > NQ ? N : NQ) /*rq*/ + P * p /*DcO64*/;
@@ -439,7 +439,7 @@ __device__ void refine_tiled(const double* f, double* x, double* q, int steps, d
   for (int it = 0; it <= steps; ++it) {
     for (int i = tid; i < N; i += NT) ut[i] = is_e(i) ? 0.0 : x[i];
     __syncthreads();
-    apply_A64<K, NT>(ut, r, alpha, 0.0, false, g6, gd, Vc, Dc, Vo, U, Wv, Dv, xc, t1, t2);
+    apply_mass64<K, NT>(ut, r, alpha, g6, Vc, Vo, U, Wv, t1, t2);
     apply_D64<K, NT>(q, rq, dofcode, DcO64, bmask);
     for (int i = tid; i < N; i += NT) vec[i] = (float)(is_e(i) ? f[i] - x[i] : f[i] - r[i] - rq[i]);
     __syncthreads();
@@ -554,7 +554,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     const double* coef = args.load + e * (int64_t)N;
     for (int i = tid; i < N; i += NT) ut[i] = coef[i];
     __syncthreads();
-    apply_A64<K, NT>(ut, f, 1.0, 0.0, false, g6, gd, Vc, Dc, Vo, U, Wv, Dv, xc, t1, t2);
+    apply_mass64<K, NT>(ut, f, 1.0, g6, Vc, Vo, U, Wv, t1, t2);
     if (bmask) {
       const double* ue = args.ess ? args.ess + e * (int64_t)N : nullptr;
       if (ue) {
