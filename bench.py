@@ -76,6 +76,17 @@ def dist_init(backend):
     return rank, local, world
 
 
+def build_once(local):
+    """Compile the library on the node's first rank only (the others would write the same
+    files), then load it everywhere."""
+    import __graft_entry__
+    if local == 0:
+        __graft_entry__.build()
+    barrier()
+    if local != 0:
+        __graft_entry__.build()          # up to date by now: loads the library
+
+
 def barrier():
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
@@ -285,10 +296,10 @@ def run_ours(args):
 
     import __graft_entry__
     rank, local, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", 1)) > 1 else "gloo")
-    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    build_once(local)
     from paper_1801_08914_gb300 import hyb, inputs
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     cfg = int(args.config)
@@ -492,10 +503,10 @@ def run_batch(args):
 
     import __graft_entry__
     rank, local, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", 1)) > 1 else "gloo")
-    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    build_once(local)
     from paper_1801_08914_gb300 import hyb, inputs
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     probs = inputs.batch_problems(count=args.batch_count)
