@@ -443,7 +443,7 @@ def run_ours(args):
         f32 = element_flops_mixed(p.order)
         # FP32 elements at the FP32 peak plus FP64 elements at the FP64 peak bound the phase from below
         t_min = (n32 * f32 / (fp32_peak * 1e12) + n64 * elem_flops / (fp64_peak * 1e12))
-        element_roofline = {"kernel": f"element_mixed_kernel<{p.order}> (FP32) + element_kernel<{p.order}> (FP64)",
+        element_roofline = {"kernel": f"element_tiled_kernel<{p.order}> (FP32) + element_kernel<{p.order}> (FP64)",
                             "bound": "alu", "achieved": (n32 * f32 + n64 * elem_flops) / (elem_ms * 1e-3) / 1e12,
                             "peak": (n32 * f32 + n64 * elem_flops) / t_min / 1e12 if t_min > 0 else None,
                             "unit": "TFLOP/s", "frac": t_min / (elem_ms * 1e-3) if elem_ms > 0 else None,

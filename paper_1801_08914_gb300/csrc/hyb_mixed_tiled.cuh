@@ -4,7 +4,7 @@
 // translation unit's FP64 helpers (geometry64, load_element64, apply_mass64/A64/D64/Dt64/G64) and
 // its constant tables.
 //
-// The same algebra as the untiled kernel:
+// The algebra (hyb_mixed.cu's header derives it):
 //    L_M = chol(M), Xd = L_M^{-1} D, L_Z = chol(G^{-1} + Xd^T Xd),
 //    Y = L_M,bb^{-1}, P = Xd_b^T Y, V = L_Z^{-1} P,  (A^{-1})_bb = Y^T Y - V^T V,
 // with the matrices held as TB x TB tiles in shared memory so that every step is a short
@@ -421,7 +421,10 @@ __device__ void mixed_solve_tiled(const float* Lt, const float* Xd, const float*
 }
 
 // ---- refinement of the element solve in the mixed variables (x, q = G D^T x) against FP64
-// residuals, as in the untiled kernel, with the tiled FP32 solve.
+// residuals of that saddle system (well conditioned at any contrast; refining A x = f
+// directly would not converge, the two Woodbury terms cancelling in FP32):
+//   r1 = f - M x - D q on free rows, f_e - x_e on essential rows;  rho = G D^T x - q;
+// each correction is one tiled FP32 solve.
 template <int K>
 __device__ void refine_tiled(const double* f, double* x, double* q, int steps, double alpha, double beta, int bmask,
                              const double* g6, const double* gd, const double* Vc, const double* Dc, const double* Vo,

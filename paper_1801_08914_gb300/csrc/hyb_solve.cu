@@ -2,12 +2,14 @@
 // system (H of eq. 2.4, or the static-condensation matrix S of eq. 3.2),
 // stopping when ||r||_2 <= rtol ||r_0||_2 (the paper's criterion, Sec. 6.1).
 //
-// Every scalar of the iteration lives in device memory: the SpMV kernel
-// forms p^T H p, the vector kernel forms r^T z and r^T r, and the last block
-// of each grid (ticket counter) finishes the reduction in a fixed block
-// order, so results are bitwise reproducible. A converged / breakdown flag
-// makes every later kernel of the chunk a no-op, so the host launches
-// iterations in chunks and reads the flags once per chunk.
+// Two forms of the same iteration. The fused form (default) runs 64 iterations in one
+// cooperative launch with two grid barriers per iteration (pcg_fused_kernel; a team of
+// blocks per problem in the batch form). The three-launch form runs an SpMV kernel that forms
+// p^T H p and two vector kernels that form r^T z and r^T r; the last block of each grid
+// (ticket counter) finishes the reduction. Every scalar lives in device memory and every
+// reduction sums per-block partials in a fixed block order, so results are bitwise
+// reproducible. A converged / breakdown flag makes later work of a chunk a no-op, so the
+// host launches iterations in chunks and reads the flags once per chunk.
 #include <cuda_runtime.h>
 
 #include <algorithm>
