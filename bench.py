@@ -248,11 +248,12 @@ def pcg_iteration_bytes(n, nnz, nfn):
     return spmv_bytes(n, nnz, nfn) + 8 * 8 * n + 3 * 8 * n
 
 
-def element_flops(k):
+def element_flops(k, condense=False):
     """Algorithmic FP64 flops of one element elimination (what the method needs, not what a
     kernel issues): sum-factorised A_T (6 blocks, 3 stages, mass + divergence terms),
     the load f = M c, Cholesky n^3/3, z = L^{-1} f, Y = L_bb^{-1} (n_b^3/3),
-    Y^T Y (n_b^3/3), g = Y^T z_b."""
+    Y^T Y (n_b^3/3), g = Y^T z_b. Static condensation stops the Cholesky before the face
+    block (n^3/3 - n_b^3/3) and forms the condensed load f_b - L_bi z_i instead."""
     P, p, Q = k + 2, k + 1, k + 2
     nfn, ni = p * p, 3 * k * p * p
     nb = 6 * nfn
@@ -266,6 +267,8 @@ def element_flops(k):
         st3 = P * nja * p * njb * p * p * Q * 2 // (2 if diag else 1)
         asm += st1 + st2 + st3
     load = 2 * 3 * 2 * (nc * Q + nc * Q + nc * Q)
+    if condense:
+        return asm + load + n ** 3 // 3 - nb ** 3 // 3 + ni * ni + 2 * ni * nb
     chol = n ** 3 // 3 + n * n
     inv = nb ** 3 // 3
     gram = nb ** 3 // 3
@@ -432,7 +435,7 @@ def run_ours(args):
     launches = sum(v[1] for v in prof.values())
     phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
     elem_ms = prof["element"][0] / args.steps
-    elem_flops = element_flops(p.order)
+    elem_flops = element_flops(p.order, condense=args.mode == "sc")
     if not mixed:
         elem_tflops = E * elem_flops / (elem_ms * 1e-3) / 1e12 if elem_ms > 0 else None
         element_roofline = {"kernel": f"element_kernel<{p.order}> (FP64)", "bound": "alu",

@@ -22,6 +22,7 @@
 
 #include "hyb_device.h"
 #include "hyb_internal.h"
+#include "hyb_tiles.cuh"
 
 namespace hyb {
 
@@ -45,8 +46,14 @@ struct EK {
   static constexpr int P = K + 2, p = K + 1, Q = K + 2, NQ = Q * Q * Q;
   static constexpr int NFN = p * p, NI = 3 * K * p * p, NB = 6 * NFN, N = NI + NB;
   static constexpr int NC = P * p * p;                 // functions per component
-  static constexpr int NT = K == 0 ? 32 : K == 1 ? 64 : K == 2 ? 128 : 256;
+  static constexpr int NT = K == 0 ? 32 : K == 1 ? 64 : K == 2 ? 128 : 512;
   static constexpr bool A_SMEM = K <= 2;
+  // RT_3: the elimination runs on 16 x 16 tiles (element_tail_tiled): interior block L_ii and
+  // interface rows L_bi resident together, then the Schur complement of the face block
+  static constexpr int TB = 16, TI = NI / TB, TBB = NB / TB;
+  static constexpr int R1 = TI * (TI + 1) / 2 * TB * TB;     // L_ii tiles, later the face-block tiles
+  static constexpr int R2 = TBB * TI * TB * TB;              // L_bi tiles, later Y = L_bb^{-1} (NB x NB)
+  static constexpr int TILED = K == 3 ? R1 + R2 : 0;
   static constexpr int TRI = N * (N + 1) / 2;
   static constexpr int TRIB = NB * (NB + 1) / 2;
   // 1-D tables: Vc, Dc (P x Q), Vo (p x Q), products VcVc, DcDc (P P Q), VcVo, DcVo (P p Q), VoVo (p p Q)
@@ -57,7 +64,8 @@ struct EK {
   static constexpr int LBUF = 3 * P * P * Q;
   static constexpr int ASM = T1SZ + T2SZ + 13 * NQ + 2 * LBUF + 6 * NQ;
   static constexpr int POST = 2 * TRIB;                // Y, Y^T Y (row-major packed)
-  static constexpr int UNION = ASM > POST ? ASM : POST;
+  static constexpr int UNION0 = ASM > POST ? ASM : POST;
+  static constexpr int UNION = UNION0 > TILED ? UNION0 : TILED;
   static constexpr int SMEM_DOUBLES = (A_SMEM ? TRI : 0) + 3 * N + 48 + TAB + UNION + 4;
   static constexpr size_t SMEM_BYTES = sizeof(double) * SMEM_DOUBLES;
 };
@@ -260,6 +268,224 @@ __device__ void load_vector(const double* coef, const Tabs& tb, const double* Gu
   __syncthreads();
 }
 
+// ---- RT_3 elimination on tiles, after the assembly has written A_T (packed, row-major
+// lower, essential rows already identity) to its factor slot A and the load to f:
+//   1. the first TI tile columns (interior dofs) with all rows in shared memory: L_ii and L_bi
+//      (blocked right-looking Cholesky restricted to those columns);
+//   2. z_i = L_ii^{-1} f_i, f_b -= L_bi z_i; L_ii and L_bi go to the factor slot;
+//   3. the face block A_bb - L_bi L_bi^T (its Schur complement, Sec. 3.1);
+//   4. static condensation: scatter it and f_b; hybridization: L_bb = chol(.), z_b, Y = L_bb^{-1},
+//      S_T = D Y^T Y D and g_T = D Y^T z_b scattered, Y into the slot in place of L_bb.
+// The factor slot keeps the packed layout the recovery reads.
+template <int MODE>
+__device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double* A, double* f, double* R,
+                                   double* flag, const double* wf) {
+  using S = EK<3>;
+  constexpr int NI = S::NI, NB = S::NB, NFN = S::NFN, NT = S::NT, TB = S::TB, TI = S::TI, TBB = S::TBB;
+  constexpr int T = TI + TBB, TT = TB * TB, MR = 4, MC = 4;
+  const int tid = threadIdx.x;
+  double* R1 = R;                                   // L_ii tiles (packed over TI), then A_bb tiles
+  double* R2 = R + S::R1;                           // L_bi tiles [I - TI][J], then Y
+  auto tp = [&](int I, int J) -> double* {
+    return I < TI ? R1 + tiles::tcol(I, J, TI) * TT : R2 + ((I - TI) * TI + J) * TT;
+  };
+  // ---- 1. load the interior tile columns, eliminate them
+  for (int t = tid; t < S::R1 + S::R2; t += NT) {
+    int I, J;
+    const int w = t % TT;
+    if (t < S::R1) {
+      int rem = t / TT;
+      J = 0;
+      while (rem >= TI - J) { rem -= TI - J; ++J; }
+      I = J + rem;
+    } else {
+      const int tile = (t - S::R1) / TT;
+      I = TI + tile / TI;
+      J = tile % TI;
+    }
+    const int i = I * TB + w % TB, j = J * TB + w / TB;
+    R[t] = i >= j ? A[tri(i, j)] : 0.0;
+  }
+  __syncthreads();
+  auto out = [&](int J) {
+    return [A, J](int i, int l, double v) { A[tri(J * 16 + i, J * 16 + l)] = v; };
+  };
+  if (!tiles::tile_chol<double, TB, MR, MC, NT>(tp, T, TI, TI, (double*)nullptr, 0, flag, out)) {
+    if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
+    return;
+  }
+  // ---- 2. forward substitution of the load; the off-diagonal factor tiles to the slot
+  tiles::tile_fwd_vec<double, TB, NT>(R1, TI, f);
+  for (int ib = tid; ib < NB; ib += NT) {
+    const int I = ib / TB, r = ib % TB;
+    double s = 0.0;
+    for (int J = 0; J < TI; ++J) {
+      const double* L = R2 + (I * TI + J) * TT;
+#pragma unroll
+      for (int c = 0; c < TB; ++c) s = fma(L[r + c * TB], f[J * TB + c], s);
+    }
+    f[NI + ib] -= s;
+  }
+  for (int t = tid; t < S::R1 + S::R2; t += NT) {
+    int I, J;
+    const int w = t % TT;
+    if (t < S::R1) {
+      int rem = t / TT;
+      J = 0;
+      while (rem >= TI - J) { rem -= TI - J; ++J; }
+      I = J + rem;
+      if (I == J) continue;                        // diagonal tiles: written by the factorisation
+    } else {
+      const int tile = (t - S::R1) / TT;
+      I = TI + tile / TI;
+      J = tile % TI;
+    }
+    A[tri(I * TB + w % TB, J * TB + w / TB)] = R[t];
+  }
+  __syncthreads();
+  // ---- 3. the face block and its Schur complement A_bb - L_bi L_bi^T (packed tiles in R1)
+  for (int t = tid; t < TBB * (TBB + 1) / 2 * TT; t += NT) {
+    int rem = t / TT, J = 0;
+    while (rem >= TBB - J) { rem -= TBB - J; ++J; }
+    const int I = J + rem, w = t % TT;
+    const int i = NI + I * TB + w % TB, j = NI + J * TB + w / TB;
+    R1[t] = i >= j ? A[tri(i, j)] : 0.0;
+  }
+  __syncthreads();
+  {
+    constexpr int PM = (TB / MR) * (TB / MC);
+    for (int it = tid; it < TBB * (TBB + 1) / 2 * PM; it += NT) {
+      const int tile = it / PM, u = it % PM;
+      int rem = tile, J2 = 0;
+      while (rem >= TBB - J2) { rem -= TBB - J2; ++J2; }
+      const int I2 = J2 + rem;
+      const int r0 = (u / (TB / MC)) * MR, c0 = (u % (TB / MC)) * MC;
+      double acc[MR][MC];
+#pragma unroll
+      for (int a = 0; a < MR; ++a)
+#pragma unroll
+        for (int b = 0; b < MC; ++b) acc[a][b] = 0.0;
+      for (int J = 0; J < TI; ++J) {
+        const double* LA = R2 + (I2 * TI + J) * TT;
+        const double* LB = R2 + (J2 * TI + J) * TT;
+#pragma unroll 4
+        for (int k = 0; k < TB; ++k) {
+          double x[MR], y[MC];
+#pragma unroll
+          for (int a = 0; a < MR; ++a) x[a] = LA[r0 + a + k * TB];
+#pragma unroll
+          for (int b = 0; b < MC; ++b) y[b] = LB[c0 + b + k * TB];
+#pragma unroll
+          for (int a = 0; a < MR; ++a)
+#pragma unroll
+            for (int b = 0; b < MC; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
+        }
+      }
+      double* C = R1 + tile * TT;
+#pragma unroll
+      for (int a = 0; a < MR; ++a)
+#pragma unroll
+        for (int b = 0; b < MC; ++b) C[(r0 + a) + (c0 + b) * TB] -= acc[a][b];
+    }
+  }
+  __syncthreads();
+  const int32_t* ef = args.elem_face + e * 6;
+  const int64_t* boff = args.blockoff + e * 36;
+  __shared__ int64_t s_row0[6];
+  __shared__ int s_rlen[6];
+  if (tid < 6) {
+    const int64_t r0 = ef[tid] >= 0 ? args.row_ptr[(int64_t)ef[tid] * NFN] : 0;
+    s_row0[tid] = r0;
+    s_rlen[tid] = ef[tid] >= 0 ? (int)(args.row_ptr[(int64_t)ef[tid] * NFN + 1] - r0) : 0;
+  }
+  __syncthreads();
+  auto put = [&](int ib, int jb, double v, bool weighted) {
+    const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
+    if (ef[a] < 0 || ef[b] < 0) return;
+    if (weighted) v *= (((a ^ b) & 1) ? -1.0 : 1.0) * wf[m1] * wf[m2];
+    const int64_t pos = boff[a * 6 + b] + m1 * (int64_t)s_rlen[a] + m2;
+    if (a == b && args.colour == 1) args.val[pos] += v;
+    else args.val[pos] = v;
+  };
+  if (MODE == MODE_SC) {
+    // ---- 4a. static condensation: the Schur complement and rhs_b = f_b - L_bi z_i
+    double* zs = args.zstore + e * (int64_t)S::N;
+    for (int i = tid; i < S::N; i += NT) zs[i] = f[i];
+    for (int t = tid; t < NB * NB; t += NT) {
+      const int ib = t / NB, jb = t % NB;
+      const int gi = ib >= jb ? ib : jb, gj = ib >= jb ? jb : ib;
+      put(ib, jb, R1[tiles::tcol(gi / TB, gj / TB, TBB) * TT + (gi % TB) + (gj % TB) * TB], false);
+    }
+    for (int ib = tid; ib < NB; ib += NT) {
+      const int a = ib / NFN, m1 = ib % NFN;
+      if (ef[a] < 0) continue;
+      const int64_t gi = (int64_t)ef[a] * NFN + m1;
+      if (args.colour == 1) args.rhs[gi] += f[NI + ib];
+      else args.rhs[gi] = f[NI + ib];
+    }
+    return;
+  }
+  // ---- 4b. hybridization: L_bb, z_b, Y = L_bb^{-1} (in R2), S_T and g_T, Y into the slot
+  if (!tiles::tile_chol<double, TB, MR, MC, NT>(tiles::Packed<double, TB>{R1, TBB}, TBB, TBB, TBB,
+                                                (double*)nullptr, 0, flag, [](int) { return tiles::NoOut{}; })) {
+    if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
+    return;
+  }
+  tiles::tile_fwd_vec<double, TB, NT>(R1, TBB, f + NI);
+  double* zs = args.zstore + e * (int64_t)S::N;
+  for (int i = tid; i < S::N; i += NT) zs[i] = f[i];
+  double* Y = R2;                                    // [NB][NB], row-major
+  for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0 : 0.0;
+  __syncthreads();
+  tiles::tile_fwd_mat<double, TB, MR, MC, NT>(R1, TBB, 0, Y, NB);
+  for (int ib = tid; ib < NB; ib += NT) {           // g_T = D Y^T z_b
+    const int a = ib / NFN, m1 = ib % NFN;
+    if (ef[a] < 0) continue;
+    double acc = 0.0;
+    for (int m = ib; m < NB; ++m) acc = fma(Y[m * NB + ib], f[NI + m], acc);
+    const double v = ((a & 1) ? 1.0 : -1.0) * wf[m1] * acc;
+    const int64_t gi = (int64_t)ef[a] * NFN + m1;
+    if (args.colour == 1) args.rhs[gi] += v;
+    else args.rhs[gi] = v;
+  }
+  {                                                  // S = Y^T Y, lower micro-tiles, mirrored
+    constexpr int RM = NB / MR, CM = NB / MC;
+    for (int it = tid; it < RM * CM; it += NT) {
+      const int i0 = (it / CM) * MR, j0 = (it % CM) * MC;
+      if (i0 + MR - 1 < j0) continue;
+      double acc[MR][MC];
+#pragma unroll
+      for (int a = 0; a < MR; ++a)
+#pragma unroll
+        for (int b = 0; b < MC; ++b) acc[a][b] = 0.0;
+      for (int k = i0 < j0 ? j0 : i0; k < NB; ++k) {   // rows k < max(i, j) of Y^T Y's terms vanish
+        double x[MR], y[MC];
+#pragma unroll
+        for (int a = 0; a < MR; ++a) x[a] = Y[k * NB + i0 + a];
+#pragma unroll
+        for (int b = 0; b < MC; ++b) y[b] = Y[k * NB + j0 + b];
+#pragma unroll
+        for (int a = 0; a < MR; ++a)
+#pragma unroll
+          for (int b = 0; b < MC; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < MR; ++a)
+#pragma unroll
+        for (int b = 0; b < MC; ++b) {
+          const int ib = i0 + a, jb = j0 + b;
+          if (ib < jb) continue;
+          put(ib, jb, acc[a][b], true);
+          if (ib != jb) put(jb, ib, acc[a][b], true);
+        }
+    }
+  }
+  for (int t = tid; t < NB * NB; t += NT) {          // Y in place of L_bb
+    const int i = t / NB, j = t % NB;
+    if (j <= i) A[tri(NI + i, NI + j)] = Y[t];
+  }
+}
+
 template <int K, int MODE>
 __device__ __forceinline__ void element_body(const ElemArgs& args, const int64_t e, double* smem) {
   using S = EK<K>;
@@ -436,6 +662,10 @@ __device__ __forceinline__ void element_body(const ElemArgs& args, const int64_t
     }
   }
   __syncthreads();
+  if constexpr (K == 3) {
+    element_tail_tiled<MODE>(args, e, A, f, U, flag, wf);
+    return;
+  }
 
   // ---- 5. Cholesky (right-looking, packed lower) fused with z = L^{-1} f. Every trailing
   // update is spread over all threads (entry (i, l) of the trailing triangle, then f), and the

@@ -20,6 +20,7 @@
 
 #include "hyb_device.h"
 #include "hyb_internal.h"
+#include "hyb_tiles.cuh"
 
 namespace hyb {
 

@@ -82,308 +82,13 @@ struct MT {
 // kappa(M, Z) u_32 <= 5e-5, so two steps take the FP32 solve (1e-7) below FP64 rounding.
 constexpr int kRefineSteps = 2;
 
-__device__ __forceinline__ int tcol(int I, int J, int T) { return J * T - J * (J - 1) / 2 + (I - J); }
+using tiles::tcol;
 
-// ---- one warp: Cholesky of the lower triangle of a TB x TB column-major tile in place,
-// then replace it by the inverse of the factor (strict upper part zero). Lane i holds row i
-// in registers and the columns travel by shuffles, so there is no shared-memory round trip or
-// index arithmetic inside the elimination. flag[0] = 1 on a bad pivot (every lane leaves at
-// the same step: the pivot is broadcast).
-template <int TB>
-__device__ void diag_factor_invert(float* D, float* flag) {
-  const int lane = threadIdx.x & 31;
-  constexpr unsigned FULL = 0xffffffffu;
-  float row[TB], rv[TB];
-#pragma unroll
-  for (int l = 0; l < TB; ++l) row[l] = (lane < TB && l <= lane) ? D[lane + l * TB] : 0.0f;
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < TB; ++k) {
-    const float d = __shfl_sync(FULL, row[k], k);          // pivot, after the previous updates
-    if (!(d > 0.0f) || !(d < INFINITY)) {
-      ok = false;
-      break;
-    }
-    const float r = dev::rsqrt_newton(d);
-    rv[k] = r;                                             // 1 / L_kk, in every lane
-    row[k] = lane == k ? d * r : row[k] * r;               // column k of L (rows > k, and the pivot)
-#pragma unroll
-    for (int l = k + 1; l < TB; ++l) {                     // row_i[l] -= L_ik L_lk, k < l <= i
-      const float lk = __shfl_sync(FULL, row[k], l);
-      if (lane >= l) row[l] = fmaf(-row[k], lk, row[l]);
-    }
-  }
-  if (!ok) {
-    if (lane == 0) flag[0] = 1.0f;
-    __syncwarp();
-    return;
-  }
-  // column c of L^{-1} in lane c: col_i = -(sum_{c <= k < i} L_ik col_k) / L_ii, col_c = 1 / L_cc;
-  // L_ik comes from lane i by shuffle
-  float col[TB];
-#pragma unroll
-  for (int i = 0; i < TB; ++i) {
-    float s = 0.0f;
-#pragma unroll
-    for (int k = 0; k < i; ++k) s = fmaf(__shfl_sync(FULL, row[k], i), col[k], s);
-    col[i] = i < lane ? 0.0f : (i == lane ? rv[i] : -s * rv[i]);
-  }
-  if (lane < TB) {
-#pragma unroll
-    for (int i = 0; i < TB; ++i) D[i + lane * TB] = col[i];
-  }
-  __syncwarp();
-}
-
-// ---- CTA: X_J <- Dinv_J X_J (rows J TB .. of X, row-major with ld MX), one thread per column.
-template <int TB, int NT>
-__device__ __forceinline__ void scale_rows_item(const float* Dv, float* XJ, int MX, int cx) {
-  float x[TB];
-#pragma unroll
-  for (int k = 0; k < TB; ++k) x[k] = XJ[k * MX + cx];
-#pragma unroll
-  for (int r = 0; r < TB; ++r) {
-    float s = 0.0f;
-#pragma unroll
-    for (int k = 0; k <= r; ++k) s = fmaf(Dv[r + k * TB], x[k], s);
-    XJ[r * MX + cx] = s;
-  }
-}
-
-// ---- micro-tile: C (MR x MC block at r0, c0) -= A(rows r0..) * B(rows c0..)^T, K dim TB,
-// A and B column-major TB x TB tiles; C column-major with leading dimension TB.
-template <int TB, int MR, int MC>
-__device__ __forceinline__ void syrk_micro(const float* A, const float* B, float* C, int r0, int c0) {
-  float acc[MR][MC];
-#pragma unroll
-  for (int i = 0; i < MR; ++i)
-#pragma unroll
-    for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
-#pragma unroll 2
-  for (int k = 0; k < TB; ++k) {
-    float a[MR], b[MC];
-#pragma unroll
-    for (int i = 0; i < MR; ++i) a[i] = A[r0 + i + k * TB];
-#pragma unroll
-    for (int j = 0; j < MC; ++j) b[j] = B[c0 + j + k * TB];
-#pragma unroll
-    for (int i = 0; i < MR; ++i)
-#pragma unroll
-      for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-  }
-#pragma unroll
-  for (int i = 0; i < MR; ++i)
-#pragma unroll
-    for (int j = 0; j < MC; ++j) C[(r0 + i) + (c0 + j) * TB] -= acc[i][j];
-}
-
-// ---- micro-tile: XI (MR x MC block at r0, c0; row-major, ld MX) -= A(rows r0..) * XJ, K dim TB
-template <int TB, int MR, int MC>
-__device__ __forceinline__ void gemm_x_micro(const float* A, const float* XJ, float* XI, int MX, int r0, int c0) {
-  float acc[MR][MC];
-#pragma unroll
-  for (int i = 0; i < MR; ++i)
-#pragma unroll
-    for (int j = 0; j < MC; ++j) acc[i][j] = 0.0f;
-#pragma unroll 2
-  for (int k = 0; k < TB; ++k) {
-    float a[MR], b[MC];
-#pragma unroll
-    for (int i = 0; i < MR; ++i) a[i] = A[r0 + i + k * TB];
-#pragma unroll
-    for (int j = 0; j < MC; ++j) b[j] = XJ[k * MX + c0 + j];
-#pragma unroll
-    for (int i = 0; i < MR; ++i)
-#pragma unroll
-      for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-  }
-#pragma unroll
-  for (int i = 0; i < MR; ++i)
-#pragma unroll
-    for (int j = 0; j < MC; ++j) XI[(r0 + i) * MX + c0 + j] -= acc[i][j];
-}
-
-// ---- CTA: blocked Cholesky of T x T tiles (packed by tile columns) fused with
-// X <- L^{-1} X (T TB rows, ld MX; X may be null). Returns false in every thread on a bad pivot.
+// FP32 tile factorisations of this kernel: whole triangles, no write-out of the factor
 template <int TB, int MR, int MC, int NT>
-__device__ bool tile_chol(float* Lt, int T, float* X, int MX, float* flag) {
-  constexpr int TT = TB * TB;
-  const int tid = threadIdx.x;
-  if (tid == 0) flag[0] = 0.0f;
-  __syncthreads();
-  for (int J = 0; J < T; ++J) {
-    float* Dv = Lt + tcol(J, J, T) * TT;
-    if (tid < 32) diag_factor_invert<TB>(Dv, flag);
-    __syncthreads();
-    if (flag[0] != 0.0f) return false;
-    // panel: A_IJ <- A_IJ Dinv^T (one thread per row), X_J <- Dinv X_J (one thread per column)
-    const int nrows = (T - J - 1) * TB, ncols = X ? MX : 0;
-    for (int it = tid; it < nrows + ncols; it += NT) {
-      if (it < nrows) {
-        float* A = Lt + tcol(J + 1 + it / TB, J, T) * TT;
-        const int r = it % TB;
-        float a[TB];
-#pragma unroll
-        for (int k = 0; k < TB; ++k) a[k] = A[r + k * TB];
-#pragma unroll
-        for (int c = 0; c < TB; ++c) {
-          float s = 0.0f;
-#pragma unroll
-          for (int k = 0; k <= c; ++k) s = fmaf(a[k], Dv[c + k * TB], s);
-          A[r + c * TB] = s;
-        }
-      } else {
-        scale_rows_item<TB, NT>(Dv, X + J * TB * MX, MX, it - nrows);
-      }
-    }
-    __syncthreads();
-    // trailing update of the tiles (I, K2), J < K2 <= I, and of the rows I > J of X
-    const int m = T - J - 1;
-    constexpr int PM = (TB / MR) * (TB / MC);
-    const int npair = m * (m + 1) / 2 * PM;
-    const int xm = (TB / MR) * (MX / MC);
-    const int nx = X ? m * xm : 0;
-    for (int it = tid; it < npair + nx; it += NT) {
-      if (it < npair) {
-        const int q = it / PM, u = it % PM;
-        int ip = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
-        while ((ip + 1) * (ip + 2) / 2 <= q) ++ip;
-        while (ip * (ip + 1) / 2 > q) --ip;
-        const int kp = q - ip * (ip + 1) / 2;
-        const int I = J + 1 + ip, K2 = J + 1 + kp;
-        syrk_micro<TB, MR, MC>(Lt + tcol(I, J, T) * TT, Lt + tcol(K2, J, T) * TT, Lt + tcol(I, K2, T) * TT,
-                               (u / (TB / MC)) * MR, (u % (TB / MC)) * MC);
-      } else {
-        const int it2 = it - npair, ti = it2 / xm, u = it2 % xm;
-        const int I = J + 1 + ti;
-        gemm_x_micro<TB, MR, MC>(Lt + tcol(I, J, T) * TT, X + J * TB * MX, X + I * TB * MX, MX,
-                                 (u / (MX / MC)) * MR, (u % (MX / MC)) * MC);
-      }
-    }
-    __syncthreads();
-  }
-  return true;
-}
-
-// ---- CTA: X <- L^{-1} X for the tiles J0..T-1 of a factored L (diagonal tiles inverted);
-// X holds the rows of those tiles ((J - J0) TB + r), ld MX.
-template <int TB, int MR, int MC, int NT>
-__device__ void tile_fwd_mat(const float* Lt, int T, int J0, float* X, int MX) {
-  constexpr int TT = TB * TB;
-  const int tid = threadIdx.x;
-  for (int J = J0; J < T; ++J) {
-    const float* Dv = Lt + tcol(J, J, T) * TT;
-    float* XJ = X + (J - J0) * TB * MX;
-    for (int cx = tid; cx < MX; cx += NT) scale_rows_item<TB, NT>(Dv, XJ, MX, cx);
-    __syncthreads();
-    const int m = T - J - 1, xm = (TB / MR) * (MX / MC);
-    for (int it = tid; it < m * xm; it += NT) {
-      const int ti = it / xm, u = it % xm;
-      const int I = J + 1 + ti;
-      gemm_x_micro<TB, MR, MC>(Lt + tcol(I, J, T) * TT, XJ, X + (I - J0) * TB * MX, MX, (u / (MX / MC)) * MR,
-                               (u % (MX / MC)) * MC);
-    }
-    __syncthreads();
-  }
-}
-
-// ---- CTA: X <- L^{-T} X (all T tiles), X row-major with ld MX (small systems: G^{-1}).
-template <int TB, int NT>
-__device__ void tile_bwd_mat(const float* Lt, int T, float* X, int MX) {
-  constexpr int TT = TB * TB;
-  const int tid = threadIdx.x;
-  for (int J = T - 1; J >= 0; --J) {
-    const float* Dv = Lt + tcol(J, J, T) * TT;
-    float* XJ = X + J * TB * MX;
-    for (int cx = tid; cx < MX; cx += NT) {          // X_J <- Dinv^T X_J
-      float x[TB];
-#pragma unroll
-      for (int k = 0; k < TB; ++k) x[k] = XJ[k * MX + cx];
-#pragma unroll
-      for (int c = 0; c < TB; ++c) {
-        float s = 0.0f;
-#pragma unroll
-        for (int r = c; r < TB; ++r) s = fmaf(Dv[r + c * TB], x[r], s);
-        XJ[c * MX + cx] = s;
-      }
-    }
-    __syncthreads();
-    for (int it = tid; it < J * TB * MX; it += NT) {   // X_K2 -= L_J,K2^T X_J
-      const int row = it / MX, cx = it % MX;
-      const int K2 = row / TB, c = row % TB;
-      const float* L = Lt + tcol(J, K2, T) * TT;
-      float s = 0.0f;
-#pragma unroll
-      for (int r = 0; r < TB; ++r) s = fmaf(L[r + c * TB], XJ[r * MX + cx], s);
-      X[row * MX + cx] -= s;
-    }
-    __syncthreads();
-  }
-}
-
-// ---- CTA: v <- L^{-1} v (one right-hand side, T TB entries)
-template <int TB, int NT>
-__device__ void tile_fwd_vec(const float* Lt, int T, float* v) {
-  constexpr int TT = TB * TB;
-  const int tid = threadIdx.x;
-  for (int J = 0; J < T; ++J) {
-    const float* Dv = Lt + tcol(J, J, T) * TT;
-    float* vJ = v + J * TB;
-    if (tid < 32) {
-      float y = 0.0f;
-      if (tid < TB) {
-#pragma unroll
-        for (int k = 0; k < TB; ++k)
-          if (k <= tid) y = fmaf(Dv[tid + k * TB], vJ[k], y);
-      }
-      __syncwarp();
-      if (tid < TB) vJ[tid] = y;
-    }
-    __syncthreads();
-    for (int i = tid; i < (T - J - 1) * TB; i += NT) {
-      const int I = J + 1 + i / TB, r = i % TB;
-      const float* L = Lt + tcol(I, J, T) * TT;
-      float s = 0.0f;
-#pragma unroll
-      for (int k = 0; k < TB; ++k) s = fmaf(L[r + k * TB], vJ[k], s);
-      v[I * TB + r] -= s;
-    }
-    __syncthreads();
-  }
-}
-
-// ---- CTA: v <- L^{-T} v
-template <int TB, int NT>
-__device__ void tile_bwd_vec(const float* Lt, int T, float* v) {
-  constexpr int TT = TB * TB;
-  const int tid = threadIdx.x;
-  for (int J = T - 1; J >= 0; --J) {
-    const float* Dv = Lt + tcol(J, J, T) * TT;
-    float* vJ = v + J * TB;
-    if (tid < 32) {
-      float x = 0.0f;
-      if (tid < TB) {
-#pragma unroll
-        for (int r = 0; r < TB; ++r)
-          if (r >= tid) x = fmaf(Dv[r + tid * TB], vJ[r], x);
-      }
-      __syncwarp();
-      if (tid < TB) vJ[tid] = x;
-    }
-    __syncthreads();
-    for (int i = tid; i < J * TB; i += NT) {          // v_K2 -= L_J,K2^T x_J
-      const int K2 = i / TB, c = i % TB;
-      const float* L = Lt + tcol(J, K2, T) * TT;
-      float s = 0.0f;
-#pragma unroll
-      for (int t = 0; t < TB; ++t) {
-        const int r = (c + t) % TB;                  // rotated start: no bank conflicts across c
-        s = fmaf(L[r + c * TB], vJ[r], s);
-      }
-      v[i] -= s;
-    }
-    __syncthreads();
-  }
+__device__ __forceinline__ bool chol_tiles32(float* Lt, int T, float* X, int MX, float* flag) {
+  return tiles::tile_chol<float, TB, MR, MC, NT>(tiles::Packed<float, TB>{Lt, T}, T, T, T, X, MX, flag,
+                                                 [](int) { return tiles::NoOut{}; });
 }
 
 // ---- CTA: one FP32 solve of the mixed-form saddle system with the tiled factors.
@@ -395,7 +100,7 @@ __device__ void mixed_solve_tiled(const float* Lt, const float* Xd, const float*
   using S = MT<K>;
   constexpr int N = S::N, NQK = S::NQK, NQP = S::NQP, NT = S::NT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  tile_fwd_vec<S::TB, NT>(Lt, S::T, v);
+  tiles::tile_fwd_vec<float, S::TB, NT>(Lt, S::T, v);
   for (int a = warp; a < NQP; a += NT / 32) {
     float acc = 0.0f;
     if (a < NQK) {
@@ -409,15 +114,15 @@ __device__ void mixed_solve_tiled(const float* Lt, const float* Xd, const float*
   __syncthreads();
   for (int a = tid; a < NQP; a += NT) t[a] = tmp[a];
   __syncthreads();
-  tile_fwd_vec<S::TB, NT>(Zt, S::TQ, t);
-  tile_bwd_vec<S::TB, NT>(Zt, S::TQ, t);
+  tiles::tile_fwd_vec<float, S::TB, NT>(Zt, S::TQ, t);
+  tiles::tile_bwd_vec<float, S::TB, NT>(Zt, S::TQ, t);
   for (int i = tid; i < N; i += NT) {
     float acc = v[i];
     for (int a = 0; a < NQK; ++a) acc = fmaf(-Xd[i * NQP + a], t[a], acc);
     v[i] = acc;
   }
   __syncthreads();
-  tile_bwd_vec<S::TB, NT>(Lt, S::T, v);
+  tiles::tile_bwd_vec<float, S::TB, NT>(Lt, S::T, v);
 }
 
 // ---- refinement of the element solve in the mixed variables (x, q = G D^T x) against FP64
@@ -635,11 +340,11 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     }
     for (int t = tid; t < NQP * NQP; t += NT) Xg[t] = (t / NQP == t % NQP) ? 1.0f : 0.0f;
     __syncthreads();
-    if (!tile_chol<TB, MR, MC, NT>(Gt, TQ, Xg, NQP, flag)) {
+    if (!chol_tiles32<TB, MR, MC, NT>(Gt, TQ, Xg, NQP, flag)) {
       if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
       return;
     }
-    tile_bwd_mat<TB, NT>(Gt, TQ, Xg, NQP);
+    tiles::tile_bwd_mat<float, TB, NT>(Gt, TQ, Xg, NQP);
     for (int t = tid; t < NQK * NQK; t += NT) Gi[t] = Xg[(t / NQK) * NQP + t % NQK];
     __syncthreads();
   }
@@ -739,7 +444,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     Xd[t] = v;
   }
   __syncthreads();
-  if (!tile_chol<TB, MR, MC, NT>(Lt, T, Xd, NQP, flag)) {
+  if (!chol_tiles32<TB, MR, MC, NT>(Lt, T, Xd, NQP, flag)) {
     if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
     return;
   }
@@ -780,7 +485,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
         }
     }
     __syncthreads();
-    if (!tile_chol<TB, MR, MC, NT>(Zt, TQ, nullptr, 0, flag)) {
+    if (!chol_tiles32<TB, MR, MC, NT>(Zt, TQ, nullptr, 0, flag)) {
       if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
       return;
     }
@@ -817,7 +522,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     __syncthreads();
     for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0f : 0.0f;
     __syncthreads();
-    tile_fwd_mat<TB, MR, MC, NT>(Lt, T, S::TI, Y, NB);
+    tiles::tile_fwd_mat<float, TB, MR, MC, NT>(Lt, T, S::TI, Y, NB);
     {
       constexpr int RM = NQP / MR, CM = NB / MC;
       for (int it = tid; it < RM * CM; it += NT) {  // P[a][j] = sum_i Xd[NI + i][a] Y[i][j]
@@ -845,7 +550,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
       }
     }
     __syncthreads();
-    tile_fwd_mat<TB, MR, MC, NT>(Zt, TQ, 0, Pv, NB);
+    tiles::tile_fwd_mat<float, TB, MR, MC, NT>(Zt, TQ, 0, Pv, NB);
     // ---- S[i][j] = sum_m Y[m][i] Y[m][j] - sum_a V[a][i] V[a][j] for i >= j, in register
     // micro-tiles, scattered as S_T = D_c S D_c straight into the FP64 CSR values: entry (i, j)
     // and its mirror (j, i) get the same value, so both face blocks of a pair are bitwise

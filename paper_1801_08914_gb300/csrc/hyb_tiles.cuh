@@ -1,0 +1,346 @@
+// Blocked dense kernels on TB x TB tiles in shared memory, generic in the scalar type (float
+// for the mixed-precision elimination, double for the FP64 one). Used inside element kernels:
+// every function is called by all threads of the CTA unless it says one warp.
+//
+// Tile layout: a lower-triangular matrix of T x T tiles is stored as "packed tiles", column
+// of tiles after column of tiles (tile (I, J), I >= J, at J T - J (J - 1) / 2 + I - J), each
+// tile column-major inside. After a factorisation a diagonal tile holds the inverse of its
+// triangle (what the panel step, the triangular solves and inverses use). tile_chol takes a
+// tile-address functor instead, so that a factorisation can run over tiles split between
+// several regions (the FP64 elimination keeps the interior and the interface rows apart).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hyb_device.h"
+
+namespace hyb {
+namespace tiles {
+
+__device__ __forceinline__ int tcol(int I, int J, int T) { return J * T - J * (J - 1) / 2 + (I - J); }
+
+// tile address of packed tiles
+template <typename F, int TB>
+struct Packed {
+  F* base;
+  int T;
+  __device__ __forceinline__ F* operator()(int I, int J) const { return base + tcol(I, J, T) * (TB * TB); }
+};
+
+// no write-out of the diagonal factor
+struct NoOut {
+  template <typename F>
+  __device__ __forceinline__ void operator()(int, int, F) const {}
+};
+
+// ---- one warp: Cholesky of the lower triangle of a TB x TB column-major tile in place,
+// then replace it by the inverse of the factor (strict upper part zero). Lane i holds row i
+// in registers and the columns travel by shuffles, so there is no shared-memory round trip or
+// index arithmetic inside the elimination. out(i, l, L_il) receives the factor itself (l <= i)
+// before the inversion. flag[0] = 1 on a bad pivot (every lane leaves at the same step: the
+// pivot is broadcast).
+template <typename F, int TB, typename Out>
+__device__ void diag_factor_invert(F* D, F* flag, const Out& out) {
+  const int lane = threadIdx.x & 31;
+  constexpr unsigned FULL = 0xffffffffu;
+  F row[TB], rv[TB];
+#pragma unroll
+  for (int l = 0; l < TB; ++l) row[l] = (lane < TB && l <= lane) ? D[lane + l * TB] : F(0);
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < TB; ++k) {
+    const F d = __shfl_sync(FULL, row[k], k);             // pivot, after the previous updates
+    if (!(d > F(0)) || !(d < F(INFINITY))) {
+      ok = false;
+      break;
+    }
+    const F r = dev::rsqrt_newton(d);
+    rv[k] = r;                                             // 1 / L_kk, in every lane
+    row[k] = lane == k ? d * r : row[k] * r;               // column k of L (rows > k, and the pivot)
+#pragma unroll
+    for (int l = k + 1; l < TB; ++l) {                     // row_i[l] -= L_ik L_lk, k < l <= i
+      const F lk = __shfl_sync(FULL, row[k], l);
+      if (lane >= l) row[l] = fma(-row[k], lk, row[l]);
+    }
+  }
+  if (!ok) {
+    if (lane == 0) flag[0] = F(1);
+    __syncwarp();
+    return;
+  }
+  if (lane < TB) {
+#pragma unroll
+    for (int l = 0; l < TB; ++l)
+      if (l <= lane) out(lane, l, row[l]);
+  }
+  // column c of L^{-1} in lane c: col_i = -(sum_{c <= k < i} L_ik col_k) / L_ii, col_c = 1 / L_cc;
+  // L_ik comes from lane i by shuffle
+  F col[TB];
+#pragma unroll
+  for (int i = 0; i < TB; ++i) {
+    F s = F(0);
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = fma(__shfl_sync(FULL, row[k], i), col[k], s);
+    col[i] = i < lane ? F(0) : (i == lane ? rv[i] : -s * rv[i]);
+  }
+  if (lane < TB) {
+#pragma unroll
+    for (int i = 0; i < TB; ++i) D[i + lane * TB] = col[i];
+  }
+  __syncwarp();
+}
+
+// ---- one thread: column cx of X_J <- Dinv_J X_J (X_J: TB rows, row-major with ld MX)
+template <typename F, int TB>
+__device__ __forceinline__ void scale_rows_item(const F* Dv, F* XJ, int MX, int cx) {
+  F x[TB];
+#pragma unroll
+  for (int k = 0; k < TB; ++k) x[k] = XJ[k * MX + cx];
+#pragma unroll
+  for (int r = 0; r < TB; ++r) {
+    F s = F(0);
+#pragma unroll
+    for (int k = 0; k <= r; ++k) s = fma(Dv[r + k * TB], x[k], s);
+    XJ[r * MX + cx] = s;
+  }
+}
+
+// ---- one thread: C (MR x MC block at r0, c0) -= A(rows r0..) * B(rows c0..)^T, K dim TB,
+// A and B column-major TB x TB tiles; C column-major with leading dimension TB.
+template <typename F, int TB, int MR, int MC>
+__device__ __forceinline__ void syrk_micro(const F* A, const F* B, F* C, int r0, int c0) {
+  F acc[MR][MC];
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int j = 0; j < MC; ++j) acc[i][j] = F(0);
+#pragma unroll 2
+  for (int k = 0; k < TB; ++k) {
+    F a[MR], b[MC];
+#pragma unroll
+    for (int i = 0; i < MR; ++i) a[i] = A[r0 + i + k * TB];
+#pragma unroll
+    for (int j = 0; j < MC; ++j) b[j] = B[c0 + j + k * TB];
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+      for (int j = 0; j < MC; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int j = 0; j < MC; ++j) C[(r0 + i) + (c0 + j) * TB] -= acc[i][j];
+}
+
+// ---- one thread: XI (MR x MC block at r0, c0; row-major, ld MX) -= A(rows r0..) * XJ, K dim TB
+template <typename F, int TB, int MR, int MC>
+__device__ __forceinline__ void gemm_x_micro(const F* A, const F* XJ, F* XI, int MX, int r0, int c0) {
+  F acc[MR][MC];
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int j = 0; j < MC; ++j) acc[i][j] = F(0);
+#pragma unroll 2
+  for (int k = 0; k < TB; ++k) {
+    F a[MR], b[MC];
+#pragma unroll
+    for (int i = 0; i < MR; ++i) a[i] = A[r0 + i + k * TB];
+#pragma unroll
+    for (int j = 0; j < MC; ++j) b[j] = XJ[k * MX + c0 + j];
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+      for (int j = 0; j < MC; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int j = 0; j < MC; ++j) XI[(r0 + i) * MX + c0 + j] -= acc[i][j];
+}
+
+// ---- blocked right-looking Cholesky of the tile columns J < Jend of a T x T tile triangle
+// (tiles addressed by tp), fused with X <- L^{-1} X (T TB rows, ld MX; X may be null). The
+// rank-TB updates reach the tiles (I, K2) with K2 < Kend only: with Jend = Kend = T this is
+// the whole factorisation; with Jend = Kend = TI < T it eliminates the first TI tile columns
+// and leaves the trailing block untouched (its Schur update is the caller's). out(J) gives the
+// write-out functor of diagonal tile J. Per tile column: one warp factors and inverts the
+// diagonal tile, the CTA scales the panel (one thread per row) and the rows of X (one thread
+// per column), the CTA applies the update with MR x MC register micro-tiles: three barriers.
+// Returns false in every thread on a bad pivot.
+template <typename F, int TB, int MR, int MC, int NT, typename TP, typename OutJ>
+__device__ bool tile_chol(const TP& tp, int T, int Jend, int Kend, F* X, int MX, F* flag, const OutJ& out) {
+  const int tid = threadIdx.x;
+  if (tid == 0) flag[0] = F(0);
+  __syncthreads();
+  for (int J = 0; J < Jend; ++J) {
+    F* Dv = tp(J, J);
+    if (tid < 32) diag_factor_invert<F, TB>(Dv, flag, out(J));
+    __syncthreads();
+    if (flag[0] != F(0)) return false;
+    const int nrows = (T - J - 1) * TB, ncols = X ? MX : 0;
+    for (int it = tid; it < nrows + ncols; it += NT) {
+      if (it < nrows) {                            // A_IJ <- A_IJ Dinv^T
+        F* A = tp(J + 1 + it / TB, J);
+        const int r = it % TB;
+        F a[TB];
+#pragma unroll
+        for (int k = 0; k < TB; ++k) a[k] = A[r + k * TB];
+#pragma unroll
+        for (int c = 0; c < TB; ++c) {
+          F s = F(0);
+#pragma unroll
+          for (int k = 0; k <= c; ++k) s = fma(a[k], Dv[c + k * TB], s);
+          A[r + c * TB] = s;
+        }
+      } else {
+        scale_rows_item<F, TB>(Dv, X + J * TB * MX, MX, it - nrows);
+      }
+    }
+    __syncthreads();
+    // tile pairs (I, K2), J < K2 < Kend, K2 <= I < T, enumerated column by column
+    const int m = T - J - 1, mk = (Kend < T ? Kend : T) - J - 1;
+    const int npairs = mk * m - mk * (mk - 1) / 2;
+    constexpr int PM = (TB / MR) * (TB / MC);
+    const int xm = X ? (TB / MR) * (MX / MC) : 0;
+    for (int it = tid; it < npairs * PM + m * xm; it += NT) {
+      if (it < npairs * PM) {
+        const int q = it / PM, u = it % PM;
+        int kp = 0, rem = q;                       // column kp of the trailing part has m - kp tiles
+        while (rem >= m - kp) { rem -= m - kp; ++kp; }
+        const int K2 = J + 1 + kp, I = K2 + rem;
+        syrk_micro<F, TB, MR, MC>(tp(I, J), tp(K2, J), tp(I, K2), (u / (TB / MC)) * MR, (u % (TB / MC)) * MC);
+      } else {
+        const int it2 = it - npairs * PM, ti = it2 / xm, u = it2 % xm;
+        const int I = J + 1 + ti;
+        gemm_x_micro<F, TB, MR, MC>(tp(I, J), X + J * TB * MX, X + I * TB * MX, MX, (u / (MX / MC)) * MR,
+                                    (u % (MX / MC)) * MC);
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// ---- X <- L^{-1} X for the tiles J0..T-1 of a factored packed tile triangle; X holds the
+// rows of those tiles ((J - J0) TB + r), ld MX.
+template <typename F, int TB, int MR, int MC, int NT>
+__device__ void tile_fwd_mat(const F* Lt, int T, int J0, F* X, int MX) {
+  constexpr int TT = TB * TB;
+  const int tid = threadIdx.x;
+  for (int J = J0; J < T; ++J) {
+    const F* Dv = Lt + tcol(J, J, T) * TT;
+    F* XJ = X + (J - J0) * TB * MX;
+    for (int cx = tid; cx < MX; cx += NT) scale_rows_item<F, TB>(Dv, XJ, MX, cx);
+    __syncthreads();
+    const int m = T - J - 1, xm = (TB / MR) * (MX / MC);
+    for (int it = tid; it < m * xm; it += NT) {
+      const int ti = it / xm, u = it % xm;
+      const int I = J + 1 + ti;
+      gemm_x_micro<F, TB, MR, MC>(Lt + tcol(I, J, T) * TT, XJ, X + (I - J0) * TB * MX, MX, (u / (MX / MC)) * MR,
+                                  (u % (MX / MC)) * MC);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- X <- L^{-T} X (all T tiles), X row-major with ld MX (small systems).
+template <typename F, int TB, int NT>
+__device__ void tile_bwd_mat(const F* Lt, int T, F* X, int MX) {
+  constexpr int TT = TB * TB;
+  const int tid = threadIdx.x;
+  for (int J = T - 1; J >= 0; --J) {
+    const F* Dv = Lt + tcol(J, J, T) * TT;
+    F* XJ = X + J * TB * MX;
+    for (int cx = tid; cx < MX; cx += NT) {          // X_J <- Dinv^T X_J
+      F x[TB];
+#pragma unroll
+      for (int k = 0; k < TB; ++k) x[k] = XJ[k * MX + cx];
+#pragma unroll
+      for (int c = 0; c < TB; ++c) {
+        F s = F(0);
+#pragma unroll
+        for (int r = c; r < TB; ++r) s = fma(Dv[r + c * TB], x[r], s);
+        XJ[c * MX + cx] = s;
+      }
+    }
+    __syncthreads();
+    for (int it = tid; it < J * TB * MX; it += NT) {   // X_K2 -= L_J,K2^T X_J
+      const int row = it / MX, cx = it % MX;
+      const int K2 = row / TB, c = row % TB;
+      const F* L = Lt + tcol(J, K2, T) * TT;
+      F s = F(0);
+#pragma unroll
+      for (int r = 0; r < TB; ++r) s = fma(L[r + c * TB], XJ[r * MX + cx], s);
+      X[row * MX + cx] -= s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- v <- L^{-1} v (one right-hand side, T TB entries)
+template <typename F, int TB, int NT>
+__device__ void tile_fwd_vec(const F* Lt, int T, F* v) {
+  constexpr int TT = TB * TB;
+  const int tid = threadIdx.x;
+  for (int J = 0; J < T; ++J) {
+    const F* Dv = Lt + tcol(J, J, T) * TT;
+    F* vJ = v + J * TB;
+    if (tid < 32) {
+      F y = F(0);
+      if (tid < TB) {
+#pragma unroll
+        for (int k = 0; k < TB; ++k)
+          if (k <= tid) y = fma(Dv[tid + k * TB], vJ[k], y);
+      }
+      __syncwarp();
+      if (tid < TB) vJ[tid] = y;
+    }
+    __syncthreads();
+    for (int i = tid; i < (T - J - 1) * TB; i += NT) {
+      const int I = J + 1 + i / TB, r = i % TB;
+      const F* L = Lt + tcol(I, J, T) * TT;
+      F s = F(0);
+#pragma unroll
+      for (int k = 0; k < TB; ++k) s = fma(L[r + k * TB], vJ[k], s);
+      v[I * TB + r] -= s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- v <- L^{-T} v
+template <typename F, int TB, int NT>
+__device__ void tile_bwd_vec(const F* Lt, int T, F* v) {
+  constexpr int TT = TB * TB;
+  const int tid = threadIdx.x;
+  for (int J = T - 1; J >= 0; --J) {
+    const F* Dv = Lt + tcol(J, J, T) * TT;
+    F* vJ = v + J * TB;
+    if (tid < 32) {
+      F x = F(0);
+      if (tid < TB) {
+#pragma unroll
+        for (int r = 0; r < TB; ++r)
+          if (r >= tid) x = fma(Dv[r + tid * TB], vJ[r], x);
+      }
+      __syncwarp();
+      if (tid < TB) vJ[tid] = x;
+    }
+    __syncthreads();
+    for (int i = tid; i < J * TB; i += NT) {          // v_K2 -= L_J,K2^T x_J
+      const int K2 = i / TB, c = i % TB;
+      const F* L = Lt + tcol(J, K2, T) * TT;
+      F s = F(0);
+#pragma unroll
+      for (int t = 0; t < TB; ++t) {
+        const int r = (c + t) % TB;                  // rotated start: no bank conflicts across c
+        s = fma(L[r + c * TB], vJ[r], s);
+      }
+      v[i] -= s;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace tiles
+}  // namespace hyb
