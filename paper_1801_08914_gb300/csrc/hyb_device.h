@@ -51,6 +51,36 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   r = r * fma(-0.5 * d, r * r, 1.5);
   return r;
 }
+// 1 / sqrt(d) for a positive normal double, without FP64 conversions or range branches (on
+// GPUs whose FP64 unit takes tens of cycles per warp instruction, those dominate a pivot):
+// write d = m 4^s with m in [1, 4); build m as a float from its exponent and leading mantissa
+// bits with integer operations, take the single-precision hardware estimate of m^{-1/2}, and
+// scale it by 2^{-s} back into a double, again with integer operations (about 21 correct
+// bits). One third-order step of the binomial series (1 - e)^{-1/2} = 1 + e/2 + 3 e^2/8 + ...
+// with e = 1 - d r0^2 then gives the full double: the neglected term 5 e^3 / 16 is below
+// 2^-60. u = d r0 is rounded before e = 1 - u r0 is formed; that adds about 2^-53 to e and so
+// to the result. The caller checks that d is a positive normal number (a negative, zero or
+// non-finite d gives a meaningless value, no trap).
+__device__ __forceinline__ double rsqrt_h3(double d) {
+  const int hi = __double2hiint(d), lo = __double2loint(d);
+  const int ex = ((hi >> 20) & 0x7ff) - 1023;
+  const int s = ex >> 1;                                    // floor(ex / 2)
+  const unsigned mb = ((unsigned)(127 + ex - 2 * s) << 23) | (((unsigned)hi & 0xfffffu) << 3) |
+                      ((unsigned)lo >> 29);
+  const unsigned rb = __float_as_uint(rsqrtf(__uint_as_float(mb)));
+  const int rexp = (int)((rb >> 23) & 0xffu) - 127;
+  const double r0 = __hiloint2double((int)(((unsigned)(rexp + 1023 - s) << 20) | ((rb & 0x7fffffu) >> 3)),
+                                     (int)((rb & 7u) << 29));
+  const double u = d * r0;
+  const double e = fma(-u, r0, 1.0);
+  const double ep = e * fma(e, 0.375, 0.5);
+  return fma(r0, ep, r0);
+}
+// d > 0, finite and normal, from its high word (integer compares only)
+__device__ __forceinline__ bool positive_normal(double d) {
+  const int hi = __double2hiint(d);
+  return hi > 0x000fffff && hi < 0x7ff00000;
+}
 // single precision: the hardware estimate and one Newton step
 __device__ __forceinline__ float rsqrt_newton(float d) {
   float r = rsqrtf(d);

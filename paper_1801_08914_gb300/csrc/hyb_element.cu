@@ -282,7 +282,7 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
                                    double* flag, const double* wf) {
   using S = EK<3>;
   constexpr int NI = S::NI, NB = S::NB, NFN = S::NFN, NT = S::NT, TB = S::TB, TI = S::TI, TBB = S::TBB;
-  constexpr int T = TI + TBB, TT = TB * TB, MR = 4, MC = 4;
+  constexpr int T = TI + TBB, TT = TB * TB, MR = 2, MC = 2;   // small micro-tiles: more items to spread
   const int tid = threadIdx.x;
   double* R1 = R;                                   // L_ii tiles (packed over TI), then A_bb tiles
   double* R2 = R + S::R1;                           // L_bi tiles [I - TI][J], then Y
@@ -310,7 +310,7 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
   auto out = [&](int J) {
     return [A, J](int i, int l, double v) { A[tri(J * 16 + i, J * 16 + l)] = v; };
   };
-  if (!tiles::tile_chol<double, TB, MR, MC, NT>(tp, T, TI, TI, (double*)nullptr, 0, flag, out)) {
+  if (!tiles::tile_chol_la<double, TB, MR, MC, NT>(tp, T, TI, TI, flag, out)) {
     if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
     return;
   }
@@ -426,8 +426,8 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
     return;
   }
   // ---- 4b. hybridization: L_bb, z_b, Y = L_bb^{-1} (in R2), S_T and g_T, Y into the slot
-  if (!tiles::tile_chol<double, TB, MR, MC, NT>(tiles::Packed<double, TB>{R1, TBB}, TBB, TBB, TBB,
-                                                (double*)nullptr, 0, flag, [](int) { return tiles::NoOut{}; })) {
+  if (!tiles::tile_chol_la<double, TB, MR, MC, NT>(tiles::Packed<double, TB>{R1, TBB}, TBB, TBB, TBB, flag,
+                                                   [](int) { return tiles::NoOut{}; })) {
     if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
     return;
   }
@@ -437,7 +437,7 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
   double* Y = R2;                                    // [NB][NB], row-major
   for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0 : 0.0;
   __syncthreads();
-  tiles::tile_fwd_mat<double, TB, MR, MC, NT>(R1, TBB, 0, Y, NB);
+  tiles::tile_fwd_mat<double, TB, MR, MC, NT, true>(R1, TBB, 0, Y, NB);
   for (int ib = tid; ib < NB; ib += NT) {           // g_T = D Y^T z_b
     const int a = ib / NFN, m1 = ib % NFN;
     if (ef[a] < 0) continue;
@@ -448,17 +448,23 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
     if (args.colour == 1) args.rhs[gi] += v;
     else args.rhs[gi] = v;
   }
-  {                                                  // S = Y^T Y, lower micro-tiles, mirrored
-    constexpr int RM = NB / MR, CM = NB / MC;
-    for (int it = tid; it < RM * CM; it += NT) {
-      const int i0 = (it / CM) * MR, j0 = (it % CM) * MC;
+  {
+    // S = Y^T Y on the lower tiles (I2, J2), tile rows in increasing order (decreasing work),
+    // MR x MC micro-tiles; Y is lower triangular, so entry (i, j), i >= j, sums rows k >= i only
+    constexpr int PM = (TB / MR) * (TB / MC);
+    for (int it = tid; it < TBB * (TBB + 1) / 2 * PM; it += NT) {
+      const int q = it / PM, u = it % PM;
+      int I2 = 0;
+      while ((I2 + 1) * (I2 + 2) / 2 <= q) ++I2;
+      const int J2 = q - I2 * (I2 + 1) / 2;
+      const int i0 = I2 * TB + (u / (TB / MC)) * MR, j0 = J2 * TB + (u % (TB / MC)) * MC;
       if (i0 + MR - 1 < j0) continue;
       double acc[MR][MC];
 #pragma unroll
       for (int a = 0; a < MR; ++a)
 #pragma unroll
         for (int b = 0; b < MC; ++b) acc[a][b] = 0.0;
-      for (int k = i0 < j0 ? j0 : i0; k < NB; ++k) {   // rows k < max(i, j) of Y^T Y's terms vanish
+      for (int k = i0; k < NB; ++k) {
         double x[MR], y[MC];
 #pragma unroll
         for (int a = 0; a < MR; ++a) x[a] = Y[k * NB + i0 + a];

@@ -90,6 +90,70 @@ __device__ void diag_factor_invert(F* D, F* flag, const Out& out) {
   __syncwarp();
 }
 
+// ---- one warp, FP64, 16 x 16 tile: the same factorisation and inversion, laid out for an
+// FP64 unit that takes as long for one warp instruction as for its dependent successor,
+// whatever the number of active lanes: what counts is the number of FP64 instructions the warp
+// issues. Lane (i, h) = (lane & 15, lane >> 4) keeps the columns l = 2 j + h of row i in c[j],
+// and the rows 2 j + h of column i of L^{-1} in x[j], so that one instruction updates two
+// entries (both halves of the warp at once). The inverse is formed right-looking in the same
+// pass: once column k of L is known, x_k = x_k / L_kk is final and x_l -= L_lk x_k for l > k,
+// with the L_lk the factor update has just fetched. The pivot's inverse square root comes from
+// rsqrt_h3 (no FP64 conversions or branches) and the pivot check is on its integer bits. About
+// half the FP64 instructions of the one-row-per-lane form.
+template <typename Out>
+__device__ void diag_factor_invert64(double* D, double* flag, const Out& out) {
+  constexpr int TB = 16, H = 8;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, i = lane & 15, h = lane >> 4;
+  double c[H], x[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    const int l = 2 * j + h;
+    c[j] = l <= i ? D[i + l * TB] : 0.0;
+    x[j] = l == i ? 1.0 : 0.0;
+  }
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < TB; ++k) {
+    const int jk = k >> 1, hk = k & 1;
+    const double d = __shfl_sync(FULL, c[jk], k + 16 * hk);        // pivot, after the updates
+    ok = ok && dev::positive_normal(d);
+    const double r = dev::rsqrt_h3(d);
+    const double lik = __shfl_sync(FULL, c[jk], i + 16 * hk) * r;  // L_ik (L_kk in row k)
+    if (h == hk) {
+      c[jk] = lik;
+      x[jk] *= r;                                                  // x_k of column i, final
+    }
+    const double xk = __shfl_sync(FULL, x[jk], i + 16 * hk);
+#pragma unroll
+    for (int j = (k + 1) >> 1; j < H; ++j) {
+      const int l = 2 * j + h;
+      const double llk = __shfl_sync(FULL, lik, l);                // L_lk, from row l
+      if (l > k && l <= i) c[j] = fma(-lik, llk, c[j]);
+      if (l > k) x[j] = fma(-llk, xk, x[j]);
+    }
+  }
+  __syncwarp();
+  if (!ok) {
+    if (lane == 0) flag[0] = 1.0;
+    __syncwarp();
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    const int l = 2 * j + h;
+    if (l <= i) out(i, l, c[j]);
+    D[l + i * TB] = x[j];
+  }
+  __syncwarp();
+}
+
+template <typename F, int TB, typename Out>
+__device__ __forceinline__ void diag_step(F* D, F* flag, const Out& out) {
+  if constexpr (sizeof(F) == 8 && TB == 16) diag_factor_invert64(D, flag, out);
+  else diag_factor_invert<F, TB>(D, flag, out);
+}
+
 // ---- one thread: column cx of X_J <- Dinv_J X_J (X_J: TB rows, row-major with ld MX)
 template <typename F, int TB>
 __device__ __forceinline__ void scale_rows_item(const F* Dv, F* XJ, int MX, int cx) {
@@ -221,23 +285,88 @@ __device__ bool tile_chol(const TP& tp, int T, int Jend, int Kend, F* X, int MX,
   return true;
 }
 
+// ---- the same factorisation (X = null) with a look-ahead of one tile column: after the panel
+// of column J is scaled, warp 0 applies that column's update to the next diagonal tile and
+// factors it while the other warps apply the rest of the update, so that the one-warp diagonal
+// step overlaps the CTA-wide update instead of running alone between two barriers. Two
+// barriers per tile column. For the FP64 eliminations, where every FP64 warp instruction holds
+// its sub-partition's FP64 unit for many cycles and a lone warp leaves three of the four idle.
+template <typename F, int TB, int MR, int MC, int NT, typename TP, typename OutJ>
+__device__ bool tile_chol_la(const TP& tp, int T, int Jend, int Kend, F* flag, const OutJ& out) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int PM = (TB / MR) * (TB / MC);
+  if (tid == 0) flag[0] = F(0);
+  __syncthreads();
+  if (warp == 0 && Jend > 0) diag_step<F, TB>(tp(0, 0), flag, out(0));
+  __syncthreads();
+  for (int J = 0; J < Jend; ++J) {
+    if (flag[0] != F(0)) return false;
+    const F* Dv = tp(J, J);
+    const int nrows = (T - J - 1) * TB;
+    for (int it = tid; it < nrows; it += NT) {     // A_IJ <- A_IJ Dinv^T
+      F* A = tp(J + 1 + it / TB, J);
+      const int r = it % TB;
+      F a[TB];
+#pragma unroll
+      for (int k = 0; k < TB; ++k) a[k] = A[r + k * TB];
+#pragma unroll
+      for (int c = 0; c < TB; ++c) {
+        F s = F(0);
+#pragma unroll
+        for (int k = 0; k <= c; ++k) s = fma(a[k], Dv[c + k * TB], s);
+        A[r + c * TB] = s;
+      }
+    }
+    __syncthreads();
+    const int m = T - J - 1, mk = (Kend < T ? Kend : T) - J - 1;
+    const bool next = J + 1 < Jend && mk > 0;
+    const int npairs = mk * m - mk * (mk - 1) / 2;
+    if (next && warp == 0) {
+      // pair 0 of the column-by-column enumeration is the next diagonal tile (J+1, J+1): its
+      // lower micro-tiles, then its factorisation
+      F* Dn = tp(J + 1, J + 1);
+      const F* P = tp(J + 1, J);
+      for (int u = lane; u < PM; u += 32) {
+        const int r0 = (u / (TB / MC)) * MR, c0 = (u % (TB / MC)) * MC;
+        if (r0 + MR - 1 >= c0) syrk_micro<F, TB, MR, MC>(P, P, Dn, r0, c0);
+      }
+      __syncwarp();
+      diag_step<F, TB>(Dn, flag, out(J + 1));
+    } else {
+      const int q0 = next ? 1 : 0, t0 = next ? tid - 32 : tid, nth = next ? NT - 32 : NT;
+      for (int it = t0; it < (npairs - q0) * PM; it += nth) {
+        const int q = q0 + it / PM, u = it % PM;
+        int kp = 0, rem = q;                       // column kp of the trailing part has m - kp tiles
+        while (rem >= m - kp) { rem -= m - kp; ++kp; }
+        const int K2 = J + 1 + kp, I = K2 + rem;
+        syrk_micro<F, TB, MR, MC>(tp(I, J), tp(K2, J), tp(I, K2), (u / (TB / MC)) * MR, (u % (TB / MC)) * MC);
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 // ---- X <- L^{-1} X for the tiles J0..T-1 of a factored packed tile triangle; X holds the
-// rows of those tiles ((J - J0) TB + r), ld MX.
-template <typename F, int TB, int MR, int MC, int NT>
+// rows of those tiles ((J - J0) TB + r), ld MX. LOWER: X is block lower triangular on entry
+// (the identity, for L^{-1} itself), so that tile row J - J0 has no nonzero beyond column
+// (J - J0 + 1) TB, at every step; the work on those zero columns is skipped.
+template <typename F, int TB, int MR, int MC, int NT, bool LOWER = false>
 __device__ void tile_fwd_mat(const F* Lt, int T, int J0, F* X, int MX) {
   constexpr int TT = TB * TB;
   const int tid = threadIdx.x;
   for (int J = J0; J < T; ++J) {
     const F* Dv = Lt + tcol(J, J, T) * TT;
     F* XJ = X + (J - J0) * TB * MX;
-    for (int cx = tid; cx < MX; cx += NT) scale_rows_item<F, TB>(Dv, XJ, MX, cx);
+    const int ncol = LOWER ? (J - J0 + 1) * TB : MX;
+    for (int cx = tid; cx < ncol; cx += NT) scale_rows_item<F, TB>(Dv, XJ, MX, cx);
     __syncthreads();
-    const int m = T - J - 1, xm = (TB / MR) * (MX / MC);
+    const int m = T - J - 1, xm = (TB / MR) * (ncol / MC);
     for (int it = tid; it < m * xm; it += NT) {
       const int ti = it / xm, u = it % xm;
       const int I = J + 1 + ti;
-      gemm_x_micro<F, TB, MR, MC>(Lt + tcol(I, J, T) * TT, XJ, X + (I - J0) * TB * MX, MX, (u / (MX / MC)) * MR,
-                                  (u % (MX / MC)) * MC);
+      gemm_x_micro<F, TB, MR, MC>(Lt + tcol(I, J, T) * TT, XJ, X + (I - J0) * TB * MX, MX, (u / (ncol / MC)) * MR,
+                                  (u % (ncol / MC)) * MC);
     }
     __syncthreads();
   }
