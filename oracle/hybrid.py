@@ -20,7 +20,11 @@ Readings where the paper is silent:
     axis, -w_m on the neighbour above; w_m the tensor Gauss-Legendre weight on the
     reference face [0,1]^2 (M_s is diagonal: Q_k x Q_k is integrated exactly).
   * Element loads f_T = M_T c_T for f = sum_j c_j u_j given in the broken RT_k basis.
-  * All boundary faces carry essential normal-trace data.
+  * Boundary faces carry essential normal-trace data, or (natural=True) none: the weak form
+    is then posed over all of H(div) (eq. 5.1 as the soft-hard test of Sec. 6.1 states it),
+    the boundary-face dofs stay unknowns of their element and carry no multiplier.
+    Static condensation is only defined here with essential boundary faces (its global
+    unknowns are the interior faces' dofs).
 """
 from __future__ import annotations
 
@@ -41,8 +45,9 @@ class NotSPDError(ValueError):
 class Discretization:
     """Mesh, basis, element data and the constraint pattern of one problem."""
 
-    def __init__(self, nx, ny, nz, order, vertices, alpha, beta, load, ess=None, nq1d=None):
+    def __init__(self, nx, ny, nz, order, vertices, alpha, beta, load, ess=None, nq1d=None, natural=False):
         self.k = order
+        self.natural = bool(natural)
         self.mesh = StructuredHexMesh(nx, ny, nz, vertices)
         self.integ = ElementIntegrator(order, nq1d)
         self.basis = self.integ.basis
@@ -60,7 +65,8 @@ class Discretization:
 
     @classmethod
     def from_problem(cls, p, nq1d=None):
-        return cls(p.nx, p.ny, p.nz, p.order, p.vertices, p.alpha, p.beta, p.load, p.ess, nq1d)
+        return cls(p.nx, p.ny, p.nz, p.order, p.vertices, p.alpha, p.beta, p.load, p.ess, nq1d,
+                   getattr(p, "natural", False))
 
     # ---- one element -------------------------------------------------------------------------
     def element(self, e):
@@ -76,7 +82,7 @@ class Discretization:
         b = self.basis
         is_e = np.zeros(self.n, dtype=bool)
         for a, (_, fint) in enumerate(faces):
-            if fint < 0:
+            if fint < 0 and not self.natural:
                 is_e[b.n_interior + a * self.nfn: b.n_interior + (a + 1) * self.nfn] = True
         edofs = np.nonzero(is_e)[0]
         free = np.nonzero(~is_e)[0]
@@ -187,6 +193,8 @@ class Discretization:
 
         Global unknowns: the face dofs of interior faces, numbered like the multipliers.
         """
+        if self.natural:
+            raise NotImplementedError("static condensation with natural boundary faces")
         E = self.mesh.n_elem
         b = self.basis
         I, J, V = [], [], []
@@ -242,7 +250,8 @@ class Discretization:
 
     # ---- conforming assembly (eq. 2.1-2.2) -----------------------------------------------------
     def conforming_solve(self):
-        """Solve P^T A_hat P x = P^T f_hat with essential face dofs fixed; returns P x as (E, n)."""
+        """Solve P^T A_hat P x = P^T f_hat with essential face dofs fixed (natural: all face dofs
+        unknown); returns P x as (E, n)."""
         E = self.mesh.n_elem
         b = self.basis
         nfd = self.mesh.n_faces * self.nfn
@@ -262,7 +271,7 @@ class Discretization:
             for a, (fid, fint) in enumerate(faces):
                 sl = slice(b.n_interior + a * self.nfn, b.n_interior + (a + 1) * self.nfn)
                 gl[sl] = fid * self.nfn + np.arange(self.nfn)
-                if fint < 0:
+                if fint < 0 and not self.natural:
                     is_ess[gl[sl]] = True
                     if self.ess is not None:
                         ess_val[gl[sl]] = self.ess[e, sl]

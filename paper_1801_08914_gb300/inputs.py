@@ -85,6 +85,12 @@ class Problem:
     beta     : (E,) divergence coefficient per element
     load     : (E, n_loc) coefficients of f in the broken RT_k basis (element-local dof order)
     ess      : (E, n_loc) essential normal-trace values, read only at boundary-face dofs, or None (= 0)
+    natural  : True when the boundary faces carry no essential data (their dofs stay unknowns)
+
+    Element-local dof order (the contract both implementations read): the interior dofs of the
+    x, y, z reference components (k (k+1)^2 each, component by component), then the face dofs
+    of the faces x=0, x=1, y=0, y=1, z=0, z=1 ((k+1)^2 each); a face's dofs belong to the
+    component normal to it.
     """
     nx: int
     ny: int
@@ -96,6 +102,7 @@ class Problem:
     load: np.ndarray
     ess: np.ndarray | None
     name: str = ""
+    natural: bool = False
 
     @property
     def n_elem(self) -> int:
@@ -177,6 +184,50 @@ def manufactured_rt0_problem(n: int, gamma: float, seed: int) -> Problem:
         load[:, f] = area * u[:, axis]
     ess = load.copy()
     return Problem(nx, ny, nz, order, verts, np.ones(E), np.ones(E), load, ess, "manufactured")
+
+
+def dof_component(order: int) -> np.ndarray:
+    """Reference component (0, 1, 2) of every element-local dof, in the order of Problem's doc."""
+    k, p = order, order + 1
+    ni = k * p * p
+    comp = [c for c in range(3) for _ in range(ni)]
+    comp += [f // 2 for f in range(6) for _ in range(p * p)]
+    return np.array(comp, dtype=np.int64)
+
+
+# mesh of the soft-hard test per order (Sec. 6.1, its table of initial meshes): nx = ny = 2 nz
+SOFT_HARD_NZ = {0: 32, 1: 16, 2: 12, 3: 8}
+
+
+def soft_hard_problem(order: int, p: float, nz: int | None = None) -> Problem:
+    """The soft-hard materials test of Sec. 6.1 on an unjittered 2nz x 2nz x nz grid.
+
+    The paper's coefficients, in this package's naming (alpha multiplies the mass term,
+    beta the divergence term): beta = 1 everywhere and alpha = 10^p on the two cubes
+    [1/4, 1/2]^3 and [1/2, 3/4]^3 (an element belongs to them when its centre does; nz a
+    multiple of 4 makes the cubes unions of elements), 1 elsewhere. The source is the
+    constant field g = (1, 1, 1) and no boundary face carries essential data. On the box
+    cell [h_x] x [h_y] x [h_z] the reference field of a constant g under the Piola map is
+    (h_y h_z g_x, h_x h_z g_y, h_x h_y g_z) at every point, so every dof of component c takes
+    the product of the two other spacings: that is the load in the broken RT_k basis, exact.
+    """
+    nz = SOFT_HARD_NZ.get(order, 8) if nz is None else nz
+    if nz % 4:
+        raise ValueError("nz must be a multiple of 4")
+    nx = ny = 2 * nz
+    E = nx * ny * nz
+    verts = mesh_vertices(nx, ny, nz, 0.0, 0)
+    e = np.arange(E)
+    cx = ((e % nx) + 0.5) / nx
+    cy = (((e // nx) % ny) + 0.5) / ny
+    cz = ((e // (nx * ny)) + 0.5) / nz
+    inner = lambda lo, hi: (cx > lo) & (cx < hi) & (cy > lo) & (cy < hi) & (cz > lo) & (cz < hi)
+    alpha = np.where(inner(0.25, 0.5) | inner(0.5, 0.75), 10.0 ** p, 1.0)
+    beta = np.ones(E)
+    h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
+    per_comp = np.array([h[1] * h[2], h[0] * h[2], h[0] * h[1]])
+    load = np.tile(per_comp[dof_component(order)], (E, 1))
+    return Problem(nx, ny, nz, order, verts, alpha, beta, load, None, f"softhard_p{p:g}", natural=True)
 
 
 # The five workloads (sizes as the benchmark definitions state them).
