@@ -45,7 +45,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="mesh size override (parity / profiling runs)")
     ap.add_argument("--config", default="2",
-                    help="workload: 2 (32^3 RT_1, default), 3 (96^3 RT_2), 4 (256-problem batch), 5 (64^3 RT_3)")
+                    help="workload: 2 (32^3 RT_1, default), 3 (96^3 RT_2), 4 (256-problem batch), 5 (64^3 RT_3), "
+                         "softhard (Sec. 6.1's two-cube inclusion, natural boundary, --sh-order / --sh-p)")
+    ap.add_argument("--sh-order", type=int, default=1, help="softhard: RT order (mesh 2n x 2n x n of the paper's table)")
+    ap.add_argument("--sh-p", type=float, default=-8.0, help="softhard: mass coefficient 10^p in the inclusion")
     ap.add_argument("--batch-count", type=int, default=256, help="problems in the batched workload")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="fp64, or mixed: FP32 mixed-form elimination below the contrast threshold")
@@ -305,8 +308,12 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    cfg = int(args.config)
-    p = inputs.make_config(cfg, n=args.n)
+    cfg = str(args.config)
+    if cfg == "softhard":
+        p = inputs.soft_hard_problem(args.sh_order, args.sh_p, nz=args.n)
+    else:
+        cfg = int(cfg)
+        p = inputs.make_config(cfg, n=args.n)
     tt = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     verts, alpha, beta, load = tt(p.vertices), tt(p.alpha), tt(p.beta), tt(p.load)
     mixed = args.precision == "mixed"
@@ -314,6 +321,8 @@ def run_ours(args):
                         precision=hyb.HYB_MIXED if mixed else hyb.HYB_FP64,
                         contrast_threshold=args.threshold if mixed else 0.0)
     hyb.hyb_set_pcg_fused(ctx, args.pcg == "fused")
+    if p.natural:
+        hyb.hyb_set_natural_bc(ctx, True)
     n64, n32, theta = ctx.precision_split()
     sz = ctx.sizes()
     E, n_loc, N, nnz = sz["n_elem"], sz["n_loc"], sz["n_lambda"], sz["nnz"]
@@ -452,7 +461,11 @@ def run_ours(args):
                             "unit": "TFLOP/s", "frac": t_min / (elem_ms * 1e-3) if elem_ms > 0 else None,
                             "algorithmic_flops_per_element_fp32": f32, "algorithmic_flops_per_element_fp64": elem_flops,
                             "elements_fp64": n64, "elements_fp32": n32, "contrast_threshold": theta}
-    workload = WORKLOAD if cfg == 2 else f"config {cfg}: {p.nx}^3 jittered hex mesh, RT_{p.order}, FP64"
+    if cfg == "softhard":
+        workload = (f"soft-hard (Sec. 6.1): {p.nx}x{p.ny}x{p.nz} hex mesh, RT_{p.order}, mass coefficient "
+                    f"10^{args.sh_p:g} on [1/4,1/2]^3 u [1/2,3/4]^3, g = (1,1,1), natural boundary, FP64")
+    else:
+        workload = WORKLOAD if cfg == 2 else f"config {cfg}: {p.nx}^3 jittered hex mesh, RT_{p.order}, FP64"
     if mixed:
         how = "autotuned " if args.threshold == 0 else ""
         workload = workload.replace("FP64", f"mixed FP32/FP64 ({how}threshold {theta:g}: {n32} FP32 + {n64} FP64 elements)")

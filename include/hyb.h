@@ -81,13 +81,14 @@ typedef struct hyb_ctx hyb_ctx;
  *               conditioned), with the load term and the recovery refined against an FP64
  *               residual; the others use the FP64 path. The reduced system, PCG and the
  *               recovered u stay FP64. Static condensation needs an HYB_FP64 context.
- *  contrast_threshold : HYB_MIXED only (ignored for HYB_FP64); > 0 as given, 0 = autotuned:
- *               the FP32 elimination's error bound does not grow with beta/alpha, so the
- *               threshold only trades speed. The first HYB_MIXED set-up of each order on
- *               a device times both element kernels on a 16^3 (RT_3: 12^3) unit-cube mesh
- *               and puts every element on the faster path (threshold 1e300 or 0); the
- *               choice is cached for the process. hyb_get_precision_split reports it.
- *               Negative values: HYB_ERR_INVALID_ARG.
+ *  contrast_threshold : HYB_MIXED only (ignored for HYB_FP64); > 0 as given, 0 = autotuned.
+ *               The FP32 elimination's relative error in S_T grows like u_32 beta/alpha
+ *               (the 1/alpha part of A^-1 on the faces cancels in it); up to 1e6 the FP64
+ *               refinement corrects it, at 1e8 it does not. The first HYB_MIXED set-up of
+ *               each order on a device times both element kernels on a 16^3 (RT_3: 12^3)
+ *               unit-cube mesh: FP32 faster -> threshold 1e6 (elements above it stay
+ *               FP64), else 0 (all FP64); the choice is cached for the process.
+ *               hyb_get_precision_split reports it. Negative values: HYB_ERR_INVALID_ARG.
  *  cuda_stream: cudaStream_t to enqueue on (NULL = legacy default stream).
  *  out        : host, receives the new context.
  *  Builds the CSR pattern of H (int64 row pointers, int32 columns), per-element
@@ -191,6 +192,19 @@ int hyb_export_reduced(hyb_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val
  */
 int hyb_refine(hyb_ctx* ctx, int steps, double inner_rtol, int maxit, double* lambda, double* u,
                double* jump);
+
+/*
+ * hyb_set_natural_bc -- boundary reading of the next assembly.
+ *  0 (default): every boundary face carries essential normal-trace data (the values
+ *  passed as `ess`, zero when NULL); its dofs are eliminated (Sec. 5).
+ *  1: natural: the weak form is posed over all of H(div) (eq. 5.1, as in the soft-hard
+ *  test of Sec. 6.1); boundary-face dofs stay unknowns of their element, carry no
+ *  multiplier, and `ess` is ignored. Hybridization (both precisions), hyb_recover and
+ *  hyb_refine follow it; staticcond_assemble returns HYB_ERR_INVALID_ARG (its global
+ *  unknowns are the interior faces' dofs).
+ *  Resets the context's assembled state. HYB_ERR_INVALID_ARG for other values.
+ */
+int hyb_set_natural_bc(hyb_ctx* ctx, int natural);
 
 /*
  * hyb_set_pcg_fused -- choose the PCG launch form used by hyb_solve_reduced:

@@ -121,6 +121,7 @@ struct hyb_ctx {
   double* dlam = nullptr;
   double* rnorm = nullptr;                 // 2 doubles: ||rho||^2, ||g||^2
   unsigned long long* gridbar = nullptr;   // arrival counter of the fused PCG kernel's grid barrier
+  int natural = 0;                         // boundary faces: essential (0) or natural (1)
   int fused = 1;                           // PCG: one cooperative launch per chunk (1) or 3 launches/iteration (0)
   int nblocks = 0;
   int mode = MODE_NONE;
@@ -213,6 +214,7 @@ ElemArgs elem_args(hyb_ctx* c, const double* load, const double* ess, int colour
   a.zstore = c->zstore;
   a.status = c->status;
   a.err_elem = c->err_elem;
+  a.natural = c->natural;
   return a;
 }
 
@@ -436,12 +438,17 @@ int assemble_impl(hyb_ctx* c, const double* load, const double* ess, int mode) {
   return st;
 }
 
-// ---- contrast-threshold autotuner. The mixed-form FP32 elimination keeps its error (about
-// kappa(M, Z) u_32, bounds independent of beta / alpha) at every contrast, so the threshold
-// only trades speed: both element paths are timed on a unit-cube mesh of the same order
-// (alpha = beta = 1, zero load; the element work does not depend on the values), and every
-// element goes to the faster one: threshold 1e300 (all FP32) or 0 (all FP64). Measured once
-// per order and device, then cached for the process.
+// ---- contrast-threshold autotuner. Speed: both element paths are timed on a unit-cube mesh
+// of the same order (alpha = beta = 1, zero load; the element work does not depend on the
+// values). Accuracy: on the faces, A_T^{-1} has a part of size 1 / alpha (divergence-free
+// fields through the element) and a part of size 1 / beta; the FP32 mixed form obtains S_T as
+// Y^T Y - V^T V, where the 1 / alpha parts cancel, so the 1 / beta part carries an absolute
+// error of about u_32 / alpha, i.e. u_32 beta / alpha relative. Up to beta / alpha = 1e6 the
+// FP64 refinement still converges (measured); at 1e8 (soft-hard test, Sec. 6.1, p = -8) the
+// FP32 H of RT_1 is indefinite and the refinement of RT_2 / RT_3 stalls. So when FP32 is the
+// faster path the threshold is kMixedContrastMax (elements above it stay FP64), else 0 (all
+// FP64). Measured once per order and device, then cached for the process.
+constexpr double kMixedContrastMax = 1e6;
 std::mutex g_tune_mutex;
 std::map<std::pair<int, int>, double> g_tuned;
 
@@ -497,7 +504,7 @@ int autotune_theta(int order, cudaStream_t s, double* theta) {
   }
   cudaFree(buf);
   if (st != HYB_OK) return st;
-  *theta = ms[1] < ms[0] ? 1e300 : 0.0;
+  *theta = ms[1] < ms[0] ? kMixedContrastMax : 0.0;
   g_tuned[key] = *theta;
   return HYB_OK;
 }
@@ -574,6 +581,7 @@ int hyb_assemble_reduced(hyb_ctx* ctx, const double* load, const double* ess) {
 }
 
 int staticcond_assemble(hyb_ctx* ctx, const double* load, const double* ess) {
+  if (ctx && ctx->natural) return HYB_ERR_INVALID_ARG;
   return assemble_impl(ctx, load, ess, MODE_SC);
 }
 
@@ -683,6 +691,13 @@ int hyb_refine(hyb_ctx* c, int steps, double inner_rtol, int maxit, double* lamb
   }
   e = cudaStreamSynchronize(c->stream);
   return e == cudaSuccess ? HYB_OK : cuda_status(e);
+}
+
+int hyb_set_natural_bc(hyb_ctx* c, int natural) {
+  if (!c || (natural != 0 && natural != 1)) return HYB_ERR_INVALID_ARG;
+  c->natural = natural;
+  c->mode = MODE_NONE;                     // factors of the other reading are stale
+  return HYB_OK;
 }
 
 int hyb_set_pcg_fused(hyb_ctx* c, int on) {

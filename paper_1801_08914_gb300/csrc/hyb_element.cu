@@ -630,7 +630,7 @@ __device__ __forceinline__ void element_body(const ElemArgs& args, const int64_t
   const int32_t* ef = args.elem_face + e * 6;
   int bmask = 0;
 #pragma unroll
-  for (int a = 0; a < 6; ++a) bmask |= (ef[a] < 0) << a;
+  for (int a = 0; a < 6; ++a) bmask |= (ef[a] < 0 && !args.natural) << a;
   if (bmask) {
     const double* ue = args.ess ? args.ess + e * (int64_t)N : nullptr;
     if (ue) {

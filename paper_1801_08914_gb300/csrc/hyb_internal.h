@@ -60,6 +60,7 @@ struct ElemArgs {
   float* Lstore32;            // FP32 path: per element the tiles of L_M | Xd | L_Z | G^{-1}
   int* status;
   long long* err_elem;
+  int natural;                // 1: boundary faces carry no essential data (their dofs stay unknowns)
 };
 
 // Launch profile: CUDA events around each launch, accumulated per kernel class

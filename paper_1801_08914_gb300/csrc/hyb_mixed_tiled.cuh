@@ -252,7 +252,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   const int32_t* ef = args.elem_face + e * 6;
   int bmask = 0;
 #pragma unroll
-  for (int a = 0; a < 6; ++a) bmask |= (ef[a] < 0) << a;
+  for (int a = 0; a < 6; ++a) bmask |= (ef[a] < 0 && !args.natural) << a;
   auto is_e = [&](int i) { return i >= NI && ((bmask >> ((i - NI) / NFN)) & 1); };
 
   // ---- FP64 right-hand side: assembly forms f = M c (essential values folded in) and keeps

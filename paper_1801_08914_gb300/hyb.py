@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_destroy_batch.restype = None
     lib.hyb_set_profiling.argtypes = [P, I]
     lib.hyb_set_pcg_fused.argtypes = [P, I]
+    lib.hyb_set_natural_bc.argtypes = [P, I]
     lib.hyb_refine.argtypes = [P, I, D, I, P, P, ctypes.POINTER(D)]
     lib.hyb_barrier_selftest.argtypes = [I, I, P]
     lib.hyb_get_profile.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
@@ -263,6 +264,13 @@ def hyb_refine(ctx, steps, inner_rtol, maxit, lam, u, check=True):
     if check:
         _check(st, "hyb_refine")
     return list(jump), st
+
+
+def hyb_set_natural_bc(ctx, natural, check=True):
+    """Boundary reading of the next assembly: False = essential data on every boundary face
+    (default), True = natural (no boundary data, boundary-face dofs stay unknowns)."""
+    st = lib().hyb_set_natural_bc(ctx.handle, int(bool(natural)))
+    return _check(st, "hyb_set_natural_bc") if check else st
 
 
 def hyb_set_pcg_fused(ctx, on):

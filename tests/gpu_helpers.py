@@ -17,6 +17,8 @@ def gpu_run(p, mode="hyb", rtol=1e-14, maxit=100000, solve=True, precision=0, th
     from paper_1801_08914_gb300 import hyb
     ctx = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta),
                         precision=precision, contrast_threshold=threshold)
+    if getattr(p, "natural", False):
+        hyb.hyb_set_natural_bc(ctx, True)
     load = dev(p.load)
     ess = None if p.ess is None else dev(p.ess)
     if mode == "hyb":

@@ -116,8 +116,8 @@ def test_threshold_autotune():
                             precision=hyb.HYB_MIXED, contrast_threshold=0.0)
         n64, n32, theta = ctx.precision_split()
         ctx.close()
-        assert theta in (0.0, 1e300) and n64 + n32 == p.n_elem
-        assert (n32 == p.n_elem) if theta == 1e300 else (n64 == p.n_elem)
+        assert theta in (0.0, 1e6) and n64 + n32 == p.n_elem
+        assert (n32 == int(np.sum(p.beta / p.alpha <= 1e6))) if theta == 1e6 else (n64 == p.n_elem)
         t = time.perf_counter()
         ctx = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta),
                             precision=hyb.HYB_MIXED, contrast_threshold=0.0)
