@@ -237,6 +237,11 @@ def spmv_bytes(n, nnz, nfn):
 # DRAM bytes per PCG iteration of pcg_fused_kernel from one ncu capture of the unchanged kernel,
 # keyed by (config, mesh size, order); remove an entry when the kernel changes.
 FUSED_TRAFFIC = {(2, 32, 1): 163.0e6}
+# DRAM bytes per element of the FP64 element kernel (hybridization), from one ncu capture of
+# a smaller mesh of the same order (profiles/element_kernel_fp64.md: 16^3 RT_3, 2,048 elements
+# per launch, 23.6 MB read + 578.2 MB written); per-element work is uniform, so a launch's
+# traffic is this times its elements
+ELEMENT_TRAFFIC_PER_ELEMENT = {3: 293.8e3}
 
 
 def pcg_iteration_flops(n, nnz):
@@ -451,6 +456,11 @@ def run_ours(args):
                             "achieved": elem_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                             "frac": elem_tflops / fp64_peak if elem_tflops else None,
                             "algorithmic_flops_per_element": elem_flops}
+        tpe = ELEMENT_TRAFFIC_PER_ELEMENT.get(p.order) if not sc else None
+        el_launches = prof["element"][1] / args.steps
+        element_roofline["traffic"] = tpe * E / el_launches if tpe and el_launches else None
+        element_roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per element x elements "
+                                              "per launch (profiles/element_kernel_fp64.md)" if tpe else None)
     else:
         f32 = element_flops_mixed(p.order)
         # FP32 elements at the FP32 peak plus FP64 elements at the FP64 peak bound the phase from below

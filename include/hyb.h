@@ -290,6 +290,18 @@ int hyb_pcg_solve_noalloc(const int64_t* row_ptr, const int32_t* col, const doub
  */
 int hyb_measure_fma_peak(int fp64, void* cuda_stream, double* tflops);
 
+/*
+ * hyb_rsqrt_probe -- the element kernels' pivot inverse square root (an FP32 seed built
+ *  from the exponent and mantissa bits, then one third-order correction of the binomial
+ *  series of (1 - e)^{-1/2}) and their pivot check, evaluated on n given doubles, for
+ *  accuracy tests. Implementation check with no counterpart in the paper.
+ *  x : device, n doubles; out : device, n doubles, receives the inverse square roots
+ *  (meaningful where the check passes); positive_normal : device, n ints, receives 1 where
+ *  x[i] is a positive normal double, else 0. Synchronises cuda_stream.
+ *  HYB_ERR_INVALID_ARG for n < 0 or a null pointer with n > 0.
+ */
+int hyb_rsqrt_probe(int64_t n, const double* x, double* out, int* positive_normal, void* cuda_stream);
+
 /* hyb_get_precision_split -- host outputs (any may be NULL): elements on the FP64 and the
  *  FP32 path and the contrast threshold in use (0 for HYB_FP64 contexts). */
 int hyb_get_precision_split(const hyb_ctx* ctx, int64_t* n_fp64, int64_t* n_fp32, double* threshold);

@@ -277,6 +277,102 @@ __device__ void load_vector(const double* coef, const Tabs& tb, const double* Gu
 //   4. static condensation: scatter it and f_b; hybridization: L_bb = chol(.), z_b, Y = L_bb^{-1},
 //      S_T = D Y^T Y D and g_T = D Y^T z_b scattered, Y into the slot in place of L_bb.
 // The factor slot keeps the packed layout the recovery reads.
+
+// The face block of the hybridization in one look-ahead pass over its 6 x 6 tiles of 16 x 16:
+// L_bb = chol(A_bb - L_bi L_bi^T) (packed tiles in Lt, diagonal tiles inverted), Y = L_bb^{-1}
+// (row-major in Y, ld 96, formed from the identity) and S = Y^T Y (lower tiles, packed, in Sg).
+// Once tile column J is scaled, block row J of Y is final too, so the trailing update of L_bb,
+// the update of Y's later block rows and the rank-16 term Y_J^T Y_J of S share one phase; it
+// fills the sub-partitions that the one-warp diagonal step (warp 0, look-ahead) leaves idle.
+// Two barriers per tile column. Returns false in every thread on a bad pivot.
+template <int NT, int MR, int MC>
+__device__ bool face_block_hyb(double* Lt, double* Y, double* Sg, double* flag) {
+  constexpr int TB = 16, T = 6, NB = T * TB, TT = TB * TB, PM = (TB / MR) * (TB / MC);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto tp = [&](int I, int J) { return Lt + tiles::tcol(I, J, T) * TT; };
+  for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0 : 0.0;
+  for (int t = tid; t < T * (T + 1) / 2 * TT; t += NT) Sg[t] = 0.0;
+  if (tid == 0) flag[0] = 0.0;
+  __syncthreads();
+  if (warp == 0) tiles::diag_step<double, TB>(tp(0, 0), flag, tiles::NoOut{});
+  __syncthreads();
+  for (int J = 0; J < T; ++J) {
+    if (flag[0] != 0.0) return false;
+    const double* Dv = tp(J, J);
+    const int nrows = (T - J - 1) * TB, ncy = (J + 1) * TB;   // Y_J: zero beyond column ncy
+    double* YJ = Y + J * TB * NB;
+    for (int it = tid; it < nrows + ncy; it += NT) {
+      if (it < nrows) tiles::panel_row_item<double, TB>(Dv, tp(J + 1 + it / TB, J), it % TB);
+      else tiles::scale_rows_item<double, TB>(Dv, YJ, NB, it - nrows);
+    }
+    __syncthreads();
+    const bool next = J + 1 < T;
+    const int m = T - J - 1, npairs = m * (m + 1) / 2;
+    if (next && warp == 0) {
+      double* Dn = tp(J + 1, J + 1);
+      const double* P = tp(J + 1, J);
+      for (int u = lane; u < PM; u += 32) {
+        const int r0 = (u / (TB / MC)) * MR, c0 = (u % (TB / MC)) * MC;
+        if (r0 + MR - 1 >= c0) tiles::syrk_micro<double, TB, MR, MC>(P, P, Dn, r0, c0);
+      }
+      __syncwarp();
+      tiles::diag_step<double, TB>(Dn, flag, tiles::NoOut{});
+    } else {
+      const int q0 = next ? 1 : 0;
+      const int na = (npairs - q0) * PM;                  // trailing tile pairs of L_bb
+      const int xm = (TB / MR) * (ncy / MC), nb = m * xm;  // Y's later block rows
+      const int nsc = (J + 1) * (J + 2) / 2 * PM;          // S tiles (I2 >= J2, both <= J)
+      const tiles::LaWorkers wk(NT, (na + nb + nsc) * TB * MR * MC / 32);
+      const int t0 = next ? wk.id : tid, nth = next ? wk.n : NT;
+      for (int it = t0 >= 0 ? t0 : na + nb + nsc; it < na + nb + nsc; it += nth) {
+        if (it < na) {
+          const int q = q0 + it / PM, u = it % PM;
+          int kp = 0, rem = q;
+          while (rem >= m - kp) { rem -= m - kp; ++kp; }
+          const int K2 = J + 1 + kp, I = K2 + rem;
+          tiles::syrk_micro<double, TB, MR, MC>(tp(I, J), tp(K2, J), tp(I, K2), (u / (TB / MC)) * MR,
+                                                (u % (TB / MC)) * MC);
+        } else if (it < na + nb) {
+          const int it2 = it - na, ti = it2 / xm, u = it2 % xm;
+          tiles::gemm_x_micro<double, TB, MR, MC>(tp(J + 1 + ti, J), YJ, Y + (J + 1 + ti) * TB * NB, NB,
+                                                  (u / (ncy / MC)) * MR, (u % (ncy / MC)) * MC);
+        } else {
+          const int it3 = it - na - nb, q = it3 / PM, u = it3 % PM;
+          int I2 = 0;
+          while ((I2 + 1) * (I2 + 2) / 2 <= q) ++I2;
+          const int J2 = q - I2 * (I2 + 1) / 2;
+          const int a0 = (u / (TB / MC)) * MR, b0 = (u % (TB / MC)) * MC;
+          if (I2 == J2 && a0 + MR - 1 < b0) continue;
+          double acc[MR][MC];
+#pragma unroll
+          for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j) acc[i][j] = 0.0;
+#pragma unroll 4
+          for (int k = 0; k < TB; ++k) {
+            double x[MR], y[MC];
+#pragma unroll
+            for (int i = 0; i < MR; ++i) x[i] = YJ[k * NB + I2 * TB + a0 + i];
+#pragma unroll
+            for (int j = 0; j < MC; ++j) y[j] = YJ[k * NB + J2 * TB + b0 + j];
+#pragma unroll
+            for (int i = 0; i < MR; ++i)
+#pragma unroll
+              for (int j = 0; j < MC; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
+          }
+          double* St = Sg + tiles::tcol(I2, J2, T) * TT;
+#pragma unroll
+          for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j) St[(a0 + i) + (b0 + j) * TB] += acc[i][j];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 template <int MODE>
 __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double* A, double* f, double* R,
                                    double* flag, const double* wf) {
@@ -289,22 +385,38 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
   auto tp = [&](int I, int J) -> double* {
     return I < TI ? R1 + tiles::tcol(I, J, TI) * TT : R2 + ((I - TI) * TI + J) * TT;
   };
-  // ---- 1. load the interior tile columns, eliminate them
-  for (int t = tid; t < S::R1 + S::R2; t += NT) {
-    int I, J;
-    const int w = t % TT;
-    if (t < S::R1) {
-      int rem = t / TT;
-      J = 0;
-      while (rem >= TI - J) { rem -= TI - J; ++J; }
-      I = J + rem;
-    } else {
-      const int tile = (t - S::R1) / TT;
-      I = TI + tile / TI;
-      J = tile % TI;
+  // ---- 1. load the interior tile columns, eliminate them. Consecutive threads read
+  // consecutive columns of one row (contiguous in packed A); four loads in flight per thread.
+  constexpr int NLD = S::R1 + S::R2, LB = 4;
+  for (int t0 = tid; t0 < NLD; t0 += LB * NT) {
+    double v[LB];
+    int dst[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int t = t0 + u * NT;
+      dst[u] = -1;
+      v[u] = 0.0;
+      if (t < NLD) {
+        int I, J;
+        const int w = t % TT;
+        if (t < S::R1) {
+          int rem = t / TT;
+          J = 0;
+          while (rem >= TI - J) { rem -= TI - J; ++J; }
+          I = J + rem;
+        } else {
+          const int tile = (t - S::R1) / TT;
+          I = TI + tile / TI;
+          J = tile % TI;
+        }
+        const int r = w / TB, c = w % TB, i = I * TB + r, j = J * TB + c;
+        dst[u] = t - w + r + c * TB;
+        if (i >= j) v[u] = A[tri(i, j)];
+      }
     }
-    const int i = I * TB + w % TB, j = J * TB + w / TB;
-    R[t] = i >= j ? A[tri(i, j)] : 0.0;
+#pragma unroll
+    for (int u = 0; u < LB; ++u)
+      if (dst[u] >= 0) R[dst[u]] = v[u];
   }
   __syncthreads();
   auto out = [&](int J) {
@@ -344,12 +456,27 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
   }
   __syncthreads();
   // ---- 3. the face block and its Schur complement A_bb - L_bi L_bi^T (packed tiles in R1)
-  for (int t = tid; t < TBB * (TBB + 1) / 2 * TT; t += NT) {
-    int rem = t / TT, J = 0;
-    while (rem >= TBB - J) { rem -= TBB - J; ++J; }
-    const int I = J + rem, w = t % TT;
-    const int i = NI + I * TB + w % TB, j = NI + J * TB + w / TB;
-    R1[t] = i >= j ? A[tri(i, j)] : 0.0;
+  constexpr int NBB = TBB * (TBB + 1) / 2 * TT;
+  for (int t0 = tid; t0 < NBB; t0 += LB * NT) {
+    double v[LB];
+    int dst[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int t = t0 + u * NT;
+      dst[u] = -1;
+      v[u] = 0.0;
+      if (t < NBB) {
+        int rem = t / TT, J = 0;
+        while (rem >= TBB - J) { rem -= TBB - J; ++J; }
+        const int I = J + rem, w = t % TT;
+        const int r = w / TB, c = w % TB, i = NI + I * TB + r, j = NI + J * TB + c;
+        dst[u] = t - w + r + c * TB;
+        if (i >= j) v[u] = A[tri(i, j)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u)
+      if (dst[u] >= 0) R1[dst[u]] = v[u];
   }
   __syncthreads();
   {
@@ -425,19 +552,18 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
     }
     return;
   }
-  // ---- 4b. hybridization: L_bb, z_b, Y = L_bb^{-1} (in R2), S_T and g_T, Y into the slot
-  if (!tiles::tile_chol_la<double, TB, MR, MC, NT>(tiles::Packed<double, TB>{R1, TBB}, TBB, TBB, TBB, flag,
-                                                   [](int) { return tiles::NoOut{}; })) {
+  // ---- 4b. hybridization: L_bb, Y = L_bb^{-1} (in R2) and S = Y^T Y (tiles after the
+  // face block's in R1) in one pass; z_b, g_T, S_T scattered, Y into the slot
+  double* Y = R2;                                    // [NB][NB], row-major
+  double* Sg = R1 + TBB * (TBB + 1) / 2 * TT;
+  static_assert(2 * TBB * (TBB + 1) / 2 * TT <= S::R1 && NB * NB <= S::R2, "face block buffers");
+  if (!face_block_hyb<NT, MR, MC>(R1, Y, Sg, flag)) {
     if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
     return;
   }
   tiles::tile_fwd_vec<double, TB, NT>(R1, TBB, f + NI);
   double* zs = args.zstore + e * (int64_t)S::N;
   for (int i = tid; i < S::N; i += NT) zs[i] = f[i];
-  double* Y = R2;                                    // [NB][NB], row-major
-  for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0 : 0.0;
-  __syncthreads();
-  tiles::tile_fwd_mat<double, TB, MR, MC, NT, true>(R1, TBB, 0, Y, NB);
   for (int ib = tid; ib < NB; ib += NT) {           // g_T = D Y^T z_b
     const int a = ib / NFN, m1 = ib % NFN;
     if (ef[a] < 0) continue;
@@ -448,43 +574,10 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
     if (args.colour == 1) args.rhs[gi] += v;
     else args.rhs[gi] = v;
   }
-  {
-    // S = Y^T Y on the lower tiles (I2, J2), tile rows in increasing order (decreasing work),
-    // MR x MC micro-tiles; Y is lower triangular, so entry (i, j), i >= j, sums rows k >= i only
-    constexpr int PM = (TB / MR) * (TB / MC);
-    for (int it = tid; it < TBB * (TBB + 1) / 2 * PM; it += NT) {
-      const int q = it / PM, u = it % PM;
-      int I2 = 0;
-      while ((I2 + 1) * (I2 + 2) / 2 <= q) ++I2;
-      const int J2 = q - I2 * (I2 + 1) / 2;
-      const int i0 = I2 * TB + (u / (TB / MC)) * MR, j0 = J2 * TB + (u % (TB / MC)) * MC;
-      if (i0 + MR - 1 < j0) continue;
-      double acc[MR][MC];
-#pragma unroll
-      for (int a = 0; a < MR; ++a)
-#pragma unroll
-        for (int b = 0; b < MC; ++b) acc[a][b] = 0.0;
-      for (int k = i0; k < NB; ++k) {
-        double x[MR], y[MC];
-#pragma unroll
-        for (int a = 0; a < MR; ++a) x[a] = Y[k * NB + i0 + a];
-#pragma unroll
-        for (int b = 0; b < MC; ++b) y[b] = Y[k * NB + j0 + b];
-#pragma unroll
-        for (int a = 0; a < MR; ++a)
-#pragma unroll
-          for (int b = 0; b < MC; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
-      }
-#pragma unroll
-      for (int a = 0; a < MR; ++a)
-#pragma unroll
-        for (int b = 0; b < MC; ++b) {
-          const int ib = i0 + a, jb = j0 + b;
-          if (ib < jb) continue;
-          put(ib, jb, acc[a][b], true);
-          if (ib != jb) put(jb, ib, acc[a][b], true);
-        }
-    }
+  for (int t = tid; t < NB * NB; t += NT) {          // S_T = D S D, both triangles from the lower tiles
+    const int ib = t / NB, jb = t % NB;
+    const int gi = ib >= jb ? ib : jb, gj = ib >= jb ? jb : ib;
+    put(ib, jb, Sg[tiles::tcol(gi / TB, gj / TB, TBB) * TT + (gi % TB) + (gj % TB) * TB], true);
   }
   for (int t = tid; t < NB * NB; t += NT) {          // Y in place of L_bb
     const int i = t / NB, j = t % NB;

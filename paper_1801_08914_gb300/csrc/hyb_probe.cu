@@ -1,7 +1,9 @@
 // Arithmetic throughput probe used as the roofline denominator for ALU-bound kernels:
-// a grid of 8 independent FMA chains per thread, timed with CUDA events.
+// a grid of 8 independent FMA chains per thread, timed with CUDA events. Also the element
+// kernels' pivot inverse square root evaluated on given inputs, for its accuracy test.
 #include <cuda_runtime.h>
 
+#include "hyb_device.h"
 #include "hyb_internal.h"
 
 namespace hyb {
@@ -50,8 +52,26 @@ int measure(cudaStream_t s, int iters, double* tflops) {
   return HYB_OK;
 }
 
+__global__ void rsqrt_probe_kernel(int64_t n, const double* x, double* out, int* ok) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    out[i] = dev::rsqrt_h3(x[i]);
+    ok[i] = dev::positive_normal(x[i]) ? 1 : 0;
+  }
+}
+
 }  // namespace
 }  // namespace hyb
+
+extern "C" int hyb_rsqrt_probe(int64_t n, const double* x, double* out, int* positive_normal, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!x || !out || !positive_normal))) return HYB_ERR_INVALID_ARG;
+  if (n == 0) return HYB_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int64_t blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  hyb::rsqrt_probe_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, x, out, positive_normal);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? HYB_OK : HYB_ERR_CUDA;
+}
 
 extern "C" int hyb_measure_fma_peak(int fp64, void* cuda_stream, double* tflops) {
   if (!tflops) return HYB_ERR_INVALID_ARG;

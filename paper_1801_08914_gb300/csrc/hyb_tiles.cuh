@@ -148,6 +148,24 @@ __device__ void diag_factor_invert64(double* D, double* flag, const Out& out) {
   __syncwarp();
 }
 
+// Workers of a look-ahead update phase, while warp 0 factors the next diagonal tile. Warps w
+// run on sub-partition w % 4. A small update leaves sub-partition 0 to warp 0 alone (its
+// dependent chain would otherwise wait behind the other warps' FP64 instructions there); a
+// large one uses every other warp. `work` = FP64 warp instructions of the update.
+struct LaWorkers {
+  int id, n;   // worker index (-1: not a worker) and worker count
+  __device__ LaWorkers(int nthreads, int work) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (work > 3000) {
+      id = warp == 0 ? -1 : (int)threadIdx.x - 32;
+      n = nthreads - 32;
+    } else {
+      id = (warp & 3) == 0 ? -1 : (warp - (warp >> 2) - 1) * 32 + lane;
+      n = (nthreads >> 5) / 4 * 3 * 32;
+    }
+  }
+};
+
 template <typename F, int TB, typename Out>
 __device__ __forceinline__ void diag_step(F* D, F* flag, const Out& out) {
   if constexpr (sizeof(F) == 8 && TB == 16) diag_factor_invert64(D, flag, out);
@@ -166,6 +184,21 @@ __device__ __forceinline__ void scale_rows_item(const F* Dv, F* XJ, int MX, int 
 #pragma unroll
     for (int k = 0; k <= r; ++k) s = fma(Dv[r + k * TB], x[k], s);
     XJ[r * MX + cx] = s;
+  }
+}
+
+// ---- one thread: row r of a panel tile A_IJ <- A_IJ Dinv_J^T (Dinv lower triangular)
+template <typename F, int TB>
+__device__ __forceinline__ void panel_row_item(const F* Dv, F* A, int r) {
+  F a[TB];
+#pragma unroll
+  for (int k = 0; k < TB; ++k) a[k] = A[r + k * TB];
+#pragma unroll
+  for (int c = 0; c < TB; ++c) {
+    F s = F(0);
+#pragma unroll
+    for (int k = 0; k <= c; ++k) s = fma(a[k], Dv[c + k * TB], s);
+    A[r + c * TB] = s;
   }
 }
 
@@ -303,20 +336,8 @@ __device__ bool tile_chol_la(const TP& tp, int T, int Jend, int Kend, F* flag, c
     if (flag[0] != F(0)) return false;
     const F* Dv = tp(J, J);
     const int nrows = (T - J - 1) * TB;
-    for (int it = tid; it < nrows; it += NT) {     // A_IJ <- A_IJ Dinv^T
-      F* A = tp(J + 1 + it / TB, J);
-      const int r = it % TB;
-      F a[TB];
-#pragma unroll
-      for (int k = 0; k < TB; ++k) a[k] = A[r + k * TB];
-#pragma unroll
-      for (int c = 0; c < TB; ++c) {
-        F s = F(0);
-#pragma unroll
-        for (int k = 0; k <= c; ++k) s = fma(a[k], Dv[c + k * TB], s);
-        A[r + c * TB] = s;
-      }
-    }
+    for (int it = tid; it < nrows; it += NT)       // A_IJ <- A_IJ Dinv^T
+      panel_row_item<F, TB>(Dv, tp(J + 1 + it / TB, J), it % TB);
     __syncthreads();
     const int m = T - J - 1, mk = (Kend < T ? Kend : T) - J - 1;
     const bool next = J + 1 < Jend && mk > 0;
@@ -333,8 +354,10 @@ __device__ bool tile_chol_la(const TP& tp, int T, int Jend, int Kend, F* flag, c
       __syncwarp();
       diag_step<F, TB>(Dn, flag, out(J + 1));
     } else {
-      const int q0 = next ? 1 : 0, t0 = next ? tid - 32 : tid, nth = next ? NT - 32 : NT;
-      for (int it = t0; it < (npairs - q0) * PM; it += nth) {
+      const int q0 = next ? 1 : 0;
+      const LaWorkers wk(NT, (npairs - q0) * PM * TB * MR * MC / 32);
+      const int t0 = next ? wk.id : tid, nth = next ? wk.n : NT;
+      for (int it = t0 >= 0 ? t0 : (npairs - q0) * PM; it < (npairs - q0) * PM; it += nth) {
         const int q = q0 + it / PM, u = it % PM;
         int kp = 0, rem = q;                       // column kp of the trailing part has m - kp tiles
         while (rem >= m - kp) { rem -= m - kp; ++kp; }

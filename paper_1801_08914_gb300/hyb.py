@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_destroy_batch.restype = None
     lib.hyb_set_profiling.argtypes = [P, I]
     lib.hyb_set_pcg_fused.argtypes = [P, I]
+    lib.hyb_rsqrt_probe.argtypes = [ctypes.c_int64, P, P, P, P]
     lib.hyb_set_natural_bc.argtypes = [P, I]
     lib.hyb_refine.argtypes = [P, I, D, I, P, P, ctypes.POINTER(D)]
     lib.hyb_barrier_selftest.argtypes = [I, I, P]
@@ -264,6 +265,12 @@ def hyb_refine(ctx, steps, inner_rtol, maxit, lam, u, check=True):
     if check:
         _check(st, "hyb_refine")
     return list(jump), st
+
+
+def hyb_rsqrt_probe(x, out, positive_normal, stream=None):
+    """Status; out / positive_normal receive the kernels' pivot inverse square root and check."""
+    return lib().hyb_rsqrt_probe(int(x.numel()), _ptr(x, "x"), _ptr(out, "out"),
+                                 _ptr(positive_normal, "positive_normal", torch.int32), _stream(stream))
 
 
 def hyb_set_natural_bc(ctx, natural, check=True):
