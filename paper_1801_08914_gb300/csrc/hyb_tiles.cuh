@@ -35,32 +35,37 @@ struct NoOut {
 
 // ---- one warp: Cholesky of the lower triangle of a TB x TB column-major tile in place,
 // then replace it by the inverse of the factor (strict upper part zero). Lane i holds row i
-// in registers and the columns travel by shuffles, so there is no shared-memory round trip or
-// index arithmetic inside the elimination. out(i, l, L_il) receives the factor itself (l <= i)
-// before the inversion. flag[0] = 1 on a bad pivot (every lane leaves at the same step: the
-// pivot is broadcast).
+// of the factor and column i of its inverse in registers; the columns of the factor travel
+// by shuffles, so there is no shared-memory round trip or index arithmetic inside the
+// elimination. The inverse is formed right-looking in the same pass: once column k of L is
+// known, x_k = x_k / L_kk is final in every lane's column and x_l -= L_lk x_k for l > k, with
+// the L_lk the factor update has just fetched (the lane's own x_k needs no shuffle). No
+// data-dependent exit: a bad pivot only sets a flag, so the loops unroll and every array stays
+// in registers. out(i, l, L_il) receives the factor itself (l <= i); flag[0] = 1 on a bad
+// pivot (non-positive or non-finite), in which case nothing is written.
 template <typename F, int TB, typename Out>
-__device__ void diag_factor_invert(F* D, F* flag, const Out& out) {
+__device__ __forceinline__ void diag_factor_invert(F* D, F* flag, const Out& out) {
   const int lane = threadIdx.x & 31;
   constexpr unsigned FULL = 0xffffffffu;
-  F row[TB], rv[TB];
+  F row[TB], x[TB];
 #pragma unroll
-  for (int l = 0; l < TB; ++l) row[l] = (lane < TB && l <= lane) ? D[lane + l * TB] : F(0);
+  for (int l = 0; l < TB; ++l) {
+    row[l] = (lane < TB && l <= lane) ? D[lane + l * TB] : F(0);
+    x[l] = l == lane ? F(1) : F(0);
+  }
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < TB; ++k) {
     const F d = __shfl_sync(FULL, row[k], k);             // pivot, after the previous updates
-    if (!(d > F(0)) || !(d < F(INFINITY))) {
-      ok = false;
-      break;
-    }
+    ok = ok && d > F(0) && d < F(INFINITY);
     const F r = dev::rsqrt_newton(d);
-    rv[k] = r;                                             // 1 / L_kk, in every lane
     row[k] = lane == k ? d * r : row[k] * r;               // column k of L (rows > k, and the pivot)
+    x[k] *= r;                                             // x_k of this lane's column, final
 #pragma unroll
-    for (int l = k + 1; l < TB; ++l) {                     // row_i[l] -= L_ik L_lk, k < l <= i
-      const F lk = __shfl_sync(FULL, row[k], l);
-      if (lane >= l) row[l] = fma(-row[k], lk, row[l]);
+    for (int l = k + 1; l < TB; ++l) {
+      const F lk = __shfl_sync(FULL, row[k], l);          // L_lk
+      if (lane >= l) row[l] = fma(-row[k], lk, row[l]);    // row_i[l] -= L_ik L_lk, k < l <= i
+      x[l] = fma(-lk, x[k], x[l]);
     }
   }
   if (!ok) {
@@ -72,80 +77,83 @@ __device__ void diag_factor_invert(F* D, F* flag, const Out& out) {
 #pragma unroll
     for (int l = 0; l < TB; ++l)
       if (l <= lane) out(lane, l, row[l]);
-  }
-  // column c of L^{-1} in lane c: col_i = -(sum_{c <= k < i} L_ik col_k) / L_ii, col_c = 1 / L_cc;
-  // L_ik comes from lane i by shuffle
-  F col[TB];
 #pragma unroll
-  for (int i = 0; i < TB; ++i) {
-    F s = F(0);
-#pragma unroll
-    for (int k = 0; k < i; ++k) s = fma(__shfl_sync(FULL, row[k], i), col[k], s);
-    col[i] = i < lane ? F(0) : (i == lane ? rv[i] : -s * rv[i]);
-  }
-  if (lane < TB) {
-#pragma unroll
-    for (int i = 0; i < TB; ++i) D[i + lane * TB] = col[i];
+    for (int i = 0; i < TB; ++i) D[i + lane * TB] = x[i];
   }
   __syncwarp();
 }
 
-// ---- one warp, FP64, 16 x 16 tile: the same factorisation and inversion, laid out for an
-// FP64 unit that takes as long for one warp instruction as for its dependent successor,
-// whatever the number of active lanes: what counts is the number of FP64 instructions the warp
-// issues. Lane (i, h) = (lane & 15, lane >> 4) keeps the columns l = 2 j + h of row i in c[j],
-// and the rows 2 j + h of column i of L^{-1} in x[j], so that one instruction updates two
-// entries (both halves of the warp at once). The inverse is formed right-looking in the same
-// pass: once column k of L is known, x_k = x_k / L_kk is final and x_l -= L_lk x_k for l > k,
-// with the L_lk the factor update has just fetched. The pivot's inverse square root comes from
-// rsqrt_h3 (no FP64 conversions or branches) and the pivot check is on its integer bits. About
-// half the FP64 instructions of the one-row-per-lane form.
-template <typename Out>
-__device__ void diag_factor_invert64(double* D, double* flag, const Out& out) {
-  constexpr int TB = 16, H = 8;
+// ---- one warp, TB even and at most 16: the same factorisation and inversion with two
+// columns per instruction. On this part an FP64 warp instruction holds its sub-partition's
+// FP64 unit as long as its dependent successor waits, whatever the number of active lanes, so
+// what counts is the number of instructions the warp issues; in FP32 the halved per-lane
+// arrays keep the factor in registers inside large kernels. Lane (i, h) = (lane & 15,
+// lane >> 4) keeps the columns l = 2 j + h of row i in c[j] and the rows 2 j + h of column i of
+// L^{-1} in x[j] (lanes with i >= TB carry zeros). The inverse is formed right-looking in the
+// same pass, with the L_lk the factor update has just fetched. FP64 pivots take their inverse
+// square root from rsqrt_h3 (no FP64 conversions or branches) and are checked on their
+// integer bits. About half the instructions of the one-row-per-lane form.
+template <typename F, int TB, typename Out>
+__device__ __forceinline__ void diag_factor_invert2(F* D, F* flag, const Out& out) {
+  static_assert(TB % 2 == 0 && TB <= 16, "two half-warps of at most 8 columns");
+  constexpr int H = TB / 2;
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, i = lane & 15, h = lane >> 4;
-  double c[H], x[H];
+  F c[H], x[H];
 #pragma unroll
   for (int j = 0; j < H; ++j) {
     const int l = 2 * j + h;
-    c[j] = l <= i ? D[i + l * TB] : 0.0;
-    x[j] = l == i ? 1.0 : 0.0;
+    c[j] = (i < TB && l <= i) ? D[i + l * TB] : F(0);
+    x[j] = l == i ? F(1) : F(0);
   }
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < TB; ++k) {
     const int jk = k >> 1, hk = k & 1;
-    const double d = __shfl_sync(FULL, c[jk], k + 16 * hk);        // pivot, after the updates
-    ok = ok && dev::positive_normal(d);
-    const double r = dev::rsqrt_h3(d);
-    const double lik = __shfl_sync(FULL, c[jk], i + 16 * hk) * r;  // L_ik (L_kk in row k)
+    const F d = __shfl_sync(FULL, c[jk], k + 16 * hk);             // pivot, after the updates
+    F r;
+    if constexpr (sizeof(F) == 8) {
+      ok = ok && dev::positive_normal(d);
+      r = dev::rsqrt_h3(d);
+    } else {
+      ok = ok && d > F(0) && d < F(INFINITY);
+      r = dev::rsqrt_newton(d);
+    }
+    const F lik = __shfl_sync(FULL, c[jk], (i & 15) + 16 * hk) * r; // L_ik (L_kk in row k)
     if (h == hk) {
       c[jk] = lik;
       x[jk] *= r;                                                  // x_k of column i, final
     }
-    const double xk = __shfl_sync(FULL, x[jk], i + 16 * hk);
+    const F xk = __shfl_sync(FULL, x[jk], (i & 15) + 16 * hk);
 #pragma unroll
     for (int j = (k + 1) >> 1; j < H; ++j) {
       const int l = 2 * j + h;
-      const double llk = __shfl_sync(FULL, lik, l);                // L_lk, from row l
+      const F llk = __shfl_sync(FULL, lik, l);                     // L_lk, from row l
       if (l > k && l <= i) c[j] = fma(-lik, llk, c[j]);
       if (l > k) x[j] = fma(-llk, xk, x[j]);
     }
   }
   __syncwarp();
   if (!ok) {
-    if (lane == 0) flag[0] = 1.0;
+    if (lane == 0) flag[0] = F(1);
     __syncwarp();
     return;
   }
+  if (i < TB) {
 #pragma unroll
-  for (int j = 0; j < H; ++j) {
-    const int l = 2 * j + h;
-    if (l <= i) out(i, l, c[j]);
-    D[l + i * TB] = x[j];
+    for (int j = 0; j < H; ++j) {
+      const int l = 2 * j + h;
+      if (l <= i) out(i, l, c[j]);
+      D[l + i * TB] = x[j];
+    }
   }
   __syncwarp();
+}
+
+template <typename F, int TB, typename Out>
+__device__ __forceinline__ void diag_step(F* D, F* flag, const Out& out) {
+  if constexpr (TB % 2 == 0 && TB <= 16) diag_factor_invert2<F, TB>(D, flag, out);
+  else diag_factor_invert<F, TB>(D, flag, out);
 }
 
 // Workers of a look-ahead update phase, while warp 0 factors the next diagonal tile. Warps w
@@ -166,11 +174,6 @@ struct LaWorkers {
   }
 };
 
-template <typename F, int TB, typename Out>
-__device__ __forceinline__ void diag_step(F* D, F* flag, const Out& out) {
-  if constexpr (sizeof(F) == 8 && TB == 16) diag_factor_invert64(D, flag, out);
-  else diag_factor_invert<F, TB>(D, flag, out);
-}
 
 // ---- one thread: column cx of X_J <- Dinv_J X_J (X_J: TB rows, row-major with ld MX)
 template <typename F, int TB>
@@ -271,7 +274,7 @@ __device__ bool tile_chol(const TP& tp, int T, int Jend, int Kend, F* X, int MX,
   __syncthreads();
   for (int J = 0; J < Jend; ++J) {
     F* Dv = tp(J, J);
-    if (tid < 32) diag_factor_invert<F, TB>(Dv, flag, out(J));
+    if (tid < 32) diag_step<F, TB>(Dv, flag, out(J));
     __syncthreads();
     if (flag[0] != F(0)) return false;
     const int nrows = (T - J - 1) * TB, ncols = X ? MX : 0;
