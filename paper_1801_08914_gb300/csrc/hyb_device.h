@@ -76,6 +76,16 @@ __device__ __forceinline__ double rsqrt_h3(double d) {
   const double ep = e * fma(e, 0.375, 0.5);
   return fma(r0, ep, r0);
 }
+// Exact float -> double widening with integer operations (sign, re-biased exponent, mantissa
+// shifted into place), for kernels where an FP64-pipe conversion per value is the cost; zero,
+// denormal, infinite and NaN inputs take the hardware conversion.
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)((u & 7u) << 29));
+}
 // d > 0, finite and normal, from its high word (integer compares only)
 __device__ __forceinline__ bool positive_normal(double d) {
   const int hi = __double2hiint(d);

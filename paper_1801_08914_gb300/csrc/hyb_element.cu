@@ -525,11 +525,16 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
     s_row0[tid] = r0;
     s_rlen[tid] = ef[tid] >= 0 ? (int)(args.row_ptr[(int64_t)ef[tid] * NFN + 1] - r0) : 0;
   }
+  __shared__ double s_ww[2 * NFN * NFN];             // +-w_m1 w_m2 (sign of the face pair)
+  for (int t = tid; t < 2 * NFN * NFN; t += NT) {
+    const int m1 = (t / NFN) % NFN, m2 = t % NFN;
+    s_ww[t] = (t < NFN * NFN ? 1.0 : -1.0) * wf[m1] * wf[m2];
+  }
   __syncthreads();
   auto put = [&](int ib, int jb, double v, bool weighted) {
     const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
     if (ef[a] < 0 || ef[b] < 0) return;
-    if (weighted) v *= (((a ^ b) & 1) ? -1.0 : 1.0) * wf[m1] * wf[m2];
+    if (weighted) v *= s_ww[((a ^ b) & 1) * NFN * NFN + m1 * NFN + m2];
     const int64_t pos = boff[a * 6 + b] + m1 * (int64_t)s_rlen[a] + m2;
     if (a == b && args.colour == 1) args.val[pos] += v;
     else args.val[pos] = v;

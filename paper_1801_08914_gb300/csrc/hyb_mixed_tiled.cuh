@@ -558,17 +558,22 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     // transposed.
     __shared__ int64_t s_row0[6];
     __shared__ int s_rlen[6];
+    __shared__ float s_wf[NFN];
     if (tid < 6) {
       const int64_t r0 = ef[tid] >= 0 ? args.row_ptr[(int64_t)ef[tid] * NFN] : 0;
       s_row0[tid] = r0;
       s_rlen[tid] = ef[tid] >= 0 ? (int)(args.row_ptr[(int64_t)ef[tid] * NFN + 1] - r0) : 0;
     }
+    for (int m = tid; m < NFN; m += NT) s_wf[m] = (float)wf[m];
     __syncthreads();
     const int64_t* boff = args.blockoff + e * 36;
+    // S_T = D_c S D_c in FP32 (S itself carries ~1e-7), widened exactly to FP64 with integer
+    // operations: no FP64 instruction per entry
     auto put = [&](int ib, int jb, float sv) {
       const int a = ib / NFN, m1 = ib % NFN, b = jb / NFN, m2 = jb % NFN;
       if (ef[a] < 0 || ef[b] < 0) return;
-      const double v = (((a ^ b) & 1) ? -1.0 : 1.0) * wf[m1] * wf[m2] * (double)sv;
+      const float w = sv * (s_wf[m1] * s_wf[m2]);      // w_m1 w_m2 = w_m2 w_m1: the mirror gets the same value
+      const double v = dev::widen_f32(((a ^ b) & 1) ? -w : w);
       const int64_t pos = boff[a * 6 + b] + m1 * (int64_t)s_rlen[a] + m2;
       if (a == b && args.colour == 1) args.val[pos] += v;
       else args.val[pos] = v;
