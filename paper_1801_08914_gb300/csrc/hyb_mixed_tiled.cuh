@@ -85,11 +85,12 @@ constexpr int kRefineSteps = 1;
 
 using tiles::tcol;
 
-// FP32 tile factorisations of this kernel: whole triangles, no write-out of the factor
+// FP32 tile factorisations of this kernel: whole triangles, no write-out of the factor,
+// look-ahead form (warp 0 factors the next diagonal tile during the trailing update)
 template <int TB, int MR, int MC, int NT>
 __device__ __forceinline__ bool chol_tiles32(float* Lt, int T, float* X, int MX, float* flag) {
-  return tiles::tile_chol<float, TB, MR, MC, NT>(tiles::Packed<float, TB>{Lt, T}, T, T, T, X, MX, flag,
-                                                 [](int) { return tiles::NoOut{}; });
+  return tiles::tile_chol_la<float, TB, MR, MC, NT>(tiles::Packed<float, TB>{Lt, T}, T, T, T, flag,
+                                                    [](int) { return tiles::NoOut{}; }, X, MX);
 }
 
 // ---- CTA: one FP32 solve of the mixed-form saddle system with the tiled factors.
@@ -146,16 +147,22 @@ __device__ void refine_tiled(const double* f, double* x, double* q, int steps, d
   for (int a = tid; a < NQK; a += NT) q[a] = 0.0;
   __syncthreads();
   for (int it = 0; it <= steps; ++it) {
-    for (int i = tid; i < N; i += NT) ut[i] = is_e(i) ? 0.0 : x[i];
-    __syncthreads();
-    apply_mass64<K, NT>(ut, r, alpha, g6, Vc, Vo, U, Wv, t1, t2);
-    apply_D64<K, NT>(q, rq, dofcode, DcO64, bmask);
-    for (int i = tid; i < N; i += NT) vec[i] = (float)(is_e(i) ? f[i] - x[i] : f[i] - r[i] - rq[i]);
-    __syncthreads();
-    apply_Dt64<K, NT>(ut, rq, DcO64, bmask);
-    apply_G64<K, NT>(rq, r, beta, gd, Vo, U, t1, t2);
-    for (int a = tid; a < NQP; a += NT) tq[a] = a < NQK ? (float)(r[a] - q[a]) : 0.0f;
-    __syncthreads();
+    if (it == 0) {                                  // x = 0, q = 0: the residuals are (f, 0)
+      for (int i = tid; i < N; i += NT) vec[i] = (float)f[i];
+      for (int a = tid; a < NQP; a += NT) tq[a] = 0.0f;
+      __syncthreads();
+    } else {
+      for (int i = tid; i < N; i += NT) ut[i] = is_e(i) ? 0.0 : x[i];
+      __syncthreads();
+      apply_mass64<K, NT>(ut, r, alpha, g6, Vc, Vo, U, Wv, t1, t2);
+      apply_D64<K, NT>(q, rq, dofcode, DcO64, bmask);
+      for (int i = tid; i < N; i += NT) vec[i] = (float)(is_e(i) ? f[i] - x[i] : f[i] - r[i] - rq[i]);
+      __syncthreads();
+      apply_Dt64<K, NT>(ut, rq, DcO64, bmask);
+      apply_G64<K, NT>(rq, r, beta, gd, Vo, U, t1, t2);
+      for (int a = tid; a < NQP; a += NT) tq[a] = a < NQK ? (float)(r[a] - q[a]) : 0.0f;
+      __syncthreads();
+    }
     mixed_solve_tiled<K>(Lt, Xd, Zt, Gi, vec, tq, tmp);
     for (int i = tid; i < N; i += NT) x[i] += (double)vec[i];
     for (int a = tid; a < NQK; a += NT) q[a] += (double)tq[a];

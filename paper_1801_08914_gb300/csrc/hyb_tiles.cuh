@@ -328,19 +328,23 @@ __device__ bool tile_chol(const TP& tp, int T, int Jend, int Kend, F* X, int MX,
 // barriers per tile column. For the FP64 eliminations, where every FP64 warp instruction holds
 // its sub-partition's FP64 unit for many cycles and a lone warp leaves three of the four idle.
 template <typename F, int TB, int MR, int MC, int NT, typename TP, typename OutJ>
-__device__ bool tile_chol_la(const TP& tp, int T, int Jend, int Kend, F* flag, const OutJ& out) {
+__device__ bool tile_chol_la(const TP& tp, int T, int Jend, int Kend, F* flag, const OutJ& out, F* X = nullptr,
+                             int MX = 0) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int PM = (TB / MR) * (TB / MC);
   if (tid == 0) flag[0] = F(0);
   __syncthreads();
   if (warp == 0 && Jend > 0) diag_step<F, TB>(tp(0, 0), flag, out(0));
   __syncthreads();
+  const int ncx = X ? MX : 0, xm = X ? (TB / MR) * (MX / MC) : 0;
   for (int J = 0; J < Jend; ++J) {
     if (flag[0] != F(0)) return false;
     const F* Dv = tp(J, J);
     const int nrows = (T - J - 1) * TB;
-    for (int it = tid; it < nrows; it += NT)       // A_IJ <- A_IJ Dinv^T
-      panel_row_item<F, TB>(Dv, tp(J + 1 + it / TB, J), it % TB);
+    for (int it = tid; it < nrows + ncx; it += NT) {   // A_IJ <- A_IJ Dinv^T; X_J <- Dinv X_J
+      if (it < nrows) panel_row_item<F, TB>(Dv, tp(J + 1 + it / TB, J), it % TB);
+      else scale_rows_item<F, TB>(Dv, X + J * TB * MX, MX, it - nrows);
+    }
     __syncthreads();
     const int m = T - J - 1, mk = (Kend < T ? Kend : T) - J - 1;
     const bool next = J + 1 < Jend && mk > 0;
@@ -358,14 +362,22 @@ __device__ bool tile_chol_la(const TP& tp, int T, int Jend, int Kend, F* flag, c
       diag_step<F, TB>(Dn, flag, out(J + 1));
     } else {
       const int q0 = next ? 1 : 0;
-      const LaWorkers wk(NT, (npairs - q0) * PM * TB * MR * MC / 32);
+      const int na = (npairs - q0) * PM, nx = m * xm, ntot = na + nx;
+      // FP32: every warp but 0 (the sub-partition contention is an FP64 matter)
+      const LaWorkers wk(NT, sizeof(F) == 8 ? ntot * TB * MR * MC / 32 : 1 << 30);
       const int t0 = next ? wk.id : tid, nth = next ? wk.n : NT;
-      for (int it = t0 >= 0 ? t0 : (npairs - q0) * PM; it < (npairs - q0) * PM; it += nth) {
-        const int q = q0 + it / PM, u = it % PM;
-        int kp = 0, rem = q;                       // column kp of the trailing part has m - kp tiles
-        while (rem >= m - kp) { rem -= m - kp; ++kp; }
-        const int K2 = J + 1 + kp, I = K2 + rem;
-        syrk_micro<F, TB, MR, MC>(tp(I, J), tp(K2, J), tp(I, K2), (u / (TB / MC)) * MR, (u % (TB / MC)) * MC);
+      for (int it = t0 >= 0 ? t0 : ntot; it < ntot; it += nth) {
+        if (it < na) {
+          const int q = q0 + it / PM, u = it % PM;
+          int kp = 0, rem = q;                     // column kp of the trailing part has m - kp tiles
+          while (rem >= m - kp) { rem -= m - kp; ++kp; }
+          const int K2 = J + 1 + kp, I = K2 + rem;
+          syrk_micro<F, TB, MR, MC>(tp(I, J), tp(K2, J), tp(I, K2), (u / (TB / MC)) * MR, (u % (TB / MC)) * MC);
+        } else {                                   // X_I -= L_IJ X_J, I > J
+          const int it2 = it - na, I = J + 1 + it2 / xm, u = it2 % xm;
+          gemm_x_micro<F, TB, MR, MC>(tp(I, J), X + J * TB * MX, X + I * TB * MX, MX, (u / (MX / MC)) * MR,
+                                      (u % (MX / MC)) * MC);
+        }
       }
     }
     __syncthreads();
