@@ -18,6 +18,8 @@
 // high contrast because the two Woodbury terms cancel in FP32.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "hyb_device.h"
 #include "hyb_internal.h"
 #include "hyb_tiles.cuh"

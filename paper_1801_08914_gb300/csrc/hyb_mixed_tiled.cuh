@@ -367,29 +367,33 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     float* T2 = T1 + Q * Q * P * P;
     for (int t = tid; t < 6 * NQ; t += NT) Ga32[t] = (float)(alpha * g6[t]);
     __syncthreads();
-    for (int blk = 0; blk < 6; ++blk) {
-      const int c = blk < 3 ? blk : (blk == 3 ? 1 : 2);
-      const int cp = blk < 3 ? blk : (blk == 5 ? 1 : 0);
-      const bool diag = c == cp;
-      const int da = c, db = diag ? (c + 1) % 3 : cp, dL = 3 - da - db;
-      const int nia = P, nja = diag ? P : p, nib = p, njb = diag ? p : P;
-      const int sa = da == 0 ? 1 : da == 1 ? Q : Q * Q;
-      const int sb = db == 0 ? 1 : db == 1 ? Q : Q * Q;
-      const int sL = dL == 0 ? 1 : dL == 1 ? Q : Q * Q;
+    // one (c, cp) block of the mass per call, block index a compile-time constant so that the
+    // index decompositions divide by constants
+    auto mass_block = [&](auto blk_c) {
+      constexpr int blk = decltype(blk_c)::value;
+      constexpr int c = blk < 3 ? blk : (blk == 3 ? 1 : 2);
+      constexpr int cp = blk < 3 ? blk : (blk == 5 ? 1 : 0);
+      constexpr bool diag = c == cp;
+      constexpr int da = c, db = diag ? (c + 1) % 3 : cp, dL = 3 - da - db;
+      constexpr int nia = P, nja = diag ? P : p, nib = p, njb = diag ? p : P;
+      constexpr int sa = da == 0 ? 1 : da == 1 ? Q : Q * Q;
+      constexpr int sb = db == 0 ? 1 : db == 1 ? Q : Q * Q;
+      constexpr int sL = dL == 0 ? 1 : dL == 1 ? Q : Q * Q;
       const float* Gm = Ga32 + gslot(c, cp) * NQ;
       const float* Pm = diag ? VcVc : VcVo;
-      const int n1 = Q * Q * nia * nja;
+      constexpr int n1 = Q * Q * nia * nja;
       for (int idx = tid; idx < n1; idx += NT) {
         int rr = idx;
         const int ja = rr % nja; rr /= nja;
         const int ia = rr % nia; rr /= nia;
         const int qL = rr % Q, qb = rr / Q;
         float acc = 0.f;
+#pragma unroll
         for (int qa = 0; qa < Q; ++qa) acc = fmaf(Gm[qa * sa + qb * sb + qL * sL], Pm[(ia * nja + ja) * Q + qa], acc);
         T1[idx] = acc;
       }
       __syncthreads();
-      const int n2 = Q * nia * nja * nib * njb;
+      constexpr int n2 = Q * nia * nja * nib * njb;
       for (int idx = tid; idx < n2; idx += NT) {
         int rr = idx;
         const int jb = rr % njb; rr /= njb;
@@ -397,6 +401,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
         const int ja = rr % nja; rr /= nja;
         const int ia = rr % nia, qL = rr / nia;
         float acc = 0.f;
+#pragma unroll
         for (int qb = 0; qb < Q; ++qb) {
           const float tv = T1[((qb * Q + qL) * nia + ia) * nja + ja];
           acc = fmaf(tv, diag ? VoVo[(ib * p + jb) * Q + qb] : VcVo[(jb * p + ib) * Q + qb], acc);
@@ -404,7 +409,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
         T2[idx] = acc;
       }
       __syncthreads();
-      const int s2 = nia * nja * nib * njb;
+      constexpr int s2 = nia * nja * nib * njb;
       for (int idx = tid; idx < s2 * p * p; idx += NT) {
         int rr = idx;
         const int jL = rr % p; rr /= p;
@@ -420,12 +425,19 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
         if (diag && ra < sa2) continue;
         const int tt = ((ia * nja + ja) * nib + ib) * njb + jb;
         float acc = 0.f;
+#pragma unroll
         for (int qL = 0; qL < Q; ++qL) acc = fmaf(T2[qL * s2 + tt], VoVo[(iL * p + jL) * Q + qL], acc);
         const int gi = ra >= sa2 ? ra : sa2, gj = ra >= sa2 ? sa2 : ra;
         Lt[tcol(gi / TB, gj / TB, T) * TT + (gi % TB) + (gj % TB) * TB] = acc;
       }
       __syncthreads();
-    }
+    };
+    mass_block(std::integral_constant<int, 0>{});
+    mass_block(std::integral_constant<int, 1>{});
+    mass_block(std::integral_constant<int, 2>{});
+    mass_block(std::integral_constant<int, 3>{});
+    mass_block(std::integral_constant<int, 4>{});
+    mass_block(std::integral_constant<int, 5>{});
     if (bmask) {
       for (int t = tid; t < NB * N; t += NT) {   // essential rows and columns -> identity
         const int i = NI + t / N, j = t % N;
