@@ -13,10 +13,10 @@
 //    I >= J, at J T - J (J - 1) / 2 + I - J), column-major inside a tile. After the
 //    factorisation a diagonal tile holds the inverse of its triangle, which is what the
 //    panel step, the triangular solves and the inverse Y use.
-//  * Cholesky: right-looking by tile columns; per column one warp factors and inverts the
-//    diagonal tile, the CTA scales the panel (and the matching rows of the fused right-hand
-//    sides), and the CTA applies the rank-TB update to the trailing tiles with MR x MC
-//    register micro-tiles: three barriers per tile column.
+//  * Cholesky: right-looking by tile columns; per column the CTA scales the panel (and the
+//    matching rows of the fused right-hand sides), then warp 0 factors and inverts the next
+//    diagonal tile (look-ahead) while the other warps apply the rank-TB update to the
+//    trailing tiles with MR x MC register micro-tiles: two barriers per tile column.
 //  * Triangular solves with one right-hand side (the refinement): two barriers per tile.
 // TB divides both the interior and the face block of the local ordering (interior dofs
 // first), so the face block is a trailing square of whole tiles. The assembly stores the

@@ -5,7 +5,7 @@
 // Tile layout: a lower-triangular matrix of T x T tiles is stored as "packed tiles", column
 // of tiles after column of tiles (tile (I, J), I >= J, at J T - J (J - 1) / 2 + I - J), each
 // tile column-major inside. After a factorisation a diagonal tile holds the inverse of its
-// triangle (what the panel step, the triangular solves and inverses use). tile_chol takes a
+// triangle (what the panel step, the triangular solves and inverses use). tile_chol_la takes a
 // tile-address functor instead, so that a factorisation can run over tiles split between
 // several regions (the FP64 elimination keeps the interior and the interface rows apart).
 #pragma once
@@ -263,70 +263,13 @@ __device__ __forceinline__ void gemm_x_micro(const F* A, const F* XJ, F* XI, int
 // rank-TB updates reach the tiles (I, K2) with K2 < Kend only: with Jend = Kend = T this is
 // the whole factorisation; with Jend = Kend = TI < T it eliminates the first TI tile columns
 // and leaves the trailing block untouched (its Schur update is the caller's). out(J) gives the
-// write-out functor of diagonal tile J. Per tile column: one warp factors and inverts the
-// diagonal tile, the CTA scales the panel (one thread per row) and the rows of X (one thread
-// per column), the CTA applies the update with MR x MC register micro-tiles: three barriers.
-// Returns false in every thread on a bad pivot.
-template <typename F, int TB, int MR, int MC, int NT, typename TP, typename OutJ>
-__device__ bool tile_chol(const TP& tp, int T, int Jend, int Kend, F* X, int MX, F* flag, const OutJ& out) {
-  const int tid = threadIdx.x;
-  if (tid == 0) flag[0] = F(0);
-  __syncthreads();
-  for (int J = 0; J < Jend; ++J) {
-    F* Dv = tp(J, J);
-    if (tid < 32) diag_step<F, TB>(Dv, flag, out(J));
-    __syncthreads();
-    if (flag[0] != F(0)) return false;
-    const int nrows = (T - J - 1) * TB, ncols = X ? MX : 0;
-    for (int it = tid; it < nrows + ncols; it += NT) {
-      if (it < nrows) {                            // A_IJ <- A_IJ Dinv^T
-        F* A = tp(J + 1 + it / TB, J);
-        const int r = it % TB;
-        F a[TB];
-#pragma unroll
-        for (int k = 0; k < TB; ++k) a[k] = A[r + k * TB];
-#pragma unroll
-        for (int c = 0; c < TB; ++c) {
-          F s = F(0);
-#pragma unroll
-          for (int k = 0; k <= c; ++k) s = fma(a[k], Dv[c + k * TB], s);
-          A[r + c * TB] = s;
-        }
-      } else {
-        scale_rows_item<F, TB>(Dv, X + J * TB * MX, MX, it - nrows);
-      }
-    }
-    __syncthreads();
-    // tile pairs (I, K2), J < K2 < Kend, K2 <= I < T, enumerated column by column
-    const int m = T - J - 1, mk = (Kend < T ? Kend : T) - J - 1;
-    const int npairs = mk * m - mk * (mk - 1) / 2;
-    constexpr int PM = (TB / MR) * (TB / MC);
-    const int xm = X ? (TB / MR) * (MX / MC) : 0;
-    for (int it = tid; it < npairs * PM + m * xm; it += NT) {
-      if (it < npairs * PM) {
-        const int q = it / PM, u = it % PM;
-        int kp = 0, rem = q;                       // column kp of the trailing part has m - kp tiles
-        while (rem >= m - kp) { rem -= m - kp; ++kp; }
-        const int K2 = J + 1 + kp, I = K2 + rem;
-        syrk_micro<F, TB, MR, MC>(tp(I, J), tp(K2, J), tp(I, K2), (u / (TB / MC)) * MR, (u % (TB / MC)) * MC);
-      } else {
-        const int it2 = it - npairs * PM, ti = it2 / xm, u = it2 % xm;
-        const int I = J + 1 + ti;
-        gemm_x_micro<F, TB, MR, MC>(tp(I, J), X + J * TB * MX, X + I * TB * MX, MX, (u / (MX / MC)) * MR,
-                                    (u % (MX / MC)) * MC);
-      }
-    }
-    __syncthreads();
-  }
-  return true;
-}
-
-// ---- the same factorisation (X = null) with a look-ahead of one tile column: after the panel
-// of column J is scaled, warp 0 applies that column's update to the next diagonal tile and
-// factors it while the other warps apply the rest of the update, so that the one-warp diagonal
-// step overlaps the CTA-wide update instead of running alone between two barriers. Two
-// barriers per tile column. For the FP64 eliminations, where every FP64 warp instruction holds
-// its sub-partition's FP64 unit for many cycles and a lone warp leaves three of the four idle.
+// write-out functor of diagonal tile J. Per tile column: the CTA scales the panel (one thread
+// per row) and the rows of X (one thread per column); then, with a look-ahead of one tile
+// column, warp 0 applies that column's update to the next diagonal tile and factors and
+// inverts it while the other warps apply the rest of the update (and of X) with MR x MC
+// register micro-tiles, so that the one-warp diagonal step overlaps the CTA-wide update
+// instead of running alone between two barriers: two barriers per tile column. Returns false
+// in every thread on a bad pivot.
 template <typename F, int TB, int MR, int MC, int NT, typename TP, typename OutJ>
 __device__ bool tile_chol_la(const TP& tp, int T, int Jend, int Kend, F* flag, const OutJ& out, F* X = nullptr,
                              int MX = 0) {
