@@ -301,6 +301,34 @@ def element_flops_mixed(k):
             + nq * nq * nb + nb ** 3 // 3 + nb * nb * nq + 2 * 2 * (2 * n * n + 2 * n * nq + 2 * nq * nq))
 
 
+def workload_name(cfg, p, args, mixed=False, sc=False, theta=0.0, n32=0, n64=0):
+    """The workload as what it is, with its sizes: mesh, order, coefficients, precision, phases."""
+    import math
+    from paper_1801_08914_gb300 import inputs
+    if cfg == "softhard":
+        w = (f"soft-hard (Sec. 6.1): {p.nx}x{p.ny}x{p.nz} hex mesh, RT_{p.order}, mass coefficient "
+             f"10^{args.sh_p:g} on [1/4,1/2]^3 u [1/2,3/4]^3, g = (1,1,1), natural boundary, FP64 hybridization: "
+             f"assemble + diag-PCG {args.rtol:g} + recover")
+    elif cfg == 2 and p.nx == 32:
+        w = WORKLOAD
+    else:
+        c = inputs.CONFIGS[cfg]
+        lo, hi = (math.log10(v) for v in c["contrast"])
+        w = (f"{p.nx}x{p.ny}x{p.nz} jittered hex mesh (+-{c['gamma']:g}h), RT_{p.order}, alpha lognormal(0,1), "
+             f"beta/alpha 10^U({lo:g},{hi:g}), N(0,1) loads, FP64 hybridization: assemble + diag-PCG "
+             f"{args.rtol:g} + recover")
+    if mixed:
+        how = "autotuned " if args.threshold == 0 else ""
+        w = w.replace("FP64", f"mixed FP32/FP64 ({how}threshold {theta:g}: {n32} FP32 + {n64} FP64 elements)", 1)
+    if args.refine and not args.assembly_only:
+        w += f", {args.refine} FP64 refinement steps"
+    if sc:
+        w = w.replace("hybridization", "static condensation")
+    if args.assembly_only:
+        w += " (element phase only: assemble + recover)"
+    return w
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -471,20 +499,7 @@ def run_ours(args):
                             "unit": "TFLOP/s", "frac": t_min / (elem_ms * 1e-3) if elem_ms > 0 else None,
                             "algorithmic_flops_per_element_fp32": f32, "algorithmic_flops_per_element_fp64": elem_flops,
                             "elements_fp64": n64, "elements_fp32": n32, "contrast_threshold": theta}
-    if cfg == "softhard":
-        workload = (f"soft-hard (Sec. 6.1): {p.nx}x{p.ny}x{p.nz} hex mesh, RT_{p.order}, mass coefficient "
-                    f"10^{args.sh_p:g} on [1/4,1/2]^3 u [1/2,3/4]^3, g = (1,1,1), natural boundary, FP64")
-    else:
-        workload = WORKLOAD if cfg == 2 else f"config {cfg}: {p.nx}^3 jittered hex mesh, RT_{p.order}, FP64"
-    if mixed:
-        how = "autotuned " if args.threshold == 0 else ""
-        workload = workload.replace("FP64", f"mixed FP32/FP64 ({how}threshold {theta:g}: {n32} FP32 + {n64} FP64 elements)")
-    if args.refine and not args.assembly_only:
-        workload += f", {args.refine} FP64 refinement steps"
-    if sc:
-        workload = workload.replace("hybridization", "static condensation").replace("FP64", "FP64 static condensation")
-    if args.assembly_only:
-        workload += " (element phase only: assemble + recover)"
+    workload = workload_name(cfg, p, args, mixed, sc, theta, n32, n64)
     line = {
         "metric": (METRIC.replace("hybridized", "statically condensed") if sc else
                    METRIC.replace("FP64 GPU path", "mixed FP32/FP64 GPU path") if mixed else METRIC),

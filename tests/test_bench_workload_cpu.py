@@ -1,0 +1,21 @@
+"""The bench's workload descriptions (host logic only, no GPU): every workload it can run is
+named by what it is, with its sizes, and the default one matches the reference arm's."""
+import bench
+from paper_1801_08914_gb300 import inputs
+
+
+def test_workload_names():
+    args = bench.parse_args([])
+    p = inputs.make_config(2)
+    assert bench.workload_name(2, p, args) == bench.WORKLOAD
+    for cfg, n in ((3, 6), (5, 4), (2, 8)):
+        p = inputs.make_config(cfg, n=n)
+        w = bench.workload_name(cfg, p, args)
+        assert w.startswith(f"{n}x{n}x{n} jittered hex mesh") and f"RT_{p.order}" in w and "config" not in w
+        wm = bench.workload_name(cfg, p, bench.parse_args(["--precision", "mixed", "--refine", "2"]), True, False, 1e6, 10, 2)
+        assert "mixed FP32/FP64 (autotuned threshold 1e+06: 10 FP32 + 2 FP64 elements)" in wm and "2 FP64 refinement" in wm
+        ws = bench.workload_name(cfg, p, bench.parse_args(["--mode", "sc", "--assembly-only"]), False, True)
+        assert "static condensation" in ws and ws.endswith("(element phase only: assemble + recover)")
+    p = inputs.soft_hard_problem(1, -8.0, nz=4)
+    w = bench.workload_name("softhard", p, bench.parse_args(["--config", "softhard", "--sh-p", "-8"]))
+    assert w.startswith("soft-hard (Sec. 6.1): 8x8x4 hex mesh, RT_1, mass coefficient 10^-8")
