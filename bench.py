@@ -301,6 +301,24 @@ def element_flops_mixed(k):
             + nq * nq * nb + nb ** 3 // 3 + nb * nb * nq + 2 * 2 * (2 * n * n + 2 * n * nq + 2 * nq * nq))
 
 
+def recover_bytes_per_element(k):
+    """Algorithmic DRAM bytes of one FP64 hybridization recovery: the stored factor (packed lower
+    triangle, Y in place of L_bb) and z read, lambda_T gathered, u written."""
+    n, nb = 3 * (k + 1) ** 2 * (k + 2), 6 * (k + 1) ** 2
+    return 8 * (n * (n + 1) // 2 + 2 * n + nb)
+
+
+def recover_roofline_of(k, E, rec_ms, hbm_peak):
+    """HBM roofline of the FP64 recovery phase (None when it did not run)."""
+    if not rec_ms or rec_ms <= 0:
+        return None
+    bpe = recover_bytes_per_element(k)
+    gbs = E * bpe / (rec_ms * 1e-3) / 1e9
+    return {"kernel": f"recover_kernel<{k}> (FP64)", "bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+            "unit": "GB/s", "frac": gbs / hbm_peak, "algorithmic_bytes_per_element": bpe,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+
 def workload_name(cfg, p, args, mixed=False, sc=False, theta=0.0, n32=0, n64=0):
     """The workload as what it is, with its sizes: mesh, order, coefficients, precision, phases."""
     import math
@@ -514,6 +532,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "roofline": roof if not args.assembly_only else element_roofline,
         "element_roofline": element_roofline,
+        "recover_roofline": (recover_roofline_of(p.order, E, prof["recover"][0] / args.steps, hbm_peak)
+                             if not mixed and not sc else None),
         "phases": phases,
         "assembly_elements_per_s": E / (elem_ms * 1e-3) if elem_ms > 0 else None,
         "pcg_ms_per_iteration": ((prof["spmv"][0] + prof["pcg_vector"][0] + prof["pcg_fused"][0]) / it_total

@@ -19,3 +19,13 @@ def test_workload_names():
     p = inputs.soft_hard_problem(1, -8.0, nz=4)
     w = bench.workload_name("softhard", p, bench.parse_args(["--config", "softhard", "--sh-p", "-8"]))
     assert w.startswith("soft-hard (Sec. 6.1): 8x8x4 hex mesh, RT_1, mass coefficient 10^-8")
+
+
+def test_recover_roofline_arithmetic():
+    """Bytes of the FP64 recovery per element: packed factor n(n+1)/2, z and u (n each), lambda_T
+    (n_b), 8 bytes each; RT_3: n = 240, n_b = 96."""
+    assert bench.recover_bytes_per_element(3) == 8 * (240 * 241 // 2 + 2 * 240 + 96)
+    assert bench.recover_bytes_per_element(0) == 8 * (6 * 7 // 2 + 12 + 6)
+    r = bench.recover_roofline_of(3, 1000, 2.0, 6771.0)
+    assert r["bound"] == "hbm" and abs(r["achieved"] - 1000 * bench.recover_bytes_per_element(3) / 2e-3 / 1e9) < 1e-9
+    assert bench.recover_roofline_of(3, 1000, 0.0, 6771.0) is None
