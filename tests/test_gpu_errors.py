@@ -74,12 +74,14 @@ def test_inverted_element_is_a_mesh_error():
     ctx.close()
 
 
+@pytest.mark.parametrize("order", [2, 3])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_non_spd_element_is_reported(precision):
+def test_non_spd_element_is_reported(precision, order):
     """alpha < 0 on one element makes its local matrix (and, in the mixed form, its alpha
-    mass) indefinite: the factorisation reports HYB_ERR_NOT_SPD with that element."""
+    mass) indefinite: the factorisation (RT_3: the tiled look-ahead one) reports
+    HYB_ERR_NOT_SPD with that element."""
     from paper_1801_08914_gb300 import hyb
-    p = inputs.random_problem(3, 2, 0.2, 903, 1e-2, 1e2)
+    p = inputs.random_problem(3, order, 0.2, 903, 1e-2, 1e2)
     bad = 13
     p.alpha = np.array(p.alpha, copy=True)
     p.alpha[bad] = -1.0
