@@ -95,3 +95,19 @@ def test_static_condensation_needs_essential_faces():
     p = inputs.soft_hard_problem(0, 0.0, nz=4)
     with pytest.raises(NotImplementedError):
         Discretization.from_problem(p).static_condense()
+
+
+def test_default_meshes_are_the_papers():
+    """The generator's default mesh per order is the paper's initial mesh (Sec. 6.1), whose
+    global RT_k dof count is the size its tables print (tests/golden/paper_sizes.txt)."""
+    import os
+    golden = os.path.join(os.path.dirname(__file__), "golden", "paper_sizes.txt")
+    rows = [l.split() for l in open(golden) if l.strip() and l[0] != "#"]
+    sh = {int(r[3]): tuple(map(int, r[:3])) + (int(r[4]),) for r in rows if "6.1" in " ".join(r[5:])}
+    assert set(sh) == {0, 1, 3}
+    for k, (nx, ny, nz, size) in sh.items():
+        p = inputs.soft_hard_problem(k, 0.0)
+        assert (p.nx, p.ny, p.nz) == (nx, ny, nz)
+        b = RTBasis(k)
+        faces = (nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1)
+        assert faces * b.n_face_nodes + p.n_elem * b.n_interior == size
