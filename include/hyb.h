@@ -268,8 +268,10 @@ int hyb_get_profile(const hyb_ctx* ctx, int kernel_class, double* total_ms, int6
  *  in it; calls that can overlap on the GPU (other streams, other host threads)
  *  race on it and must be serialised by the caller.
  *  The first call on a device looks up the array's device address
- *  (cudaGetSymbolAddress) and caches it per device; make that first call before
- *  any stream capture on that device.
+ *  (cudaGetSymbolAddress) and caches it per device. Every call copies the solver's
+ *  flags to host memory and synchronises cuda_stream between chunks of iterations, so
+ *  it must not be called while cuda_stream, or any stream capturing in global mode,
+ *  is being captured into a CUDA graph.
  *  row_ptr (n+1 int64), col (nnz int32), val (nnz doubles), b (n doubles): device,
  *  the SPD system. x: device, n doubles, receives the solution (x0 = 0).
  *  n <= 524288 rows, else HYB_ERR_INVALID_ARG (nothing is enqueued).

@@ -83,6 +83,12 @@ class ElementIntegrator:
         detJ = np.linalg.det(J)
         if not np.all(detJ > 0.0):
             raise MeshError(f"det J = {detJ.min()} <= 0")
+        # the map must be orientation-preserving on the whole cell, not only at the points of
+        # the rule: det J of a trilinear map can change sign between the quadrature points and
+        # the corners (a corner folded inwards), so the 8 corners are checked as well
+        dc = self.corner_detJ(X8)
+        if not np.all(dc > 0.0):
+            raise MeshError(f"det J = {dc.min()} <= 0 at a corner")
         u = np.einsum("qnd,qid->qni", self.val, J) / detJ[:, None, None]   # Piola: J u_hat / det J
         dv = self.div / detJ[:, None]                                        # div_hat u_hat / det J
         dx = self.wts * detJ

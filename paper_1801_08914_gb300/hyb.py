@@ -238,7 +238,20 @@ def hyb_export_reduced(ctx):
 
 def hyb_pcg_solve_noalloc(row_ptr, col, val, b, x, rows_per_face, rtol, maxit, stream=None, check=True):
     """Allocation-free PCG on a caller-supplied CSR system (see include/hyb.h).
-    Returns (iterations, relative residual, status)."""
+    Returns (iterations, relative residual, status).
+
+    The library trusts the sizes it is given, so they are checked here first: a short x,
+    row_ptr or col would make the kernels read or write past the caller's buffers. The
+    last check reads row_ptr[n] back to the host (one 8-byte copy)."""
+    n = b.numel()
+    if x.numel() != n:
+        raise ValueError(f"x has {x.numel()} entries, b has {n}")
+    if row_ptr.numel() != n + 1:
+        raise ValueError(f"row_ptr has {row_ptr.numel()} entries, expected n + 1 = {n + 1}")
+    if col.numel() != val.numel():
+        raise ValueError(f"col ({col.numel()}) and val ({val.numel()}) differ in length")
+    if n > 0 and int(row_ptr[n].item()) > col.numel():
+        raise ValueError(f"row_ptr[n] = {int(row_ptr[n].item())} exceeds the {col.numel()} stored entries")
     it = ctypes.c_int()
     rr = ctypes.c_double()
     st = lib().hyb_pcg_solve_noalloc(_ptr(row_ptr, "row_ptr", torch.int64), _ptr(col, "col", torch.int32),

@@ -41,3 +41,30 @@ def test_binding_refuses_cpu_tensors():
     from paper_1801_08914_gb300 import hyb
     with pytest.raises(TypeError):
         hyb._ptr(torch.zeros(3, dtype=torch.float64), "x")
+
+
+def test_noalloc_binding_checks_sizes_before_the_call():
+    """The allocation-free solve trusts the sizes it gets; the binding refuses inconsistent
+    ones before any pointer reaches the library (checked here on host tensors: the size
+    checks come first, the device check after them)."""
+    import pytest
+    import torch
+    from paper_1801_08914_gb300 import hyb
+    f64, i64, i32 = torch.float64, torch.int64, torch.int32
+    n = 4
+    rp = torch.arange(n + 1, dtype=i64)
+    col = torch.arange(n, dtype=i32)
+    val = torch.ones(n, dtype=f64)
+    b = torch.ones(n, dtype=f64)
+    with pytest.raises(ValueError, match="x has"):
+        hyb.hyb_pcg_solve_noalloc(rp, col, val, b, torch.zeros(n - 1, dtype=f64), 1, 1e-12, 10)
+    with pytest.raises(ValueError, match="row_ptr has"):
+        hyb.hyb_pcg_solve_noalloc(rp[:-1], col, val, b, torch.zeros(n, dtype=f64), 1, 1e-12, 10)
+    with pytest.raises(ValueError, match="differ in length"):
+        hyb.hyb_pcg_solve_noalloc(rp, col[:-1], val, b, torch.zeros(n, dtype=f64), 1, 1e-12, 10)
+    bad = rp.clone()
+    bad[n] = n + 1
+    with pytest.raises(ValueError, match="exceeds"):
+        hyb.hyb_pcg_solve_noalloc(bad, col, val, b, torch.zeros(n, dtype=f64), 1, 1e-12, 10)
+    with pytest.raises(TypeError):                       # consistent sizes, but host memory
+        hyb.hyb_pcg_solve_noalloc(rp, col, val, b, torch.zeros(n, dtype=f64), 1, 1e-12, 10)

@@ -74,6 +74,23 @@ def test_inverted_element_rejected():
         ElementIntegrator(0).matrices(X8, 1.0, 1.0)
 
 
+@pytest.mark.parametrize("k", [0, 1])
+def test_corner_inverted_element_rejected(k):
+    """Corner (1,1,1) pulled to 0.6 (1,1,1): det J is still positive at every Gauss point
+    (the rule never sees the fold) but negative at that corner, where the three edge vectors
+    (-0.4, -0.4, 0.6) and permutations span a negatively oriented frame: det = -0.2. The cell
+    is not a valid (orientation-preserving) image of the reference cube, so it is refused,
+    as the GPU set-up refuses it."""
+    integ = ElementIntegrator(k)
+    X8 = cube(1.0)
+    X8[7] = 0.6
+    J = np.einsum("ci,qcd->qid", X8, integ.dN)
+    assert np.linalg.det(J).min() > 0.0                 # invisible to the quadrature rule
+    assert integ.corner_detJ(X8)[7] == pytest.approx(-0.2)
+    with pytest.raises(MeshError):
+        integ.matrices(X8, 1.0, 1.0)
+
+
 @pytest.mark.parametrize("k", [0, 1, 2])
 def test_energy_identity_on_parallelepiped(k):
     """For linear fields u = a + B x in RT_k on a parallelepiped x = x0 + S xi (any B for k >= 1;

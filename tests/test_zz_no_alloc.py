@@ -4,7 +4,8 @@ Callers that cannot allocate device memory (all of it reserved by another alloca
 unable to afford a call that blocks the device) solve through this entry point, whose
 scratch is a fixed device array inside the library. It is checked through the C ABI on
 two calls in a row (the array keeps the previous call's contents) against the solution of
-the context's own solver, within the 1e-12 relative tolerance of the parity tests. This
+the context's own solver, within the 1e-12 relative tolerance of the parity tests, and the
+device's free memory is checked to stay put across the calls after the first. This
 file is collected last so that a stop-at-first-failure run has already run the rest.
 """
 import numpy as np
@@ -31,11 +32,20 @@ def test_noalloc_pcg_matches_context_solver(case):
     ref = torch.zeros(n, dtype=torch.float64, device="cuda")
     it_ref, rr_ref, _ = hyb.hyb_solve_reduced(ctx, 1e-12, 10000, ref)
     nfn = (p.order + 1) ** 2
-    for call in range(2):
-        x = torch.full((n,), float("nan") if call else 0.0, dtype=torch.float64, device="cuda")
+    # every output buffer exists before the first call, so nothing below needs the caching
+    # allocator; after the first call (which may load the module and look up the scratch
+    # array's address) the device's free memory must not move
+    xs = [torch.full((n,), float("nan") if call else 0.0, dtype=torch.float64, device="cuda") for call in range(3)]
+    torch.cuda.synchronize()
+    free_after_first = None
+    for call, x in enumerate(xs):
         it, rr, st = hyb.hyb_pcg_solve_noalloc(red["row_ptr"], red["col"], red["val"], red["rhs"], x,
                                                nfn, 1e-12, 10000)
         torch.cuda.synchronize()
+        if call == 0:
+            free_after_first = torch.cuda.mem_get_info()[0]
+        else:
+            assert torch.cuda.mem_get_info()[0] == free_after_first, "the entry point allocated device memory"
         assert st == hyb.HYB_OK and it == it_ref
         assert rr <= 1e-12
         assert rel(x.cpu().numpy(), ref.cpu().numpy()) <= 1e-12
