@@ -155,13 +155,45 @@ class Discretization:
 
     def hybridize(self, elements=None):
         """Assemble H and g (eq. 2.4); keeps per-element factors for the back substitution."""
+        return self._assemble_reduced(self.element_reduced, elements)
+
+    def hybridize_mixed(self, elements=None):
+        """H~ and g~ of the hybridized mixed form (Sec. 3.2, eq. 3.3-3.6), element by element
+        through element_reduced_mixed; H~ = H in exact arithmetic (end of Sec. 3.2).
+
+        Why a second route: the primal route factors A_T = alpha M + beta K, whose condition
+        number grows like (beta / alpha) h^-2, and forming its entries in FP64 already rounds
+        away the divergence-free structure that A_T^{-1} C_T^T depends on, so at contrast
+        1e6 its S_T carries errors of order kappa(A_T) eps_64 (1e-8..1e-7, measured against
+        an extended-precision evaluation in the tests). The mixed form never forms
+        alpha M + beta K: its saddle matrix [M B^T; B -W] is well conditioned at any
+        contrast, and its FP64 result is the accurate reference at high contrast."""
+        return self._assemble_reduced(self.element_reduced_mixed, elements)
+
+    def recover_mixed(self, lam):
+        """x_hat_T of the back substitution (Thm 2.1) through the mixed form: the element saddle
+        system [M B^T; B -W][x; q] = [f_T - C_T^T lam_T; 0] (eq. 3.3 with q = W^{-1} B x,
+        so that M x + B^T W^{-1} B x = A_T x), essential dofs re-inserted; returns (E, n)."""
+        u = np.zeros((self.mesh.n_elem, self.n))
+        for e in range(self.mesh.n_elem):
+            M, B, W, d = self.mixed_form_blocks(e)
+            nf = M.shape[0]
+            K = np.block([[M, B.T], [B, -W]])
+            rhs = np.zeros(nf + W.shape[0])
+            rhs[:nf] = d["f"] - d["C"].T @ lam[d["lam"]]
+            u[e, d["free"]] = np.linalg.solve(K, rhs)[:nf]
+            u[e, d["edofs"]] = d["ue"]
+        return u
+
+    def _assemble_reduced(self, reduce_element, elements=None):
+        """Sum the element contributions S_T, g_T of reduce_element into H and g (eq. 2.4)."""
         E = self.mesh.n_elem
         elems = range(E) if elements is None else elements
         I, J, V = [], [], []
         g = np.zeros(self.n_lambda)
         self.factors = {}
         for e in elems:
-            d = self.element_reduced(e)
+            d = reduce_element(e)
             lam = d["lam"]
             if lam.size:
                 I.append(np.repeat(lam, lam.size))
@@ -201,37 +233,43 @@ class Discretization:
         rhs = np.zeros(self.n_lambda)
         self.sc = {}
         for e in range(E):
-            d = self.element(e)
-            free = d["free"]
-            ii = np.nonzero(free < b.n_interior)[0]      # positions (within free) of interior dofs
-            bb = np.nonzero(free >= b.n_interior)[0]     # positions of free face dofs
-            A = d["A"]
-            Aii, Aib, Abi, Abb = A[np.ix_(ii, ii)], A[np.ix_(ii, bb)], A[np.ix_(bb, ii)], A[np.ix_(bb, bb)]
-            fi, fb = d["f"][ii], d["f"][bb]
-            if ii.size:
-                Shat = Abb - Abi @ np.linalg.solve(Aii, Aib)
-                r = fb - Abi @ np.linalg.solve(Aii, fi)
-            else:
-                Shat, r = Abb.copy(), fb.copy()
-            # global index of each free face dof
-            gidx = []
-            for p in bb:
-                ldof = free[p]
-                a = b.face_of_dof[ldof]
-                m = b.face_node_of_dof[ldof]
-                gidx.append(d["faces"][a][1] * self.nfn + m)
-            gidx = np.array(gidx, dtype=np.int64)
+            c = self.element_condensed(e)
+            gidx, Shat, r = c["gidx"], c["Shat"], c["r"]
             if gidx.size:
                 I.append(np.repeat(gidx, gidx.size))
                 J.append(np.tile(gidx, gidx.size))
                 V.append(Shat.ravel())
                 np.add.at(rhs, gidx, r)
-            self.sc[e] = dict(d=d, ii=ii, bb=bb, gidx=gidx, Shat=Shat, r=r)
+            self.sc[e] = c
         S = sp.coo_matrix((np.concatenate(V), (np.concatenate(I), np.concatenate(J))),
                           shape=(self.n_lambda, self.n_lambda)).tocsr()
         S.sum_duplicates()
         S.sort_indices()
         return S, rhs
+
+    def element_condensed(self, e):
+        """One element's static condensation (Sec. 3.1, eq. 3.1): S_hat = A_bb - A_bi A_ii^{-1} A_ib,
+        r = f_b - A_bi A_ii^{-1} f_i, and the global index of each free face dof."""
+        b = self.basis
+        d = self.element(e)
+        free = d["free"]
+        ii = np.nonzero(free < b.n_interior)[0]      # positions (within free) of interior dofs
+        bb = np.nonzero(free >= b.n_interior)[0]     # positions of free face dofs
+        A = d["A"]
+        Aii, Aib, Abi, Abb = A[np.ix_(ii, ii)], A[np.ix_(ii, bb)], A[np.ix_(bb, ii)], A[np.ix_(bb, bb)]
+        fi, fb = d["f"][ii], d["f"][bb]
+        if ii.size:
+            Shat = Abb - Abi @ np.linalg.solve(Aii, Aib)
+            r = fb - Abi @ np.linalg.solve(Aii, fi)
+        else:
+            Shat, r = Abb.copy(), fb.copy()
+        gidx = []
+        for p in bb:
+            ldof = free[p]
+            a = b.face_of_dof[ldof]
+            m = b.face_node_of_dof[ldof]
+            gidx.append(d["faces"][a][1] * self.nfn + m)
+        return dict(d=d, ii=ii, bb=bb, gidx=np.array(gidx, dtype=np.int64), Shat=Shat, r=r)
 
     def sc_recover(self, ub):
         """u_i = A_ii^{-1}(f_i - A_ib u_b) per element; face dofs copied from ub, e-dofs from ue."""

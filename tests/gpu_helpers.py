@@ -48,8 +48,37 @@ def csr(red):
 
 
 def rel(a, b):
+    """Norm-wise relative difference ||a - b||_2 / ||b||_2 (printed beside the entry-wise ones)."""
     nb = np.linalg.norm(np.ravel(b))
     return np.linalg.norm(np.ravel(a) - np.ravel(b)) / (nb if nb > 0 else 1.0)
+
+
+def rel_inf(a, b):
+    """Entry-wise relative difference against the largest entry: max_i |a_i - b_i| / max_i |b_i|.
+    A single wrong entry cannot hide under the norm of many right ones."""
+    a, b = np.ravel(a), np.ravel(b)
+    s = np.abs(b).max() if b.size else 0.0
+    return (np.abs(a - b).max() / (s if s > 0 else 1.0)) if a.size else 0.0
+
+
+def rel_groups(a, b, g):
+    """Entry-wise relative difference per group of g consecutive entries (an element's dofs):
+    max over groups of max |a - b| / max |b| within the group."""
+    a, b = np.reshape(a, (-1, g)), np.reshape(b, (-1, g))
+    d, s = np.abs(a - b).max(axis=1), np.abs(b).max(axis=1)
+    return float((d / np.where(s > 0, s, 1.0)).max()) if d.size else 0.0
+
+
+def rel_rows(val, ref, row_ptr):
+    """Entry-wise relative difference per CSR row (same pattern on both sides): max over rows
+    of max_j |val_rj - ref_rj| / max_j |ref_rj|."""
+    val, ref = np.ravel(val), np.ravel(ref)
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    nonempty = row_ptr[1:] > row_ptr[:-1]
+    starts = row_ptr[:-1][nonempty]
+    d = np.maximum.reduceat(np.abs(val - ref), starts)
+    s = np.maximum.reduceat(np.abs(ref), starts)
+    return float((d / np.where(s > 0, s, 1.0)).max()) if d.size else 0.0
 
 
 def element_kappa(D, elements=None):
