@@ -1,18 +1,30 @@
 #!/usr/bin/env python
-"""Benchmark: hybridized elements/s of the full hot path on one GB300 (per rank).
+"""Benchmark: hybridized elements/s on one GB300, FP64 against mixed precision (per rank).
 
-A step is one pass of the whole path over the 32x32x32 jittered hex mesh with
-RT_1 (the bench workload): hyb_assemble_reduced (element elimination + atomic-free
-scatter), hyb_solve_reduced (diagonal PCG to ||r|| <= 1e-12 ||r0||) and
-hyb_recover, all through the C ABI with inputs resident in HBM. L2 is flushed
-(a 512 MiB write) before every timed step, outside its events.
+Default workload (the precision workload): a 96x96x96 hex mesh jittered by +-0.2h, RT_2
+(108 dofs and 54 multipliers per element), alpha lognormal(0,1), beta/alpha log-uniform in
+[1e-2, 1e6], N(0,1) load coefficients, zero normal essential data. A timed step is the
+element phase a1-a6, hyb_assemble_reduced: per element the local matrix by quadrature
+through the Piola map, the elimination and S_T, g_T, scattered without atomics into the CSR
+reduced system. value = elements / that time, for the mixed-precision context (contrast
+threshold autotuned by the library: elements up to beta/alpha = 1e6 eliminated in FP32 through
+the hybridized mixed form, the reduced system, PCG and recovery FP64); the FP64 context is timed
+the same way in the same run. Once per arm the rest of the path follows (diagonal PCG to
+1e-12, back substitution, and for the mixed arm two FP64 refinement steps), timed per phase.
+Relative errors of S, lambda and u of both arms are measured on an 8^3 mesh of the same recipe
+against the CPU FP64 oracle's two routes (primal, and the hybridized mixed form that stays
+accurate at this contrast). Inputs are resident in HBM; L2 is flushed (a 512 MiB write)
+before every timed step, outside its events.
 
-Output: one JSON line (rank 0). Under torchrun every rank runs an independent
-replica (the path has no exchange step on one GPU per problem) and the slowest
-rank's time is reported; value = all ranks' elements / that time.
+--config 2 (32^3 RT_1, FP64 full step), 4 (256-problem batch), 5 (64^3 RT_3, the precision
+workload with RT_3) and softhard select the other workloads.
 
---impl reference times the CPU FP64 oracle, as it stands, on a bounded sample of
-the same workload (the same recipe on a 20^3 mesh) on the host cores.
+Output: one JSON line (rank 0). Under torchrun every rank runs an independent replica (the
+path has no exchange step on one GPU per problem) and the slowest rank's time is reported;
+value = all ranks' elements / that time.
+
+--impl reference times the CPU FP64 oracle, as it stands, on the host cores: the element phase
+of the same recipe on a bounded sample mesh, one worker process per core.
 """
 from __future__ import annotations
 
@@ -31,7 +43,12 @@ if ROOT not in sys.path:
 
 WORKLOAD = "32x32x32 jittered hex mesh (+-0.2h), RT_1, FP64 hybridization: assemble + diag-PCG 1e-12 + recover"
 METRIC = "hybridized elements/s (FP64 GPU path)"
-SAMPLE_N = 20          # oracle sample mesh (same recipe, 8000 elements)
+PRECISION_METRIC = "hybridized elements/s, FP64 vs mixed (same GB300), rel err vs FP64 oracle"
+SAMPLE_N = 20          # oracle sample mesh of the 32^3 RT_1 workload (same recipe, 8000 elements)
+# oracle element-phase samples of the precision workloads: (mesh size, element stride) for the
+# one-core leg and the mesh size of the all-core leg (every core takes a strided share)
+PHASE_SAMPLE = {3: dict(one=(12, 2), all_n=24), 5: dict(one=(6, 2), all_n=12)}
+ERR_N = 8              # mesh size of the error measurement (same recipe as the workload)
 
 
 def parse_args(argv=None):
@@ -44,9 +61,14 @@ def parse_args(argv=None):
     ap.add_argument("--maxit", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="mesh size override (parity / profiling runs)")
-    ap.add_argument("--config", default="2",
-                    help="workload: 2 (32^3 RT_1, default), 3 (96^3 RT_2), 4 (256-problem batch), 5 (64^3 RT_3), "
-                         "softhard (Sec. 6.1's two-cube inclusion, natural boundary, --sh-order / --sh-p)")
+    ap.add_argument("--config", default="3",
+                    help="workload: 3 (96^3 RT_2, default) and 5 (64^3 RT_3): the precision workloads, mixed and "
+                         "FP64 arms in one run; 2 (32^3 RT_1, FP64 full step), 4 (256-problem batch), softhard "
+                         "(Sec. 6.1's two-cube inclusion, natural boundary, --sh-order / --sh-p)")
+    ap.add_argument("--single-arm", action="store_true",
+                    help="configs 3/5: the one-arm full-step measurement (--precision) instead of both arms")
+    ap.add_argument("--no-full", action="store_true", help="configs 3/5: skip the one-pass full-path timing")
+    ap.add_argument("--no-errors", action="store_true", help="configs 3/5: skip the error measurement")
     ap.add_argument("--sh-order", type=int, default=1, help="softhard: RT order (mesh 2n x 2n x n of the paper's table)")
     ap.add_argument("--sh-p", type=float, default=-8.0, help="softhard: mass coefficient 10^p in the inclusion")
     ap.add_argument("--batch-count", type=int, default=256, help="problems in the batched workload")
@@ -56,14 +78,17 @@ def parse_args(argv=None):
                     help="mixed: contrast above which elements stay FP64 (0: autotuned by the library)")
     ap.add_argument("--mode", choices=["hyb", "sc"], default="hyb",
                     help="hybridization, or static condensation of the interior dofs (FP64 only)")
-    ap.add_argument("--refine", type=int, default=0,
+    ap.add_argument("--refine", type=int, default=None,
                     help="FP64 refinement steps after the solve (hyb_refine; for --precision mixed)")
     ap.add_argument("--refine-rtol", type=float, default=1e-6, help="inner PCG tolerance of a refinement step")
     ap.add_argument("--pcg", choices=["fused", "split"], default="fused",
                     help="PCG launch form: one cooperative launch per 64 iterations, or 3 launches per iteration")
     ap.add_argument("--assembly-only", action="store_true",
                     help="time only the element phase (assemble + recover with lambda = 0); per-config rates")
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    if args.refine is None:          # the precision workloads refine the mixed arm twice by default
+        args.refine = 2 if str(args.config) in ("3", "5") and not args.single_arm else 0
+    return args
 
 
 # ---------------------------------------------------------------- distributed plumbing
@@ -140,6 +165,13 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.halt()
+        return self.summarize(self.lines)
+
+    def halt(self):
+        """Stop sampling and keep the lines (summarize several samplers' lines together)."""
+        if self.proc is None:
+            return []
         time.sleep(0.25)
         self.proc.terminate()
         try:
@@ -147,9 +179,13 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+        return self.lines
+
+    @staticmethod
+    def summarize(lines):
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -207,9 +243,110 @@ def cpu_baseline(steps=1):
                       f"{t:.1f} s on 1 host core"}
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "processor name"):
+                    return ln.split(":", 1)[1].strip()
+        with open("/proc/cpuinfo") as f:          # Arm: implementer / part numbers only
+            parts = {}
+            for ln in f:
+                if ":" in ln:
+                    k, v = (x.strip() for x in ln.split(":", 1))
+                    if k in ("CPU implementer", "CPU part") and k not in parts:
+                        parts[k] = v
+            if parts:
+                return "Arm " + ", ".join(f"{k} {v}" for k, v in parts.items())
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_phase_worker(cfg, n, first, stride, steps):
+    """Element phase of the CPU FP64 oracle (A_T by quadrature, Cholesky, S_T = C A^-1 C^T, g_T,
+    assembly of H and g: a1-a6) over elements first, first + stride, ... of the n^3 mesh of
+    workload cfg, `steps` times; prints [(elements, seconds)] per step."""
+    from oracle.hybrid import Discretization
+    from paper_1801_08914_gb300 import inputs
+    p = inputs.make_config(cfg, n=n)
+    D = Discretization.from_problem(p)
+    els = list(range(first, p.n_elem, stride))
+    out = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        D.hybridize(elements=els)
+        out.append((len(els), time.perf_counter() - t0))
+    print(json.dumps(out))
+
+
+def oracle_phase_rate(cfg, n, workers, stride=1, steps=1):
+    """Runs `workers` single-threaded oracle processes at once (BLAS threads pinned to 1);
+    worker w takes elements w, w + workers * stride, ... Returns per step (elements, seconds):
+    all workers' elements over the slowest worker's time."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs = [subprocess.Popen([sys.executable, "-c", f"import bench; bench._oracle_phase_worker("
+                               f"{cfg}, {n}, {w * stride}, {workers * stride}, {steps})"],
+                              cwd=ROOT, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+             for w in range(workers)]
+    res = []
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    return [(sum(r[k][0] for r in res), max(r[k][1] for r in res)) for k in range(steps)]
+
+
+def cpu_baseline_phase(cfg):
+    """The oracle's element phase timed on the host cores: all cores (one worker process per
+    core, strided shares of the all-core sample mesh) and one core (the one-core sample)."""
+    smp = PHASE_SAMPLE[cfg]
+    n1, m1 = smp["one"]
+    E1, t1 = oracle_phase_rate(cfg, n1, 1, stride=m1)[0]
+    C = host_cores()
+    Ea, ta = oracle_phase_rate(cfg, smp["all_n"], C)[0]
+    return {"value": Ea / ta, "unit": "elements/s", "cores": C, "kind": "oracle",
+            "sample": f"element phase a1-a6 (hybridize: A_T, Cholesky, S_T, g_T, assembly) of the same recipe: "
+                      f"all {C} cores on the {smp['all_n']}^3 mesh ({Ea} elements, {ta:.1f} s, one process per core), "
+                      f"one core on every {m1}-th element of the {n1}^3 mesh ({E1} elements, {t1:.1f} s)",
+            "one_core": {"value": E1 / t1, "unit": "elements/s", "cores": 1},
+            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
+        return
+    if str(args.config) in ("3", "5"):
+        cfg = int(args.config)
+        W, K = args.warmup, args.steps
+        n = PHASE_SAMPLE[cfg]["one"][0]
+        C = host_cores()
+        res = oracle_phase_rate(cfg, n, C, steps=W + K)[W:]
+        E = sum(r[0] for r in res)
+        t = sum(r[1] for r in res)
+        v = E / t
+        line = {"impl": "reference", "metric": PRECISION_METRIC, "value": v, "unit": "elements/s",
+                "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": 1e3 * t / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": precision_workload_name(cfg),
+                           "sample": f"{n}^3 mesh of the same recipe per step, element phase a1-a6, "
+                                     f"one oracle process per core", "parallelism": "none"},
+                "cpu_baseline": {"value": v, "unit": "elements/s", "cores": C, "kind": "oracle",
+                                 "sample": f"element phase of the {n}^3 mesh of the same recipe per step",
+                                 "nproc": os.cpu_count(), "cpu_model": cpu_model()},
+                "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     W, K = args.warmup, args.steps
     res = run_oracle_subprocess(SAMPLE_N, W + K)[W:]
@@ -242,6 +379,9 @@ FUSED_TRAFFIC = {(2, 32, 1): 163.0e6}
 # per launch, 23.6 MB read + 578.2 MB written); per-element work is uniform, so a launch's
 # traffic is this times its elements
 ELEMENT_TRAFFIC_PER_ELEMENT = {3: 293.8e3}
+# DRAM bytes per element of the FP32 mixed-form element kernel (element_tiled_kernel<k>), from one
+# ncu capture of the unchanged kernel on a smaller mesh of the same order; empty until captured
+MIXED_ELEMENT_TRAFFIC_PER_ELEMENT = {}
 
 
 def pcg_iteration_flops(n, nnz):
@@ -557,6 +697,341 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def precision_workload_name(cfg, n=None):
+    import math
+    from paper_1801_08914_gb300 import inputs
+    c = inputs.CONFIGS[cfg]
+    n = c["n"] if n is None else n
+    lo, hi = (math.log10(v) for v in c["contrast"])
+    return (f"{n}x{n}x{n} jittered hex mesh (+-{c['gamma']:g}h), RT_{c['order']}, alpha lognormal(0,1), "
+            f"beta/alpha 10^U({lo:g},{hi:g}), N(0,1) loads, zero essential BC; timed step: element phase a1-a6 "
+            f"(hyb_assemble_reduced), mixed FP32/FP64 (autotuned contrast threshold) against FP64")
+
+
+def _event_pair():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_element_phase(hyb, ctx, load, warmup, steps, flush, stream):
+    """W untimed and K timed hyb_assemble_reduced calls (L2 flushed before each, outside the
+    events); returns the per-step device times (ms) and the launch profile of the timed steps."""
+    import torch
+    for _ in range(warmup):
+        hyb.hyb_assemble_reduced(ctx, load)
+    torch.cuda.synchronize()
+    hyb.hyb_set_profiling(ctx, True)
+    ev = [_event_pair() for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        hyb.hyb_assemble_reduced(ctx, load)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    prof = hyb.hyb_get_profile(ctx)
+    hyb.hyb_set_profiling(ctx, False)
+    return [a.elapsed_time(b) for a, b in ev], prof
+
+
+def time_full_path(hyb, ctx, load, lam, u, args, refine, flush, stream):
+    """One pass of the whole path: assemble, diagonal PCG (rtol), recover, and `refine` FP64
+    refinement steps; device time per phase (ms) from events on the library's stream."""
+    import torch
+    flush.fill_(7)
+    ev = [_event_pair()[0] for _ in range(5)]
+    hyb.hyb_set_profiling(ctx, True)
+    ev[0].record(stream)
+    hyb.hyb_assemble_reduced(ctx, load)
+    ev[1].record(stream)
+    it, rr, st = hyb.hyb_solve_reduced(ctx, args.rtol, args.maxit, lam, check=False)
+    if st != hyb.HYB_OK:
+        raise hyb.HybError(st, "hyb_solve_reduced")
+    ev[2].record(stream)
+    hyb.hyb_recover(ctx, lam, u)
+    ev[3].record(stream)
+    jumps = None
+    if refine:
+        jumps, _ = hyb.hyb_refine(ctx, refine, args.refine_rtol, args.maxit, lam, u)
+    ev[4].record(stream)
+    torch.cuda.synchronize()
+    prof = hyb.hyb_get_profile(ctx)
+    hyb.hyb_set_profiling(ctx, False)
+    ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+    total = sum(ms)
+    E = ctx.sizes()["n_elem"]
+    out = {"elements_per_s": E / (total * 1e-3), "ms": total, "assemble_ms": ms[0], "pcg_ms": ms[1],
+           "pcg_iterations": it, "pcg_rel_res": rr, "recover_ms": ms[2],
+           "launches": int(sum(v[1] for v in prof.values())),
+           "pcg_ms_per_iteration": None}
+    if refine:
+        out.update(refine_ms=ms[3], refine_steps=refine, refine_inner_rtol=args.refine_rtol,
+                   jump_per_step=jumps)
+    pcg_dev = prof["spmv"][0] + prof["pcg_vector"][0] + prof["pcg_fused"][0]
+    out["pcg_ms_per_iteration"] = ms[1] / it if it else None
+    out["reduced_dofs_per_s"] = ctx.sizes()["n_lambda"] / (ms[1] * 1e-3) if ms[1] > 0 else None
+    out["pcg_device_ms_all_solves"] = pcg_dev
+    return out
+
+
+def _err_oracle_worker(cfg, n, route, path):
+    """CPU FP64 oracle on the n^3 mesh of workload cfg through one route (primal: A_T and its
+    Cholesky; mixed: the hybridized mixed form of Sec. 3.2); saves H values, g, lambda, u."""
+    import numpy as np
+    from oracle.hybrid import Discretization, solve_sparse_direct
+    from paper_1801_08914_gb300 import inputs
+    p = inputs.make_config(cfg, n=n)
+    D = Discretization.from_problem(p)
+    H, g = D.hybridize_mixed() if route == "mixed" else D.hybridize()
+    lam = solve_sparse_direct(H, g)
+    u = D.recover_mixed(lam) if route == "mixed" else D.recover(lam)
+    np.savez(path, val=H.data, indptr=H.indptr, indices=H.indices, g=g, lam=lam, u=u)
+
+
+def start_error_oracle(cfg, n, tmpdir):
+    env = dict(os.environ, OMP_NUM_THREADS="2", OPENBLAS_NUM_THREADS="2", MKL_NUM_THREADS="2")
+    procs = {}
+    for route in ("primal", "mixed"):
+        path = os.path.join(tmpdir, f"oracle_{route}.npz")
+        procs[route] = (subprocess.Popen([sys.executable, "-c", f"import bench; bench._err_oracle_worker("
+                                          f"{cfg}, {n}, {route!r}, {path!r})"], cwd=ROOT, env=env,
+                                         stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True), path)
+    return procs
+
+
+def measure_errors(hyb, cfg, n, args, oracle_procs, dev):
+    """Relative errors of both GPU arms on the n^3 mesh of the workload against both oracle routes:
+    S entry-wise per CSR row (max |S - S_o| / max |S_o| over a row, worst row) and norm-wise,
+    lambda entry-wise (against max |lambda_o|) and norm-wise, u entry-wise per element and norm-wise."""
+    import numpy as np
+    import torch
+    from paper_1801_08914_gb300 import inputs
+    p = inputs.make_config(cfg, n=n)
+    tt = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    gpu = {}
+    for arm in ("mixed", "fp64"):
+        mixed = arm == "mixed"
+        ctx = hyb.hyb_setup(tt(p.vertices), p.nx, p.ny, p.nz, p.order, tt(p.alpha), tt(p.beta),
+                            precision=hyb.HYB_MIXED if mixed else hyb.HYB_FP64, contrast_threshold=0.0)
+        hyb.hyb_assemble_reduced(ctx, tt(p.load))
+        red = {k: v.cpu().numpy() for k, v in hyb.hyb_export_reduced(ctx).items()}
+        sz = ctx.sizes()
+        lam = torch.zeros(sz["n_lambda"], dtype=torch.float64, device=dev)
+        u = torch.zeros(sz["n_elem"], sz["n_loc"], dtype=torch.float64, device=dev)
+        hyb.hyb_solve_reduced(ctx, args.rtol, args.maxit, lam)
+        hyb.hyb_recover(ctx, lam, u)
+        g0 = dict(lam=lam.cpu().numpy().copy(), u=u.cpu().numpy().copy())
+        if mixed and args.refine:
+            hyb.hyb_refine(ctx, args.refine, args.refine_rtol, args.maxit, lam, u)
+        torch.cuda.synchronize()
+        gpu[arm] = dict(red=red, lam=lam.cpu().numpy(), u=u.cpu().numpy(), unrefined=g0, split=ctx.precision_split())
+        ctx.close()
+    ref = {}
+    for route, (pr, path) in oracle_procs.items():
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        ref[route] = dict(np.load(path))
+
+    def rn(a, b):
+        return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+    def rinf(a, b):
+        return float(np.abs(np.ravel(a) - np.ravel(b)).max() / np.abs(b).max())
+
+    def rgroups(a, b, g):
+        a, b = np.reshape(a, (-1, g)), np.reshape(b, (-1, g))
+        return float((np.abs(a - b).max(1) / np.abs(b).max(1)).max())
+
+    def rrows(a, b, rp):
+        st = rp[:-1][rp[1:] > rp[:-1]]
+        return float((np.maximum.reduceat(np.abs(a - b), st) / np.maximum.reduceat(np.abs(b), st)).max())
+
+    nloc = p.load.shape[1]
+    out = {"mesh": f"{n}^3 mesh of the same recipe ({p.n_elem} elements, "
+                   f"{ref['primal']['g'].size} multipliers, seed {inputs.CONFIGS[cfg]['seed']})",
+           "note": "S: worst CSR row of max|S - S_o| / max|S_o| (entry-wise) and ||S - S_o|| / ||S_o||; lambda: "
+                   "max|d| / max|lambda_o| and norm-wise; u: worst element of max|d| / max|u_o| and norm-wise. "
+                   "primal oracle = A_T = alpha M + beta K and its Cholesky (FP64, accurate to kappa(A_T) eps: "
+                   "~1e-7 in u at this contrast); mixed-form oracle = Sec. 3.2's saddle route (FP64, accurate "
+                   "at any contrast)",
+           "solve": {"pcg_rtol": args.rtol, "refine_steps_mixed": args.refine, "refine_inner_rtol": args.refine_rtol}}
+    for arm, gv in gpu.items():
+        red = gv["red"]
+        for route, r in ref.items():
+            assert np.array_equal(red["row_ptr"], r["indptr"]) and np.array_equal(red["col"], r["indices"])
+            e = {"S_row": rrows(red["val"], r["val"], r["indptr"]), "S_norm": rn(red["val"], r["val"]),
+                 "g_inf": rinf(red["rhs"], r["g"]),
+                 "lambda_inf": rinf(gv["lam"], r["lam"]), "lambda_norm": rn(gv["lam"], r["lam"]),
+                 "u_element": rgroups(gv["u"], r["u"], nloc), "u_norm": rn(gv["u"], r["u"])}
+            if arm == "mixed" and args.refine:
+                e["u_element_before_refinement"] = rgroups(gv["unrefined"]["u"], r["u"], nloc)
+                e["lambda_inf_before_refinement"] = rinf(gv["unrefined"]["lam"], r["lam"])
+            out[f"{arm}_vs_{route}_oracle"] = e
+    out["mixed_split"] = {"fp64_elements": gpu["mixed"]["split"][0], "fp32_elements": gpu["mixed"]["split"][1],
+                          "threshold": gpu["mixed"]["split"][2]}
+    return out
+
+
+def run_precision(args):
+    """The precision workloads (96^3 RT_2; 64^3 RT_3): mixed and FP64 arms in one run."""
+    import tempfile
+
+    import numpy as np
+    import torch
+
+    rank, local, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", 1)) > 1 else "gloo")
+    torch.cuda.set_device(local)
+    cfg = int(args.config)
+    tmpdir = tempfile.mkdtemp(prefix="hyb_bench_")
+    measure_err = rank == 0 and not args.no_errors
+    oracle_procs = start_error_oracle(cfg, ERR_N, tmpdir) if measure_err else None
+    build_once(local)
+    from paper_1801_08914_gb300 import hyb, inputs
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    p = inputs.make_config(cfg, n=args.n)
+    tt = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    verts, alpha, beta, load = tt(p.vertices), tt(p.alpha), tt(p.beta), tt(p.load)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    fp64_peak = hyb.hyb_measure_fma_peak(True)
+    fp32_peak = hyb.hyb_measure_fma_peak(False)
+    clock_lines = []
+
+    def sampled(fn):
+        """Run fn with nvidia-smi sampling the clocks (only the timed regions are sampled)."""
+        c = ClockSampler(local)
+        c.start()
+        try:
+            return fn()
+        finally:
+            clock_lines.extend(c.halt())
+
+    arms = {}
+    for arm in ("mixed", "fp64"):
+        mixed = arm == "mixed"
+        t0 = time.perf_counter()
+        ctx = hyb.hyb_setup(verts, p.nx, p.ny, p.nz, p.order, alpha, beta,
+                            precision=hyb.HYB_MIXED if mixed else hyb.HYB_FP64,
+                            contrast_threshold=args.threshold if mixed else 0.0)
+        t_setup = time.perf_counter() - t0
+        n64, n32, theta = ctx.precision_split()
+        sz = ctx.sizes()
+        E, n_loc, N, nnz = sz["n_elem"], sz["n_loc"], sz["n_lambda"], sz["nnz"]
+        barrier()
+        ms, prof = sampled(lambda: time_element_phase(hyb, ctx, load, args.warmup, args.steps, flush, stream))
+        barrier()
+        a = {"ms_steps": ms, "prof": prof, "setup_s": t_setup, "split": (n64, n32, theta)}
+        if mixed:
+            # end to end through the C ABI from host memory: pinned load -> device, the element
+            # phase, the reduced right-hand side g -> pinned host buffer, every step
+            load_h = torch.from_numpy(np.ascontiguousarray(p.load)).pin_memory()
+            g_h = torch.empty(N, dtype=torch.float64).pin_memory()
+            load_d = torch.empty_like(load)
+            g_dev = torch.empty(N, dtype=torch.float64, device=dev)
+            ke = max(1, min(args.steps, 5))
+            e0, e1 = _event_pair()
+            torch.cuda.synchronize()
+            barrier()
+            e0.record(stream)
+            for _ in range(ke):
+                load_d.copy_(load_h, non_blocking=True)
+                hyb.hyb_assemble_reduced(ctx, load_d)
+                hyb.hyb_export_rhs(ctx, g_dev)
+                g_h.copy_(g_dev, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            a["e2e_ms"] = e0.elapsed_time(e1) / ke
+            a["e2e_bytes"] = (int(p.load.nbytes), int(N * 8))
+            del load_h, g_h, load_d, g_dev
+        if not args.no_full:
+            lam = torch.zeros(N, dtype=torch.float64, device=dev)
+            u = torch.zeros(E, n_loc, dtype=torch.float64, device=dev)
+            a["full"] = sampled(lambda: time_full_path(hyb, ctx, load, lam, u, args, args.refine if mixed else 0,
+                                                       flush, stream))
+            del lam, u
+        ctx.close()
+        torch.cuda.synchronize()
+        arms[arm] = a
+    ck = ClockSampler.summarize(clock_lines) if clock_lines else \
+        {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+
+    E = p.n_elem
+    res = {}
+    for arm, a in arms.items():
+        ms = sum(a["ms_steps"])
+        value, ms_max = aggregate(E * args.steps, ms, world, device=dev)
+        res[arm] = (value, ms_max)
+    value, ms_max = res["mixed"]
+    fp64_value = res["fp64"][0]
+    n64, n32, theta = arms["mixed"]["split"]
+    f32 = element_flops_mixed(p.order)
+    f64 = element_flops(p.order)
+    pm = arms["mixed"]["prof"]
+    el_ms_m = pm["element"][0] / args.steps
+    el_launch_m = pm["element"][1] / args.steps
+    # the dominant kernel of the timed step: the FP32 mixed-form element kernel (every element
+    # of contrast <= the threshold); its algorithmic FP32 flops per launch over its average launch
+    tflops = (n32 * f32 + n64 * f64) / (el_ms_m * 1e-3) / 1e12 if el_ms_m > 0 else None
+    roof = {"kernel": f"element_tiled_kernel<{p.order}> (FP32 mixed-form elimination"
+                      + (f") + element_kernel<{p.order}> (FP64)" if n64 else ")"),
+            "bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": tflops / fp32_peak if tflops else None,
+            "peak_source": "FP32 FMA throughput measured in this run (hyb_measure_fma_peak: independent FMA "
+                           "chains on every SM)",
+            "traffic": MIXED_ELEMENT_TRAFFIC_PER_ELEMENT.get(p.order) and
+                       MIXED_ELEMENT_TRAFFIC_PER_ELEMENT[p.order] * E / el_launch_m,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per element x elements per launch "
+                               "(profiles/element_tiled_kernel_rt2_rt3.md)"
+                               if p.order in MIXED_ELEMENT_TRAFFIC_PER_ELEMENT else None),
+            "algorithmic_flops_per_element": f32, "elements_per_launch": E / el_launch_m,
+            "avg_launch_ms": el_ms_m / el_launch_m, "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak}
+    pf = arms["fp64"]["prof"]
+    el_ms_f = pf["element"][0] / args.steps
+    tf64 = E * f64 / (el_ms_f * 1e-3) / 1e12 if el_ms_f > 0 else None
+    fp64_roof = {"kernel": f"element_kernel<{p.order}> (FP64)", "bound": "alu", "achieved": tf64, "peak": fp64_peak,
+                 "unit": "TFLOP/s", "frac": tf64 / fp64_peak if tf64 else None,
+                 "algorithmic_flops_per_element": f64, "avg_launch_ms": el_ms_f / max(1, pf["element"][1] / args.steps)}
+    workload = precision_workload_name(cfg, p.nx)
+    line = {
+        "metric": PRECISION_METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": workload, "elements": E, "order": p.order, "n_loc": p.load.shape[1],
+                   "step": "element phase a1-a6 of the mixed-precision context (hyb_assemble_reduced)",
+                   "contrast_threshold": theta, "elements_fp32": n32, "elements_fp64": n64,
+                   "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) before each timed step"},
+        "fp64": {"value": fp64_value, "unit": "elements/s", "ms_per_step": res["fp64"][1] / args.steps,
+                 "step": "element phase a1-a6 of the FP64 context", "element_roofline": fp64_roof},
+        "mixed_over_fp64": value / fp64_value,
+        "e2e": {"value": E / (arms["mixed"]["e2e_ms"] * 1e-3), "unit": "elements/s",
+                "h2d_bytes_per_step": arms["mixed"]["e2e_bytes"][0], "d2h_bytes_per_step": arms["mixed"]["e2e_bytes"][1],
+                "path": "pinned host load -> hyb_assemble_reduced (mixed) -> reduced right-hand side to pinned host"},
+        "gpu_launches": int(sum(v[1] for v in pm.values())),
+        "roofline": roof,
+        "clocks": ck,
+        "setup_s": {arm: a["setup_s"] for arm, a in arms.items()},
+    }
+    if not args.no_full:
+        line["full_step"] = {arm: a["full"] for arm, a in arms.items()}
+        line["full_step"]["note"] = ("one pass of the whole path per arm: assemble, diagonal PCG to rtol, back "
+                                     "substitution; the mixed arm adds FP64 refinement steps (hyb_refine)")
+        fm, ff = arms["mixed"]["full"], arms["fp64"]["full"]
+        line["full_step"]["mixed_over_fp64"] = fm["elements_per_s"] / ff["elements_per_s"]
+    if measure_err:
+        try:
+            line["errors"] = measure_errors(hyb, cfg, ERR_N, args, oracle_procs, dev)
+        except Exception as exc:  # reported, not fatal
+            line["errors"] = {"error": str(exc)[:300]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_phase(cfg)
+        except Exception as exc:  # reported, not fatal
+            line["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_batch(args):
     """The batched workload: 256 independent problems, n ~ U{6..24}, k ~ U{0..3}, one context."""
     import numpy as np
@@ -648,6 +1123,8 @@ def main(argv=None):
         run_reference(args)
     elif str(args.config) == "4":
         run_batch(args)
+    elif str(args.config) in ("3", "5") and not args.single_arm:
+        run_precision(args)
     else:
         run_ours(args)
     import torch.distributed as dist

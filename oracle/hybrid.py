@@ -176,14 +176,20 @@ class Discretization:
         so that M x + B^T W^{-1} B x = A_T x), essential dofs re-inserted; returns (E, n)."""
         u = np.zeros((self.mesh.n_elem, self.n))
         for e in range(self.mesh.n_elem):
-            M, B, W, d = self.mixed_form_blocks(e)
-            nf = M.shape[0]
-            K = np.block([[M, B.T], [B, -W]])
-            rhs = np.zeros(nf + W.shape[0])
-            rhs[:nf] = d["f"] - d["C"].T @ lam[d["lam"]]
-            u[e, d["free"]] = np.linalg.solve(K, rhs)[:nf]
-            u[e, d["edofs"]] = d["ue"]
+            u[e] = self.recover_mixed_element(e, lam)
         return u
+
+    def recover_mixed_element(self, e, lam):
+        """recover_mixed for the single element e; returns its n dofs."""
+        M, B, W, d = self.mixed_form_blocks(e)
+        nf = M.shape[0]
+        K = np.block([[M, B.T], [B, -W]])
+        rhs = np.zeros(nf + W.shape[0])
+        rhs[:nf] = d["f"] - d["C"].T @ lam[d["lam"]]
+        x = np.zeros(self.n)
+        x[d["free"]] = np.linalg.solve(K, rhs)[:nf]
+        x[d["edofs"]] = d["ue"]
+        return x
 
     def _assemble_reduced(self, reduce_element, elements=None):
         """Sum the element contributions S_T, g_T of reduce_element into H and g (eq. 2.4)."""

@@ -236,6 +236,13 @@ def hyb_export_reduced(ctx):
     return out
 
 
+def hyb_export_rhs(ctx, out):
+    """Copy the reduced right-hand side g into the caller's device tensor `out` (N_lambda doubles)."""
+    if out.numel() != ctx.sizes()["n_lambda"]:
+        raise ValueError("out must hold N_lambda doubles")
+    return _check(lib().hyb_export_reduced(ctx.handle, None, None, None, _ptr(out, "out")), "hyb_export_reduced")
+
+
 def hyb_pcg_solve_noalloc(row_ptr, col, val, b, x, rows_per_face, rtol, maxit, stream=None, check=True):
     """Allocation-free PCG on a caller-supplied CSR system (see include/hyb.h).
     Returns (iterations, relative residual, status).

@@ -84,3 +84,16 @@ def rel_rows(val, ref, row_ptr):
 def element_kappa(D, elements=None):
     es = range(D.mesh.n_elem) if elements is None else elements
     return max(np.linalg.cond(D.element(e)["A"]) for e in es)
+
+
+def kappa_w(D, elements=None):
+    """Largest condition number of the factored matrices of the FP32 mixed form, M and
+    Z = W^{-1} (W + B M^{-1} B^T) W^{-1}, over the elements (Sec. 3.2's blocks)."""
+    out = 1.0
+    es = range(D.mesh.n_elem) if elements is None else elements
+    for e in es:
+        M, B, W, _ = D.mixed_form_blocks(e)
+        Wi = np.linalg.inv(W)
+        Z = Wi @ (W + B @ np.linalg.solve(M, B.T)) @ Wi
+        out = max(out, np.linalg.cond(M), np.linalg.cond(Z))
+    return out

@@ -5,7 +5,7 @@ from paper_1801_08914_gb300 import inputs
 
 
 def test_workload_names():
-    args = bench.parse_args([])
+    args = bench.parse_args(["--config", "2"])
     p = inputs.make_config(2)
     assert bench.workload_name(2, p, args) == bench.WORKLOAD
     for cfg, n in ((3, 6), (5, 4), (2, 8)):
@@ -29,3 +29,16 @@ def test_recover_roofline_arithmetic():
     r = bench.recover_roofline_of(3, 1000, 2.0, 6771.0)
     assert r["bound"] == "hbm" and abs(r["achieved"] - 1000 * bench.recover_bytes_per_element(3) / 2e-3 / 1e9) < 1e-9
     assert bench.recover_roofline_of(3, 1000, 0.0, 6771.0) is None
+
+
+def test_precision_workload_defaults():
+    """The default run is the precision workload (96^3 RT_2, contrast up to 1e6) with both arms and
+    two refinement steps on the mixed arm; its name states the mesh, order, coefficients and step."""
+    args = bench.parse_args([])
+    assert str(args.config) == "3" and not args.single_arm and args.refine == 2
+    w = bench.precision_workload_name(3)
+    assert w.startswith("96x96x96 jittered hex mesh (+-0.2h), RT_2") and "beta/alpha 10^U(-2,6)" in w
+    assert "element phase a1-a6" in w and "config" not in w
+    assert bench.precision_workload_name(5).startswith("64x64x64 jittered hex mesh (+-0.2h), RT_3")
+    assert bench.parse_args(["--config", "2"]).refine == 0
+    assert bench.parse_args(["--config", "3", "--single-arm"]).refine == 0

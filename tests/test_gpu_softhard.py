@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from gpu_helpers import EPS, dev, element_kappa, gpu_run, rel
+from gpu_helpers import EPS, dev, element_kappa, gpu_run, rel, rel_groups, rel_inf, rel_rows
 from oracle.hybrid import Discretization, solve_sparse_direct
 from paper_1801_08914_gb300 import inputs
 
@@ -49,9 +49,11 @@ def test_parity_fp64(k, pexp):
     assert np.array_equal(red["col"], H.indices.astype(np.int32))
     kT, kH = element_kappa(D), kappa_sparse(H)
     tol_S, tol_u = max(1e-12, kT * EPS), max(1e-12, max(kT, kH) * EPS)
-    eS, eg, el, eu = rel(red["val"], H.data), rel(red["rhs"], g), rel(r["lam"], lam), rel(r["u"], u)
-    print(f"soft-hard k={k} p={pexp:+.0f}: kT {kT:.1e} kH {kH:.1e} S {eS:.1e} g {eg:.1e} lam {el:.1e} "
-          f"u {eu:.1e} (tol {tol_S:.1e}/{tol_u:.1e}) PCG {r['it']} it")
+    eS, eg = rel_rows(red["val"], H.data, H.indptr), rel_inf(red["rhs"], g)
+    el, eu = rel_inf(r["lam"], lam), rel_groups(r["u"], u, D.n)
+    print(f"soft-hard k={k} p={pexp:+.0f}: kT {kT:.1e} kH {kH:.1e} entry-wise S/row {eS:.1e} g {eg:.1e} "
+          f"lam {el:.1e} u/element {eu:.1e} (tol {tol_S:.1e}/{tol_u:.1e}); norm-wise u {rel(r['u'], u):.1e}; "
+          f"PCG {r['it']} it")
     assert eS <= tol_S and eg <= tol_S
     assert el <= tol_u and eu <= tol_u
     assert r["status"] == 0
