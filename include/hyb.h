@@ -79,8 +79,10 @@ typedef struct hyb_ctx hyb_ctx;
  *               contrast_threshold are eliminated in FP32 through the hybridized mixed
  *               form (Sec. 3.2: A^-1 = M^-1 - M^-1 D Z^-1 D^T M^-1, every factor well
  *               conditioned), with the load term and the recovery refined against an FP64
- *               residual; the others use the FP64 path. The reduced system, PCG and the
- *               recovered u stay FP64. Static condensation needs an HYB_FP64 context.
+ *               residual; the others use the FP64 path. The reduced system is accumulated
+ *               in FP64; the PCG keeps its iterate, residual and reductions in FP64 and
+ *               applies H from an FP32 copy of its values (hyb_set_mixed_operator); the
+ *               recovered u is FP64. Static condensation needs an HYB_FP64 context.
  *  contrast_threshold : HYB_MIXED only (ignored for HYB_FP64); > 0 as given, 0 = autotuned.
  *               The FP32 elimination's relative error in S_T grows like u_32 beta/alpha
  *               (the 1/alpha part of A^-1 on the faces cancels in it); up to 1e6 the FP64
@@ -214,6 +216,24 @@ int hyb_set_natural_bc(hyb_ctx* ctx, int natural);
  *  cooperative kernels.
  */
 int hyb_set_pcg_fused(hyb_ctx* ctx, int on);
+
+/*
+ * hyb_set_mixed_operator -- HYB_MIXED contexts: the operator that the PCG of hyb_solve_reduced
+ *  and hyb_refine applies.
+ *  1 (default): when any element is eliminated in FP32, an FP32 copy of H's values, rounded
+ *  once the assembly's FP64 accumulation is complete (a context whose elements all take the
+ *  FP64 path keeps the FP64 values). Each lane forms its share of a row from FP32 products of those values and of an FP32
+ *  copy of the preconditioned residual; the lanes' partial sums are added in FP64, and the
+ *  iterate, residual, direction and every reduction stay FP64. H of a mixed context carries the
+ *  FP32 elimination's error (~1e-7 relative) already; the rounding adds error of the same kind and
+ *  size. hyb_refine measures its residual as the FP64 jump of the recovered flux, which does not
+ *  depend on this operator, so the refined solution does not either.
+ *  0: the FP64 values.
+ *  The fused form only (hyb_set_pcg_fused(ctx, 1), the default); the three-launch form applies the
+ *  FP64 values. Implementation choice with no counterpart in the paper.
+ *  HYB_ERR_INVALID_ARG on an HYB_FP64 context or for other values.
+ */
+int hyb_set_mixed_operator(hyb_ctx* ctx, int fp32);
 
 /*
  * hyb_barrier_selftest -- exercise the grid barrier of the fused PCG kernel.

@@ -108,6 +108,9 @@ struct hyb_ctx {
   int64_t n_path[2] = {0, 0};
   int32_t* slot = nullptr;
   float* Lstore32 = nullptr;
+  float* val32 = nullptr;                  // mixed: FP32 copy of the reduced-system values (PCG operator)
+  float* z32 = nullptr;                    // mixed: FP32 copy of the preconditioned residual
+  int op32 = 1;                            // mixed: PCG applies H from val32 (1) or from val (0)
   std::vector<int32_t> h_list[2][2];       // host copies: [colour][path] (path 0 = FP64, 1 = FP32)
   double* Lstore = nullptr;
   double* zstore = nullptr;
@@ -361,6 +364,8 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
       return HYB_ERR_CUDA;
     if ((st = dalloc(c, &c->Lstore, (size_t)c->n_path[0] * (size_t)tri_size(s.n)))) return st;
     if ((st = dalloc(c, &c->Lstore32, (size_t)c->n_path[1] * (size_t)mixed_store_floats(order)))) return st;
+    if ((st = dalloc(c, &c->val32, c->nnz))) return st;
+    if ((st = dalloc(c, &c->z32, c->n_lambda))) return st;
   } else {
     if ((st = dalloc(c, &c->Lstore, (size_t)E * (size_t)tri_size(s.n)))) return st;
     for (int col = 0; col < 2; ++col) c->h_list[col][0] = lists[col];
@@ -431,6 +436,12 @@ int assemble_impl(hyb_ctx* c, const double* load, const double* ess, int mode) {
       continue;
     }
     cudaError_t e = launch_element(c->k, mode, a, c->stream, &c->prof);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (c->precision == HYB_MIXED && c->n_path[1] > 0) {
+    // the FP32 copy of H that the mixed context's PCG applies (H carries the FP32 elimination's
+    // error anyway; the FP64 accumulation above stays the reference for the refinement)
+    cudaError_t e = launch_round_values(c->nnz, c->val, c->val32, c->stream, &c->prof);
     if (e != cudaSuccess) return cuda_status(e);
   }
   st = finish_phase(c);
@@ -606,6 +617,10 @@ int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lamb
   a.flags = c->flags;
   a.nblocks = c->nblocks;
   a.nfn = c->sz.nfn;
+  if (c->precision == HYB_MIXED && c->n_path[1] > 0 && c->fused && c->op32 && c->mode == MODE_HYB) {
+    a.val32 = c->val32;
+    a.z32 = c->z32;
+  }
   cudaError_t e = pcg_init(a, c->stream, &c->prof);
   if (e != cudaSuccess) return cuda_status(e);
   int hf[4] = {0, 0, 0, 0};
@@ -697,6 +712,13 @@ int hyb_set_natural_bc(hyb_ctx* c, int natural) {
   if (!c || (natural != 0 && natural != 1)) return HYB_ERR_INVALID_ARG;
   c->natural = natural;
   c->mode = MODE_NONE;                     // factors of the other reading are stale
+  return HYB_OK;
+}
+
+int hyb_set_mixed_operator(hyb_ctx* c, int fp32) {
+  if (!c || (fp32 != 0 && fp32 != 1)) return HYB_ERR_INVALID_ARG;
+  if (c->precision != HYB_MIXED) return HYB_ERR_INVALID_ARG;
+  c->op32 = fp32;
   return HYB_OK;
 }
 

@@ -99,6 +99,9 @@ struct PcgArgs {
   double* q;
   double* dinv;
   double* z;                 // preconditioned residual (fused form only; NULL otherwise)
+  const float* val32;        // mixed contexts, fused form: the values rounded to FP32, applied with
+                             // FP32 products (NULL: the FP64 values)
+  float* z32;                // with val32: z rounded to FP32 for the SpMV's gathers
   unsigned long long* bar;   // fused form in a batch: this problem's barrier counter (16 bytes, zeroed per launch)
   double* partial;           // per-block partial sums
   double* scal;              // device scalars
@@ -151,6 +154,9 @@ cudaError_t launch_norm2(int64_t n, const double* v, double* partial, int nblock
                          cudaStream_t s, Prof* prof);
 // y += x
 cudaError_t launch_axpy(int64_t n, const double* x, double* y, cudaStream_t s, Prof* prof);
+// o[i] = (float)v[i], i < n (the FP32 operator of a mixed context's PCG); profiled with the
+// element phase, whose last step it is
+cudaError_t launch_round_values(int64_t n, const double* v, float* o, cudaStream_t s, Prof* prof);
 
 struct RecoverArgs {
   int k;

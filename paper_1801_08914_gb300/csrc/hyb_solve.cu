@@ -151,6 +151,7 @@ __global__ void pcg_init_kernel(PcgArgs a) {
     a.r[i] = r;
     a.p[i] = z;
     if (a.z) a.z[i] = z;
+    if (a.z32) a.z32[i] = (float)z;
     rz = fma(r, z, rz);
     rr = fma(r, r, rr);
   }
@@ -415,7 +416,11 @@ struct GridBar {
 // The iteration loop of one problem run by nvb cooperating blocks (vb = this block's index
 // among them); `bar` is their arrival counter. The single-problem kernel runs it with the
 // whole grid, the batch kernel with a team of blocks per problem.
-template <int NFN, int W>
+// F32: the operator is the FP32 copy of the values (mixed contexts): each lane forms its share
+// of a row in FP32 (products of FP32 values and the FP32 copy of z, ~len / W terms), the
+// lanes' partial sums are combined in FP64, and every vector, scalar and reduction of the
+// iteration stays FP64.
+template <int NFN, int W, bool F32>
 __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, double rtol2, GridBar* bar, int vb,
                                                int nvb, double* sh, double* bc) {
   constexpr int NP = padded_rows<NFN, W>();
@@ -446,11 +451,25 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
         const int64_t r0 = f * NFN;
         const int64_t lo = __ldcs(a.row_ptr + r0);
         const int len = (int)(__ldcs(a.row_ptr + r0 + 1) - lo);
-#pragma unroll 4
-        for (int t = gl; t < len; t += W) {
-          const double zj = __ldcg(a.z + __ldcs(a.col + lo + t));
+        if constexpr (F32) {
+          float acc32[NFN];
 #pragma unroll
-          for (int m = 0; m < NFN; ++m) acc[m] = fma(__ldcs(a.val + lo + (int64_t)m * len + t), zj, acc[m]);
+          for (int m = 0; m < NFN; ++m) acc32[m] = 0.0f;
+#pragma unroll 4
+          for (int t = gl; t < len; t += W) {
+            const float zj = __ldcg(a.z32 + __ldcs(a.col + lo + t));
+#pragma unroll
+            for (int m = 0; m < NFN; ++m) acc32[m] = fmaf(__ldcs(a.val32 + lo + (int64_t)m * len + t), zj, acc32[m]);
+          }
+#pragma unroll
+          for (int m = 0; m < NFN; ++m) acc[m] = (double)acc32[m];
+        } else {
+#pragma unroll 4
+          for (int t = gl; t < len; t += W) {
+            const double zj = __ldcg(a.z + __ldcs(a.col + lo + t));
+#pragma unroll
+            for (int m = 0; m < NFN; ++m) acc[m] = fma(__ldcs(a.val + lo + (int64_t)m * len + t), zj, acc[m]);
+          }
         }
       }
       face_reduce<NP, W>(acc, gl);
@@ -516,6 +535,7 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
         a.r[i] = r;
         const double z = a.dinv[i] * r;
         a.z[i] = z;
+        if constexpr (F32) a.z32[i] = (float)z;
         rzl = fma(r, z, rzl);
         rrl = fma(r, r, rrl);
       }
@@ -554,12 +574,25 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
   }
 }
 
-template <int NFN, int W>
+template <int NFN, int W, bool F32>
 __global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
     pcg_fused_kernel(PcgArgs a, int count, double rtol2, GridBar* bar) {
   __shared__ double sh[kThreads];
   __shared__ double bc[3];
-  pcg_fused_body<NFN, W>(a, count, rtol2, bar, blockIdx.x, gridDim.x, sh, bc);
+  pcg_fused_body<NFN, W, F32>(a, count, rtol2, bar, blockIdx.x, gridDim.x, sh, bc);
+}
+
+// The FP32 copy of the reduced-system values (mixed contexts), rounded to nearest.
+__global__ void round_values_kernel(int64_t n, const double* __restrict__ v, float* __restrict__ o) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n2 = n / 2;
+  const double2* v2 = reinterpret_cast<const double2*>(v);
+  float2* o2 = reinterpret_cast<float2*>(o);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const double2 x = __ldcs(v2 + i);
+    __stcs(o2 + i, make_float2((float)x.x, (float)x.y));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) o[n - 1] = (float)v[n - 1];
 }
 
 // Batch: block b works for problem team[b].x as block team[b].y of team[b].z, with that
@@ -573,10 +606,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   const PcgArgs& a = probs[t.x];
   GridBar* bar = reinterpret_cast<GridBar*>(a.bar);
   switch (a.nfn) {
-    case 1: pcg_fused_body<1, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
-    case 4: pcg_fused_body<4, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
-    case 9: pcg_fused_body<9, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
-    default: pcg_fused_body<16, 4>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
+    case 1: pcg_fused_body<1, 4, false>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
+    case 4: pcg_fused_body<4, 4, false>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
+    case 9: pcg_fused_body<9, 4, false>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
+    default: pcg_fused_body<16, 4, false>(a, count, rtol2, bar, t.y, t.z, sh, bc); break;
   }
 }
 
@@ -740,12 +773,13 @@ cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_
   return cudaGetLastError();
 }
 
-template <int NFN, int W>
+template <int NFN, int W, bool F32>
 cudaError_t launch_fused(const PcgArgs& a, int count, double rtol, void* bar, cudaStream_t s) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_fused_kernel<NFN, W>, kThreads, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_fused_kernel<NFN, W, F32>, kThreads, 0);
   if (e != cudaSuccess) return e;
   int grid = sms * per_sm;
   if (grid > a.nblocks / 2) grid = a.nblocks / 2;         // two buffers of pairs: 4 * grid <= 2 * nblocks
@@ -754,7 +788,7 @@ cudaError_t launch_fused(const PcgArgs& a, int count, double rtol, void* bar, cu
   double rtol2 = rtol * rtol;
   GridBar* gb = static_cast<GridBar*>(bar);
   void* params[] = {&aa, &count, &rtol2, &gb};
-  return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<NFN, W>, grid, kThreads, params, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<NFN, W, F32>, grid, kThreads, params, 0, s);
 }
 
 __global__ void zero_bars_kernel(const PcgArgs* probs, int n) {
@@ -791,15 +825,34 @@ cudaError_t pcg_iterations_team(const PcgArgs* probs, const int4* team, int nblo
 cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void* bar, cudaStream_t s, Prof* prof) {
   const int tok = prof_begin(prof, HYB_K_PCG_FUSED, s);
   cudaError_t e;
-  switch (a.nfn) {
-    case 1: e = launch_fused<1, 4>(a, count, rtol, bar, s); break;
-    case 4: e = launch_fused<4, 4>(a, count, rtol, bar, s); break;
-    case 9: e = launch_fused<9, 4>(a, count, rtol, bar, s); break;
-    case 16: e = launch_fused<16, 4>(a, count, rtol, bar, s); break;
-    default: e = cudaErrorInvalidValue;
+  if (a.val32 && !a.z32) return cudaErrorInvalidValue;
+  if (a.val32) {
+    switch (a.nfn) {
+      case 1: e = launch_fused<1, 4, true>(a, count, rtol, bar, s); break;
+      case 4: e = launch_fused<4, 4, true>(a, count, rtol, bar, s); break;
+      case 9: e = launch_fused<9, 4, true>(a, count, rtol, bar, s); break;
+      case 16: e = launch_fused<16, 4, true>(a, count, rtol, bar, s); break;
+      default: e = cudaErrorInvalidValue;
+    }
+  } else {
+    switch (a.nfn) {
+      case 1: e = launch_fused<1, 4, false>(a, count, rtol, bar, s); break;
+      case 4: e = launch_fused<4, 4, false>(a, count, rtol, bar, s); break;
+      case 9: e = launch_fused<9, 4, false>(a, count, rtol, bar, s); break;
+      case 16: e = launch_fused<16, 4, false>(a, count, rtol, bar, s); break;
+      default: e = cudaErrorInvalidValue;
+    }
   }
   prof_end(prof, tok, s);
   return e;
+}
+
+cudaError_t launch_round_values(int64_t n, const double* v, float* o, cudaStream_t s, Prof* prof) {
+  if (n == 0) return cudaSuccess;
+  const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+  round_values_kernel<<<152 * 8, kThreads, 0, s>>>(n, v, o);
+  prof_end(prof, tok, s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_face_jump(const JumpArgs& a, cudaStream_t s, Prof* prof) {

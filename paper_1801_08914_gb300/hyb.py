@@ -34,7 +34,7 @@ EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recove
            "hyb_set_profiling", "hyb_get_profile", "hyb_pcg_solve_noalloc", "hyb_measure_fma_peak",
            "hyb_get_precision_split", "hyb_setup_batch", "hyb_assemble_reduced_batch", "hyb_solve_reduced_batch",
            "hyb_recover_batch", "hyb_batch_context", "hyb_batch_set_profiling", "hyb_batch_get_profile",
-           "hyb_destroy_batch",
+           "hyb_destroy_batch", "hyb_set_mixed_operator",
            "hyb_last_error_element", "hyb_destroy", "hyb_status_string"]
 
 
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_destroy_batch.restype = None
     lib.hyb_set_profiling.argtypes = [P, I]
     lib.hyb_set_pcg_fused.argtypes = [P, I]
+    lib.hyb_set_mixed_operator.argtypes = [P, I]
     lib.hyb_rsqrt_probe.argtypes = [ctypes.c_int64, P, P, P, P]
     lib.hyb_set_natural_bc.argtypes = [P, I]
     lib.hyb_refine.argtypes = [P, I, D, I, P, P, ctypes.POINTER(D)]
@@ -303,6 +304,12 @@ def hyb_set_natural_bc(ctx, natural, check=True):
 def hyb_set_pcg_fused(ctx, on):
     """PCG launch form: True = one cooperative launch per 64 iterations, False = 3 per iteration."""
     return _check(lib().hyb_set_pcg_fused(ctx.handle, int(bool(on))), "hyb_set_pcg_fused")
+
+
+def hyb_set_mixed_operator(ctx, fp32, check=True):
+    """Mixed contexts: the PCG applies H from its FP32 copy (True, default) or its FP64 values."""
+    st = lib().hyb_set_mixed_operator(ctx.handle, int(bool(fp32)))
+    return _check(st, "hyb_set_mixed_operator") if check else st
 
 
 def hyb_barrier_selftest(absent, rounds, stream=None):

@@ -11,12 +11,15 @@ def dev(a, dtype=None):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
 
 
-def gpu_run(p, mode="hyb", rtol=1e-14, maxit=100000, solve=True, precision=0, threshold=0.0):
-    """setup -> assemble -> export reduced system -> PCG -> recover, all through libhyb."""
+def gpu_run(p, mode="hyb", rtol=1e-14, maxit=100000, solve=True, precision=0, threshold=0.0, op32=None):
+    """setup -> assemble -> export reduced system -> PCG -> recover, all through libhyb.
+    op32: for mixed contexts, the PCG operator (None: the library's default)."""
     import torch
     from paper_1801_08914_gb300 import hyb
     ctx = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta),
                         precision=precision, contrast_threshold=threshold)
+    if op32 is not None:
+        hyb.hyb_set_mixed_operator(ctx, op32)
     if getattr(p, "natural", False):
         hyb.hyb_set_natural_bc(ctx, True)
     load = dev(p.load)

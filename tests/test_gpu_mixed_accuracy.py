@@ -19,11 +19,13 @@ pytestmark = pytest.mark.gpu
 STEPS, INNER = 2, 1e-6
 
 
-def run(p, precision, threshold, steps):
+def run(p, precision, threshold, steps, op32=True):
     import torch
     from paper_1801_08914_gb300 import hyb
     ctx = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta),
                         precision=precision, contrast_threshold=threshold)
+    if precision == hyb.HYB_MIXED:
+        hyb.hyb_set_mixed_operator(ctx, op32)
     split = ctx.precision_split()
     hyb.hyb_assemble_reduced(ctx, dev(p.load), None)
     red = {k: v.cpu().numpy() for k, v in hyb.hyb_export_reduced(ctx).items()}
@@ -38,8 +40,10 @@ def run(p, precision, threshold, steps):
     return dict(split=split, red=red, lam0=lam0, u0=u0, lam=lam.cpu().numpy(), u=u.cpu().numpy(), jumps=jumps)
 
 
-@pytest.mark.parametrize("k,n", [(2, 4), (3, 3)])
-def test_autotuned_mixed_path_reaches_1e9_at_contrast_1e6(k, n):
+@pytest.mark.parametrize("k,n,op32", [(2, 4, True), (3, 3, True), (2, 4, False)])
+def test_autotuned_mixed_path_reaches_1e9_at_contrast_1e6(k, n, op32):
+    """op32: the PCG applies H from its FP32 copy (the default of mixed contexts) or from the FP64
+    values; the refined solution is the same to the stated accuracy either way."""
     from paper_1801_08914_gb300 import hyb
     p = inputs.random_problem(n, k, 0.2, 470 + k, 1e-2, 1e6, name="accuracy")
     D = Discretization.from_problem(p)
@@ -49,7 +53,7 @@ def test_autotuned_mixed_path_reaches_1e9_at_contrast_1e6(k, n):
     H, g = D.hybridize()
     lam_p = solve_dense(H, g)
     u_p = D.recover(lam_p)
-    r = run(p, hyb.HYB_MIXED, 0.0, STEPS)
+    r = run(p, hyb.HYB_MIXED, 0.0, STEPS, op32)
     n64, n32, theta = r["split"]
     assert theta == 1e6 and n32 == p.n_elem, r["split"]       # FP32 is the faster path for RT_2 / RT_3
     f = run(p, hyb.HYB_FP64, 0.0, 0)
@@ -57,7 +61,8 @@ def test_autotuned_mixed_path_reaches_1e9_at_contrast_1e6(k, n):
     before = rel_inf(r["lam0"], lam_m), rel_groups(r["u0"], u_m, D.n)
     after = rel_inf(r["lam"], lam_m), rel_groups(r["u"], u_m, D.n)
     norm_u = rel(r["u"], u_m)
-    print(f"RT_{k} {n}^3 contrast <= 1e6, {n32} FP32 elements: S/row {eS:.1e}; lambda {before[0]:.1e} -> "
+    print(f"RT_{k} {n}^3 contrast <= 1e6, {n32} FP32 elements, {'FP32' if op32 else 'FP64'} PCG operator: "
+          f"S/row {eS:.1e}; lambda {before[0]:.1e} -> "
           f"{after[0]:.1e}, u/element {before[1]:.1e} -> {after[1]:.1e} (norm-wise {norm_u:.1e}); jumps "
           + " ".join(f"{j:.1e}" for j in r["jumps"])
           + f" | against the primal oracle: u/element {rel_groups(r['u'], u_p, D.n):.1e}; FP64 GPU path against "
@@ -66,3 +71,17 @@ def test_autotuned_mixed_path_reaches_1e9_at_contrast_1e6(k, n):
     assert after[1] <= 1e-9 and norm_u <= 1e-9
     assert after[0] <= 1e-8
     assert r["jumps"][-1] < 1e-3 * r["jumps"][0]
+
+
+def test_mixed_operator_rules():
+    """The operator switch exists on mixed contexts only and validates its argument."""
+    from paper_1801_08914_gb300 import hyb
+    p = inputs.random_problem(3, 1, 0.2, 480, 1e-2, 1e2)
+    c64 = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta))
+    assert hyb.hyb_set_mixed_operator(c64, True, check=False) == hyb.HYB_ERR_INVALID_ARG
+    c64.close()
+    cm = hyb.hyb_setup(dev(p.vertices), p.nx, p.ny, p.nz, p.order, dev(p.alpha), dev(p.beta),
+                       precision=hyb.HYB_MIXED, contrast_threshold=1e6)
+    assert hyb.lib().hyb_set_mixed_operator(cm.handle, 2) == hyb.HYB_ERR_INVALID_ARG
+    assert hyb.hyb_set_mixed_operator(cm, False) == hyb.HYB_OK
+    cm.close()
