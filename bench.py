@@ -80,14 +80,21 @@ def parse_args(argv=None):
                     help="hybridization, or static condensation of the interior dofs (FP64 only)")
     ap.add_argument("--refine", type=int, default=None,
                     help="FP64 refinement steps after the solve (hyb_refine; for --precision mixed)")
-    ap.add_argument("--refine-rtol", type=float, default=1e-6, help="inner PCG tolerance of a refinement step")
+    ap.add_argument("--refine-rtol", type=float, default=None,
+                    help="inner PCG tolerance of a refinement step (configs 3/5: 1e-3, else 1e-6)")
+    ap.add_argument("--mixed-rtol", type=float, default=1e-4,
+                    help="configs 3/5: PCG tolerance of the mixed arm's first solve (its refinement steps then "
+                         "run until ||C u|| / ||g|| <= --rtol, at most --refine steps)")
     ap.add_argument("--pcg", choices=["fused", "split"], default="fused",
                     help="PCG launch form: one cooperative launch per 64 iterations, or 3 launches per iteration")
     ap.add_argument("--assembly-only", action="store_true",
                     help="time only the element phase (assemble + recover with lambda = 0); per-config rates")
     args = ap.parse_args(argv)
-    if args.refine is None:          # the precision workloads refine the mixed arm twice by default
-        args.refine = 2 if str(args.config) in ("3", "5") and not args.single_arm else 0
+    precision = str(args.config) in ("3", "5") and not args.single_arm
+    if args.refine is None:          # the precision workloads refine the mixed arm (at most 4 steps)
+        args.refine = 4 if precision else 0
+    if args.refine_rtol is None:
+        args.refine_rtol = 1e-3 if precision else 1e-6
     return args
 
 
@@ -740,18 +747,29 @@ def time_full_path(hyb, ctx, load, lam, u, args, refine, flush, stream):
     flush.fill_(7)
     ev = [_event_pair()[0] for _ in range(5)]
     hyb.hyb_set_profiling(ctx, True)
+    rtol0 = args.mixed_rtol if refine else args.rtol
     ev[0].record(stream)
     hyb.hyb_assemble_reduced(ctx, load)
     ev[1].record(stream)
-    it, rr, st = hyb.hyb_solve_reduced(ctx, args.rtol, args.maxit, lam, check=False)
+    it, rr, st = hyb.hyb_solve_reduced(ctx, rtol0, args.maxit, lam, check=False)
     if st != hyb.HYB_OK:
         raise hyb.HybError(st, "hyb_solve_reduced")
     ev[2].record(stream)
     hyb.hyb_recover(ctx, lam, u)
     ev[3].record(stream)
-    jumps = None
+    jumps, steps = None, 0
     if refine:
-        jumps, _ = hyb.hyb_refine(ctx, refine, args.refine_rtol, args.maxit, lam, u)
+        # FP64 refinement steps until the jump ||C u|| / ||g|| (the reduced residual with the exact
+        # H) meets the FP64 arm's stopping rule rtol, at most `refine` steps
+        jumps = []
+        for _ in range(refine):
+            jj, _ = hyb.hyb_refine(ctx, 1, args.refine_rtol, args.maxit, lam, u)
+            if not jumps:
+                jumps.append(jj[0])
+            jumps.append(jj[1])
+            steps += 1
+            if jj[1] <= args.rtol:
+                break
     ev[4].record(stream)
     torch.cuda.synchronize()
     prof = hyb.hyb_get_profile(ctx)
@@ -764,8 +782,8 @@ def time_full_path(hyb, ctx, load, lam, u, args, refine, flush, stream):
            "launches": int(sum(v[1] for v in prof.values())),
            "pcg_ms_per_iteration": None}
     if refine:
-        out.update(refine_ms=ms[3], refine_steps=refine, refine_inner_rtol=args.refine_rtol,
-                   jump_per_step=jumps)
+        out.update(pcg_rtol=rtol0, refine_ms=ms[3], refine_steps=steps, refine_inner_rtol=args.refine_rtol,
+                   jump_per_step=jumps, jump_target=args.rtol)
     pcg_dev = prof["spmv"][0] + prof["pcg_vector"][0] + prof["pcg_fused"][0]
     out["pcg_ms_per_iteration"] = ms[1] / it if it else None
     out["reduced_dofs_per_s"] = ctx.sizes()["n_lambda"] / (ms[1] * 1e-3) if ms[1] > 0 else None
@@ -817,13 +835,21 @@ def measure_errors(hyb, cfg, n, args, oracle_procs, dev):
         sz = ctx.sizes()
         lam = torch.zeros(sz["n_lambda"], dtype=torch.float64, device=dev)
         u = torch.zeros(sz["n_elem"], sz["n_loc"], dtype=torch.float64, device=dev)
-        hyb.hyb_solve_reduced(ctx, args.rtol, args.maxit, lam)
+        # the schedule of the timed full path: the mixed arm's first solve to --mixed-rtol, then
+        # refinement steps until ||C u|| / ||g|| <= --rtol
+        hyb.hyb_solve_reduced(ctx, args.mixed_rtol if mixed and args.refine else args.rtol, args.maxit, lam)
         hyb.hyb_recover(ctx, lam, u)
         g0 = dict(lam=lam.cpu().numpy().copy(), u=u.cpu().numpy().copy())
+        jumps = []
         if mixed and args.refine:
-            hyb.hyb_refine(ctx, args.refine, args.refine_rtol, args.maxit, lam, u)
+            for _ in range(args.refine):
+                jj, _ = hyb.hyb_refine(ctx, 1, args.refine_rtol, args.maxit, lam, u)
+                jumps += jj if not jumps else jj[1:]
+                if jj[1] <= args.rtol:
+                    break
         torch.cuda.synchronize()
-        gpu[arm] = dict(red=red, lam=lam.cpu().numpy(), u=u.cpu().numpy(), unrefined=g0, split=ctx.precision_split())
+        gpu[arm] = dict(red=red, lam=lam.cpu().numpy(), u=u.cpu().numpy(), unrefined=g0, split=ctx.precision_split(),
+                        jumps=jumps)
         ctx.close()
     ref = {}
     for route, (pr, path) in oracle_procs.items():
@@ -854,7 +880,8 @@ def measure_errors(hyb, cfg, n, args, oracle_procs, dev):
                    "primal oracle = A_T = alpha M + beta K and its Cholesky (FP64, accurate to kappa(A_T) eps: "
                    "~1e-7 in u at this contrast); mixed-form oracle = Sec. 3.2's saddle route (FP64, accurate "
                    "at any contrast)",
-           "solve": {"pcg_rtol": args.rtol, "refine_steps_mixed": args.refine, "refine_inner_rtol": args.refine_rtol}}
+           "solve": {"pcg_rtol": args.rtol, "mixed_first_rtol": args.mixed_rtol, "refine_max_steps": args.refine,
+                     "refine_inner_rtol": args.refine_rtol}}
     for arm, gv in gpu.items():
         red = gv["red"]
         for route, r in ref.items():
@@ -867,6 +894,7 @@ def measure_errors(hyb, cfg, n, args, oracle_procs, dev):
                 e["u_element_before_refinement"] = rgroups(gv["unrefined"]["u"], r["u"], nloc)
                 e["lambda_inf_before_refinement"] = rinf(gv["unrefined"]["lam"], r["lam"])
             out[f"{arm}_vs_{route}_oracle"] = e
+    out["mixed_jumps"] = gpu["mixed"]["jumps"]
     out["mixed_split"] = {"fp64_elements": gpu["mixed"]["split"][0], "fp32_elements": gpu["mixed"]["split"][1],
                           "threshold": gpu["mixed"]["split"][2]}
     return out

@@ -78,7 +78,8 @@ typedef struct hyb_ctx hyb_ctx;
  *  precision  : HYB_FP64, or HYB_MIXED: elements whose contrast beta/alpha is at most
  *               contrast_threshold are eliminated in FP32 through the hybridized mixed
  *               form (Sec. 3.2: A^-1 = M^-1 - M^-1 D Z^-1 D^T M^-1, every factor well
- *               conditioned), with the load term and the recovery refined against an FP64
+ *               conditioned): S_T and the load term g_T carry FP32-level error (hyb_refine
+ *               removes it), the recovery's element solve is refined against an FP64
  *               residual; the others use the FP64 path. The reduced system is accumulated
  *               in FP64; the PCG keeps its iterate, residual and reductions in FP64 and
  *               applies H from an FP32 copy of its values (hyb_set_mixed_operator); the
@@ -222,10 +223,10 @@ int hyb_set_pcg_fused(hyb_ctx* ctx, int on);
  *  and hyb_refine applies.
  *  1 (default): when any element is eliminated in FP32, an FP32 copy of H's values, rounded
  *  once the assembly's FP64 accumulation is complete (a context whose elements all take the
- *  FP64 path keeps the FP64 values). Each lane forms its share of a row from FP32 products of those values and of an FP32
- *  copy of the preconditioned residual; the lanes' partial sums are added in FP64, and the
- *  iterate, residual, direction and every reduction stay FP64. H of a mixed context carries the
- *  FP32 elimination's error (~1e-7 relative) already; the rounding adds error of the same kind and
+ *  FP64 path keeps the FP64 values). Row sums are formed in FP32 from products of those values
+ *  and of an FP32 copy of the preconditioned residual, then widened to FP64; the iterate,
+ *  residual, direction and every reduction stay FP64. H of a mixed context carries the FP32
+ *  elimination's error (~1e-7 relative) already; the rounding adds error of the same kind and
  *  size. hyb_refine measures its residual as the FP64 jump of the recovered flux, which does not
  *  depend on this operator, so the refined solution does not either.
  *  0: the FP64 values.

@@ -11,8 +11,9 @@
 //    L_M = chol(M), Xd = L_M^{-1} D, L_Z = chol(G^{-1} + Xd^T Xd),
 //    Y = L_M,bb^{-1}, P = Xd_b^T Y, V = L_Z^{-1} P,
 //    (A^{-1})_bb = Y^T Y - V^T V,   S_T = D_c (A^{-1})_bb D_c   (C_T = [0 D_c]),
-// accumulated into the FP64 CSR values. The load term g_T = C_T A^{-1} f_T and the
-// recovery x_T = A^{-1}(f_T - C_T^T lambda) are refined in the mixed variables (x, q),
+// accumulated into the FP64 CSR values, and the load term g_T = C_T A^{-1} f_T from one
+// FP32 solve (both carry FP32-level error, which the global FP64 refinement removes). The
+// recovery x_T = A^{-1}(f_T - C_T^T lambda) is refined in the mixed variables (x, q),
 // q = G D^T x, against FP64 residuals of that (well-conditioned) saddle system, with M, D,
 // D^T and G applied matrix-free in FP64; refining A x = f directly does not converge at
 // high contrast because the two Woodbury terms cancel in FP32.

@@ -78,10 +78,14 @@ struct MT {
   static_assert(ZTS % 4 == 0 && (D64 * 2) % 4 == 0, "16-byte aligned tile blocks");
 };
 
-// Refinement steps of each element solve: every step multiplies the error by about
-// kappa(M, Z) u_32 <= 5e-5, so one step takes the FP32 solve (1e-7) to ~5e-12, far below the
-// error the FP32 S_T puts into lambda (1e-6) and below what the global FP64 refinement needs.
+// Refinement steps of the recovery's element solve: every step multiplies the error by about
+// kappa(M, Z) u_32 <= 5e-5, so one step takes the FP32 solve (1e-7) to ~5e-12, below what the
+// global FP64 refinement needs: its residual, the jump C u of the recovered flux, is only as
+// accurate as u_T. The assembly's load term g_T = C_T A^{-1} f_T is left at the FP32 solve's
+// accuracy: its error enters the reduced right-hand side as the FP32 S_T's error enters H, and
+// the global refinement, whose residual does not depend on g, removes both.
 constexpr int kRefineSteps = 1;
+constexpr int kAssemblyRefineSteps = 0;
 
 using tiles::tcol;
 
@@ -520,7 +524,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   }
 
   // ---- the refined element solve: g_T (assembly) or u_T (recovery)
-  refine_tiled<K>(f, x, qv, kRefineSteps, alpha, beta, bmask, g6, gd, Vc, Dc, Vo, DcO64, dofcode, Lt, Xd, Zt, Gi, r, ut, rq,
+  refine_tiled<K>(f, x, qv, RECOVER ? kRefineSteps : kAssemblyRefineSteps, alpha, beta, bmask, g6, gd, Vc, Dc, Vo, DcO64, dofcode, Lt, Xd, Zt, Gi, r, ut, rq,
                   U, Wv, Dv, xc, t1, t2, vec, tq, tmpq);
   if constexpr (RECOVER) {
     double* ue = u_out + e * (int64_t)N;

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "hyb_internal.h"
 
@@ -87,16 +88,16 @@ __device__ __forceinline__ int scatter_row(int j, int gl) {
   return row;
 }
 
-template <int NFN, int W>
-__device__ __forceinline__ void face_reduce(double (&acc)[NFN], int gl) {
+template <int NFN, int W, typename T = double>
+__device__ __forceinline__ void face_reduce(T (&acc)[NFN], int gl) {
   if constexpr (NFN % W == 0) {
 #pragma unroll
     for (int o = W / 2, S = NFN; o > 0; o >>= 1, S >>= 1) {
       const bool hi = gl & o;
 #pragma unroll
       for (int j = 0; j < S / 2; ++j) {
-        const double keep = hi ? acc[j + S / 2] : acc[j];
-        const double send = hi ? acc[j] : acc[j + S / 2];
+        const T keep = hi ? acc[j + S / 2] : acc[j];
+        const T send = hi ? acc[j] : acc[j + S / 2];
         acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o, W);
       }
     }
@@ -416,10 +417,10 @@ struct GridBar {
 // The iteration loop of one problem run by nvb cooperating blocks (vb = this block's index
 // among them); `bar` is their arrival counter. The single-problem kernel runs it with the
 // whole grid, the batch kernel with a team of blocks per problem.
-// F32: the operator is the FP32 copy of the values (mixed contexts): each lane forms its share
-// of a row in FP32 (products of FP32 values and the FP32 copy of z, ~len / W terms), the
-// lanes' partial sums are combined in FP64, and every vector, scalar and reduction of the
-// iteration stays FP64.
+// F32: the operator is the FP32 copy of the values (mixed contexts): each of the W lanes of a
+// face forms its share of the face's rows in FP32 (products of FP32 values and the FP32 copy of
+// z, ~len / W terms), the lanes' partial sums are reduced in FP32 and the row sums widened to
+// FP64; every vector, scalar and reduction of the iteration stays FP64.
 template <int NFN, int W, bool F32>
 __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, double rtol2, GridBar* bar, int vb,
                                                int nvb, double* sh, double* bc) {
@@ -444,25 +445,21 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
     double pq = 0.0;
     for (int64_t base = warp * FPW; base < nfaces; base += nwarps * FPW) {
       const int64_t f = base + sub;
-      double acc[NP];
+      using AccT = typename std::conditional<F32, float, double>::type;
+      AccT acc[NP];
 #pragma unroll
-      for (int m = 0; m < NP; ++m) acc[m] = 0.0;
+      for (int m = 0; m < NP; ++m) acc[m] = AccT(0);
       if (f < nfaces) {
         const int64_t r0 = f * NFN;
         const int64_t lo = __ldcs(a.row_ptr + r0);
         const int len = (int)(__ldcs(a.row_ptr + r0 + 1) - lo);
         if constexpr (F32) {
-          float acc32[NFN];
-#pragma unroll
-          for (int m = 0; m < NFN; ++m) acc32[m] = 0.0f;
 #pragma unroll 4
           for (int t = gl; t < len; t += W) {
             const float zj = __ldcg(a.z32 + __ldcs(a.col + lo + t));
 #pragma unroll
-            for (int m = 0; m < NFN; ++m) acc32[m] = fmaf(__ldcs(a.val32 + lo + (int64_t)m * len + t), zj, acc32[m]);
+            for (int m = 0; m < NFN; ++m) acc[m] = fmaf(__ldcs(a.val32 + lo + (int64_t)m * len + t), zj, acc[m]);
           }
-#pragma unroll
-          for (int m = 0; m < NFN; ++m) acc[m] = (double)acc32[m];
         } else {
 #pragma unroll 4
           for (int t = gl; t < len; t += W) {
@@ -472,7 +469,7 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
           }
         }
       }
-      face_reduce<NP, W>(acc, gl);
+      face_reduce<NP, W, AccT>(acc, gl);
       if constexpr (kScatter) {
         if (f < nfaces) {
 #pragma unroll
@@ -481,8 +478,9 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
             if (row >= NFN) continue;
             const int64_t i = f * NFN + row;
             const double zi = __ldcg(a.z + i);
+            const double hz = (double)acc[j];
             const double pi = first ? zi : fma(beta, a.p[i], zi);
-            const double qi = first ? acc[j] : fma(beta, a.q[i], acc[j]);
+            const double qi = first ? hz : fma(beta, a.q[i], hz);
             a.p[i] = pi;
             a.q[i] = qi;
             pq = fma(pi, qi, pq);
@@ -495,8 +493,9 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
             if (gl == m % W) {
               const int64_t i = f * NFN + m;
               const double zi = __ldcg(a.z + i);
+              const double hz = (double)acc[m];
               const double pi = first ? zi : fma(beta, a.p[i], zi);
-              const double qi = first ? acc[m] : fma(beta, a.q[i], acc[m]);
+              const double qi = first ? hz : fma(beta, a.q[i], hz);
               a.p[i] = pi;
               a.q[i] = qi;
               pq = fma(pi, qi, pq);
@@ -827,11 +826,13 @@ cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void*
   cudaError_t e;
   if (a.val32 && !a.z32) return cudaErrorInvalidValue;
   if (a.val32) {
+    // FP32 values: 8 lanes per face load 32 contiguous bytes of a row per step (a full sector),
+    // and the lanes' partial sums are reduced in FP32
     switch (a.nfn) {
-      case 1: e = launch_fused<1, 4, true>(a, count, rtol, bar, s); break;
-      case 4: e = launch_fused<4, 4, true>(a, count, rtol, bar, s); break;
-      case 9: e = launch_fused<9, 4, true>(a, count, rtol, bar, s); break;
-      case 16: e = launch_fused<16, 4, true>(a, count, rtol, bar, s); break;
+      case 1: e = launch_fused<1, 8, true>(a, count, rtol, bar, s); break;
+      case 4: e = launch_fused<4, 8, true>(a, count, rtol, bar, s); break;
+      case 9: e = launch_fused<9, 8, true>(a, count, rtol, bar, s); break;
+      case 16: e = launch_fused<16, 8, true>(a, count, rtol, bar, s); break;
       default: e = cudaErrorInvalidValue;
     }
   } else {

@@ -127,8 +127,8 @@ def test_full_size_sampled_rows_and_recovery(cfg, nsample):
 def test_full_size_mixed_sampled_rows_and_recovery(cfg, nsample):
     """Mixed precision, autotuned threshold (all elements FP32 up to beta/alpha = 1e6) at the
     precision workloads 96^3 RT_2 and 64^3 RT_3. The reference is the oracle's mixed-form
-    route (Sec. 3.2), accurate at this contrast. Bounds: S per row 100 u_32 kappa_w (the
-    FP32 elimination of the well-conditioned M and Z); g and the refined element solve of the
+    route (Sec. 3.2), accurate at this contrast. Bounds: S and g per row 100 u_32 kappa_w (the
+    FP32 elimination of the well-conditioned M and Z); the refined element solve of the
     recovery (lambda = 0) (100 u_32 kappa_w)^2, one FP64-residual refinement step applied to
     an FP32 solve, floored at 1e-10."""
     import torch
@@ -145,7 +145,7 @@ def test_full_size_mixed_sampled_rows_and_recovery(cfg, nsample):
     sample = [int(x) for x in rng.choice(E, size=nsample, replace=False)]
     bS = lambda *es: 100 * U32 * kappa_w(D, es)
     bg = lambda *es: max(1e-10, bS(*es) ** 2)
-    checked, wS, wg = sampled_rows(ctx, p, D, sample, D.element_reduced_mixed, bS, bg)
+    checked, wS, wg = sampled_rows(ctx, p, D, sample, D.element_reduced_mixed, bS, bS)
     sz = ctx.sizes()
     lam0 = torch.zeros(sz["n_lambda"], dtype=torch.float64, device="cuda")
     u = torch.empty(E, sz["n_loc"], dtype=torch.float64, device="cuda")

@@ -94,7 +94,9 @@ def test_mixed_threshold_and_refinement(k, pexp):
     hyb.hyb_assemble_reduced(ctx, dev(p.load))
     sz = ctx.sizes()
     lam = torch.zeros(sz["n_lambda"], dtype=torch.float64, device="cuda")
-    it, rr, st = hyb.hyb_solve_reduced(ctx, 1e-15, 50000, lam, check=False)
+    # the mixed context's PCG applies H from its FP32 copy: its first solve goes to 1e-10, the
+    # FP64 refinement steps take the jump the rest of the way
+    it, rr, st = hyb.hyb_solve_reduced(ctx, 1e-10, 50000, lam, check=False)
     assert st == hyb.HYB_OK
     u = torch.zeros(sz["n_elem"], sz["n_loc"], dtype=torch.float64, device="cuda")
     hyb.hyb_recover(ctx, lam, u)
