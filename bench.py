@@ -81,7 +81,7 @@ def parse_args(argv=None):
     ap.add_argument("--refine", type=int, default=None,
                     help="FP64 refinement steps after the solve (hyb_refine; for --precision mixed)")
     ap.add_argument("--refine-rtol", type=float, default=None,
-                    help="inner PCG tolerance of a refinement step (configs 3/5: 1e-3, else 1e-6)")
+                    help="inner PCG tolerance of a refinement step (configs 3/5: 1e-4, else 1e-6)")
     ap.add_argument("--mixed-rtol", type=float, default=1e-4,
                     help="configs 3/5: PCG tolerance of the mixed arm's first solve (its refinement steps then "
                          "run until ||C u|| / ||g|| <= --rtol, at most --refine steps)")
@@ -94,7 +94,7 @@ def parse_args(argv=None):
     if args.refine is None:          # the precision workloads refine the mixed arm (at most 4 steps)
         args.refine = 4 if precision else 0
     if args.refine_rtol is None:
-        args.refine_rtol = 1e-3 if precision else 1e-6
+        args.refine_rtol = 1e-4 if precision else 1e-6
     return args
 
 
@@ -761,15 +761,8 @@ def time_full_path(hyb, ctx, load, lam, u, args, refine, flush, stream):
     if refine:
         # FP64 refinement steps until the jump ||C u|| / ||g|| (the reduced residual with the exact
         # H) meets the FP64 arm's stopping rule rtol, at most `refine` steps
-        jumps = []
-        for _ in range(refine):
-            jj, _ = hyb.hyb_refine(ctx, 1, args.refine_rtol, args.maxit, lam, u)
-            if not jumps:
-                jumps.append(jj[0])
-            jumps.append(jj[1])
-            steps += 1
-            if jj[1] <= args.rtol:
-                break
+        jumps = refine_until(hyb, ctx, args, lam, u)
+        steps = len(jumps) - 1
     ev[4].record(stream)
     torch.cuda.synchronize()
     prof = hyb.hyb_get_profile(ctx)
@@ -789,6 +782,25 @@ def time_full_path(hyb, ctx, load, lam, u, args, refine, flush, stream):
     out["reduced_dofs_per_s"] = ctx.sizes()["n_lambda"] / (ms[1] * 1e-3) if ms[1] > 0 else None
     out["pcg_device_ms_all_solves"] = pcg_dev
     return out
+
+
+def refine_until(hyb, ctx, args, lam, u):
+    """FP64 refinement steps (hyb_refine) until ||C u|| / ||g|| <= args.rtol, at most args.refine.
+    Each step's inner PCG tolerance is args.refine_rtol, loosened to half the reduction still
+    needed when that is less (each step contracts the jump by about its inner tolerance).
+    Returns the jump before the first step and after every step."""
+    jumps = []
+    j = None
+    for _ in range(args.refine):
+        inner = args.refine_rtol if j is None else max(args.refine_rtol, min(0.5, 0.5 * args.rtol / j))
+        jj, _ = hyb.hyb_refine(ctx, 1, inner, args.maxit, lam, u)
+        if not jumps:
+            jumps.append(jj[0])
+        jumps.append(jj[1])
+        j = jj[1]
+        if j <= args.rtol:
+            break
+    return jumps
 
 
 def _err_oracle_worker(cfg, n, route, path):
@@ -840,13 +852,7 @@ def measure_errors(hyb, cfg, n, args, oracle_procs, dev):
         hyb.hyb_solve_reduced(ctx, args.mixed_rtol if mixed and args.refine else args.rtol, args.maxit, lam)
         hyb.hyb_recover(ctx, lam, u)
         g0 = dict(lam=lam.cpu().numpy().copy(), u=u.cpu().numpy().copy())
-        jumps = []
-        if mixed and args.refine:
-            for _ in range(args.refine):
-                jj, _ = hyb.hyb_refine(ctx, 1, args.refine_rtol, args.maxit, lam, u)
-                jumps += jj if not jumps else jj[1:]
-                if jj[1] <= args.rtol:
-                    break
+        jumps = refine_until(hyb, ctx, args, lam, u) if mixed and args.refine else []
         torch.cuda.synchronize()
         gpu[arm] = dict(red=red, lam=lam.cpu().numpy(), u=u.cpu().numpy(), unrefined=g0, split=ctx.precision_split(),
                         jumps=jumps)

@@ -221,11 +221,13 @@ int hyb_set_pcg_fused(hyb_ctx* ctx, int on);
 /*
  * hyb_set_mixed_operator -- HYB_MIXED contexts: the operator that the PCG of hyb_solve_reduced
  *  and hyb_refine applies.
- *  1 (default): when any element is eliminated in FP32, an FP32 copy of H's values, rounded
- *  once the assembly's FP64 accumulation is complete (a context whose elements all take the
- *  FP64 path keeps the FP64 values). Row sums are formed in FP32 from products of those values
- *  and of an FP32 copy of the preconditioned residual, then widened to FP64; the iterate,
- *  residual, direction and every reduction stay FP64. H of a mixed context carries the FP32
+ *  1 (default): when any element is eliminated in FP32, an FP32 copy of the diagonally scaled
+ *  H_ij / sqrt(H_ii H_jj) (unit diagonal, so rounding keeps it positive definite even across
+ *  coefficients of very different size), rounded once the assembly's FP64 accumulation is
+ *  complete (a context whose elements all take the FP64 path keeps the FP64 values). Row sums
+ *  are formed in FP32 from products of those values and of an FP32 copy of sqrt(H_jj) z_j, then
+ *  widened to FP64 and multiplied by sqrt(H_ii); the iterate, residual, direction and every
+ *  reduction stay FP64. H of a mixed context carries the FP32
  *  elimination's error (~1e-7 relative) already; the rounding adds error of the same kind and
  *  size. hyb_refine measures its residual as the FP64 jump of the recovered flux, which does not
  *  depend on this operator, so the refined solution does not either.
@@ -257,7 +259,8 @@ enum {
   HYB_K_RECOVER = 3,     /* back substitution */
   HYB_K_SETUP = 4,       /* set-up kernels (column expansion, geometry check) */
   HYB_K_PCG_FUSED = 5,   /* fused PCG iterations: SpMV, updates and reductions in one launch */
-  HYB_K_COUNT = 6
+  HYB_K_STEP = 6,        /* a whole batched step launched as one CUDA graph (hyb_batch_step) */
+  HYB_K_COUNT = 7
 };
 
 /*
@@ -367,6 +370,32 @@ int hyb_solve_reduced_batch(hyb_batch* b, double rtol, int maxit, double* const*
 
 /* hyb_recover_batch -- hyb_recover for every problem. */
 int hyb_recover_batch(hyb_batch* b, const double* const* lambdas, double* const* us);
+
+/*
+ * hyb_batch_step -- the whole hot path for every problem of the batch as ONE CUDA graph launch:
+ *  the element phase of hyb_assemble_reduced_batch (both colours in order), the batched diagonal
+ *  PCG of hyb_solve_reduced_batch (x0 = 0, ||r|| <= rtol ||r0|| per problem, at most maxit
+ *  iterations) and hyb_recover_batch. The PCG loop runs on the device: it is a WHILE node of the
+ *  graph whose body is a chunk of batched iterations followed by a one-block kernel that sets the
+ *  node's condition from every problem's converged / broken-down flags and iteration count
+ *  (cudaGraphSetConditional), so the host neither reads flags nor launches kernels between
+ *  chunks. The graph is captured on the first call and again when rtol changes; loads, ess,
+ *  lambdas, us and maxit go to device argument arrays that the graph reads, so they may change
+ *  between calls. Paper: Thm 2.1 and eq. 2.4 per problem; the batching has no counterpart.
+ *  loads, ess, lambdas, us : host arrays of nprob device pointers (ess may be NULL).
+ *  iters, rel_res : host arrays of nprob or NULL.
+ *  Returns the element phase's or the recovery's error first (HYB_ERR_NOT_SPD, ...), then
+ *  HYB_ERR_BREAKDOWN or HYB_ERR_NOT_CONVERGED (outputs still written) as hyb_solve_reduced_batch.
+ *  Synchronises the batch's stream. Afterwards the batch is in the assembled state
+ *  (hyb_recover_batch, exports and hyb_refine on its contexts apply).
+ */
+int hyb_batch_step(hyb_batch* b, const double* const* loads, const double* const* ess, double rtol, int maxit,
+                   double* const* lambdas, double* const* us, int* iters, double* rel_res);
+
+/* hyb_batch_step_kernels -- host outputs (any may be NULL) describing the step graph: kernel nodes
+ *  outside the PCG loop, kernel nodes of one pass of the loop body, and PCG iterations per pass.
+ *  HYB_ERR_INVALID_ARG before the first hyb_batch_step. */
+int hyb_batch_step_kernels(const hyb_batch* b, int64_t* outside_loop, int64_t* per_pass, int* iterations_per_pass);
 
 /* hyb_batch_context -- the single-problem context of problem i (owned by the batch; do not
  *  destroy), for sizes, exports and error queries. */

@@ -109,7 +109,8 @@ struct hyb_ctx {
   int32_t* slot = nullptr;
   float* Lstore32 = nullptr;
   float* val32 = nullptr;                  // mixed: FP32 copy of the reduced-system values (PCG operator)
-  float* z32 = nullptr;                    // mixed: FP32 copy of the preconditioned residual
+  float* z32 = nullptr;                    // mixed: FP32 copy of the scaled preconditioned residual
+  double* dsq = nullptr;                   // mixed: sqrt of H's diagonal (scaling of the FP32 operator)
   int op32 = 1;                            // mixed: PCG applies H from val32 (1) or from val (0)
   std::vector<int32_t> h_list[2][2];       // host copies: [colour][path] (path 0 = FP64, 1 = FP32)
   double* Lstore = nullptr;
@@ -366,6 +367,7 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
     if ((st = dalloc(c, &c->Lstore32, (size_t)c->n_path[1] * (size_t)mixed_store_floats(order)))) return st;
     if ((st = dalloc(c, &c->val32, c->nnz))) return st;
     if ((st = dalloc(c, &c->z32, c->n_lambda))) return st;
+    if ((st = dalloc(c, &c->dsq, c->n_lambda))) return st;
   } else {
     if ((st = dalloc(c, &c->Lstore, (size_t)E * (size_t)tri_size(s.n)))) return st;
     for (int col = 0; col < 2; ++col) c->h_list[col][0] = lists[col];
@@ -441,7 +443,8 @@ int assemble_impl(hyb_ctx* c, const double* load, const double* ess, int mode) {
   if (c->precision == HYB_MIXED && c->n_path[1] > 0) {
     // the FP32 copy of H that the mixed context's PCG applies (H carries the FP32 elimination's
     // error anyway; the FP64 accumulation above stays the reference for the refinement)
-    cudaError_t e = launch_round_values(c->nnz, c->val, c->val32, c->stream, &c->prof);
+    cudaError_t e = launch_round_values(c->n_lambda, c->row_ptr, c->col, c->val, c->dsq, c->val32, c->stream,
+                                        &c->prof);
     if (e != cudaSuccess) return cuda_status(e);
   }
   st = finish_phase(c);
@@ -620,6 +623,7 @@ int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lamb
   if (c->precision == HYB_MIXED && c->n_path[1] > 0 && c->fused && c->op32 && c->mode == MODE_HYB) {
     a.val32 = c->val32;
     a.z32 = c->z32;
+    a.dsq = c->dsq;
   }
   cudaError_t e = pcg_init(a, c->stream, &c->prof);
   if (e != cudaSuccess) return cuda_status(e);
@@ -877,6 +881,15 @@ struct hyb_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   double graph_rtol = -1.0;
+  // the whole step (hyb_batch_step) as one graph: element phase, PCG initialisation, the PCG
+  // loop as a device-driven WHILE node, recovery; rebuilt when rtol or maxit changes
+  cudaGraph_t step_graph = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  double step_rtol = -1.0;
+  int step_maxit = -1;
+  int64_t step_kernels = 0;                // kernel nodes outside the loop body
+  int64_t step_body_kernels = 0;           // kernel nodes of one pass of the loop body
+  std::vector<PcgArgs> h_pargs_step;
 };
 
 namespace {
@@ -1098,6 +1111,126 @@ int solve_batch_team(hyb_batch* b, double rtol, int maxit, int* iters, double* r
   return st;
 }
 
+// Iterations per pass of the WHILE body of the batched step (the loop stops within a pass once
+// every problem has converged: the kernels of a stopped problem return at once).
+constexpr int kStepChunk = 16;
+
+// Element phase of the batch on stream s (no profiling: it may be captured).
+cudaError_t enqueue_batch_elements(hyb_batch* b, cudaStream_t s, int64_t* kernels) {
+  cudaError_t e = cudaSuccess;
+  for (int col = 0; col < 2 && e == cudaSuccess; ++col)
+    for (int k = 0; k <= kMaxOrder && e == cudaSuccess; ++k) {
+      if (b->n_items[k][col][0]) {
+        e = launch_element_batch(k, MODE_HYB, b->d_eargs, b->items[k][col][0], b->n_items[k][col][0], col, s, nullptr);
+        ++*kernels;
+      }
+      if (e == cudaSuccess && b->n_items[k][col][1]) {
+        e = launch_mixed_batch(k, b->d_eargs, b->items[k][col][1], b->n_items[k][col][1], col, false, nullptr, nullptr,
+                               s, nullptr);
+        ++*kernels;
+      }
+    }
+  return e;
+}
+
+cudaError_t enqueue_batch_recovery(hyb_batch* b, cudaStream_t s, int64_t* kernels) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k <= kMaxOrder && e == cudaSuccess; ++k) {
+    if (b->n_ritems[k][0]) {
+      e = launch_recover_batch(k, MODE_HYB, b->d_rargs, b->ritems[k][0], b->n_ritems[k][0], s, nullptr);
+      ++*kernels;
+    }
+    if (e == cudaSuccess && b->n_ritems[k][1]) {
+      e = launch_mixed_batch(k, b->d_eargs, b->ritems[k][1], b->n_ritems[k][1], 0, true, b->d_lams, b->d_us, s,
+                             nullptr);
+      ++*kernels;
+    }
+  }
+  return e;
+}
+
+void destroy_step_graph(hyb_batch* b) {
+  if (b->step_exec) cudaGraphExecDestroy(b->step_exec);
+  if (b->step_graph) cudaGraphDestroy(b->step_graph);
+  b->step_exec = nullptr;
+  b->step_graph = nullptr;
+}
+
+// Builds the step graph by capturing on a private stream into a graph made here:
+//   [status resets, element launches (both colours in order), PCG flags reset, batched PCG
+//    initialisation] -> WHILE(condition) { kStepChunk batched iterations; condition kernel }
+//   -> [recovery launches].
+// The WHILE condition starts at 1 and is rewritten by the last kernel of every pass.
+int build_step_graph(hyb_batch* b, double rtol) {
+  destroy_step_graph(b);
+  cudaError_t e = cudaSuccess;
+  if (!b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  cudaGraph_t g = nullptr;
+  if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  b->step_graph = g;
+  cudaStream_t cs = b->cap_stream;
+  PcgBatch pb{b->d_pargs, b->spmv_prob, b->spmv_first, b->spmv_count, b->vec_prob, b->vec_first, b->vec_count,
+              b->n_spmv, b->n_vec};
+  int64_t nk = 0, nbody = 0;
+  std::vector<cudaGraphNode_t> tail;
+  e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t el = cudaMemsetAsync(b->status, 0, sizeof(int), cs);
+    for (hyb_ctx* c : b->ctx)
+      if (el == cudaSuccess) el = cudaMemsetAsync(c->err_elem, 0xff, sizeof(long long), cs);
+    if (el == cudaSuccess) el = enqueue_batch_elements(b, cs, &nk);
+    if (el == cudaSuccess) el = cudaMemsetAsync(b->flags_all, 0, 4 * (size_t)b->nprob * sizeof(int), cs);
+    if (el == cudaSuccess) el = pcg_init_batch(pb, cs, nullptr);
+    nk += 2;
+    if (el == cudaSuccess) {
+      cudaStreamCaptureStatus st;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      el = cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &nd);
+      if (el == cudaSuccess) tail.assign(deps, deps + nd);
+    }
+    e = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = el;
+  }
+  cudaGraphConditionalHandle h = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&cn, g, tail.data(), nullptr, tail.size(), &cp);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t el = pcg_iterations_batch(pb, kStepChunk, rtol, cs, nullptr);
+      if (el == cudaSuccess) el = launch_pcg_continue(b->d_pargs, b->nprob, (unsigned long long)h, cs);
+      nbody = 3 * kStepChunk + 1;
+      e = cudaStreamEndCapture(cs, &body);
+      if (e == cudaSuccess) e = el;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, &cn, nullptr, 1, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t el = enqueue_batch_recovery(b, cs, &nk);
+    e = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = el;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->step_exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    destroy_step_graph(b);
+    return cuda_status(e);
+  }
+  b->step_rtol = rtol;
+  b->step_kernels = nk;
+  b->step_body_kernels = nbody;
+  return HYB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1270,6 +1403,74 @@ int hyb_recover_batch(hyb_batch* b, const double* const* lambdas, double* const*
   return batch_finish(b);
 }
 
+int hyb_batch_step(hyb_batch* b, const double* const* loads, const double* const* ess, double rtol, int maxit,
+                   double* const* lambdas, double* const* us, int* iters, double* rel_res) {
+  if (!b || !loads || !lambdas || !us || maxit < 1 || !(rtol >= 0.0)) return HYB_ERR_INVALID_ARG;
+  for (int p = 0; p < b->nprob; ++p)
+    if (!loads[p] || !lambdas[p] || !us[p]) return HYB_ERR_INVALID_ARG;
+  b->h_pargs_step = b->h_pargs;
+  for (int p = 0; p < b->nprob; ++p) {
+    b->h_eargs[p].load = loads[p];
+    b->h_eargs[p].ess = ess ? ess[p] : nullptr;
+    PcgArgs& a = b->h_pargs_step[p];
+    a.x = lambdas[p];
+    a.z = nullptr;                               // the three-launch form keeps D^-1 r in q
+    a.maxit = maxit;
+    b->h_pargs[p].x = lambdas[p];
+    b->h_rargs[p].lambda = lambdas[p];
+    b->h_rargs[p].u = us[p];
+  }
+  cudaStream_t s = b->stream;
+  cudaError_t e = cudaMemcpyAsync(b->d_eargs, b->h_eargs.data(), b->h_eargs.size() * sizeof(ElemArgs),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_pargs, b->h_pargs_step.data(), b->h_pargs_step.size() * sizeof(PcgArgs),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_rargs, b->h_rargs.data(), b->h_rargs.size() * sizeof(RecoverArgs),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_lams, lambdas, b->nprob * sizeof(double*), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_us, us, b->nprob * sizeof(double*), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the argument arrays are in place before any capture
+  if (e != cudaSuccess) return cuda_status(e);
+  int st;
+  if (!b->step_exec || b->step_rtol != rtol) {
+    if ((st = build_step_graph(b, rtol))) return st;
+  }
+  b->step_maxit = maxit;
+  b->mode = MODE_NONE;
+  for (hyb_ctx* c : b->ctx) c->mode = MODE_NONE;
+  const int tok = prof_begin(&b->prof, HYB_K_STEP, s);
+  e = cudaGraphLaunch(b->step_exec, s);
+  prof_end(&b->prof, tok, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::vector<int> hf(4 * (size_t)b->nprob);
+  std::vector<double> hs(8 * (size_t)b->nprob);
+  e = cudaMemcpyAsync(hf.data(), b->flags_all, hf.size() * sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hs.data(), b->scal_all, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if ((st = batch_finish(b))) return st;         // synchronises; element or recovery errors first
+  b->mode = MODE_HYB;
+  for (hyb_ctx* c : b->ctx) c->mode = MODE_HYB;
+  st = HYB_OK;
+  for (int p = 0; p < b->nprob; ++p) {
+    if (iters) iters[p] = hf[4 * p];
+    if (rel_res) rel_res[p] = hs[8 * p + 1] > 0.0 ? std::sqrt(hs[8 * p + 2] / hs[8 * p + 1]) : 0.0;
+    if (hf[4 * p + 2]) st = HYB_ERR_BREAKDOWN;
+    else if (!hf[4 * p + 1] && st == HYB_OK) st = HYB_ERR_NOT_CONVERGED;
+  }
+  return st;
+}
+
+int hyb_batch_step_kernels(const hyb_batch* b, int64_t* outside_loop, int64_t* per_pass, int* iterations_per_pass) {
+  if (!b || !b->step_exec) return HYB_ERR_INVALID_ARG;
+  if (outside_loop) *outside_loop = b->step_kernels;
+  if (per_pass) *per_pass = b->step_body_kernels;
+  if (iterations_per_pass) *iterations_per_pass = kStepChunk;
+  return HYB_OK;
+}
+
 int hyb_batch_context(hyb_batch* b, int problem, hyb_ctx** ctx) {
   if (!b || !ctx || problem < 0 || problem >= b->nprob) return HYB_ERR_INVALID_ARG;
   *ctx = b->ctx[problem];
@@ -1309,6 +1510,7 @@ void hyb_destroy_batch(hyb_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  destroy_step_graph(b);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (hyb_ctx* c : b->ctx) hyb_destroy(c);
   for (void* p : b->allocs) cudaFree(p);

@@ -99,9 +99,12 @@ struct PcgArgs {
   double* q;
   double* dinv;
   double* z;                 // preconditioned residual (fused form only; NULL otherwise)
-  const float* val32;        // mixed contexts, fused form: the values rounded to FP32, applied with
-                             // FP32 products (NULL: the FP64 values)
-  float* z32;                // with val32: z rounded to FP32 for the SpMV's gathers
+  const float* val32;        // mixed contexts, fused form: H_ij / (d_i d_j) rounded to FP32, d_i =
+                             // sqrt(H_ii), applied with FP32 products (NULL: the FP64 values)
+  const double* dsq;         // with val32: d_i = sqrt(H_ii)
+  float* z32;                // with val32: (d z) rounded to FP32 for the SpMV's gathers
+  int maxit;                 // > 0: the iteration kernels stop this problem after maxit iterations
+                             // (the batched step's graph, whose loop runs on the device); <= 0: no limit
   unsigned long long* bar;   // fused form in a batch: this problem's barrier counter (16 bytes, zeroed per launch)
   double* partial;           // per-block partial sums
   double* scal;              // device scalars
@@ -117,6 +120,11 @@ struct PcgBatch {
   int n_spmv, n_vec;                        // grid sizes
 };
 cudaError_t pcg_iterations_batch(const PcgBatch& b, int count, double rtol, cudaStream_t s, Prof* prof);
+// pcg_init for every problem of a batch in two launches (flags must be zeroed first)
+cudaError_t pcg_init_batch(const PcgBatch& b, cudaStream_t s, Prof* prof);
+// one block: sets the graph conditional `handle` to 1 while any problem of the batch is neither
+// converged nor broken down and below its maxit, else 0 (the WHILE node of the batched step)
+cudaError_t launch_pcg_continue(const PcgArgs* probs, int nprob, unsigned long long handle, cudaStream_t s);
 cudaError_t pcg_init(const PcgArgs& a, cudaStream_t s, Prof* prof);
 // Up to `count` iterations in one cooperative launch (grid barriers between the phases).
 // bar: 16 bytes, zeroed before every launch; a.z must be set (pcg_init fills it).
@@ -154,9 +162,12 @@ cudaError_t launch_norm2(int64_t n, const double* v, double* partial, int nblock
                          cudaStream_t s, Prof* prof);
 // y += x
 cudaError_t launch_axpy(int64_t n, const double* x, double* y, cudaStream_t s, Prof* prof);
-// o[i] = (float)v[i], i < n (the FP32 operator of a mixed context's PCG); profiled with the
-// element phase, whose last step it is
-cudaError_t launch_round_values(int64_t n, const double* v, float* o, cudaStream_t s, Prof* prof);
+// The FP32 operator of a mixed context's PCG: dsq[i] = sqrt(H_ii), o[t] = (float)(H_ij / (dsq[i]
+// dsq[j])) (the diagonally scaled matrix: unit diagonal, |entries| <= 1 for SPD H, so rounding
+// it keeps it SPD where rounding H itself would not, e.g. across mass coefficients 10^-8..1);
+// profiled with the element phase, whose last step it is
+cudaError_t launch_round_values(int64_t n_rows, const int64_t* row_ptr, const int32_t* col, const double* v,
+                                double* dsq, float* o, cudaStream_t s, Prof* prof);
 
 struct RecoverArgs {
   int k;

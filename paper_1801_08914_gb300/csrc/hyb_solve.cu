@@ -29,6 +29,11 @@ enum { F_IT = 0, F_CONV = 1, F_BRK = 2, F_TICKET = 3 };
 
 constexpr int kThreads = 256;
 
+// A problem takes no further iterations once converged, broken down or (maxit > 0) at maxit.
+__device__ __forceinline__ bool pcg_stopped(const PcgArgs& a) {
+  return (a.flags[F_CONV] | a.flags[F_BRK]) || (a.maxit > 0 && a.flags[F_IT] >= a.maxit);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -132,8 +137,9 @@ __device__ __forceinline__ double sum_partials(const double* part, int count, in
   return block_sum(v, sh);
 }
 
-__global__ void diag_inv_kernel(PcgArgs a) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+
+__device__ __forceinline__ void diag_inv_body(const PcgArgs& a, int vb, int nvb) {
+  for (int64_t i = vb * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)nvb * blockDim.x) {
     double d = 0.0;
     for (int64_t t = a.row_ptr[i]; t < a.row_ptr[i + 1]; ++t)
       if (a.col[t] == i) d = a.val[t];
@@ -141,30 +147,29 @@ __global__ void diag_inv_kernel(PcgArgs a) {
   }
 }
 
-// x = 0, r = b, p = z = D^{-1} r; rz = r^T z, rr0 = r^T r
-__global__ void pcg_init_kernel(PcgArgs a) {
-  __shared__ double sh[32];
+// x = 0, r = b, p = z = D^{-1} r; rz = r^T z, rr0 = r^T r (blocks vb of nvb)
+__device__ __forceinline__ void pcg_init_body(const PcgArgs& a, int vb, int nvb, double* sh) {
   double rz = 0.0, rr = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = vb * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)nvb * blockDim.x) {
     const double r = a.b[i];
     const double z = a.dinv[i] * r;
     a.x[i] = 0.0;
     a.r[i] = r;
     a.p[i] = z;
     if (a.z) a.z[i] = z;
-    if (a.z32) a.z32[i] = (float)z;
+    if (a.z32) a.z32[i] = (float)(z * a.dsq[i]);
     rz = fma(r, z, rz);
     rr = fma(r, r, rr);
   }
   rz = block_sum(rz, sh);
   rr = block_sum(rr, sh);
   if (threadIdx.x == 0) {
-    a.partial[2 * blockIdx.x] = rz;
-    a.partial[2 * blockIdx.x + 1] = rr;
+    a.partial[2 * vb] = rz;
+    a.partial[2 * vb + 1] = rr;
   }
-  if (last_block(&a.flags[F_TICKET], gridDim.x)) {
-    const double s0 = sum_partials(a.partial, gridDim.x, 2, 0, sh);
-    const double s1 = sum_partials(a.partial, gridDim.x, 2, 1, sh);
+  if (last_block(&a.flags[F_TICKET], nvb)) {
+    const double s0 = sum_partials(a.partial, nvb, 2, 0, sh);
+    const double s1 = sum_partials(a.partial, nvb, 2, 1, sh);
     if (threadIdx.x == 0) {
       a.scal[S_RZ] = s0;
       a.scal[S_RR0] = s1;
@@ -178,6 +183,43 @@ __global__ void pcg_init_kernel(PcgArgs a) {
   }
 }
 
+__global__ void diag_inv_kernel(PcgArgs a) { diag_inv_body(a, blockIdx.x, gridDim.x); }
+
+__global__ void pcg_init_kernel(PcgArgs a) {
+  __shared__ double sh[32];
+  pcg_init_body(a, blockIdx.x, gridDim.x, sh);
+}
+
+__global__ void diag_inv_batch_kernel(const PcgArgs* probs, const int32_t* blk_prob, const int32_t* blk_first,
+                                      const int32_t* blk_count) {
+  const int pb = blk_prob[blockIdx.x];
+  diag_inv_body(probs[pb], blockIdx.x - blk_first[pb], blk_count[pb]);
+}
+
+__global__ void pcg_init_batch_kernel(const PcgArgs* probs, const int32_t* blk_prob, const int32_t* blk_first,
+                                      const int32_t* blk_count) {
+  __shared__ double sh[32];
+  const int pb = blk_prob[blockIdx.x];
+  const PcgArgs a = probs[pb];
+  pcg_init_body(a, blockIdx.x - blk_first[pb], blk_count[pb], sh);
+}
+
+// The WHILE condition of the batched step's PCG loop: 1 while any problem still iterates.
+__global__ void pcg_continue_kernel(const PcgArgs* probs, int nprob, cudaGraphConditionalHandle handle) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+    const PcgArgs& a = probs[p];
+    const int* f = a.flags;
+    if (!(f[F_CONV] | f[F_BRK]) && !(a.maxit > 0 && f[F_IT] >= a.maxit)) mine = 1;
+  }
+  if (mine) any = 1;                          // benign race: every writer stores 1
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
+}
+
 // q = H p, fused with the partial p^T q; last block: alpha = rz / p^T q.
 // The CSR pattern built at set-up gives every row of a face the same column list and
 // stores the (k+1)^2 rows of a face back to back. W lanes take one face: each lane
@@ -185,7 +227,7 @@ __global__ void pcg_init_kernel(PcgArgs a) {
 // so the index stream costs 4 / NFN bytes per nonzero instead of 4.
 template <int NFN, int W>
 __device__ __forceinline__ void spmv_face_body(const PcgArgs& a, int vb, int nvb, double* sh) {
-  if (a.flags[F_CONV] | a.flags[F_BRK]) return;
+  if (pcg_stopped(a)) return;
   constexpr int FPW = 32 / W;                              // faces per warp per step
   const int64_t warp = (vb * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)nvb * blockDim.x) >> 5;
@@ -258,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) spmv_face_kernel(PcgArgs a) {
 constexpr int kUnroll = 4;
 
 __device__ __forceinline__ void pcg_update_body(const PcgArgs& a, double rtol2, int vb, int nvb, double* sh) {
-  if (a.flags[F_CONV] | a.flags[F_BRK]) return;
+  if (pcg_stopped(a)) return;
   const double alpha = a.scal[S_ALPHA];
   double rz = 0.0, rr = 0.0;
   const int64_t stride = (int64_t)nvb * blockDim.x;
@@ -311,7 +353,7 @@ __global__ void __launch_bounds__(kThreads) pcg_update_kernel(PcgArgs a, double 
 
 // p = z + beta p
 __device__ __forceinline__ void pcg_direction_body(const PcgArgs& a, int vb, int nvb) {
-  if (a.flags[F_CONV] | a.flags[F_BRK]) return;
+  if (pcg_stopped(a)) return;
   const double beta = a.scal[S_BETA];
   const int64_t stride = (int64_t)nvb * blockDim.x;
   for (int64_t base = vb * (int64_t)blockDim.x + threadIdx.x; base < a.n; base += kUnroll * stride) {
@@ -478,7 +520,7 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
             if (row >= NFN) continue;
             const int64_t i = f * NFN + row;
             const double zi = __ldcg(a.z + i);
-            const double hz = (double)acc[j];
+            const double hz = F32 ? (double)acc[j] * __ldcg(a.dsq + i) : (double)acc[j];
             const double pi = first ? zi : fma(beta, a.p[i], zi);
             const double qi = first ? hz : fma(beta, a.q[i], hz);
             a.p[i] = pi;
@@ -493,7 +535,7 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
             if (gl == m % W) {
               const int64_t i = f * NFN + m;
               const double zi = __ldcg(a.z + i);
-              const double hz = (double)acc[m];
+              const double hz = F32 ? (double)acc[m] * __ldcg(a.dsq + i) : (double)acc[m];
               const double pi = first ? zi : fma(beta, a.p[i], zi);
               const double qi = first ? hz : fma(beta, a.q[i], hz);
               a.p[i] = pi;
@@ -534,7 +576,7 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
         a.r[i] = r;
         const double z = a.dinv[i] * r;
         a.z[i] = z;
-        if constexpr (F32) a.z32[i] = (float)z;
+        if constexpr (F32) a.z32[i] = (float)(z * a.dsq[i]);
         rzl = fma(r, z, rzl);
         rrl = fma(r, r, rrl);
       }
@@ -581,17 +623,29 @@ __global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
   pcg_fused_body<NFN, W, F32>(a, count, rtol2, bar, blockIdx.x, gridDim.x, sh, bc);
 }
 
-// The FP32 copy of the reduced-system values (mixed contexts), rounded to nearest.
-__global__ void round_values_kernel(int64_t n, const double* __restrict__ v, float* __restrict__ o) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t n2 = n / 2;
-  const double2* v2 = reinterpret_cast<const double2*>(v);
-  float2* o2 = reinterpret_cast<float2*>(o);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += stride) {
-    const double2 x = __ldcs(v2 + i);
-    __stcs(o2 + i, make_float2((float)x.x, (float)x.y));
+// The FP32 operator of a mixed context: first d_i = sqrt(H_ii), then the scaled values rounded
+// to nearest, one warp per row.
+__global__ void diag_sqrt_kernel(int64_t n_rows, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                 const double* __restrict__ v, double* __restrict__ dsq) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_rows; i += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int64_t t = row_ptr[i]; t < row_ptr[i + 1]; ++t)
+      if (col[t] == i) d = v[t];
+    dsq[i] = sqrt(d);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) o[n - 1] = (float)v[n - 1];
+}
+
+__global__ void round_values_kernel(int64_t n_rows, const int64_t* __restrict__ row_ptr,
+                                    const int32_t* __restrict__ col, const double* __restrict__ v,
+                                    const double* __restrict__ dsq, float* __restrict__ o) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w0; i < n_rows; i += nw) {
+    const double si = 1.0 / dsq[i];
+    for (int64_t t = row_ptr[i] + lane; t < row_ptr[i + 1]; t += 32)
+      __stcs(o + t, (float)(__ldcs(v + t) * si / dsq[col[t]]));
+  }
 }
 
 // Batch: block b works for problem team[b].x as block team[b].y of team[b].z, with that
@@ -747,6 +801,21 @@ cudaError_t pcg_init(const PcgArgs& a, cudaStream_t s, Prof* prof) {
   return cudaGetLastError();
 }
 
+cudaError_t pcg_init_batch(const PcgBatch& b, cudaStream_t s, Prof* prof) {
+  int tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
+  diag_inv_batch_kernel<<<b.n_vec, kThreads, 0, s>>>(b.probs, b.vec_prob, b.vec_first, b.vec_count);
+  prof_end(prof, tok, s);
+  tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
+  pcg_init_batch_kernel<<<b.n_vec, kThreads, 0, s>>>(b.probs, b.vec_prob, b.vec_first, b.vec_count);
+  prof_end(prof, tok, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_continue(const PcgArgs* probs, int nprob, unsigned long long handle, cudaStream_t s) {
+  pcg_continue_kernel<<<1, kThreads, 0, s>>>(probs, nprob, (cudaGraphConditionalHandle)handle);
+  return cudaGetLastError();
+}
+
 cudaError_t pcg_iterations(const PcgArgs& a, int count, double rtol, cudaStream_t s, Prof* prof) {
   for (int it = 0; it < count; ++it) {
     int tok = prof_begin(prof, HYB_K_SPMV, s);
@@ -824,7 +893,7 @@ cudaError_t pcg_iterations_team(const PcgArgs* probs, const int4* team, int nblo
 cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void* bar, cudaStream_t s, Prof* prof) {
   const int tok = prof_begin(prof, HYB_K_PCG_FUSED, s);
   cudaError_t e;
-  if (a.val32 && !a.z32) return cudaErrorInvalidValue;
+  if (a.val32 && (!a.z32 || !a.dsq)) return cudaErrorInvalidValue;
   if (a.val32) {
     // FP32 values: 8 lanes per face load 32 contiguous bytes of a row per step (a full sector),
     // and the lanes' partial sums are reduced in FP32
@@ -848,10 +917,14 @@ cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void*
   return e;
 }
 
-cudaError_t launch_round_values(int64_t n, const double* v, float* o, cudaStream_t s, Prof* prof) {
-  if (n == 0) return cudaSuccess;
-  const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
-  round_values_kernel<<<152 * 8, kThreads, 0, s>>>(n, v, o);
+cudaError_t launch_round_values(int64_t n_rows, const int64_t* row_ptr, const int32_t* col, const double* v,
+                                double* dsq, float* o, cudaStream_t s, Prof* prof) {
+  if (n_rows == 0) return cudaSuccess;
+  int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+  diag_sqrt_kernel<<<152 * 4, kThreads, 0, s>>>(n_rows, row_ptr, col, v, dsq);
+  prof_end(prof, tok, s);
+  tok = prof_begin(prof, HYB_K_ELEMENT, s);
+  round_values_kernel<<<152 * 8, kThreads, 0, s>>>(n_rows, row_ptr, col, v, dsq, o);
   prof_end(prof, tok, s);
   return cudaGetLastError();
 }

@@ -27,14 +27,14 @@ HYB_ERR_OOM = -8
 HYB_ERR_TIMEOUT = -9
 HYB_FP64 = 0
 HYB_MIXED = 1
-KERNEL_CLASSES = {"element": 0, "spmv": 1, "pcg_vector": 2, "recover": 3, "setup": 4, "pcg_fused": 5}
+KERNEL_CLASSES = {"element": 0, "spmv": 1, "pcg_vector": 2, "recover": 3, "setup": 4, "pcg_fused": 5, "step": 6}
 
 EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recover",
            "staticcond_assemble", "staticcond_recover", "hyb_get_reduced", "hyb_export_reduced", "hyb_get_sizes",
            "hyb_set_profiling", "hyb_get_profile", "hyb_pcg_solve_noalloc", "hyb_measure_fma_peak",
            "hyb_get_precision_split", "hyb_setup_batch", "hyb_assemble_reduced_batch", "hyb_solve_reduced_batch",
            "hyb_recover_batch", "hyb_batch_context", "hyb_batch_set_profiling", "hyb_batch_get_profile",
-           "hyb_destroy_batch", "hyb_set_mixed_operator",
+           "hyb_destroy_batch", "hyb_set_mixed_operator", "hyb_batch_step", "hyb_batch_step_kernels",
            "hyb_last_error_element", "hyb_destroy", "hyb_status_string"]
 
 
@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_solve_reduced_batch.argtypes = [P, D, I, PP, ctypes.POINTER(I), ctypes.POINTER(D)]
     lib.hyb_recover_batch.argtypes = [P, PP, PP]
     lib.hyb_batch_context.argtypes = [P, I, ctypes.POINTER(P)]
+    lib.hyb_batch_step.argtypes = [P, PP, PP, D, I, PP, PP, ctypes.POINTER(I), ctypes.POINTER(D)]
+    lib.hyb_batch_step_kernels.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I)]
     lib.hyb_batch_set_profiling.argtypes = [P, I]
     lib.hyb_batch_set_graphs.argtypes = [P, I]
     lib.hyb_batch_set_pcg_fused.argtypes = [P, I]
@@ -409,6 +411,25 @@ def hyb_solve_reduced_batch(batch, rtol, maxit, lambdas, check=True):
 def hyb_recover_batch(batch, lambdas, us, check=True):
     st = lib().hyb_recover_batch(batch.handle, _ptr_array(lambdas, "lambdas"), _ptr_array(us, "us"))
     return _check(st, "hyb_recover_batch") if check else st
+
+
+def hyb_batch_step(batch, loads, rtol, maxit, lambdas, us, ess=None, check=True):
+    """The whole batched step as one CUDA graph launch; returns (iterations, rel. residuals, status)."""
+    its = (ctypes.c_int * batch.n)()
+    rr = (ctypes.c_double * batch.n)()
+    st = lib().hyb_batch_step(batch.handle, _ptr_array(loads, "loads"), _ptr_array(ess, "ess", True), float(rtol),
+                              int(maxit), _ptr_array(lambdas, "lambdas"), _ptr_array(us, "us"), its, rr)
+    if check:
+        _check(st, "hyb_batch_step")
+    return list(its), list(rr), st
+
+
+def hyb_batch_step_kernels(batch):
+    """(kernel nodes outside the PCG loop, kernel nodes per loop pass, PCG iterations per pass)."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    _check(lib().hyb_batch_step_kernels(batch.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "hyb_batch_step_kernels")
+    return a.value, b.value, c.value
 
 
 def hyb_batch_set_pcg_fused(batch, on):

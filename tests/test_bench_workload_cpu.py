@@ -35,7 +35,7 @@ def test_precision_workload_defaults():
     """The default run is the precision workload (96^3 RT_2, contrast up to 1e6) with both arms and
     up to four refinement steps on the mixed arm; its name states the mesh, order, coefficients and step."""
     args = bench.parse_args([])
-    assert str(args.config) == "3" and not args.single_arm and args.refine == 4 and args.refine_rtol == 1e-3
+    assert str(args.config) == "3" and not args.single_arm and args.refine == 4 and args.refine_rtol == 1e-4
     w = bench.precision_workload_name(3)
     assert w.startswith("96x96x96 jittered hex mesh (+-0.2h), RT_2") and "beta/alpha 10^U(-2,6)" in w
     assert "element phase a1-a6" in w and "config" not in w

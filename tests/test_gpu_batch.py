@@ -115,3 +115,54 @@ def test_batch_team_fused_pcg():
         print(f"team-fused problem {i} (n={p.nx}, k={p.order}): {itf[i]} it (three-launch {itu[i]}), rel diff {d:.1e}")
         assert d <= 1e-8
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_step_graph_matches_the_three_calls(precision):
+    """hyb_batch_step (element phase, batched PCG with its loop as a device-driven WHILE node,
+    recovery: one CUDA graph launch) against hyb_assemble_reduced_batch + hyb_solve_reduced_batch +
+    hyb_recover_batch: the same reduced systems bitwise, the same iteration counts within 2 (the
+    initialisation sums its reductions over other block ranges), lambda and u at the parity tests'
+    conditioning bound; a second step with other loads reuses the graph; maxit is honoured
+    inside the graph."""
+    import torch
+    from paper_1801_08914_gb300 import hyb
+    probs = make_batch([(4, 1), (3, 2), (5, 0), (3, 3), (2, 2), (6, 1)])
+    verts = [dev(p.vertices) for p in probs]
+    b = hyb.hyb_setup_batch([(v, p.nx, p.ny, p.nz) for v, p in zip(verts, probs)], [p.order for p in probs],
+                            [dev(p.alpha) for p in probs], [dev(p.beta) for p in probs], precision=precision,
+                            contrast_threshold=1e4)
+    sizes = [b.context(i).sizes() for i in range(len(probs))]
+    zl = lambda: [torch.zeros(s["n_lambda"], dtype=torch.float64, device="cuda") for s in sizes]
+    zu = lambda: [torch.zeros(s["n_elem"], s["n_loc"], dtype=torch.float64, device="cuda") for s in sizes]
+    rng = np.random.default_rng(9)
+    for step in range(2):
+        loads = [dev(p.load * (1.0 if step == 0 else rng.uniform(0.5, 2.0))) for p in probs]
+        hyb.hyb_assemble_reduced_batch(b, loads)
+        ref_red = [{k: v.cpu().numpy() for k, v in hyb.hyb_export_reduced(b.context(i)).items()}
+                   for i in range(len(probs))]
+        l3, u3 = zl(), zu()
+        it3, _, st = hyb.hyb_solve_reduced_batch(b, 1e-13, 20000, l3)
+        assert st == hyb.HYB_OK
+        hyb.hyb_recover_batch(b, l3, u3)
+        ls, us = zl(), zu()
+        its, rrs, st = hyb.hyb_batch_step(b, loads, 1e-13, 20000, ls, us)
+        assert st == hyb.HYB_OK and max(rrs) <= 1e-13
+        for i, p in enumerate(probs):
+            red = {k: v.cpu().numpy() for k, v in hyb.hyb_export_reduced(b.context(i)).items()}
+            assert np.array_equal(red["val"], ref_red[i]["val"]) and np.array_equal(red["rhs"], ref_red[i]["rhs"])
+            D = Discretization.from_problem(p)
+            H, g = D.hybridize()
+            ev = np.linalg.eigvalsh(H.toarray())
+            tol = max(1e-12, (ev[-1] / ev[0]) * 100 * EPS)
+            el = rel_inf(ls[i].cpu().numpy(), l3[i].cpu().numpy())
+            eu = rel_inf(us[i].cpu().numpy(), u3[i].cpu().numpy())
+            print(f"step {step} problem {i} (n={p.nx}, k={p.order}, prec={precision}): graph {its[i]} it, "
+                  f"three calls {it3[i]} it; lambda {el:.1e} u {eu:.1e}")
+            assert abs(its[i] - it3[i]) <= 2 and el <= tol and eu <= tol
+    outside, per_pass, ipp = hyb.hyb_batch_step_kernels(b)
+    assert per_pass == 3 * ipp + 1 and outside > 0
+    # maxit inside the graph: every problem stops after exactly 5 iterations
+    its, rrs, st = hyb.hyb_batch_step(b, [dev(p.load) for p in probs], 1e-13, 5, zl(), zu(), check=False)
+    assert st == hyb.HYB_ERR_NOT_CONVERGED and its == [5] * len(probs)
+    b.close()
