@@ -1066,8 +1066,70 @@ def run_precision(args):
         print(json.dumps(line), flush=True)
 
 
+def _oracle_batch_worker(problems, stride, first):
+    """Element phase of the CPU FP64 oracle on every `stride`-th element (from `first`) of the given
+    problems of the batched workload; prints {order: [elements, seconds]}."""
+    from oracle.hybrid import Discretization
+    from paper_1801_08914_gb300 import inputs
+    out = {}
+    for pidx in problems:
+        p = inputs.batch_problem(pidx)
+        D = Discretization.from_problem(p)
+        els = list(range(first, p.n_elem, stride))
+        t0 = time.perf_counter()
+        D.hybridize(elements=els)
+        dt = time.perf_counter() - t0
+        e, t = out.get(p.order, (0, 0.0))
+        out[p.order] = (e + len(els), t + dt)
+    print(json.dumps(out))
+
+
+def cpu_baseline_batch(probs_orders, E_per_order, sample=16):
+    """The oracle's element phase on the batched workload: `sample` problems, every stride-th
+    element, one worker process per core; per-order rates weighted by the batch's element counts."""
+    from paper_1801_08914_gb300 import inputs
+    C = host_cores()
+    count = len(probs_orders)
+    per = max(1, sample // 4)
+    picks, seen = [], {k: 0 for k in range(4)}
+    for pidx in range(count):                       # the first `per` problems of every order
+        k = probs_orders[pidx]
+        if seen[k] < per:
+            picks.append(pidx)
+            seen[k] += 1
+    stride = 23
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs = [subprocess.Popen([sys.executable, "-c", f"import bench; bench._oracle_batch_worker({picks!r}, "
+                               f"{stride * C}, {w * stride})"], cwd=ROOT, env=env, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for w in range(C)]
+    t_start = time.perf_counter()
+    tot = {}
+    tmax = 0.0
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        d = json.loads(out.strip().splitlines()[-1])
+        for k, (e, t) in d.items():
+            a = tot.get(int(k), [0, 0.0])
+            tot[int(k)] = [a[0] + e, a[1] + t]
+    wall = time.perf_counter() - t_start
+    rate_core = {k: e / t for k, (e, t) in tot.items() if t > 0}      # elements per core-second, per order
+    # all cores: the batch's per-order element counts at C times the one-core rates
+    t_batch = sum(E_per_order[k] / (C * rate_core[k]) for k in E_per_order if E_per_order[k] and k in rate_core)
+    E = sum(E_per_order.values())
+    return {"value": E / t_batch if t_batch > 0 else None, "unit": "elements/s", "cores": C, "kind": "oracle",
+            "sample": f"element phase a1-a6 of every {stride}-th element of problems {picks} (the first {per} of each order), "
+                      f"{sum(e for e, _ in tot.values())} elements in {wall:.1f} s on {C} worker processes; "
+                      f"per-order core rates {({k: round(v, 1) for k, v in rate_core.items()})} el/s weighted by the "
+                      f"batch's elements per order",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+
+
 def run_batch(args):
-    """The batched workload: 256 independent problems, n ~ U{6..24}, k ~ U{0..3}, one context."""
+    """The batched workload: 256 independent problems, n ~ U{6..24}, k ~ U{0..3}, one batch.
+    A timed step is hyb_batch_step: the element phase, the batched diagonal PCG (its loop a
+    device-driven WHILE node) and the recovery of every problem as one CUDA graph launch."""
     import numpy as np
     import torch
 
@@ -1094,58 +1156,133 @@ def run_batch(args):
     sizes = [b.context(i).sizes() for i in range(len(probs))]
     E = sum(s["n_elem"] for s in sizes)
     N = sum(s["n_lambda"] for s in sizes)
+    nnz = sum(s["nnz"] for s in sizes)
+    orders = [p.order for p in probs]
+    tuned = {}
+    for k in sorted(set(orders)):
+        for path, name in ((0, "fp64"), (1, "fp32")):
+            m, g = hyb.hyb_batch_get_autotune(b, k, path)
+            if m or g or (path == 1) == mixed:
+                tuned[f"RT_{k} {name}"] = ("one CTA per element" if m == 0 else
+                                           f"{g} persistent CTAs ({m} x resident)")
+    E_per_order = {k: sum(s["n_elem"] for s, o in zip(sizes, orders) if o == k) for k in range(4)}
     lams = [torch.zeros(s["n_lambda"], dtype=torch.float64, device=dev) for s in sizes]
     us = [torch.zeros(s["n_elem"], s["n_loc"], dtype=torch.float64, device=dev) for s in sizes]
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    iters = []
+    its_last = []
 
-    def step():
-        hyb.hyb_assemble_reduced_batch(b, loads)
-        if not args.assembly_only:
-            its, rr, st = hyb.hyb_solve_reduced_batch(b, args.rtol, args.maxit, lams, check=False)
-            if st != hyb.HYB_OK:
-                raise hyb.HybError(st, "hyb_solve_reduced_batch")
-            iters.append(max(its))
-        hyb.hyb_recover_batch(b, lams, us)
+    def step(lds):
+        its, rr, st = hyb.hyb_batch_step(b, lds, args.rtol, args.maxit, lams, us, check=False)
+        if st != hyb.HYB_OK:
+            raise hyb.HybError(st, "hyb_batch_step")
+        its_last[:] = its
 
     for _ in range(args.warmup):
-        step()
+        step(loads)
     torch.cuda.synchronize()
-    hyb.hyb_batch_set_profiling(b, True)
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    iters.clear()
     for k in range(args.steps):
         flush.fill_(k & 0xFF)
         ev[k][0].record(stream)
-        step()
+        step(loads)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     barrier()
-    ck = clocks.stop()
-    prof = hyb.hyb_batch_get_profile(b)
     ms = sum(a.elapsed_time(c) for a, c in ev)
     value, ms_max = aggregate(E * args.steps, ms, world, device=dev)
-    elem_ms = prof["element"][0] / args.steps
-    orders = [p.order for p in probs]
+    outside, per_pass, ipp = hyb.hyb_batch_step_kernels(b)
+    passes = max(1, -(-max(its_last) // ipp))
+    launches_per_step = outside + passes * per_pass
+
+    # per-phase attribution of the same work (the three calls, profiled per kernel class)
+    hyb.hyb_batch_set_profiling(b, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hyb.hyb_assemble_reduced_batch(b, loads)
+    e1.record(stream)
+    its, rr, st = hyb.hyb_solve_reduced_batch(b, args.rtol, args.maxit, lams, check=False)
+    hyb.hyb_recover_batch(b, lams, us)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    prof = hyb.hyb_batch_get_profile(b)
+    hyb.hyb_batch_set_profiling(b, False)
+    elem_ms = e0.elapsed_time(e1)
+    pcg_ms = prof["spmv"][0] + prof["pcg_vector"][0] + prof["pcg_fused"][0]
+    it_max = max(its)
+    # roofline of the dominant phase, the batched PCG: one iteration of every problem moves the
+    # SpMV's bytes plus the vector updates' (FP64: 2 nnz flops at the FP64 pipe's rate)
+    fp64_peak = hyb.hyb_measure_fma_peak(True)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    it_ms = pcg_ms / it_max if it_max else float("nan")
+    flops_it = sum(pcg_iteration_flops(s["n_lambda"], s["nnz"]) for s in sizes)
+    bytes_it = sum(pcg_iteration_bytes(s["n_lambda"], s["nnz"], (o + 1) ** 2) for s, o in zip(sizes, orders))
+    tf, gb = flops_it / (it_ms * 1e-3) / 1e12, bytes_it / (it_ms * 1e-3) / 1e9
+    roof = {"kernel": "spmv_batch_kernel + update_batch_kernel + direction_batch_kernel (one batched PCG iteration)",
+            "bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf / fp64_peak,
+            "peak_source": "FP64 FMA throughput measured in this run (hyb_measure_fma_peak)", "traffic": None,
+            "unit_of_work": "one iteration of every problem (the last problems converge later: iterations of "
+                            "converged problems are no-ops, so this is a lower bound)",
+            "algorithmic_flops_per_iteration": flops_it, "algorithmic_bytes_per_iteration": bytes_it,
+            "achieved_gbs": gb, "hbm_peak_gbs": hbm_peak, "hbm_frac": gb / hbm_peak, "avg_iteration_ms": it_ms}
+
+    # end to end: pinned host loads -> the step -> every problem's u to pinned host memory
+    loads_h = [torch.from_numpy(np.ascontiguousarray(p.load)).pin_memory() for p in probs]
+    us_h = [torch.empty(s["n_elem"], s["n_loc"], dtype=torch.float64).pin_memory() for s in sizes]
+    loads_d = [torch.empty_like(l) for l in loads]
+    ke = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(ke):
+        for h, d in zip(loads_h, loads_d):
+            d.copy_(h, non_blocking=True)
+        step(loads_d)
+        for d, h in zip(us, us_h):
+            h.copy_(d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / ke
     line = {
-        "metric": METRIC.replace("FP64 GPU path", "batched, " + ("mixed" if mixed else "FP64")),
+        "metric": "hybridized elements/s, batched (" + ("mixed" if mixed else "FP64") + "), whole step",
         "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": f"{len(probs)} independent problems, n ~ U{{6..24}}, k ~ U{{0..3}}, jitter 0.2h, "
-                               "contrast [1e-2, 1e4]" + (" (element phase only)" if args.assembly_only else ""),
-                   "elements": E, "n_lambda": N, "problems_per_order": [orders.count(k) for k in range(4)],
-                   "pcg_rtol": args.rtol, "pcg_iterations_max": iters[0] if iters else None,
-                   "setup_s": t_setup, "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) before each step"},
-        "gpu_launches": int(sum(v[1] for v in prof.values())),
-        "phases": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()},
+                               f"alpha lognormal(0,1), beta/alpha 10^U(-2,4), N(0,1) loads; timed step: "
+                               f"hyb_batch_step (element phase, batched diagonal PCG to {args.rtol:g}, recovery) "
+                               f"as one CUDA graph launch",
+                   "elements": E, "n_lambda": N, "nnz": nnz, "problems_per_order": [orders.count(k) for k in range(4)],
+                   "elements_per_order": [E_per_order[k] for k in range(4)], "pcg_iterations_max": max(its_last),
+                   "setup_s": t_setup, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (512 MiB write) before each step"},
+        "e2e": {"value": E / (e2e_ms * 1e-3), "unit": "elements/s",
+                "h2d_bytes_per_step": int(sum(p.load.nbytes for p in probs)),
+                "d2h_bytes_per_step": int(sum(s["n_elem"] * s["n_loc"] * 8 for s in sizes)),
+                "path": "pinned host loads -> hyb_batch_step -> every problem's u to pinned host memory"},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "autotuned_element_launches": tuned,
+        "graph": {"kernel_nodes_outside_loop": outside, "kernel_nodes_per_loop_pass": per_pass,
+                  "iterations_per_pass": ipp, "loop_passes_per_step": passes, "graph_launches_per_step": 1},
+        "phases": {"element_ms": elem_ms, "pcg_ms": pcg_ms, "pcg_iterations_max": it_max,
+                   "recover_ms": prof["recover"][0],
+                   "note": "the same work through the three calls, profiled (CUDA events per launch class)"},
         "assembly_elements_per_s": E / (elem_ms * 1e-3) if elem_ms > 0 else None,
+        "roofline": roof,
         "clocks": ck,
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_batch(orders, E_per_order)
+        except Exception as exc:  # reported, not fatal
+            line["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -224,7 +224,10 @@ int hyb_set_pcg_fused(hyb_ctx* ctx, int on);
  *  1 (default): when any element is eliminated in FP32, an FP32 copy of the diagonally scaled
  *  H_ij / sqrt(H_ii H_jj) (unit diagonal, so rounding keeps it positive definite even across
  *  coefficients of very different size), rounded once the assembly's FP64 accumulation is
- *  complete (a context whose elements all take the FP64 path keeps the FP64 values). Row sums
+ *  complete. Only when EVERY element took the FP32 path (contrast <= threshold everywhere): an
+ *  element above the threshold brings a near-null mode of H whose small eigenvalue FP32 rounding
+ *  cannot hold (mass coefficients 10^-8..1 made the PCG break down), so such contexts keep the
+ *  FP64 values, as do contexts whose elements all took the FP64 path. Row sums
  *  are formed in FP32 from products of those values and of an FP32 copy of sqrt(H_jj) z_j, then
  *  widened to FP64 and multiplied by sqrt(H_ii); the iterate, residual, direction and every
  *  reduction stay FP64. H of a mixed context carries the FP32
@@ -396,6 +399,14 @@ int hyb_batch_step(hyb_batch* b, const double* const* loads, const double* const
  *  outside the PCG loop, kernel nodes of one pass of the loop body, and PCG iterations per pass.
  *  HYB_ERR_INVALID_ARG before the first hyb_batch_step. */
 int hyb_batch_step_kernels(const hyb_batch* b, int64_t* outside_loop, int64_t* per_pass, int* iterations_per_pass);
+
+/* hyb_batch_get_autotune -- the element-phase launch shape the set-up's autotuner chose for
+ *  order bin `order` (0..3) and precision path (0 FP64, 1 FP32 mixed form), host outputs (any may
+ *  be NULL): `multiple` of the CTAs resident on the GPU at once (1, 2, 4: persistent CTAs taking
+ *  about elements / grid elements each) or 0 (one CTA per element), and the resulting grid (0 for
+ *  one CTA per element). hyb_setup_batch times the candidates on a unit-cube problem of each
+ *  order and path present (cached per device for the process). No counterpart in the paper. */
+int hyb_batch_get_autotune(const hyb_batch* b, int order, int path, int* multiple, int* grid);
 
 /* hyb_batch_context -- the single-problem context of problem i (owned by the batch; do not
  *  destroy), for sizes, exports and error queries. */

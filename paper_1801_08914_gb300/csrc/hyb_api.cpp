@@ -20,6 +20,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -440,7 +441,7 @@ int assemble_impl(hyb_ctx* c, const double* load, const double* ess, int mode) {
     cudaError_t e = launch_element(c->k, mode, a, c->stream, &c->prof);
     if (e != cudaSuccess) return cuda_status(e);
   }
-  if (c->precision == HYB_MIXED && c->n_path[1] > 0) {
+  if (c->precision == HYB_MIXED && c->n_path[1] > 0 && c->n_path[0] == 0) {
     // the FP32 copy of H that the mixed context's PCG applies (H carries the FP32 elimination's
     // error anyway; the FP64 accumulation above stays the reference for the refinement)
     cudaError_t e = launch_round_values(c->n_lambda, c->row_ptr, c->col, c->val, c->dsq, c->val32, c->stream,
@@ -620,7 +621,11 @@ int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lamb
   a.flags = c->flags;
   a.nblocks = c->nblocks;
   a.nfn = c->sz.nfn;
-  if (c->precision == HYB_MIXED && c->n_path[1] > 0 && c->fused && c->op32 && c->mode == MODE_HYB) {
+  // the FP32 operator only where every element took the FP32 path (contrast <= threshold
+  // everywhere): an element above the threshold brings a near-null mode of H whose eigenvalue
+  // the FP32 rounding cannot hold (soft-hard test, Sec. 6.1, mass 10^-8: PCG breakdown)
+  if (c->precision == HYB_MIXED && c->n_path[1] > 0 && c->n_path[0] == 0 && c->fused && c->op32 &&
+      c->mode == MODE_HYB) {
     a.val32 = c->val32;
     a.z32 = c->z32;
     a.dsq = c->dsq;
@@ -858,6 +863,8 @@ struct hyb_batch {
   PcgArgs* d_pargs = nullptr;
   const double** d_lams = nullptr;
   double** d_us = nullptr;
+  int egrid[kMaxOrder + 1][2] = {};         // [order][path]: CTAs of the element launch (0: one per element)
+  int emult[kMaxOrder + 1][2] = {};         // the autotuned choice: multiple of the resident CTAs, 0 = per element
   int2* items[kMaxOrder + 1][2][2] = {};    // [order][colour][path]
   int64_t n_items[kMaxOrder + 1][2][2] = {};
   int2* ritems[kMaxOrder + 1][2] = {};      // [order][path]
@@ -1034,6 +1041,112 @@ int setup_batch_impl(hyb_batch* b, const hyb_mesh* meshes, const int* orders, co
   return cuda_status(cudaStreamSynchronize(b->stream));
 }
 
+// ---- autotuner of the batched element launches: per (device, order, precision path) the grid
+// as a multiple of the CTAs that fit on the GPU at once (1, 2 or 4: persistent CTAs, each taking
+// about elements / grid elements in turn), or 0 (one CTA per element, the hardware scheduler
+// balancing), whichever runs the element phase of a unit-cube problem of that order fastest
+// (16^3 elements, RT_3 12^3; two colours, two repetitions after a warm-up). Cached per process.
+std::mutex g_grid_mutex;
+std::map<std::tuple<int, int, int>, int> g_grid_mult;
+
+int batch_resident_ctas(int order, int path) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return sms * (path ? mixed_batch_ctas_per_sm(order) : element_batch_ctas_per_sm(order));
+}
+
+int autotune_batch_grid(int order, int path, cudaStream_t s, int* mult) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HYB_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_grid_mutex);
+  const auto key = std::make_tuple(dev, order, path);
+  const auto it = g_grid_mult.find(key);
+  if (it != g_grid_mult.end()) {
+    *mult = it->second;
+    return HYB_OK;
+  }
+  const int n = order >= 3 ? 12 : 16;
+  const int64_t E = (int64_t)n * n * n, nv = (int64_t)(n + 1) * (n + 1) * (n + 1);
+  const int nloc = Sizes::of(order).n;
+  std::vector<double> vh(3 * nv);
+  for (int l = 0; l <= n; ++l)
+    for (int j = 0; j <= n; ++j)
+      for (int i = 0; i <= n; ++i) {
+        const int64_t v = i + (int64_t)(n + 1) * (j + (int64_t)(n + 1) * l);
+        vh[3 * v] = (double)i / n;
+        vh[3 * v + 1] = (double)j / n;
+        vh[3 * v + 2] = (double)l / n;
+      }
+  std::vector<double> ones(E, 1.0);
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, (3 * nv + 2 * E + E * nloc) * sizeof(double)) != cudaSuccess) return HYB_ERR_OOM;
+  double *verts = buf, *alpha = buf + 3 * nv, *beta = alpha + E, *load = beta + E;
+  cudaError_t e = cudaMemcpyAsync(verts, vh.data(), vh.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(alpha, ones.data(), E * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(beta, ones.data(), E * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(load, 0, (size_t)E * nloc * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int st = e == cudaSuccess ? HYB_OK : cuda_status(e);
+  hyb_batch* t = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = 0;
+  if (st == HYB_OK) {
+    t = new (std::nothrow) hyb_batch();
+    if (!t) st = HYB_ERR_OOM;
+  }
+  if (st == HYB_OK) {
+    t->nprob = 1;
+    t->stream = s;
+    t->precision = path ? HYB_MIXED : HYB_FP64;
+    hyb_mesh mesh{n, n, n, verts};
+    const double* al = alpha;
+    const double* be = beta;
+    st = setup_batch_impl(t, &mesh, &order, &al, &be, path ? 1e300 : 0.0);
+  }
+  if (st == HYB_OK) {
+    t->h_eargs[0].load = load;
+    e = cudaMemcpyAsync(t->d_eargs, t->h_eargs.data(), sizeof(ElemArgs), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int resident = batch_resident_ctas(order, path);
+    float best_ms = 0.0f;
+    const int cand[4] = {0, 1, 2, 4};
+    for (int c = 0; c < 4 && e == cudaSuccess && resident > 0; ++c) {
+      const int grid = cand[c] * resident;
+      auto run = [&]() {
+        cudaError_t r = cudaSuccess;
+        for (int col = 0; col < 2 && r == cudaSuccess; ++col)
+          r = path ? launch_mixed_batch(order, t->d_eargs, t->items[order][col][1], t->n_items[order][col][1], col,
+                                        false, nullptr, nullptr, grid, s, nullptr)
+                   : launch_element_batch(order, MODE_HYB, t->d_eargs, t->items[order][col][0],
+                                          t->n_items[order][col][0], col, grid, s, nullptr);
+        return r;
+      };
+      e = run();                                       // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = run();
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+        best_ms = ms;
+        best = cand[c];
+      }
+    }
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (t) hyb_destroy_batch(t);
+  cudaFree(buf);
+  if (st != HYB_OK) return st;
+  g_grid_mult[key] = best;
+  *mult = best;
+  return HYB_OK;
+}
+
 // Batched PCG in the team-fused form: between chunks of 64 iterations the host reads every
 // problem's flags, sorts the unconverged problems by size and runs them in groups of at most
 // an eighth as many problems as the cooperative grid has blocks, one launch per group, the
@@ -1121,12 +1234,13 @@ cudaError_t enqueue_batch_elements(hyb_batch* b, cudaStream_t s, int64_t* kernel
   for (int col = 0; col < 2 && e == cudaSuccess; ++col)
     for (int k = 0; k <= kMaxOrder && e == cudaSuccess; ++k) {
       if (b->n_items[k][col][0]) {
-        e = launch_element_batch(k, MODE_HYB, b->d_eargs, b->items[k][col][0], b->n_items[k][col][0], col, s, nullptr);
+        e = launch_element_batch(k, MODE_HYB, b->d_eargs, b->items[k][col][0], b->n_items[k][col][0], col,
+                                 b->egrid[k][0], s, nullptr);
         ++*kernels;
       }
       if (e == cudaSuccess && b->n_items[k][col][1]) {
         e = launch_mixed_batch(k, b->d_eargs, b->items[k][col][1], b->n_items[k][col][1], col, false, nullptr, nullptr,
-                               s, nullptr);
+                               b->egrid[k][1], s, nullptr);
         ++*kernels;
       }
     }
@@ -1141,7 +1255,7 @@ cudaError_t enqueue_batch_recovery(hyb_batch* b, cudaStream_t s, int64_t* kernel
       ++*kernels;
     }
     if (e == cudaSuccess && b->n_ritems[k][1]) {
-      e = launch_mixed_batch(k, b->d_eargs, b->ritems[k][1], b->n_ritems[k][1], 0, true, b->d_lams, b->d_us, s,
+      e = launch_mixed_batch(k, b->d_eargs, b->ritems[k][1], b->n_ritems[k][1], 0, true, b->d_lams, b->d_us, 0, s,
                              nullptr);
       ++*kernels;
     }
@@ -1255,6 +1369,15 @@ int hyb_setup_batch(int nprob, const hyb_mesh* meshes, const int* orders, const 
   int st;
   try {
     st = setup_batch_impl(b, meshes, orders, alphas, betas, contrast_threshold);
+    // elements per CTA of every order bin and precision path present, autotuned per device
+    for (int k = 0; k <= kMaxOrder && st == HYB_OK; ++k)
+      for (int path = 0; path < 2 && st == HYB_OK; ++path) {
+        if (!b->n_items[k][0][path] && !b->n_items[k][1][path]) continue;
+        int mult = 0;
+        st = autotune_batch_grid(k, path, b->stream, &mult);
+        b->emult[k][path] = mult;
+        b->egrid[k][path] = mult * batch_resident_ctas(k, path);
+      }
   } catch (const std::bad_alloc&) {
     st = HYB_ERR_OOM;
   } catch (...) {
@@ -1283,11 +1406,11 @@ int hyb_assemble_reduced_batch(hyb_batch* b, const double* const* loads, const d
   b->mode = MODE_NONE;
   for (int col = 0; col < 2; ++col)
     for (int k = 0; k <= kMaxOrder; ++k) {
-      e = launch_element_batch(k, MODE_HYB, b->d_eargs, b->items[k][col][0], b->n_items[k][col][0], col, b->stream,
-                               &b->prof);
+      e = launch_element_batch(k, MODE_HYB, b->d_eargs, b->items[k][col][0], b->n_items[k][col][0], col,
+                               b->egrid[k][0], b->stream, &b->prof);
       if (e == cudaSuccess && b->n_items[k][col][1])
         e = launch_mixed_batch(k, b->d_eargs, b->items[k][col][1], b->n_items[k][col][1], col, false, nullptr,
-                               nullptr, b->stream, &b->prof);
+                               nullptr, b->egrid[k][1], b->stream, &b->prof);
       if (e != cudaSuccess) return cuda_status(e);
     }
   st = batch_finish(b);
@@ -1396,7 +1519,7 @@ int hyb_recover_batch(hyb_batch* b, const double* const* lambdas, double* const*
   for (int k = 0; k <= kMaxOrder; ++k) {
     e = launch_recover_batch(k, MODE_HYB, b->d_rargs, b->ritems[k][0], b->n_ritems[k][0], b->stream, &b->prof);
     if (e == cudaSuccess && b->n_ritems[k][1])
-      e = launch_mixed_batch(k, b->d_eargs, b->ritems[k][1], b->n_ritems[k][1], 0, true, b->d_lams, b->d_us,
+      e = launch_mixed_batch(k, b->d_eargs, b->ritems[k][1], b->n_ritems[k][1], 0, true, b->d_lams, b->d_us, 0,
                              b->stream, &b->prof);
     if (e != cudaSuccess) return cuda_status(e);
   }
@@ -1468,6 +1591,13 @@ int hyb_batch_step_kernels(const hyb_batch* b, int64_t* outside_loop, int64_t* p
   if (outside_loop) *outside_loop = b->step_kernels;
   if (per_pass) *per_pass = b->step_body_kernels;
   if (iterations_per_pass) *iterations_per_pass = kStepChunk;
+  return HYB_OK;
+}
+
+int hyb_batch_get_autotune(const hyb_batch* b, int order, int path, int* multiple, int* grid) {
+  if (!b || order < 0 || order > kMaxOrder || path < 0 || path > 1) return HYB_ERR_INVALID_ARG;
+  if (multiple) *multiple = b->emult[order][path];
+  if (grid) *grid = b->egrid[order][path];
   return HYB_OK;
 }
 

@@ -924,17 +924,20 @@ __global__ void __launch_bounds__(EK<K>::NT) element_kernel(ElemArgs args) {
   element_body<K, MODE>(args, args.elem_list[li], smem);
 }
 
-// Many problems in one launch: work item (problem, element) with per-problem arguments.
+// Many problems in one launch: work item (problem, element) with per-problem arguments. A CTA
+// takes items blockIdx.x, blockIdx.x + gridDim.x, ...: one per CTA when the grid covers them,
+// several (persistent CTAs) when the batch's autotuner chose a smaller grid.
 template <int K, int MODE>
 __global__ void __launch_bounds__(EK<K>::NT) element_kernel_batch(const ElemArgs* probs, const int2* items,
                                                                   int64_t n_items, int colour) {
   extern __shared__ double smem[];
-  const int64_t li = blockIdx.x;
-  if (li >= n_items) return;
-  const int2 it = items[li];
-  ElemArgs a = probs[it.x];
-  a.colour = colour;
-  element_body<K, MODE>(a, it.y, smem);
+  for (int64_t li = blockIdx.x; li < n_items; li += gridDim.x) {
+    const int2 it = items[li];
+    ElemArgs a = probs[it.x];
+    a.colour = colour;
+    element_body<K, MODE>(a, it.y, smem);
+    __syncthreads();                         // the next item overwrites this one's shared memory
+  }
 }
 
 // det J > 0 at the 8 corners and every Gauss point of every element.
@@ -1004,32 +1007,33 @@ cudaError_t launch_element_k(int mode, const ElemArgs& a, cudaStream_t s, Prof* 
 
 template <int K>
 cudaError_t launch_element_batch_k(int mode, const ElemArgs* probs, const int2* items, int64_t n, int colour,
-                                   cudaStream_t s, Prof* prof) {
+                                   int grid, cudaStream_t s, Prof* prof) {
   using S = EK<K>;
   if (n == 0) return cudaSuccess;
+  const unsigned g = (unsigned)(grid > 0 && grid < n ? grid : n);
   const size_t smem = S::SMEM_BYTES;
   cudaError_t err;
   const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
   if (mode == MODE_HYB) {
     err = cudaFuncSetAttribute(element_kernel_batch<K, MODE_HYB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    element_kernel_batch<K, MODE_HYB><<<(unsigned)n, S::NT, smem, s>>>(probs, items, n, colour);
+    element_kernel_batch<K, MODE_HYB><<<g, S::NT, smem, s>>>(probs, items, n, colour);
   } else {
     err = cudaFuncSetAttribute(element_kernel_batch<K, MODE_SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    element_kernel_batch<K, MODE_SC><<<(unsigned)n, S::NT, smem, s>>>(probs, items, n, colour);
+    element_kernel_batch<K, MODE_SC><<<g, S::NT, smem, s>>>(probs, items, n, colour);
   }
   prof_end(prof, tok, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_element_batch(int k, int mode, const ElemArgs* probs, const int2* items, int64_t n, int colour,
-                                 cudaStream_t s, Prof* prof) {
+                                 int grid, cudaStream_t s, Prof* prof) {
   switch (k) {
-    case 0: return launch_element_batch_k<0>(mode, probs, items, n, colour, s, prof);
-    case 1: return launch_element_batch_k<1>(mode, probs, items, n, colour, s, prof);
-    case 2: return launch_element_batch_k<2>(mode, probs, items, n, colour, s, prof);
-    case 3: return launch_element_batch_k<3>(mode, probs, items, n, colour, s, prof);
+    case 0: return launch_element_batch_k<0>(mode, probs, items, n, colour, grid, s, prof);
+    case 1: return launch_element_batch_k<1>(mode, probs, items, n, colour, grid, s, prof);
+    case 2: return launch_element_batch_k<2>(mode, probs, items, n, colour, grid, s, prof);
+    case 3: return launch_element_batch_k<3>(mode, probs, items, n, colour, grid, s, prof);
   }
   return cudaErrorInvalidValue;
 }
@@ -1060,4 +1064,19 @@ cudaError_t launch_check_geometry(int k, const ElemArgs& a, cudaStream_t s, Prof
   return cudaGetLastError();
 }
 
+}  // namespace hyb
+
+namespace hyb {
+// CTAs of the batched element kernel of order k that fit on one SM at once (the autotuner's unit).
+int element_batch_ctas_per_sm(int k) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (k) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_kernel_batch<0, MODE_HYB>, EK<0>::NT, EK<0>::SMEM_BYTES); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_kernel_batch<1, MODE_HYB>, EK<1>::NT, EK<1>::SMEM_BYTES); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_kernel_batch<2, MODE_HYB>, EK<2>::NT, EK<2>::SMEM_BYTES); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_kernel_batch<3, MODE_HYB>, EK<3>::NT, EK<3>::SMEM_BYTES); break;
+  }
+  return e == cudaSuccess ? n : 0;
+}
 }  // namespace hyb

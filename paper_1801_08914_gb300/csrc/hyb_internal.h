@@ -186,10 +186,15 @@ cudaError_t launch_recover(const RecoverArgs& a, cudaStream_t s, Prof* prof);
 
 // Batched forms: one launch over (problem, element) work items of one order, with the
 // per-problem arguments in device arrays.
+// grid: CTAs of the element launch; 0 (or >= n) one CTA per item, fewer: every CTA loops over
+// the items grid apart (persistent), so each takes about n / grid elements.
 cudaError_t launch_element_batch(int k, int mode, const ElemArgs* probs, const int2* items, int64_t n, int colour,
-                                 cudaStream_t s, Prof* prof);
+                                 int grid, cudaStream_t s, Prof* prof);
 cudaError_t launch_mixed_batch(int k, const ElemArgs* probs, const int2* items, int64_t n, int colour, bool recover,
-                               const double* const* lams, double* const* us, cudaStream_t s, Prof* prof);
+                               const double* const* lams, double* const* us, int grid, cudaStream_t s, Prof* prof);
+// CTAs of the batched element kernels (FP64 / FP32 mixed form) of order k resident on one SM
+int element_batch_ctas_per_sm(int k);
+int mixed_batch_ctas_per_sm(int k);
 cudaError_t launch_recover_batch(int k, int mode, const RecoverArgs* probs, const int2* items, int64_t n,
                                  cudaStream_t s, Prof* prof);
 

@@ -23,6 +23,7 @@
 
 #include "hyb_device.h"
 #include "hyb_internal.h"
+#include "hyb_tc.cuh"
 #include "hyb_tiles.cuh"
 
 namespace hyb {
@@ -351,14 +352,15 @@ cudaError_t prepare_smem(F* kernel, size_t bytes) {
 
 template <int K>
 cudaError_t launch_mixed_batch_k(const ElemArgs* probs, const int2* items, int64_t n, int colour, bool recover,
-                                 const double* const* lams, double* const* us, cudaStream_t s, Prof* prof) {
+                                 const double* const* lams, double* const* us, int grid, cudaStream_t s, Prof* prof) {
   using S = MT<K>;
   if (n == 0) return cudaSuccess;
   cudaError_t err;
   if (!recover) {
     if ((err = prepare_smem(element_tiled_kernel_batch<K>, S::SMEM)) != cudaSuccess) return err;
     const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
-    element_tiled_kernel_batch<K><<<(unsigned)n, S::NT, S::SMEM, s>>>(probs, items, n, colour);
+    const unsigned g = (unsigned)(grid > 0 && grid < n ? grid : n);
+    element_tiled_kernel_batch<K><<<g, S::NT, S::SMEM, s>>>(probs, items, n, colour);
     prof_end(prof, tok, s);
   } else {
     if ((err = prepare_smem(recover_tiled_kernel_batch<K>, S::SMEM)) != cudaSuccess) return err;
@@ -413,12 +415,12 @@ cudaError_t launch_element_mixed(int k, const ElemArgs& a, cudaStream_t s, Prof*
 }
 
 cudaError_t launch_mixed_batch(int k, const ElemArgs* probs, const int2* items, int64_t n, int colour, bool recover,
-                               const double* const* lams, double* const* us, cudaStream_t s, Prof* prof) {
+                               const double* const* lams, double* const* us, int grid, cudaStream_t s, Prof* prof) {
   switch (k) {
-    case 0: return launch_mixed_batch_k<0>(probs, items, n, colour, recover, lams, us, s, prof);
-    case 1: return launch_mixed_batch_k<1>(probs, items, n, colour, recover, lams, us, s, prof);
-    case 2: return launch_mixed_batch_k<2>(probs, items, n, colour, recover, lams, us, s, prof);
-    case 3: return launch_mixed_batch_k<3>(probs, items, n, colour, recover, lams, us, s, prof);
+    case 0: return launch_mixed_batch_k<0>(probs, items, n, colour, recover, lams, us, grid, s, prof);
+    case 1: return launch_mixed_batch_k<1>(probs, items, n, colour, recover, lams, us, grid, s, prof);
+    case 2: return launch_mixed_batch_k<2>(probs, items, n, colour, recover, lams, us, grid, s, prof);
+    case 3: return launch_mixed_batch_k<3>(probs, items, n, colour, recover, lams, us, grid, s, prof);
   }
   return cudaErrorInvalidValue;
 }
@@ -434,4 +436,18 @@ cudaError_t launch_recover_mixed(int k, const ElemArgs& a, const double* lambda,
   return cudaErrorInvalidValue;
 }
 
+}  // namespace hyb
+
+namespace hyb {
+int mixed_batch_ctas_per_sm(int k) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (k) {
+    case 0: e = prepare_smem(element_tiled_kernel_batch<0>, MT<0>::SMEM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<0>, MT<0>::NT, MT<0>::SMEM); break;
+    case 1: e = prepare_smem(element_tiled_kernel_batch<1>, MT<1>::SMEM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<1>, MT<1>::NT, MT<1>::SMEM); break;
+    case 2: e = prepare_smem(element_tiled_kernel_batch<2>, MT<2>::SMEM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<2>, MT<2>::NT, MT<2>::SMEM); break;
+    case 3: e = prepare_smem(element_tiled_kernel_batch<3>, MT<3>::SMEM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<3>, MT<3>::NT, MT<3>::SMEM); break;
+  }
+  return e == cudaSuccess ? n : 0;
+}
 }  // namespace hyb

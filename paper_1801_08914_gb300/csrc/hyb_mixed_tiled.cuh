@@ -42,6 +42,11 @@ struct TileShape<3> {
   static constexpr int TB = 16, MR = 4, MC = 4, NT = 512, MINB = 1;   // 227 KB of shared memory
 };
 
+// S = Y^T Y - V^T V on the tensor cores (s_tensor) where the dead shared memory after Y | P
+// holds the split operands: RT_3 (one CTA per SM, 227 KB)
+template <int K>
+constexpr bool kTensorS = K == 3;
+
 template <int K>
 struct MT {
   using TS = TileShape<K>;
@@ -88,6 +93,102 @@ constexpr int kRefineSteps = 1;
 constexpr int kAssemblyRefineSteps = 0;
 
 using tiles::tcol;
+
+// S = Y^T Y - V^T V on the tensor cores (tcgen05 kind::tf32), split-TF32: X = [Y; V]^T (NB rows,
+// K = NB + NQP, padded to multiples of 8) is split into TF32 parts X = X_hi + X_lo (each rounded
+// to nearest), and S = X_hi^T X_hi + T + T^T with T = X_hi^T X_lo (the sign of the V rows via
+// the MMA's negated A), which keeps FP32-level accuracy (Ootomo and Yokota's error-compensated
+// TF32 products; the dropped X_lo^T X_lo term is below FP32 rounding). Both products are one
+// M = 128 x N x 8 MMA per K step, accumulated in TMEM (S in columns 0.., T in columns 128..).
+// X_hi and X_lo take dead shared memory (xhi: 128 rows' worth may be read, the padding rows
+// landing in xlo). put(i, j, s) receives S(i, j) once per unordered pair and its mirror.
+// Returns false (after freeing the TMEM) if the MMAs did not complete within the poll limit.
+template <int K>
+struct TensorS {
+  using S = MT<K>;
+  static constexpr int NB = S::NB, NQP = S::NQP;
+  static constexpr int KY = (NB + 7) / 8 * 8, KV = (NQP + 7) / 8 * 8, KK = KY + KV;
+  static constexpr int NPAD = (NB + 15) / 16 * 16;     // MMA N: a multiple of 16 for M = 128
+  static constexpr int XFLOATS = NPAD * KK;            // one operand, rows >= NB zero
+  static constexpr uint32_t SBO = (KK / 4) * 128;
+};
+
+template <int K, class Put>
+__device__ bool s_tensor(const float* Y, const float* Pv, float* xhi, float* xlo, Put put) {
+  using TS = TensorS<K>;
+  constexpr int NB = TS::NB, NQP = TS::NQP, KY = TS::KY, KK = TS::KK, NPAD = TS::NPAD, NT = MT<K>::NT;
+  static_assert(NT % 128 == 0, "whole lane quarters of warps");
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int t = tid; t < NPAD * KK; t += NT) {
+    const int r = t % NPAD, k = t / NPAD;
+    float x = 0.0f;
+    if (r < NB) {
+      if (k < NB) x = Y[k * NB + r];
+      else if (k >= KY && k - KY < NQP) x = Pv[(k - KY) * NB + r];
+    }
+    const float hi = tc::to_tf32(x);
+    const int o = tc::kmajor_offset(r, k, KK) >> 2;
+    xhi[o] = hi;
+    xlo[o] = tc::to_tf32(x - hi);
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase, 256);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tm = tbase;
+  if (tid == 0) {
+    const uint32_t ahi = tc::smem_addr(xhi), alo = tc::smem_addr(xlo);
+#pragma unroll 1
+    for (int ks = 0; ks < KK / 8; ++ks) {
+      const uint32_t id = tc::idesc_tf32(128, NPAD, ks * 8 >= KY);
+      const uint64_t dhi = tc::smem_desc(ahi + ks * 256, 128, TS::SBO);
+      const uint64_t dlo = tc::smem_desc(alo + ks * 256, 128, TS::SBO);
+      tc::mma_tf32(tm, dhi, dhi, id, ks > 0);
+      tc::mma_tf32(tm + 128, dhi, dlo, id, ks > 0);
+    }
+    tc::commit(&mbar);
+  }
+  bool ok = tc::mbar_wait(&mbar, 0, 1ll << 22);
+  if (!ok) tc::mbar_wait(&mbar, 0, 1ll << 26);   // let MMAs in flight finish before the TMEM is freed
+  tc::fence_after_sync();
+  // T into shared memory (over X_lo, read by the completed MMAs), then S = S_hh + T + T^T
+  constexpr int TLD = NB + 1;
+  float* Ts = xlo;
+  const int q = warp & 3, g = warp >> 2;                 // lane quarter, column group
+  constexpr int NG = NT / 128, CW = (NPAD / NG + 7) / 8 * 8;
+  const int i = q * 32 + lane;
+  if (ok && q * 32 < NB)
+    for (int c = g * CW; c < (g + 1) * CW && c < NPAD; c += 8) {
+      float v[8];
+      tc::tmem_ld8(tm + 128, q, c, v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (i < NB && c + j < NB) Ts[i * TLD + c + j] = v[j];
+    }
+  __syncthreads();
+  if (ok && q * 32 < NB)
+    for (int c = g * CW; c < (g + 1) * CW && c < NPAD; c += 8) {
+      float v[8];
+      tc::tmem_ld8(tm, q, c, v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int jj = c + j;
+        if (i < NB && jj <= i) {
+          const float sv = v[j] + Ts[i * TLD + jj] + Ts[jj * TLD + i];
+          put(i, jj, sv);
+          if (jj != i) put(jj, i, sv);
+        }
+      }
+    }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tm, 256);
+  return ok;
+}
 
 // FP32 tile factorisations of this kernel: whole triangles, no write-out of the factor,
 // look-ahead form (warp 0 factors the next diagonal tile during the trailing update)
@@ -601,7 +702,13 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
       if (a == b && args.colour == 1) args.val[pos] += v;
       else args.val[pos] = v;
     };
-    {
+    if constexpr (kTensorS<K>) {
+      static_assert(S::YPS_IN_LT && S::YPS + TensorS<K>::XFLOATS <= S::LTA && TensorS<K>::XFLOATS <= S::XDA &&
+                        (128 - TensorS<K>::NPAD) * TensorS<K>::KK <= S::XDA,
+                    "X_hi after Y | P in the L_M region, X_lo over Xd, the padding rows of X_hi inside X_lo");
+      if (!s_tensor<K>(Y, Pv, Lt + S::YPS, Xd, put) && tid == 0)
+        set_error(args.status, args.err_elem, HYB_ERR_TIMEOUT, e);
+    } else {
       constexpr int RM = NB / MR, CM = NB / MC;
       for (int it = tid; it < RM * CM; it += NT) {
         const int i0 = (it / CM) * MR, j0 = (it % CM) * MC;
@@ -659,12 +766,13 @@ template <int K>
 __global__ void __launch_bounds__(MT<K>::NT, MT<K>::MINB) element_tiled_kernel_batch(const ElemArgs* probs, const int2* items,
                                                                         int64_t n_items, int colour) {
   extern __shared__ double smem[];
-  const int64_t li = blockIdx.x;
-  if (li >= n_items) return;
-  const int2 it = items[li];
-  ElemArgs a = probs[it.x];
-  a.colour = colour;
-  element_tiled_body<K, false>(a, it.y, smem, nullptr, nullptr);
+  for (int64_t li = blockIdx.x; li < n_items; li += gridDim.x) {   // persistent when the grid is smaller
+    const int2 it = items[li];
+    ElemArgs a = probs[it.x];
+    a.colour = colour;
+    element_tiled_body<K, false>(a, it.y, smem, nullptr, nullptr);
+    __syncthreads();
+  }
 }
 
 template <int K>

@@ -615,8 +615,11 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
   }
 }
 
+// Resident CTAs per SM: the FP64 form is bound by the FP64 pipe (more warps did not help), the
+// FP32-operator form by memory latency (long-scoreboard stalls with 16 warps per SM): it takes
+// a third CTA per SM (80 registers, no spills) where its row blocks are 9 x len, a second at 16.
 template <int NFN, int W, bool F32>
-__global__ void __launch_bounds__(kThreads, NFN <= 9 ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, F32 ? (NFN <= 9 ? 3 : 2) : (NFN <= 9 ? 2 : 1))
     pcg_fused_kernel(PcgArgs a, int count, double rtol2, GridBar* bar) {
   __shared__ double sh[kThreads];
   __shared__ double bc[3];

@@ -34,7 +34,7 @@ EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recove
            "hyb_set_profiling", "hyb_get_profile", "hyb_pcg_solve_noalloc", "hyb_measure_fma_peak",
            "hyb_get_precision_split", "hyb_setup_batch", "hyb_assemble_reduced_batch", "hyb_solve_reduced_batch",
            "hyb_recover_batch", "hyb_batch_context", "hyb_batch_set_profiling", "hyb_batch_get_profile",
-           "hyb_destroy_batch", "hyb_set_mixed_operator", "hyb_batch_step", "hyb_batch_step_kernels",
+           "hyb_destroy_batch", "hyb_set_mixed_operator", "hyb_batch_step", "hyb_batch_step_kernels", "hyb_batch_get_autotune",
            "hyb_last_error_element", "hyb_destroy", "hyb_status_string"]
 
 
@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_batch_context.argtypes = [P, I, ctypes.POINTER(P)]
     lib.hyb_batch_step.argtypes = [P, PP, PP, D, I, PP, PP, ctypes.POINTER(I), ctypes.POINTER(D)]
     lib.hyb_batch_step_kernels.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I)]
+    lib.hyb_batch_get_autotune.argtypes = [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.hyb_batch_set_profiling.argtypes = [P, I]
     lib.hyb_batch_set_graphs.argtypes = [P, I]
     lib.hyb_batch_set_pcg_fused.argtypes = [P, I]
@@ -430,6 +431,14 @@ def hyb_batch_step_kernels(batch):
     _check(lib().hyb_batch_step_kernels(batch.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "hyb_batch_step_kernels")
     return a.value, b.value, c.value
+
+
+def hyb_batch_get_autotune(batch, order, path):
+    """(multiple of resident CTAs or 0 = one CTA per element, grid) of an order bin and path."""
+    m, g = ctypes.c_int(), ctypes.c_int()
+    _check(lib().hyb_batch_get_autotune(batch.handle, int(order), int(path), ctypes.byref(m), ctypes.byref(g)),
+           "hyb_batch_get_autotune")
+    return m.value, g.value
 
 
 def hyb_batch_set_pcg_fused(batch, on):

@@ -253,11 +253,16 @@ def make_config(cfg, n: int | None = None) -> Problem:
 def batch_problems(count: int = 256, seed0: int = 4000, nmin: int = 6, nmax: int = 24,
                    contrast=(1e-2, 1e4)) -> list[Problem]:
     """Many independent problems of uneven size and order: n ~ U{nmin..nmax}, k ~ U{0..3}."""
-    probs = []
-    for p in range(count):
-        s = seed0 + p
-        u = uniform(s, STREAM_BATCH, 2)
-        n = nmin + int(u[0] * (nmax - nmin + 1))
-        k = int(u[1] * 4)
-        probs.append(random_problem(n, k, 0.2, s, contrast[0], contrast[1], name=f"batch{p}"))
-    return probs
+    return [batch_problem(p, seed0, nmin, nmax, contrast) for p in range(count)]
+
+
+def batch_shape(p: int, seed0: int = 4000, nmin: int = 6, nmax: int = 24) -> tuple[int, int]:
+    """(n, k) of problem p of the batched workload: n ~ U{nmin..nmax}, k ~ U{0..3}."""
+    u = uniform(seed0 + p, STREAM_BATCH, 2)
+    return nmin + int(u[0] * (nmax - nmin + 1)), int(u[1] * 4)
+
+
+def batch_problem(p: int, seed0: int = 4000, nmin: int = 6, nmax: int = 24, contrast=(1e-2, 1e4)) -> Problem:
+    """Problem p of the batched workload (seed seed0 + p)."""
+    n, k = batch_shape(p, seed0, nmin, nmax)
+    return random_problem(n, k, 0.2, seed0 + p, contrast[0], contrast[1], name=f"batch{p}")

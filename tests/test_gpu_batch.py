@@ -160,6 +160,10 @@ def test_batch_step_graph_matches_the_three_calls(precision):
             print(f"step {step} problem {i} (n={p.nx}, k={p.order}, prec={precision}): graph {its[i]} it, "
                   f"three calls {it3[i]} it; lambda {el:.1e} u {eu:.1e}")
             assert abs(its[i] - it3[i]) <= 2 and el <= tol and eu <= tol
+    for k in range(4):                       # the autotuner's choice per order bin and path
+        for path in (0, 1):
+            m, g = hyb.hyb_batch_get_autotune(b, k, path)
+            assert m in (0, 1, 2, 4) and (g == 0) == (m == 0)
     outside, per_pass, ipp = hyb.hyb_batch_step_kernels(b)
     assert per_pass == 3 * ipp + 1 and outside > 0
     # maxit inside the graph: every problem stops after exactly 5 iterations
