@@ -112,6 +112,8 @@ struct hyb_ctx {
   float* val32 = nullptr;                  // mixed: FP32 copy of the reduced-system values (PCG operator)
   float* z32 = nullptr;                    // mixed: FP32 copy of the scaled preconditioned residual
   double* dsq = nullptr;                   // mixed: sqrt of H's diagonal (scaling of the FP32 operator)
+  int64_t* fptr32 = nullptr;               // mixed: the FP32 operator's padded face layout (F + 1 offsets)
+  int32_t* col32 = nullptr;                // mixed: its padded column lists, one per face
   int op32 = 1;                            // mixed: PCG applies H from val32 (1) or from val (0)
   std::vector<int32_t> h_list[2][2];       // host copies: [colour][path] (path 0 = FP64, 1 = FP32)
   double* Lstore = nullptr;
@@ -366,7 +368,14 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
       return HYB_ERR_CUDA;
     if ((st = dalloc(c, &c->Lstore, (size_t)c->n_path[0] * (size_t)tri_size(s.n)))) return st;
     if ((st = dalloc(c, &c->Lstore32, (size_t)c->n_path[1] * (size_t)mixed_store_floats(order)))) return st;
-    if ((st = dalloc(c, &c->val32, c->nnz))) return st;
+    // the FP32 operator's layout: every face's column list padded to a multiple of 8 entries
+    std::vector<int64_t> fp32(F + 1, 0);
+    for (int64_t f = 0; f < F; ++f) fp32[f + 1] = fp32[f] + ((int64_t)adj_count[f] * nfn + 7) / 8 * 8;
+    if ((st = dalloc(c, &c->val32, (size_t)fp32[F] * nfn))) return st;
+    if ((st = dalloc(c, &c->col32, (size_t)fp32[F]))) return st;
+    if ((st = dalloc(c, &c->fptr32, (size_t)F + 1))) return st;
+    if (cudaMemcpy(c->fptr32, fp32.data(), (F + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess)
+      return HYB_ERR_CUDA;
     if ((st = dalloc(c, &c->z32, c->n_lambda))) return st;
     if ((st = dalloc(c, &c->dsq, c->n_lambda))) return st;
   } else {
@@ -444,8 +453,8 @@ int assemble_impl(hyb_ctx* c, const double* load, const double* ess, int mode) {
   if (c->precision == HYB_MIXED && c->n_path[1] > 0 && c->n_path[0] == 0) {
     // the FP32 copy of H that the mixed context's PCG applies (H carries the FP32 elimination's
     // error anyway; the FP64 accumulation above stays the reference for the refinement)
-    cudaError_t e = launch_round_values(c->n_lambda, c->row_ptr, c->col, c->val, c->dsq, c->val32, c->stream,
-                                        &c->prof);
+    cudaError_t e = launch_round_values(c->n_lambda, c->sz.nfn, c->row_ptr, c->col, c->val, c->fptr32, c->dsq,
+                                        c->val32, c->col32, c->stream, &c->prof);
     if (e != cudaSuccess) return cuda_status(e);
   }
   st = finish_phase(c);
@@ -629,6 +638,8 @@ int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lamb
     a.val32 = c->val32;
     a.z32 = c->z32;
     a.dsq = c->dsq;
+    a.fptr32 = c->fptr32;
+    a.col32 = c->col32;
   }
   cudaError_t e = pcg_init(a, c->stream, &c->prof);
   if (e != cudaSuccess) return cuda_status(e);

@@ -103,6 +103,11 @@ struct PcgArgs {
                              // sqrt(H_ii), applied with FP32 products (NULL: the FP64 values)
   const double* dsq;         // with val32: d_i = sqrt(H_ii)
   float* z32;                // with val32: (d z) rounded to FP32 for the SpMV's gathers
+  const int64_t* fptr32;     // with val32: its own layout, every face's column list padded to a multiple
+                             // of 8 (one 32-byte sector per 8 lanes): face f's list is col32[fptr32[f] ..
+                             // fptr32[f+1]) and its NFN rows start at val32[NFN fptr32[f] + m (fptr32[f+1]
+                             // - fptr32[f])]; padding entries have value 0 and column 0
+  const int32_t* col32;
   int maxit;                 // > 0: the iteration kernels stop this problem after maxit iterations
                              // (the batched step's graph, whose loop runs on the device); <= 0: no limit
   unsigned long long* bar;   // fused form in a batch: this problem's barrier counter (16 bytes, zeroed per launch)
@@ -166,8 +171,9 @@ cudaError_t launch_axpy(int64_t n, const double* x, double* y, cudaStream_t s, P
 // dsq[j])) (the diagonally scaled matrix: unit diagonal, |entries| <= 1 for SPD H, so rounding
 // it keeps it SPD where rounding H itself would not, e.g. across mass coefficients 10^-8..1);
 // profiled with the element phase, whose last step it is
-cudaError_t launch_round_values(int64_t n_rows, const int64_t* row_ptr, const int32_t* col, const double* v,
-                                double* dsq, float* o, cudaStream_t s, Prof* prof);
+cudaError_t launch_round_values(int64_t n_rows, int nfn, const int64_t* row_ptr, const int32_t* col, const double* v,
+                                const int64_t* fptr32, double* dsq, float* o, int32_t* col32, cudaStream_t s,
+                                Prof* prof);
 
 struct RecoverArgs {
   int k;

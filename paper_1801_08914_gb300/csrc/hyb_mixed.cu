@@ -357,10 +357,14 @@ cudaError_t launch_mixed_batch_k(const ElemArgs* probs, const int2* items, int64
   if (n == 0) return cudaSuccess;
   cudaError_t err;
   if (!recover) {
-    if ((err = prepare_smem(element_tiled_kernel_batch<K>, S::SMEM)) != cudaSuccess) return err;
-    const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+    if ((err = prepare_smem(mixed_load_kernel_batch<K>, LoadShape<K>::SMEM)) != cudaSuccess) return err;
+    if ((err = prepare_smem(element_tiled_kernel_batch<K>, S::SMEM_ASM)) != cudaSuccess) return err;
+    int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+    mixed_load_kernel_batch<K><<<(unsigned)n, LoadShape<K>::NT, LoadShape<K>::SMEM, s>>>(probs, items, n);
+    prof_end(prof, tok, s);
+    tok = prof_begin(prof, HYB_K_ELEMENT, s);
     const unsigned g = (unsigned)(grid > 0 && grid < n ? grid : n);
-    element_tiled_kernel_batch<K><<<g, S::NT, S::SMEM, s>>>(probs, items, n, colour);
+    element_tiled_kernel_batch<K><<<g, S::NT, S::SMEM_ASM, s>>>(probs, items, n, colour);
     prof_end(prof, tok, s);
   } else {
     if ((err = prepare_smem(recover_tiled_kernel_batch<K>, S::SMEM)) != cudaSuccess) return err;
@@ -378,9 +382,13 @@ cudaError_t launch_mixed_k(const ElemArgs& a, cudaStream_t s, Prof* prof, bool r
   if (a.n_list == 0) return cudaSuccess;
   cudaError_t err;
   if (!recover) {
-    if ((err = prepare_smem(element_tiled_kernel<K>, S::SMEM)) != cudaSuccess) return err;
-    const int tok = prof_begin(prof, HYB_K_ELEMENT, s);
-    element_tiled_kernel<K><<<(unsigned)a.n_list, S::NT, S::SMEM, s>>>(a);
+    if ((err = prepare_smem(mixed_load_kernel<K>, LoadShape<K>::SMEM)) != cudaSuccess) return err;
+    if ((err = prepare_smem(element_tiled_kernel<K>, S::SMEM_ASM)) != cudaSuccess) return err;
+    int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+    mixed_load_kernel<K><<<(unsigned)a.n_list, LoadShape<K>::NT, LoadShape<K>::SMEM, s>>>(a);
+    prof_end(prof, tok, s);
+    tok = prof_begin(prof, HYB_K_ELEMENT, s);
+    element_tiled_kernel<K><<<(unsigned)a.n_list, S::NT, S::SMEM_ASM, s>>>(a);
     prof_end(prof, tok, s);
   } else {
     if ((err = prepare_smem(recover_tiled_kernel<K>, S::SMEM)) != cudaSuccess) return err;
@@ -443,10 +451,10 @@ int mixed_batch_ctas_per_sm(int k) {
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (k) {
-    case 0: e = prepare_smem(element_tiled_kernel_batch<0>, MT<0>::SMEM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<0>, MT<0>::NT, MT<0>::SMEM); break;
-    case 1: e = prepare_smem(element_tiled_kernel_batch<1>, MT<1>::SMEM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<1>, MT<1>::NT, MT<1>::SMEM); break;
-    case 2: e = prepare_smem(element_tiled_kernel_batch<2>, MT<2>::SMEM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<2>, MT<2>::NT, MT<2>::SMEM); break;
-    case 3: e = prepare_smem(element_tiled_kernel_batch<3>, MT<3>::SMEM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<3>, MT<3>::NT, MT<3>::SMEM); break;
+    case 0: e = prepare_smem(element_tiled_kernel_batch<0>, MT<0>::SMEM_ASM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<0>, MT<0>::NT, MT<0>::SMEM_ASM); break;
+    case 1: e = prepare_smem(element_tiled_kernel_batch<1>, MT<1>::SMEM_ASM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<1>, MT<1>::NT, MT<1>::SMEM_ASM); break;
+    case 2: e = prepare_smem(element_tiled_kernel_batch<2>, MT<2>::SMEM_ASM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<2>, MT<2>::NT, MT<2>::SMEM_ASM); break;
+    case 3: e = prepare_smem(element_tiled_kernel_batch<3>, MT<3>::SMEM_ASM); if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, element_tiled_kernel_batch<3>, MT<3>::NT, MT<3>::SMEM_ASM); break;
   }
   return e == cudaSuccess ? n : 0;
 }

@@ -27,19 +27,21 @@ template <int K>
 struct TileShape;
 template <>
 struct TileShape<0> {
-  static constexpr int TB = 6, MR = 3, MC = 3, NT = 64, MINB = 8;
+  static constexpr int TB = 6, MR = 3, MC = 3, NT = 64, MINB = 8, MINB_ASM = 8;
 };
 template <>
 struct TileShape<1> {
-  static constexpr int TB = 12, MR = 3, MC = 4, NT = 128, MINB = 4;
+  static constexpr int TB = 12, MR = 3, MC = 4, NT = 128, MINB = 4, MINB_ASM = 4;
 };
 template <>
 struct TileShape<2> {
-  static constexpr int TB = 18, MR = 3, MC = 6, NT = 256, MINB = 3;   // 3 CTAs per SM (63 KB each)
+  // the recovery: 3 CTAs per SM (64 KB each); the assembly, without the FP64 residual scratch:
+  // 4 CTAs per SM (55 KB each, 64 registers)
+  static constexpr int TB = 18, MR = 3, MC = 6, NT = 256, MINB = 3, MINB_ASM = 4;
 };
 template <>
 struct TileShape<3> {
-  static constexpr int TB = 16, MR = 4, MC = 4, NT = 512, MINB = 1;   // 227 KB of shared memory
+  static constexpr int TB = 16, MR = 4, MC = 4, NT = 512, MINB = 1, MINB_ASM = 1;   // 227 KB of shared memory
 };
 
 // S = Y^T Y - V^T V on the tensor cores (s_tensor) where the dead shared memory after Y | P
@@ -50,7 +52,7 @@ constexpr bool kTensorS = K == 3;
 template <int K>
 struct MT {
   using TS = TileShape<K>;
-  static constexpr int TB = TS::TB, MR = TS::MR, MC = TS::MC, NT = TS::NT, MINB = TS::MINB;
+  static constexpr int TB = TS::TB, MR = TS::MR, MC = TS::MC, NT = TS::NT, MINB = TS::MINB, MINB_ASM = TS::MINB_ASM;
   static constexpr int P = K + 2, p = K + 1, Q = K + 2, NQ = Q * Q * Q;
   static constexpr int NFN = p * p, NI = 3 * K * p * p, NB = 6 * NFN, N = NI + NB, NC = P * p * p;
   static constexpr int NQK = p * p * p;
@@ -77,6 +79,10 @@ struct MT {
   static constexpr int F32 = TABF + LTA + XDA + ZTS + N /*vec*/ + 2 * NQP /*tq tmpq*/ + 32 /*ybuf*/ + 8 /*flag*/ +
                              (YPS_IN_LT ? 0 : YPS);
   static constexpr size_t SMEM = sizeof(double) * D64 + sizeof(float) * F32 + sizeof(int) * N;
+  // the assembly keeps only the geometry, the load and the solution in FP64 (the load is formed by
+  // mixed_load_kernel, and the assembly's element solve is not refined)
+  static constexpr int D64_ASM = (24 + 24 + 2 * P * Q + p * Q + 2 * Q + NFN + 7 * NQ + 2 * N + 8 + NQK + P * p + 1) / 2 * 2;
+  static constexpr size_t SMEM_ASM = sizeof(double) * D64_ASM + sizeof(float) * F32 + sizeof(int) * N;
   static_assert(N % TB == 0 && NI % TB == 0, "tiles must split the interior and face blocks");
   static_assert(TB % MR == 0 && TB % MC == 0 && NQP % MC == 0 && NB % MC == 0, "micro-tile shape");
   static_assert(TB <= 32, "one warp per diagonal tile");
@@ -303,18 +309,25 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   double* gd = d; d += NQ;
   double* f = d; d += N;
   double* x = d; d += N;
-  double* r = d; d += N;
-  double* ut = d; d += N;
-  double* U = d; d += 3 * NQ;
-  double* Wv = d; d += 3 * NQ;
-  double* Dv = d; d += NQ;
-  double* xc = d; d += NC;
-  double* t1 = d; d += S::TMP64;
-  double* t2 = d; d += S::TMP64;
+  double *r = nullptr, *ut = nullptr, *U = nullptr, *Wv = nullptr, *Dv = nullptr, *xc = nullptr, *t1 = nullptr,
+         *t2 = nullptr, *rq = nullptr;
+  if constexpr (RECOVER) {                        // the refinement's FP64 residual scratch
+    r = d; d += N;
+    ut = d; d += N;
+    U = d; d += 3 * NQ;
+    Wv = d; d += 3 * NQ;
+    Dv = d; d += NQ;
+    xc = d; d += NC;
+    t1 = d; d += S::TMP64;
+    t2 = d; d += S::TMP64;
+  }
   d += 8;
   double* qv = d; d += NQK;
-  double* rq = d; d += (N > NQ ? N : NQ);
+  if constexpr (RECOVER) {
+    rq = d; d += (N > NQ ? N : NQ);
+  }
   double* DcO64 = d; d += P * p;
+  d = smem + (RECOVER ? S::D64 : S::D64_ASM);      // the float region starts where the launch sized it
   float* fl = reinterpret_cast<float*>(d);
   float* Vcf = fl; fl += P * Q;
   float* Dcf = fl; fl += P * Q;
@@ -368,38 +381,18 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   for (int a = 0; a < 6; ++a) bmask |= (ef[a] < 0 && !args.natural) << a;
   auto is_e = [&](int i) { return i >= NI && ((bmask >> ((i - NI) / NFN)) & 1); };
 
-  // ---- FP64 right-hand side: assembly forms f = M c (essential values folded in) and keeps
-  // it for the recovery; the recovery reads it back and subtracts C^T lambda
+  // ---- FP64 right-hand side f_T = M_T c_T (essential values folded in), formed by
+  // mixed_load_kernel before the assembly; the recovery subtracts C^T lambda
   double* fs = args.zstore + e * (int64_t)N;
-  if (!RECOVER) {
-    const double* coef = args.load + e * (int64_t)N;
-    for (int i = tid; i < N; i += NT) ut[i] = coef[i];
-    __syncthreads();
-    apply_mass64<K, NT>(ut, f, 1.0, g6, Vc, Vo, U, Wv, t1, t2);
-    if (bmask) {
-      const double* ue = args.ess ? args.ess + e * (int64_t)N : nullptr;
-      if (ue) {
-        for (int i = tid; i < N; i += NT) ut[i] = is_e(i) ? ue[i] : 0.0;
-        __syncthreads();
-        apply_A64<K, NT>(ut, r, alpha, beta, true, g6, gd, Vc, Dc, Vo, U, Wv, Dv, xc, t1, t2);
-        for (int i = tid; i < N; i += NT) f[i] = is_e(i) ? ue[i] : f[i] - r[i];
-      } else {
-        for (int i = tid; i < N; i += NT)
-          if (is_e(i)) f[i] = 0.0;
-      }
-      __syncthreads();
+  for (int i = tid; i < N; i += NT) {
+    double v = fs[i];
+    if (RECOVER && i >= NI) {
+      const int a = (i - NI) / NFN, m = (i - NI) % NFN;
+      if (ef[a] >= 0) v -= ((a & 1) ? 1.0 : -1.0) * wf[m] * lambda[(int64_t)ef[a] * NFN + m];
     }
-    for (int i = tid; i < N; i += NT) fs[i] = f[i];
-  } else {
-    for (int i = tid; i < N; i += NT) {
-      double v = fs[i];
-      if (i >= NI) {
-        const int a = (i - NI) / NFN, m = (i - NI) % NFN;
-        if (ef[a] >= 0) v -= ((a & 1) ? 1.0 : -1.0) * wf[m] * lambda[(int64_t)ef[a] * NFN + m];
-      }
-      f[i] = v;                                  // f_T - C_T^T lambda
-    }
+    f[i] = v;                                    // f_T, or f_T - C_T^T lambda
   }
+  __syncthreads();
 
   if (RECOVER) {
     // ---- the stored factors back into shared memory
@@ -754,8 +747,93 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   }
 }
 
+// ---- FP64 element load of the mixed path, before the FP32 elimination: f_T = M_T c_T by sum
+// factorisation; on boundary faces with essential data f_T -= A_{:,e} u_e (free rows) and
+// f_T = u_e (essential rows), zero essential data clearing the essential rows. Stored in the
+// element's slot of zstore, where the assembly (g_T) and the recovery read it.
 template <int K>
-__global__ void __launch_bounds__(MT<K>::NT, MT<K>::MINB) element_tiled_kernel(ElemArgs args) {
+struct LoadShape {
+  static constexpr int P = K + 2, p = K + 1, Q = K + 2, NQ = Q * Q * Q, NFN = p * p, N = 3 * K * p * p + 6 * NFN;
+  static constexpr int NC = P * p * p, TMP64 = 3 * P * Q * Q, NT = 128;
+  static constexpr int D64 = 24 + 24 + 2 * P * Q + p * Q + 2 * Q + NFN + 7 * NQ + 3 * N + 6 * NQ + NQ + NC + 2 * TMP64;
+  static constexpr size_t SMEM = sizeof(double) * D64;
+};
+
+template <int K>
+__device__ void mixed_load_body(const ElemArgs& args, const int64_t e, double* smem) {
+  using L = LoadShape<K>;
+  constexpr int P = L::P, p = L::p, Q = L::Q, NQ = L::NQ, NFN = L::NFN, N = L::N, NT = L::NT;
+  constexpr int NI = 3 * K * p * p;
+  const int tid = threadIdx.x;
+  double* d = smem;
+  double* X8 = d; d += 24;
+  double* Mc = d; d += 24;
+  double* Vc = d; d += P * Q;
+  double* Dc = d; d += P * Q;
+  double* Vo = d; d += p * Q;
+  double* qx = d; d += Q;
+  double* qw = d; d += Q;
+  double* wf = d; d += NFN;
+  double* g6 = d; d += 6 * NQ;
+  double* gd = d; d += NQ;
+  double* f = d; d += N;
+  double* ut = d; d += N;
+  double* r = d; d += N;
+  double* U = d; d += 3 * NQ;
+  double* Wv = d; d += 3 * NQ;
+  double* Dv = d; d += NQ;
+  double* xc = d; d += L::NC;
+  double* t1 = d; d += L::TMP64;
+  double* t2 = d; d += L::TMP64;
+  load_element64<K, NT>(args, e, X8, Mc, Vc, Dc, Vo, qx, qw, wf);
+  geometry64<K, NT>(Mc, qx, qw, g6, gd, args.status, args.err_elem, e);
+  const double alpha = args.alpha[e], beta = args.beta[e];
+  const int32_t* ef = args.elem_face + e * 6;
+  int bmask = 0;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) bmask |= (ef[a] < 0 && !args.natural) << a;
+  auto is_e = [&](int i) { return i >= NI && ((bmask >> ((i - NI) / NFN)) & 1); };
+  const double* coef = args.load + e * (int64_t)N;
+  for (int i = tid; i < N; i += NT) ut[i] = coef[i];
+  __syncthreads();
+  apply_mass64<K, NT>(ut, f, 1.0, g6, Vc, Vo, U, Wv, t1, t2);
+  if (bmask) {
+    const double* ue = args.ess ? args.ess + e * (int64_t)N : nullptr;
+    if (ue) {
+      for (int i = tid; i < N; i += NT) ut[i] = is_e(i) ? ue[i] : 0.0;
+      __syncthreads();
+      apply_A64<K, NT>(ut, r, alpha, beta, true, g6, gd, Vc, Dc, Vo, U, Wv, Dv, xc, t1, t2);
+      for (int i = tid; i < N; i += NT) f[i] = is_e(i) ? ue[i] : f[i] - r[i];
+    } else {
+      for (int i = tid; i < N; i += NT)
+        if (is_e(i)) f[i] = 0.0;
+    }
+    __syncthreads();
+  }
+  double* fs = args.zstore + e * (int64_t)N;
+  for (int i = tid; i < N; i += NT) fs[i] = f[i];
+}
+
+template <int K>
+__global__ void __launch_bounds__(LoadShape<K>::NT) mixed_load_kernel(ElemArgs args) {
+  extern __shared__ double smem[];
+  const int64_t li = blockIdx.x;
+  if (li >= args.n_list) return;
+  mixed_load_body<K>(args, args.elem_list[li], smem);
+}
+
+template <int K>
+__global__ void __launch_bounds__(LoadShape<K>::NT) mixed_load_kernel_batch(const ElemArgs* probs, const int2* items,
+                                                                           int64_t n_items) {
+  extern __shared__ double smem[];
+  const int64_t li = blockIdx.x;
+  if (li >= n_items) return;
+  const int2 it = items[li];
+  mixed_load_body<K>(probs[it.x], it.y, smem);
+}
+
+template <int K>
+__global__ void __launch_bounds__(MT<K>::NT, MT<K>::MINB_ASM) element_tiled_kernel(ElemArgs args) {
   extern __shared__ double smem[];
   const int64_t li = blockIdx.x;
   if (li >= args.n_list) return;
@@ -763,7 +841,7 @@ __global__ void __launch_bounds__(MT<K>::NT, MT<K>::MINB) element_tiled_kernel(E
 }
 
 template <int K>
-__global__ void __launch_bounds__(MT<K>::NT, MT<K>::MINB) element_tiled_kernel_batch(const ElemArgs* probs, const int2* items,
+__global__ void __launch_bounds__(MT<K>::NT, MT<K>::MINB_ASM) element_tiled_kernel_batch(const ElemArgs* probs, const int2* items,
                                                                         int64_t n_items, int colour) {
   extern __shared__ double smem[];
   for (int64_t li = blockIdx.x; li < n_items; li += gridDim.x) {   // persistent when the grid is smaller

@@ -492,17 +492,20 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
 #pragma unroll
       for (int m = 0; m < NP; ++m) acc[m] = AccT(0);
       if (f < nfaces) {
-        const int64_t r0 = f * NFN;
-        const int64_t lo = __ldcs(a.row_ptr + r0);
-        const int len = (int)(__ldcs(a.row_ptr + r0 + 1) - lo);
         if constexpr (F32) {
+          const int64_t c0 = __ldcs(a.fptr32 + f);
+          const int len = (int)(__ldcs(a.fptr32 + f + 1) - c0);
+          const float* vb = a.val32 + NFN * c0;
 #pragma unroll 4
           for (int t = gl; t < len; t += W) {
-            const float zj = __ldcg(a.z32 + __ldcs(a.col + lo + t));
+            const float zj = __ldcg(a.z32 + __ldcs(a.col32 + c0 + t));
 #pragma unroll
-            for (int m = 0; m < NFN; ++m) acc[m] = fmaf(__ldcs(a.val32 + lo + (int64_t)m * len + t), zj, acc[m]);
+            for (int m = 0; m < NFN; ++m) acc[m] = fmaf(__ldcs(vb + (int64_t)m * len + t), zj, acc[m]);
           }
         } else {
+          const int64_t r0 = f * NFN;
+          const int64_t lo = __ldcs(a.row_ptr + r0);
+          const int len = (int)(__ldcs(a.row_ptr + r0 + 1) - lo);
 #pragma unroll 4
           for (int t = gl; t < len; t += W) {
             const double zj = __ldcg(a.z + __ldcs(a.col + lo + t));
@@ -638,16 +641,27 @@ __global__ void diag_sqrt_kernel(int64_t n_rows, const int64_t* __restrict__ row
   }
 }
 
-__global__ void round_values_kernel(int64_t n_rows, const int64_t* __restrict__ row_ptr,
+// One warp per face: its padded column list and its NFN scaled rows in the FP32 layout.
+__global__ void round_values_kernel(int64_t n_faces, int nfn, const int64_t* __restrict__ row_ptr,
                                     const int32_t* __restrict__ col, const double* __restrict__ v,
-                                    const double* __restrict__ dsq, float* __restrict__ o) {
+                                    const int64_t* __restrict__ fptr32, const double* __restrict__ dsq,
+                                    float* __restrict__ o, int32_t* __restrict__ col32) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = w0; i < n_rows; i += nw) {
-    const double si = 1.0 / dsq[i];
-    for (int64_t t = row_ptr[i] + lane; t < row_ptr[i + 1]; t += 32)
-      __stcs(o + t, (float)(__ldcs(v + t) * si / dsq[col[t]]));
+  for (int64_t f = w0; f < n_faces; f += nw) {
+    const int64_t r0 = f * nfn, lo = row_ptr[r0];
+    const int len = (int)(row_ptr[r0 + 1] - lo);
+    const int64_t c0 = fptr32[f];
+    const int len32 = (int)(fptr32[f + 1] - c0);
+    for (int t = lane; t < len32; t += 32) col32[c0 + t] = t < len ? col[lo + t] : 0;
+    for (int m = 0; m < nfn; ++m) {
+      const double si = 1.0 / dsq[r0 + m];
+      float* orow = o + nfn * c0 + (int64_t)m * len32;
+      const double* vrow = v + lo + (int64_t)m * len;
+      for (int t = lane; t < len32; t += 32)
+        __stcs(orow + t, t < len ? (float)(__ldcs(vrow + t) * si / dsq[col[lo + t]]) : 0.0f);
+    }
   }
 }
 
@@ -896,7 +910,7 @@ cudaError_t pcg_iterations_team(const PcgArgs* probs, const int4* team, int nblo
 cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void* bar, cudaStream_t s, Prof* prof) {
   const int tok = prof_begin(prof, HYB_K_PCG_FUSED, s);
   cudaError_t e;
-  if (a.val32 && (!a.z32 || !a.dsq)) return cudaErrorInvalidValue;
+  if (a.val32 && (!a.z32 || !a.dsq || !a.fptr32 || !a.col32)) return cudaErrorInvalidValue;
   if (a.val32) {
     // FP32 values: 8 lanes per face load 32 contiguous bytes of a row per step (a full sector),
     // and the lanes' partial sums are reduced in FP32
@@ -920,14 +934,15 @@ cudaError_t pcg_iterations_fused(const PcgArgs& a, int count, double rtol, void*
   return e;
 }
 
-cudaError_t launch_round_values(int64_t n_rows, const int64_t* row_ptr, const int32_t* col, const double* v,
-                                double* dsq, float* o, cudaStream_t s, Prof* prof) {
+cudaError_t launch_round_values(int64_t n_rows, int nfn, const int64_t* row_ptr, const int32_t* col, const double* v,
+                                const int64_t* fptr32, double* dsq, float* o, int32_t* col32, cudaStream_t s,
+                                Prof* prof) {
   if (n_rows == 0) return cudaSuccess;
   int tok = prof_begin(prof, HYB_K_ELEMENT, s);
   diag_sqrt_kernel<<<152 * 4, kThreads, 0, s>>>(n_rows, row_ptr, col, v, dsq);
   prof_end(prof, tok, s);
   tok = prof_begin(prof, HYB_K_ELEMENT, s);
-  round_values_kernel<<<152 * 8, kThreads, 0, s>>>(n_rows, row_ptr, col, v, dsq, o);
+  round_values_kernel<<<152 * 8, kThreads, 0, s>>>(n_rows / nfn, nfn, row_ptr, col, v, fptr32, dsq, o, col32);
   prof_end(prof, tok, s);
   return cudaGetLastError();
 }
