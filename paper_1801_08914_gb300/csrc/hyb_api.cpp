@@ -115,6 +115,7 @@ struct hyb_ctx {
   int64_t* fptr32 = nullptr;               // mixed: the FP32 operator's padded face layout (F + 1 offsets)
   int32_t* col32 = nullptr;                // mixed: its padded column lists, one per face
   int op32 = 1;                            // mixed: PCG applies H from val32 (1) or from val (0)
+  bool val32_ready = false;                // the FP32 operator matches the current assembly
   std::vector<int32_t> h_list[2][2];       // host copies: [colour][path] (path 0 = FP64, 1 = FP32)
   double* Lstore = nullptr;
   double* zstore = nullptr;
@@ -450,13 +451,7 @@ int assemble_impl(hyb_ctx* c, const double* load, const double* ess, int mode) {
     cudaError_t e = launch_element(c->k, mode, a, c->stream, &c->prof);
     if (e != cudaSuccess) return cuda_status(e);
   }
-  if (c->precision == HYB_MIXED && c->n_path[1] > 0 && c->n_path[0] == 0) {
-    // the FP32 copy of H that the mixed context's PCG applies (H carries the FP32 elimination's
-    // error anyway; the FP64 accumulation above stays the reference for the refinement)
-    cudaError_t e = launch_round_values(c->n_lambda, c->sz.nfn, c->row_ptr, c->col, c->val, c->fptr32, c->dsq,
-                                        c->val32, c->col32, c->stream, &c->prof);
-    if (e != cudaSuccess) return cuda_status(e);
-  }
+  c->val32_ready = false;                  // the FP32 operator is prepared by the next solve
   st = finish_phase(c);
   if (st == HYB_OK) c->mode = mode;
   return st;
@@ -635,6 +630,15 @@ int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lamb
   // the FP32 rounding cannot hold (soft-hard test, Sec. 6.1, mass 10^-8: PCG breakdown)
   if (c->precision == HYB_MIXED && c->n_path[1] > 0 && c->n_path[0] == 0 && c->fused && c->op32 &&
       c->mode == MODE_HYB) {
+    if (!c->val32_ready) {
+      // the solver's preparation of the operator, like D^-1 for the FP64 values: the scaled FP32
+      // copy of H (H carries the FP32 elimination's error anyway; its FP64 values stay the
+      // reference that hyb_refine's exact residual is measured against)
+      cudaError_t e = launch_round_values(c->n_lambda, c->sz.nfn, c->row_ptr, c->col, c->val, c->fptr32, c->dsq,
+                                          c->val32, c->col32, c->stream, &c->prof);
+      if (e != cudaSuccess) return cuda_status(e);
+      c->val32_ready = true;
+    }
     a.val32 = c->val32;
     a.z32 = c->z32;
     a.dsq = c->dsq;

@@ -170,7 +170,7 @@ cudaError_t launch_axpy(int64_t n, const double* x, double* y, cudaStream_t s, P
 // The FP32 operator of a mixed context's PCG: dsq[i] = sqrt(H_ii), o[t] = (float)(H_ij / (dsq[i]
 // dsq[j])) (the diagonally scaled matrix: unit diagonal, |entries| <= 1 for SPD H, so rounding
 // it keeps it SPD where rounding H itself would not, e.g. across mass coefficients 10^-8..1);
-// profiled with the element phase, whose last step it is
+// the first solve after an assembly runs it (profiled with the PCG's vector kernels)
 cudaError_t launch_round_values(int64_t n_rows, int nfn, const int64_t* row_ptr, const int32_t* col, const double* v,
                                 const int64_t* fptr32, double* dsq, float* o, int32_t* col32, cudaStream_t s,
                                 Prof* prof);

@@ -191,8 +191,9 @@ __device__ bool s_tensor(const float* Y, const float* Pv, float* xhi, float* xlo
       }
     }
   tc::fence_before_sync();
-  __syncthreads();
+  __syncthreads();                                       // every thread is past the wait and the loads
   if (warp == 0) tc::tmem_dealloc(tm, 256);
+  if (tid == 0) tc::mbar_inval(&mbar);
   return ok;
 }
 

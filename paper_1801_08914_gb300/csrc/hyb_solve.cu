@@ -618,11 +618,13 @@ __device__ __forceinline__ void pcg_fused_body(const PcgArgs& a, int count, doub
   }
 }
 
-// Resident CTAs per SM: the FP64 form is bound by the FP64 pipe (more warps did not help), the
-// FP32-operator form by memory latency (long-scoreboard stalls with 16 warps per SM): it takes
-// a third CTA per SM (80 registers, no spills) where its row blocks are 9 x len, a second at 16.
+// Resident CTAs per SM: two (one for the FP64 form at 16 rows per face). The FP64 form is bound
+// by the FP64 pipe (more warps did not help); the FP32-operator form by memory latency, but a
+// third CTA per SM (80 registers) cost it more loads in flight per thread than it gained in
+// warps (5.9 against 3.9 ms per iteration at 96^3 RT_2), while at 16 rows per face a second CTA
+// (128 registers, no spills) helped (2.6 against 2.9 ms at 64^3 RT_3).
 template <int NFN, int W, bool F32>
-__global__ void __launch_bounds__(kThreads, F32 ? (NFN <= 9 ? 3 : 2) : (NFN <= 9 ? 2 : 1))
+__global__ void __launch_bounds__(kThreads, F32 ? 2 : (NFN <= 9 ? 2 : 1))
     pcg_fused_kernel(PcgArgs a, int count, double rtol2, GridBar* bar) {
   __shared__ double sh[kThreads];
   __shared__ double bc[3];
@@ -938,10 +940,10 @@ cudaError_t launch_round_values(int64_t n_rows, int nfn, const int64_t* row_ptr,
                                 const int64_t* fptr32, double* dsq, float* o, int32_t* col32, cudaStream_t s,
                                 Prof* prof) {
   if (n_rows == 0) return cudaSuccess;
-  int tok = prof_begin(prof, HYB_K_ELEMENT, s);
+  int tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
   diag_sqrt_kernel<<<152 * 4, kThreads, 0, s>>>(n_rows, row_ptr, col, v, dsq);
   prof_end(prof, tok, s);
-  tok = prof_begin(prof, HYB_K_ELEMENT, s);
+  tok = prof_begin(prof, HYB_K_PCG_VECTOR, s);
   round_values_kernel<<<152 * 8, kThreads, 0, s>>>(n_rows / nfn, nfn, row_ptr, col, v, fptr32, dsq, o, col32);
   prof_end(prof, tok, s);
   return cudaGetLastError();

@@ -39,10 +39,11 @@ __device__ __forceinline__ float to_tf32(float x) {
 }
 
 // One warp (all lanes) allocates `ncols` TMEM columns (a power of 2 >= 32) and writes the base
-// address to *dst (shared memory); the permit is released so other CTAs may allocate.
+// address to *dst (shared memory). The CTA keeps its permit to allocate: a CTA that processes
+// several elements in turn allocates again for each (relinquishing the permit after the first
+// allocation would make the next one illegal).
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)), "r"(ncols));
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
 }
 
 __device__ __forceinline__ void tmem_dealloc(uint32_t base, uint32_t ncols) {
@@ -66,6 +67,12 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
 // Arrive on the mbarrier once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(mbar)));
+}
+
+// Invalidate an mbarrier that no thread waits on any more, so that the same shared-memory
+// word can be initialised again (by the next element of a persistent CTA).
+__device__ __forceinline__ void mbar_inval(uint64_t* mbar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(mbar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
