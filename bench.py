@@ -448,22 +448,51 @@ def element_flops_mixed(k):
             + nq * nq * nb + nb ** 3 // 3 + nb * nb * nq + 2 * 2 * (2 * n * n + 2 * n * nq + 2 * nq * nq))
 
 
+def measured_hbm_peak():
+    """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the recipe's fallback 6800."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+    except (OSError, ValueError):
+        return 6800.0
+
+
 def recover_bytes_per_element(k):
-    """Algorithmic DRAM bytes of one FP64 hybridization recovery: the stored factor (packed lower
-    triangle, Y in place of L_bb) and z read, lambda_T gathered, u written."""
-    n, nb = 3 * (k + 1) ** 2 * (k + 2), 6 * (k + 1) ** 2
-    return 8 * (n * (n + 1) // 2 + 2 * n + nb)
+    """Algorithmic DRAM bytes of one FP64 hybridization recovery: the interior rows of the stored
+    factor (L_ii packed, L_bi), P = (A_T^{-1})_bb as a full square, z read, lambda_T gathered, u
+    written."""
+    p = k + 1
+    ni, nb = 3 * k * p * p, 6 * p * p
+    n = ni + nb
+    return 8 * (ni * (ni + 1) // 2 + nb * ni + nb * nb + 2 * n + nb)
 
 
-def recover_roofline_of(k, E, rec_ms, hbm_peak):
-    """HBM roofline of the FP64 recovery phase (None when it did not run)."""
+def recover_flops_per_element(k):
+    """FP64 flops of one recovery: one FMA per stored double read (L_ii, L_bi, P)."""
+    p = k + 1
+    ni, nb = 3 * k * p * p, 6 * p * p
+    return 2 * (ni * (ni + 1) // 2 + nb * ni + nb * nb)
+
+
+def recover_roofline_of(k, E, rec_ms, hbm_peak, fp64_peak=None):
+    """Roofline of the FP64 recovery phase (None when it did not run): its bytes against HBM and
+    its FMAs against the FP64 peak; `bound` names the larger of the two times."""
     if not rec_ms or rec_ms <= 0:
         return None
-    bpe = recover_bytes_per_element(k)
+    bpe, fpe = recover_bytes_per_element(k), recover_flops_per_element(k)
     gbs = E * bpe / (rec_ms * 1e-3) / 1e9
-    return {"kernel": f"recover_kernel<{k}> (FP64)", "bound": "hbm", "achieved": gbs, "peak": hbm_peak,
-            "unit": "GB/s", "frac": gbs / hbm_peak, "algorithmic_bytes_per_element": bpe,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    out = {"kernel": f"recover_kernel<{k}> (FP64)", "bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+           "unit": "GB/s", "frac": gbs / hbm_peak, "algorithmic_bytes_per_element": bpe,
+           "algorithmic_flops_per_element": fpe, "ms": rec_ms,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if fp64_peak:
+        tf = E * fpe / (rec_ms * 1e-3) / 1e12
+        out["fp64_tflops"] = tf
+        out["fp64_frac"] = tf / fp64_peak
+        out["hbm_frac"] = gbs / hbm_peak
+        if E * fpe / (fp64_peak * 1e12) > E * bpe / (hbm_peak * 1e9):
+            out.update(bound="alu", achieved=tf, peak=fp64_peak, unit="TFLOP/s", frac=tf / fp64_peak,
+                       peak_source="FP64 FMA throughput measured in this run (hyb_measure_fma_peak)")
+    return out
 
 
 def workload_name(cfg, p, args, mixed=False, sc=False, theta=0.0, n32=0, n64=0):
@@ -679,7 +708,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "roofline": roof if not args.assembly_only else element_roofline,
         "element_roofline": element_roofline,
-        "recover_roofline": (recover_roofline_of(p.order, E, prof["recover"][0] / args.steps, hbm_peak)
+        "recover_roofline": (recover_roofline_of(p.order, E, prof["recover"][0] / args.steps, hbm_peak, fp64_peak)
                              if not mixed and not sc else None),
         "phases": phases,
         "assembly_elements_per_s": E / (elem_ms * 1e-3) if elem_ms > 0 else None,
@@ -929,6 +958,7 @@ def run_precision(args):
     verts, alpha, beta, load = tt(p.vertices), tt(p.alpha), tt(p.beta), tt(p.load)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     fp64_peak = hyb.hyb_measure_fma_peak(True)
+    hbm_peak = measured_hbm_peak()
     fp32_peak = hyb.hyb_measure_fma_peak(False)
     clock_lines = []
 
@@ -1052,6 +1082,7 @@ def run_precision(args):
                                      "substitution; the mixed arm adds FP64 refinement steps (hyb_refine)")
         fm, ff = arms["mixed"]["full"], arms["fp64"]["full"]
         line["full_step"]["mixed_over_fp64"] = fm["elements_per_s"] / ff["elements_per_s"]
+        line["fp64"]["recover_roofline"] = recover_roofline_of(p.order, E, ff["recover_ms"], hbm_peak, fp64_peak)
     if measure_err:
         try:
             line["errors"] = measure_errors(hyb, cfg, ERR_N, args, oracle_procs, dev)

@@ -367,7 +367,7 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
     if ((st = dalloc(c, &c->slot, E))) return st;
     if (cudaMemcpy(c->slot, slot_h.data(), E * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
       return HYB_ERR_CUDA;
-    if ((st = dalloc(c, &c->Lstore, (size_t)c->n_path[0] * (size_t)tri_size(s.n)))) return st;
+    if ((st = dalloc(c, &c->Lstore, (size_t)c->n_path[0] * (size_t)fp64_store_doubles(order)))) return st;
     if ((st = dalloc(c, &c->Lstore32, (size_t)c->n_path[1] * (size_t)mixed_store_floats(order)))) return st;
     // the FP32 operator's layout: every face's column list padded to a multiple of 8 entries
     std::vector<int64_t> fp32(F + 1, 0);
@@ -380,7 +380,7 @@ int setup_impl(hyb_ctx* c, const hyb_mesh* m, int order, const double* alpha, co
     if ((st = dalloc(c, &c->z32, c->n_lambda))) return st;
     if ((st = dalloc(c, &c->dsq, c->n_lambda))) return st;
   } else {
-    if ((st = dalloc(c, &c->Lstore, (size_t)E * (size_t)tri_size(s.n)))) return st;
+    if ((st = dalloc(c, &c->Lstore, (size_t)E * (size_t)fp64_store_doubles(order)))) return st;
     for (int col = 0; col < 2; ++col) c->h_list[col][0] = lists[col];
   }
   if ((st = dalloc(c, &c->zstore, (size_t)E * s.n))) return st;
@@ -540,6 +540,8 @@ int recover_impl(hyb_ctx* c, const double* lam, double* u, int mode) {
   a.Lstore = c->Lstore;
   a.zstore = c->zstore;
   a.u = u;
+  a.status = c->status;
+  a.err_elem = c->err_elem;
   std::memcpy(a.wf, c->tabs[c->k].wf, sizeof(a.wf));
   if (c->precision == HYB_MIXED) {
     a.elem_list = c->plist[0];
@@ -1013,6 +1015,8 @@ int setup_batch_impl(hyb_batch* b, const hyb_mesh* meshes, const int* orders, co
     r.Lstore = c->Lstore;
     r.zstore = c->zstore;
     r.slot = c->slot;
+    r.status = b->status;
+    r.err_elem = c->err_elem;
     std::memcpy(r.wf, c->tabs[c->k].wf, sizeof(r.wf));
     b->h_rargs.push_back(r);
     PcgArgs g{};

@@ -568,12 +568,13 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
   }
   tiles::tile_fwd_vec<double, TB, NT>(R1, TBB, f + NI);
   double* zs = args.zstore + e * (int64_t)S::N;
-  for (int i = tid; i < S::N; i += NT) zs[i] = f[i];
-  for (int ib = tid; ib < NB; ib += NT) {           // g_T = D Y^T z_b
+  for (int i = tid; i < NI; i += NT) zs[i] = f[i];
+  for (int ib = tid; ib < NB; ib += NT) {           // x0_b = Y^T z_b (stored), g_T = D x0_b
     const int a = ib / NFN, m1 = ib % NFN;
-    if (ef[a] < 0) continue;
     double acc = 0.0;
     for (int m = ib; m < NB; ++m) acc = fma(Y[m * NB + ib], f[NI + m], acc);
+    zs[NI + ib] = acc;
+    if (ef[a] < 0) continue;
     const double v = ((a & 1) ? 1.0 : -1.0) * wf[m1] * acc;
     const int64_t gi = (int64_t)ef[a] * NFN + m1;
     if (args.colour == 1) args.rhs[gi] += v;
@@ -584,9 +585,11 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
     const int gi = ib >= jb ? ib : jb, gj = ib >= jb ? jb : ib;
     put(ib, jb, Sg[tiles::tcol(gi / TB, gj / TB, TBB) * TT + (gi % TB) + (gj % TB) * TB], true);
   }
-  for (int t = tid; t < NB * NB; t += NT) {          // Y in place of L_bb
-    const int i = t / NB, j = t % NB;
-    if (j <= i) A[tri(NI + i, NI + j)] = Y[t];
+  double* Pst = A + S::TRI;                          // P = Y^T Y for the recovery, full square
+  for (int t = tid; t < NB * NB; t += NT) {
+    const int ib = t / NB, jb = t % NB;
+    const int gi = ib >= jb ? ib : jb, gj = ib >= jb ? jb : ib;
+    __stcs(Pst + t, Sg[tiles::tcol(gi / TB, gj / TB, TBB) * TT + (gi % TB) + (gj % TB) * TB]);
   }
 }
 
@@ -601,7 +604,7 @@ __device__ __forceinline__ void element_body(const ElemArgs& args, const int64_t
 
   // ---- shared memory carve-up
   double* sp = smem;
-  double* A = S::A_SMEM ? sp : args.Lstore + es * (int64_t)S::TRI;
+  double* A = S::A_SMEM ? sp : args.Lstore + es * fp64_store_doubles(K);
   if (S::A_SMEM) sp += S::TRI;
   double* f = sp; sp += N;
   double* colbuf = sp; sp += N;
@@ -824,9 +827,9 @@ __device__ __forceinline__ void element_body(const ElemArgs& args, const int64_t
     __syncthreads();
   }
 
-  // ---- store z
+  // ---- store z (hybridization: z_i here, the face part x0_b = Y^T z_b below)
   double* zs = args.zstore + e * (int64_t)N;
-  for (int i = tid; i < N; i += NT) zs[i] = f[i];
+  for (int i = tid; i < (MODE == MODE_HYB ? NI : N); i += NT) zs[i] = f[i];
 
   // C_T = [0 D]: D_i = sign(face) * face weight on interior faces, 0 on boundary faces
   const int32_t* bo_face = ef;
@@ -870,24 +873,23 @@ __device__ __forceinline__ void element_body(const ElemArgs& args, const int64_t
     }
     for (int ib = tid; ib < NB; ib += NT) {
       const int a = ib / NFN, m1 = ib % NFN;
-      if (bo_face[a] < 0) continue;
       double acc = 0.0;
       for (int m = ib; m < NB; ++m) acc = fma(Y[tri(m, ib)], f[NI + m], acc);
+      zs[NI + ib] = acc;
+      if (bo_face[a] < 0) continue;
       const double v = ((a & 1) ? 1.0 : -1.0) * wf[m1] * acc;
       const int64_t gi = (int64_t)bo_face[a] * NFN + m1;
       if (args.colour == 1) args.rhs[gi] += v;
       else args.rhs[gi] = v;
     }
     __syncthreads();
-    // ---- store the factor with Y in place of L_bb
-    double* Ls = args.Lstore + es * (int64_t)S::TRI;
-    if (S::A_SMEM) {
-      for (int t = tid; t < S::TRI; t += NT) Ls[t] = A[t];
-      __syncthreads();
-    }
-    for (int t = tid; t < S::TRIB; t += NT) {
-      const int i = tri_row(t), jj = t - i * (i + 1) / 2;
-      Ls[tri(NI + i, NI + jj)] = Y[t];
+    // ---- store the factor (the recovery reads its interior rows) and P = Y^T Y, full square
+    double* Ls = args.Lstore + es * fp64_store_doubles(K);
+    if (S::A_SMEM)
+      for (int t = tid; t < S::TRI; t += NT) __stcs(Ls + t, A[t]);
+    for (int t = tid; t < NB * NB; t += NT) {
+      const int i = t / NB, jj = t % NB;
+      __stcs(Ls + S::TRI + t, YtY[i >= jj ? tri(i, jj) : tri(jj, i)]);
     }
   } else {
     // ---- static condensation: scatter S_hat (trailing block) and rhs_b = f_b - L_bi z_i
@@ -910,7 +912,7 @@ __device__ __forceinline__ void element_body(const ElemArgs& args, const int64_t
       else args.rhs[gi] = f[NI + ib];
     }
     if (S::A_SMEM) {
-      double* Ls = args.Lstore + es * (int64_t)S::TRI;
+      double* Ls = args.Lstore + es * fp64_store_doubles(K);
       for (int t = tid; t < S::TRI; t += NT) Ls[t] = A[t];
     }
   }

@@ -71,6 +71,15 @@ void prof_end(Prof* p, int token, cudaStream_t s);
 
 // status helpers
 __host__ __device__ inline int64_t tri_size(int n) { return (int64_t)n * (n + 1) / 2; }
+// FP64 factor store per element of order k: the packed lower factor of A_T (N (N + 1) / 2
+// doubles; the recovery reads its interior rows L_ii and L_bi) followed by P = (A_T^{-1})_bb as
+// a full NB x NB square (row-major), rounded up to an even count so that every element's store
+// starts on a 16-byte boundary (the recovery bulk-copies L_ii from there).
+__host__ __device__ constexpr int64_t fp64_store_doubles(int k) {
+  return ((int64_t)(3 * k * (k + 1) * (k + 1) + 6 * (k + 1) * (k + 1)) *
+              (3 * k * (k + 1) * (k + 1) + 6 * (k + 1) * (k + 1) + 1) / 2 +
+          (int64_t)(6 * (k + 1) * (k + 1)) * (6 * (k + 1) * (k + 1)) + 1) / 2 * 2;
+}
 
 // Host-side table construction (hyb_tables.cpp).
 void build_ref_tables(int k, RefTables* t);
@@ -183,9 +192,11 @@ struct RecoverArgs {
   int mode;
   const int32_t* elem_face;
   const double* lambda;       // multipliers (HB) or global face dofs (SC)
-  const double* Lstore;
+  const double* Lstore;       // fp64_store_doubles(k) per element (slot)
   const double* zstore;
   double* u;
+  int* status;                // HYB_ERR_TIMEOUT if a bulk copy did not complete in time
+  long long* err_elem;
   double wf[kMaxOpen * kMaxOpen];   // face Gauss weights of order k (C_T = [0 D])
 };
 cudaError_t launch_recover(const RecoverArgs& a, cudaStream_t s, Prof* prof);

@@ -403,59 +403,8 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     for (int t = tid; t < NV; t += NT) dst[t] = __ldcs(src + t);
     __syncthreads();
   } else {
-  // ---- G (Q_k mass weighted by beta / det J), its tiled Cholesky, G^{-1} -> global scratch.
-  // Scratch in the L_M region, which is free until the mass assembly.
-  {
-    float* Gf = Lt;                               // [NQK][NQK]
-    float* Gt = Gf + NQK * NQK;                   // tiles of the padded G
-    float* Xg = Gt + S::ZTS;                      // [NQP][NQP]: identity -> L^{-1} -> G^{-1}
-    float* T1 = Xg + NQP * NQP;                   // [Q][Q][p][p]
-    float* T2 = T1 + Q * Q * p * p;               // [Q][p^4]
-    float* Gd32 = T2 + Q * p * p * p * p;         // [NQ]
-    for (int q = tid; q < NQ; q += NT) Gd32[q] = (float)(beta * gd[q]);
-    __syncthreads();
-    for (int t = tid; t < Q * Q * p * p; t += NT) {
-      const int b0 = t % p, a0 = (t / p) % p, q1 = (t / (p * p)) % Q, q2 = t / (p * p * Q);
-      float acc = 0.f;
-      for (int q0 = 0; q0 < Q; ++q0) acc = fmaf(Gd32[(q2 * Q + q1) * Q + q0], VoVo[(a0 * p + b0) * Q + q0], acc);
-      T1[t] = acc;
-    }
-    __syncthreads();
-    for (int t = tid; t < Q * p * p * p * p; t += NT) {
-      const int b0 = t % p, a0 = (t / p) % p, b1 = (t / (p * p)) % p, a1 = (t / (p * p * p)) % p, q2 = t / (p * p * p * p);
-      float acc = 0.f;
-      for (int q1 = 0; q1 < Q; ++q1) acc = fmaf(T1[((q2 * Q + q1) * p + a0) * p + b0], VoVo[(a1 * p + b1) * Q + q1], acc);
-      T2[t] = acc;
-    }
-    __syncthreads();
-    for (int t = tid; t < NQK * NQK; t += NT) {
-      const int a = t / NQK, b = t % NQK;
-      const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
-      const int b0 = b % p, b1 = (b / p) % p, b2 = b / (p * p);
-      float acc = 0.f;
-      for (int q2 = 0; q2 < Q; ++q2)
-        acc = fmaf(T2[(((q2 * p + a1) * p + b1) * p + a0) * p + b0], VoVo[(a2 * p + b2) * Q + q2], acc);
-      Gf[t] = acc;
-    }
-    __syncthreads();
-    for (int t = tid; t < S::ZTS; t += NT) {      // pack the lower tiles of [[G, 0], [0, I]]
-      const int tile = t / TT, w = t % TT, rr = w % TB, cc = w / TB;
-      int J = 0, rem = tile;
-      while (rem >= TQ - J) { rem -= TQ - J; ++J; }
-      const int I = J + rem, i = I * TB + rr, j = J * TB + cc;
-      Gt[t] = (i < NQK && j < NQK) ? Gf[i * NQK + j] : (i == j ? 1.0f : 0.0f);
-    }
-    for (int t = tid; t < NQP * NQP; t += NT) Xg[t] = (t / NQP == t % NQP) ? 1.0f : 0.0f;
-    __syncthreads();
-    if (!chol_tiles32<TB, MR, MC, NT>(Gt, TQ, Xg, NQP, flag)) {
-      if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
-      return;
-    }
-    tiles::tile_bwd_mat<float, TB, NT>(Gt, TQ, Xg, NQP);
-    for (int t = tid; t < NQK * NQK; t += NT) Gi[t] = Xg[(t / NQK) * NQP + t % NQK];
-    __syncthreads();
-  }
-
+  // G^{-1} (the Q_k mass weighted by beta / det J, inverted in FP32) is in the element's store:
+  // mixed_load_kernel formed it before this launch
   // ---- FP32 alpha-mass M into the L_M tiles (lower triangle), essential rows -> identity.
   // Temporaries in the Xd region, which is free until D' is written.
   for (int t = tid; t < S::LT; t += NT) Lt[t] = 0.0f;
@@ -751,14 +700,94 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
 // ---- FP64 element load of the mixed path, before the FP32 elimination: f_T = M_T c_T by sum
 // factorisation; on boundary faces with essential data f_T -= A_{:,e} u_e (free rows) and
 // f_T = u_e (essential rows), zero essential data clearing the essential rows. Stored in the
-// element's slot of zstore, where the assembly (g_T) and the recovery read it.
+// element's slot of zstore, where the assembly (g_T) and the recovery read it. The same kernel
+// then forms the element's G^{-1} (g_inverse), which needs only the geometry and beta.
+// Layout (floats, every piece 16-byte aligned) of g_inverse's shared-memory scratch.
+template <int K>
+struct GScratch {
+  using S = MT<K>;
+  static constexpr int p = S::p, Q = S::Q;
+  static constexpr int r4(int n) { return (n + 3) / 4 * 4; }
+  static constexpr int VOVO = 0, GD = VOVO + r4(p * p * Q), GF = GD + r4(S::NQ), GT = GF + r4(S::NQK * S::NQK);
+  static constexpr int XG = GT + r4(S::ZTS), T1 = XG + r4(S::NQP * S::NQP), T2 = T1 + r4(Q * Q * p * p);
+  static constexpr int FLAG = T2 + r4(Q * p * p * p * p), TOTAL = FLAG + 8;
+};
+
 template <int K>
 struct LoadShape {
   static constexpr int P = K + 2, p = K + 1, Q = K + 2, NQ = Q * Q * Q, NFN = p * p, N = 3 * K * p * p + 6 * NFN;
   static constexpr int NC = P * p * p, TMP64 = 3 * P * Q * Q, NT = 128;
   static constexpr int D64 = 24 + 24 + 2 * P * Q + p * Q + 2 * Q + NFN + 7 * NQ + 3 * N + 6 * NQ + NQ + NC + 2 * TMP64;
-  static constexpr size_t SMEM = sizeof(double) * D64;
+  // the G^{-1} scratch (floats) starts where the FP64 load scratch (after f_T) started
+  static constexpr int PREFIX = (24 + 24 + 2 * P * Q + p * Q + 2 * Q + NFN + 7 * NQ + N + 1) / 2 * 2;
+  using S = MT<K>;
+  static constexpr int GF = GScratch<K>::TOTAL;
+  static constexpr int DTOT = D64 > PREFIX + (GF + 1) / 2 ? D64 : PREFIX + (GF + 1) / 2;
+  static constexpr size_t SMEM = sizeof(double) * DTOT;
 };
+
+// ---- G^{-1} of one element into its FP32 store (CTA of NT threads): the Q_k mass weighted by
+// beta / det J (gd: det J times the quadrature weights) by sum factorisation in FP32, its tiled
+// Cholesky with the identity carried along (X = L^{-1}), then X = L^{-T} L^{-1}. fl: GF floats.
+// Returns false (every thread) if G is not positive definite.
+template <int K, int NT>
+__device__ bool g_inverse(double beta, const double* gd, const double* Vo, float* fl, float* Gi) {
+  using S = MT<K>;
+  constexpr int p = S::p, Q = S::Q, NQ = S::NQ, NQK = S::NQK, NQP = S::NQP, TB = S::TB, TT = S::TT, TQ = S::TQ;
+  const int tid = threadIdx.x;
+  using GS = GScratch<K>;
+  float* VoVo = fl + GS::VOVO;                  // [p][p][Q]
+  float* Gd32 = fl + GS::GD;                    // [NQ]
+  float* Gf = fl + GS::GF;                      // [NQK][NQK]
+  float* Gt = fl + GS::GT;                      // tiles of the padded G
+  float* Xg = fl + GS::XG;                      // [NQP][NQP]: identity -> L^{-1} -> G^{-1}
+  float* T1 = fl + GS::T1;                      // [Q][Q][p][p]
+  float* T2 = fl + GS::T2;                      // [Q][p^4]
+  float* flag = fl + GS::FLAG;
+  for (int i = tid; i < p * p * Q; i += NT) {
+    const int q = i % Q, b = (i / Q) % p, a = i / (Q * p);
+    VoVo[i] = (float)Vo[a * Q + q] * (float)Vo[b * Q + q];
+  }
+  for (int q = tid; q < NQ; q += NT) Gd32[q] = (float)(beta * gd[q]);
+  __syncthreads();
+  for (int t = tid; t < Q * Q * p * p; t += NT) {
+    const int b0 = t % p, a0 = (t / p) % p, q1 = (t / (p * p)) % Q, q2 = t / (p * p * Q);
+    float acc = 0.f;
+    for (int q0 = 0; q0 < Q; ++q0) acc = fmaf(Gd32[(q2 * Q + q1) * Q + q0], VoVo[(a0 * p + b0) * Q + q0], acc);
+    T1[t] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < Q * p * p * p * p; t += NT) {
+    const int b0 = t % p, a0 = (t / p) % p, b1 = (t / (p * p)) % p, a1 = (t / (p * p * p)) % p, q2 = t / (p * p * p * p);
+    float acc = 0.f;
+    for (int q1 = 0; q1 < Q; ++q1) acc = fmaf(T1[((q2 * Q + q1) * p + a0) * p + b0], VoVo[(a1 * p + b1) * Q + q1], acc);
+    T2[t] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < NQK * NQK; t += NT) {
+    const int a = t / NQK, b = t % NQK;
+    const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
+    const int b0 = b % p, b1 = (b / p) % p, b2 = b / (p * p);
+    float acc = 0.f;
+    for (int q2 = 0; q2 < Q; ++q2)
+      acc = fmaf(T2[(((q2 * p + a1) * p + b1) * p + a0) * p + b0], VoVo[(a2 * p + b2) * Q + q2], acc);
+    Gf[t] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < S::ZTS; t += NT) {      // pack the lower tiles of [[G, 0], [0, I]]
+    const int tile = t / TT, w = t % TT, rr = w % TB, cc = w / TB;
+    int J = 0, rem = tile;
+    while (rem >= TQ - J) { rem -= TQ - J; ++J; }
+    const int I = J + rem, i = I * TB + rr, j = J * TB + cc;
+    Gt[t] = (i < NQK && j < NQK) ? Gf[i * NQK + j] : (i == j ? 1.0f : 0.0f);
+  }
+  for (int t = tid; t < NQP * NQP; t += NT) Xg[t] = (t / NQP == t % NQP) ? 1.0f : 0.0f;
+  __syncthreads();
+  if (!chol_tiles32<TB, S::MR, S::MC, NT>(Gt, TQ, Xg, NQP, flag)) return false;
+  tiles::tile_bwd_mat<float, TB, NT>(Gt, TQ, Xg, NQP);
+  for (int t = tid; t < NQK * NQK; t += NT) Gi[t] = Xg[(t / NQK) * NQP + t % NQK];
+  return true;
+}
 
 template <int K>
 __device__ void mixed_load_body(const ElemArgs& args, const int64_t e, double* smem) {
@@ -813,10 +842,15 @@ __device__ void mixed_load_body(const ElemArgs& args, const int64_t e, double* s
   }
   double* fs = args.zstore + e * (int64_t)N;
   for (int i = tid; i < N; i += NT) fs[i] = f[i];
+  __syncthreads();                               // the FP64 scratch after f_T is free
+  const int64_t slot = args.slot ? args.slot[e] : e;
+  float* Gi = args.Lstore32 + slot * MT<K>::STORE + MT<K>::LTA + MT<K>::XDA + MT<K>::ZTS;
+  if (!g_inverse<K, NT>(beta, gd, Vo, reinterpret_cast<float*>(smem + L::PREFIX), Gi) && tid == 0)
+    set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
 }
 
 template <int K>
-__global__ void __launch_bounds__(LoadShape<K>::NT) mixed_load_kernel(ElemArgs args) {
+__global__ void __launch_bounds__(LoadShape<K>::NT, 8) mixed_load_kernel(ElemArgs args) {
   extern __shared__ double smem[];
   const int64_t li = blockIdx.x;
   if (li >= args.n_list) return;
@@ -824,7 +858,7 @@ __global__ void __launch_bounds__(LoadShape<K>::NT) mixed_load_kernel(ElemArgs a
 }
 
 template <int K>
-__global__ void __launch_bounds__(LoadShape<K>::NT) mixed_load_kernel_batch(const ElemArgs* probs, const int2* items,
+__global__ void __launch_bounds__(LoadShape<K>::NT, 8) mixed_load_kernel_batch(const ElemArgs* probs, const int2* items,
                                                                            int64_t n_items) {
   extern __shared__ double smem[];
   const int64_t li = blockIdx.x;

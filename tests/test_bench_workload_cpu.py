@@ -22,12 +22,20 @@ def test_workload_names():
 
 
 def test_recover_roofline_arithmetic():
-    """Bytes of the FP64 recovery per element: packed factor n(n+1)/2, z and u (n each), lambda_T
-    (n_b), 8 bytes each; RT_3: n = 240, n_b = 96."""
-    assert bench.recover_bytes_per_element(3) == 8 * (240 * 241 // 2 + 2 * 240 + 96)
-    assert bench.recover_bytes_per_element(0) == 8 * (6 * 7 // 2 + 12 + 6)
+    """The FP64 recovery per element reads the interior rows of the factor (L_ii packed: n_i(n_i+1)/2,
+    L_bi: n_b n_i), P = (A^{-1})_bb as a full square (n_b^2), z (n) and lambda_T (n_b), writes u (n):
+    8 bytes each, one FMA per stored double. RT_3: n_i = 144, n_b = 96; RT_0: n_i = 0, n_b = 6."""
+    assert bench.recover_bytes_per_element(3) == 8 * (144 * 145 // 2 + 96 * 144 + 96 * 96 + 2 * 240 + 96)
+    assert bench.recover_flops_per_element(3) == 2 * (144 * 145 // 2 + 96 * 144 + 96 * 96)
+    assert bench.recover_bytes_per_element(0) == 8 * (36 + 12 + 6)
     r = bench.recover_roofline_of(3, 1000, 2.0, 6771.0)
     assert r["bound"] == "hbm" and abs(r["achieved"] - 1000 * bench.recover_bytes_per_element(3) / 2e-3 / 1e9) < 1e-9
+    # with the FP64 peak known, the larger of the two times names the bound: at 1.25 TFLOP/s the
+    # FMAs (one per 8 bytes) take longer than the bytes at 6771 GB/s
+    r = bench.recover_roofline_of(3, 1000, 2.0, 6771.0, 1.25)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 1000 * bench.recover_flops_per_element(3) / 2e-3 / 1e12) < 1e-12
+    assert abs(r["hbm_frac"] * 6771.0 - 1000 * bench.recover_bytes_per_element(3) / 2e-3 / 1e9) < 1e-6
     assert bench.recover_roofline_of(3, 1000, 0.0, 6771.0) is None
 
 
