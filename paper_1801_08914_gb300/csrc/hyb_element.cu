@@ -46,14 +46,21 @@ struct EK {
   static constexpr int P = K + 2, p = K + 1, Q = K + 2, NQ = Q * Q * Q;
   static constexpr int NFN = p * p, NI = 3 * K * p * p, NB = 6 * NFN, N = NI + NB;
   static constexpr int NC = P * p * p;                 // functions per component
-  static constexpr int NT = K == 0 ? 32 : K == 1 ? 64 : K == 2 ? 128 : 512;
-  static constexpr bool A_SMEM = K <= 2;
-  // RT_3: the elimination runs on 16 x 16 tiles (element_tail_tiled): interior block L_ii and
-  // interface rows L_bi resident together, then the Schur complement of the face block
-  static constexpr int TB = 16, TI = NI / TB, TBB = NB / TB;
+  static constexpr int NT = K == 0 ? 32 : K == 1 ? 64 : K == 2 ? 256 : 512;
+  // RT_2 and RT_3: the elimination runs on NFN x NFN tiles (element_tail_tiled; one tile per
+  // face, 3k tiles per interior component block): interior block L_ii and interface rows L_bi
+  // resident together, then the Schur complement of the face block. A_T is assembled into the
+  // element's factor store in HBM there (packed), so that the tiles fit beside it.
+  static constexpr bool TILED_PATH = K >= 2;
+  static constexpr bool A_SMEM = !TILED_PATH;
+  static constexpr int TB = TILED_PATH ? NFN : 16, TI = NI / TB, TBB = NB / TB;
+  static constexpr int MR = K == 2 ? 3 : 2, MC = MR;         // register micro-tiles of the updates
   static constexpr int R1 = TI * (TI + 1) / 2 * TB * TB;     // L_ii tiles, later the face-block tiles
   static constexpr int R2 = TBB * TI * TB * TB;              // L_bi tiles, later Y = L_bb^{-1} (NB x NB)
-  static constexpr int TILED = K == 3 ? R1 + R2 : 0;
+  // the face block needs its own tiles and those of S = Y^T Y (2 x 21 tiles): past R1 where R1
+  // is smaller (RT_2: 21 tiles)
+  static constexpr int RX = 2 * TBB * (TBB + 1) / 2 * TB * TB > R1 ? 2 * TBB * (TBB + 1) / 2 * TB * TB - R1 : 0;
+  static constexpr int TILED = TILED_PATH ? R1 + R2 + RX : 0;
   static constexpr int TRI = N * (N + 1) / 2;
   static constexpr int TRIB = NB * (NB + 1) / 2;
   // 1-D tables: Vc, Dc (P x Q), Vo (p x Q), products VcVc, DcDc (P P Q), VcVo, DcVo (P p Q), VoVo (p p Q)
@@ -285,9 +292,9 @@ __device__ void load_vector(const double* coef, const Tabs& tb, const double* Gu
 // the update of Y's later block rows and the rank-16 term Y_J^T Y_J of S share one phase; it
 // fills the sub-partitions that the one-warp diagonal step (warp 0, look-ahead) leaves idle.
 // Two barriers per tile column. Returns false in every thread on a bad pivot.
-template <int NT, int MR, int MC>
+template <int TB, int NT, int MR, int MC>
 __device__ bool face_block_hyb(double* Lt, double* Y, double* Sg, double* flag) {
-  constexpr int TB = 16, T = 6, NB = T * TB, TT = TB * TB, PM = (TB / MR) * (TB / MC);
+  constexpr int T = 6, NB = T * TB, TT = TB * TB, PM = (TB / MR) * (TB / MC);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   auto tp = [&](int I, int J) { return Lt + tiles::tcol(I, J, T) * TT; };
   for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0 : 0.0;
@@ -373,12 +380,12 @@ __device__ bool face_block_hyb(double* Lt, double* Y, double* Sg, double* flag) 
   return true;
 }
 
-template <int MODE>
+template <int K, int MODE>
 __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double* A, double* f, double* R,
                                    double* flag, const double* wf) {
-  using S = EK<3>;
+  using S = EK<K>;
   constexpr int NI = S::NI, NB = S::NB, NFN = S::NFN, NT = S::NT, TB = S::TB, TI = S::TI, TBB = S::TBB;
-  constexpr int T = TI + TBB, TT = TB * TB, MR = 2, MC = 2;   // small micro-tiles: more items to spread
+  constexpr int T = TI + TBB, TT = TB * TB, MR = S::MR, MC = S::MC;   // small micro-tiles: more items to spread
   const int tid = threadIdx.x;
   double* R1 = R;                                   // L_ii tiles (packed over TI), then A_bb tiles
   double* R2 = R + S::R1;                           // L_bi tiles [I - TI][J], then Y
@@ -419,14 +426,13 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
       if (dst[u] >= 0) R[dst[u]] = v[u];
   }
   __syncthreads();
-  auto out = [&](int J) {
-    return [A, J](int i, int l, double v) { A[tri(J * 16 + i, J * 16 + l)] = v; };
-  };
-  if (!tiles::tile_chol_la<double, TB, MR, MC, NT>(tp, T, TI, TI, flag, out)) {
+  if (!tiles::tile_chol_la<double, TB, MR, MC, NT>(tp, T, TI, TI, flag, [](int) { return tiles::NoOut{}; })) {
     if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
     return;
   }
-  // ---- 2. forward substitution of the load; the off-diagonal factor tiles to the slot
+  // ---- 2. forward substitution of the load; the factor tiles to the slot, the diagonal ones
+  // as the inverses of their triangles (lower, what the recovery's blocked back substitution
+  // applies)
   tiles::tile_fwd_vec<double, TB, NT>(R1, TI, f);
   for (int ib = tid; ib < NB; ib += NT) {
     const int I = ib / TB, r = ib % TB;
@@ -446,7 +452,7 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
       J = 0;
       while (rem >= TI - J) { rem -= TI - J; ++J; }
       I = J + rem;
-      if (I == J) continue;                        // diagonal tiles: written by the factorisation
+      if (I == J && w % TB < w / TB) continue;     // strict upper part of an inverted diagonal tile
     } else {
       const int tile = (t - S::R1) / TT;
       I = TI + tile / TI;
@@ -558,11 +564,12 @@ __device__ void element_tail_tiled(const ElemArgs& args, const int64_t e, double
     return;
   }
   // ---- 4b. hybridization: L_bb, Y = L_bb^{-1} (in R2) and S = Y^T Y (tiles after the
-  // face block's in R1) in one pass; z_b, g_T, S_T scattered, Y into the slot
+  // face block's in R1, or past R2 where R1 holds only the face block) in one pass; x0_b,
+  // g_T, S_T scattered, P = S into the store
   double* Y = R2;                                    // [NB][NB], row-major
-  double* Sg = R1 + TBB * (TBB + 1) / 2 * TT;
-  static_assert(2 * TBB * (TBB + 1) / 2 * TT <= S::R1 && NB * NB <= S::R2, "face block buffers");
-  if (!face_block_hyb<NT, MR, MC>(R1, Y, Sg, flag)) {
+  double* Sg = S::RX > 0 ? R + S::R1 + S::R2 : R1 + TBB * (TBB + 1) / 2 * TT;
+  static_assert(2 * TBB * (TBB + 1) / 2 * TT <= S::R1 + S::RX && NB * NB <= S::R2, "face block buffers");
+  if (!face_block_hyb<TB, NT, MR, MC>(R1, Y, Sg, flag)) {
     if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
     return;
   }
@@ -769,8 +776,8 @@ __device__ __forceinline__ void element_body(const ElemArgs& args, const int64_t
     }
   }
   __syncthreads();
-  if constexpr (K == 3) {
-    element_tail_tiled<MODE>(args, e, A, f, U, flag, wf);
+  if constexpr (S::TILED_PATH) {
+    element_tail_tiled<K, MODE>(args, e, A, f, U, flag, wf);
     return;
   }
 

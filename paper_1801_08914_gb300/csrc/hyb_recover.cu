@@ -13,9 +13,12 @@
 // when the CTA starts, so it lands while the CTA streams P and L_bi from HBM with coalesced
 // loads (consecutive threads read consecutive entries of one stored row; P is stored as a full
 // square so that x_b = x0_b - P w reads it once, column by column). The back substitution runs
-// on BS-row blocks from shared memory: one warp solves the BS x BS diagonal triangle (shuffle
-// broadcasts, reciprocal pivots formed in parallel beforehand), then every thread applies the
-// block's rows to the rows above it: two barriers per block instead of two per row. Every
+// on BS-row blocks from shared memory. The tiled element kernels (RT_2, RT_3) store each
+// diagonal block of L_ii as the inverse of its triangle (BS = the tile size), so a block's
+// unknowns are one short triangular product (8 lanes per unknown, shuffle sums); RT_0/RT_1
+// store the factor itself and one warp solves the diagonal triangle (shuffle broadcasts,
+// reciprocal pivots formed in parallel beforehand). Then every thread applies the block's
+// rows to the rows above it: two barriers per block instead of two per row. Every
 // stored double feeds one FMA, so on this part (2 FP64 FMAs per clock per SM) the kernel is
 // bound by FP64 issue, slightly above the HBM time of its bytes.
 #include <cuda_runtime.h>
@@ -33,9 +36,11 @@ template <int K>
 struct RK {
   static constexpr int p = K + 1, NFN = p * p, NI = 3 * K * p * p, NB = 6 * NFN, N = NI + NB;
   static constexpr int TRI = N * (N + 1) / 2, TRII = NI * (NI + 1) / 2;
-  static constexpr int NT = K <= 1 ? 32 : K == 2 ? 128 : 256;
-  static constexpr int BS = K == 3 ? 24 : K == 2 ? 18 : K == 1 ? 12 : 1;   // divides NI, <= 32
+  static constexpr int NT = K <= 1 ? 32 : K == 2 ? 128 : 512;
+  static constexpr bool INV = K >= 2;                          // diagonal blocks stored inverted
+  static constexpr int BS = INV ? NFN : K == 1 ? 12 : 1;       // divides NI, <= 32
   static constexpr int NBLK = NI / BS;
+  static_assert(NBLK * BS == NI, "whole blocks");
   static constexpr int CP = NT / NB > 0 ? NT / NB : 1;         // column chunks of x_b = x0_b - P w
   static constexpr int CI = NT / (NI > 0 ? NI : 1) > 0 ? NT / (NI > 0 ? NI : 1) : 1;   // of L_bi^T x_b
   static constexpr int LII_BYTES = (TRII * 8 + 15) / 16 * 16;  // bulk copy: a multiple of 16 bytes
@@ -45,7 +50,7 @@ struct RK {
   static constexpr int SMEM_DOUBLES = LII + N + NB + NI + NI + PART;
   static constexpr size_t SMEM = sizeof(double) * SMEM_DOUBLES;
   static_assert(K == 0 || NI % BS == 0, "blocks split the interior rows");
-  static_assert(BS <= 32, "one warp per diagonal block");
+  static_assert(BS <= 32 && (!INV || 8 * BS <= NT), "one warp per diagonal block; 8 lanes per unknown");
   static_assert(fp64_store_doubles(K) >= TRI + NB * NB, "store holds the packed factor and P");
   static_assert((fp64_store_doubles(K) * 8) % 16 == 0 && (LII == 0 || TRI >= LII), "bulk copy alignment");
 };
@@ -155,13 +160,28 @@ __device__ __forceinline__ void recover_body(const RecoverArgs& a, const int64_t
       double s = part[i];
       for (int c = 1; c < CI; ++c) s += part[c * NI + i];
       rhs[i] = z[i] - s;
-      invd[i] = 1.0 / lii[tri(i, i)];
+      if constexpr (!R::INV) invd[i] = 1.0 / lii[tri(i, i)];
     }
     csync();
     // ---- L_ii^T x_i = rhs by blocks of BS rows, last block first
     for (int blk = R::NBLK - 1; blk >= 0; --blk) {
       const int r0 = blk * BS;
-      if (warp == 0) {
+      if constexpr (R::INV) {
+        // x_J = Dinv^T rhs_J, Dinv = L_JJ^{-1} (lower): unknown c sums over the rows r >= c,
+        // the 8 lanes of its group taking every 8th row
+        const int c = tid >> 3, q = tid & 7;
+        double acc = 0.0;
+        if (c < BS)
+#pragma unroll
+          for (int r = q; r < BS; r += 8)
+            if (r >= c) acc = fma(lii[tri(r0 + r, r0 + c)], rhs[r0 + r], acc);
+        if (warp < (8 * BS + 31) / 32) {   // whole warps (lanes past the last unknown add zeros)
+          acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          if (q == 0 && c < BS) x[r0 + c] = acc;
+        }
+      } else if (warp == 0) {
         double v = lane < BS ? rhs[r0 + lane] : 0.0;
 #pragma unroll
         for (int r = BS - 1; r >= 0; --r) {
@@ -171,12 +191,16 @@ __device__ __forceinline__ void recover_body(const RecoverArgs& a, const int64_t
         }
       }
       csync();
-      // rows above the block: rhs_s -= sum_r L(r0 + r, s) x_{r0 + r}
+      // rows above the block: rhs_s -= sum_r L(r0 + r, s) x_{r0 + r} (two partial sums)
       for (int s = tid; s < r0; s += NT) {
-        double acc = rhs[s];
+        double a0 = rhs[s], a1 = 0.0;
 #pragma unroll
-        for (int r = 0; r < BS; ++r) acc = fma(-lii[tri(r0 + r, s)], x[r0 + r], acc);
-        rhs[s] = acc;
+        for (int r = 0; r + 1 < BS; r += 2) {
+          a0 = fma(-lii[tri(r0 + r, s)], x[r0 + r], a0);
+          a1 = fma(-lii[tri(r0 + r + 1, s)], x[r0 + r + 1], a1);
+        }
+        if (BS & 1) a0 = fma(-lii[tri(r0 + BS - 1, s)], x[r0 + BS - 1], a0);
+        rhs[s] = a0 + a1;
       }
       csync();
     }

@@ -83,8 +83,8 @@ __device__ __forceinline__ void diag_factor_invert(F* D, F* flag, const Out& out
   __syncwarp();
 }
 
-// ---- one warp, TB even and at most 16: the same factorisation and inversion with two
-// columns per instruction. On this part an FP64 warp instruction holds its sub-partition's
+// ---- one warp, TB at most 16: the same factorisation and inversion with two columns per
+// instruction (an odd TB leaves the last column pair half empty). On this part an FP64 warp instruction holds its sub-partition's
 // FP64 unit as long as its dependent successor waits, whatever the number of active lanes, so
 // what counts is the number of instructions the warp issues; in FP32 the halved per-lane
 // arrays keep the factor in registers inside large kernels. Lane (i, h) = (lane & 15,
@@ -95,8 +95,8 @@ __device__ __forceinline__ void diag_factor_invert(F* D, F* flag, const Out& out
 // integer bits. About half the instructions of the one-row-per-lane form.
 template <typename F, int TB, typename Out>
 __device__ __forceinline__ void diag_factor_invert2(F* D, F* flag, const Out& out) {
-  static_assert(TB % 2 == 0 && TB <= 16, "two half-warps of at most 8 columns");
-  constexpr int H = TB / 2;
+  static_assert(TB <= 16, "two half-warps of at most 8 columns");
+  constexpr int H = (TB + 1) / 2;
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, i = lane & 15, h = lane >> 4;
   F c[H], x[H];
@@ -144,7 +144,7 @@ __device__ __forceinline__ void diag_factor_invert2(F* D, F* flag, const Out& ou
     for (int j = 0; j < H; ++j) {
       const int l = 2 * j + h;
       if (l <= i) out(i, l, c[j]);
-      D[l + i * TB] = x[j];
+      if (l < TB) D[l + i * TB] = x[j];
     }
   }
   __syncwarp();
@@ -152,7 +152,7 @@ __device__ __forceinline__ void diag_factor_invert2(F* D, F* flag, const Out& ou
 
 template <typename F, int TB, typename Out>
 __device__ __forceinline__ void diag_step(F* D, F* flag, const Out& out) {
-  if constexpr (TB % 2 == 0 && TB <= 16) diag_factor_invert2<F, TB>(D, flag, out);
+  if constexpr (TB <= 16) diag_factor_invert2<F, TB>(D, flag, out);
   else diag_factor_invert<F, TB>(D, flag, out);
 }
 
