@@ -241,6 +241,52 @@ int hyb_set_pcg_fused(hyb_ctx* ctx, int on);
  */
 int hyb_set_mixed_operator(hyb_ctx* ctx, int fp32);
 
+/* Preconditioners of the reduced-system PCG. */
+enum {
+  HYB_PC_JACOBI = 0,   /* the diagonal of H (default) */
+  HYB_PC_AMG = 1       /* one V-cycle of the aggregation multigrid below */
+};
+
+/*
+ * hyb_set_preconditioner -- the preconditioner of hyb_solve_reduced and of hyb_refine's inner
+ *  solves (arXiv:1801.08914, Sec. 4: H is spectrally equivalent to a mesh-dependent H^1-type
+ *  norm of the face functions, so an H^1-type algebraic multigrid gives mesh-independent
+ *  iteration counts; Sec. 6.1 uses BoomerAMG). HYB_PC_AMG is this library's own aggregation
+ *  multigrid for the structured hexahedral mesh:
+ *   - every interior face belongs to the 2x2x2 block of cells (i/2, j/2, l/2) of its grid
+ *     position (plane index along its normal, cell indices across); all nodes of a block's
+ *     faces share one coarse unknown (piecewise-constant prolongation); coarser levels
+ *     aggregate the block grid 2x2x2 again until at most `coarsest` unknowns remain or one
+ *     point is left (a block without faces gets the equation x = 0);
+ *   - Galerkin coarse operators P^T A P (27-point operators on the block grids);
+ *   - Chebyshev smoothing of degree `chebyshev_degree` (1..4) for D^{-1} A on [lmax/30, lmax],
+ *     lmax = 1.1 x a 12-step power estimate, the same before and after the coarse correction
+ *     (a symmetric positive definite V-cycle);
+ *   - the coarsest level solved with its dense inverse (coarsest: 1..4096 unknowns).
+ *  Built on the first solve after hyb_setup (buffers: about 5 vectors of n_lambda doubles
+ *  plus the coarse levels), its numeric part on the first solve after every assembly. The
+ *  PCG starts from lambda = 0 and stops at ||r||_2 <= rtol ||b||_2, as with HYB_PC_JACOBI; it
+ *  applies the FP64 values of H (also on HYB_MIXED contexts). Static condensation's S is
+ *  H(div)-like, not H^1-like: the multigrid is built for H.
+ *  HYB_ERR_INVALID_ARG for another kind or parameters out of range.
+ */
+int hyb_set_preconditioner(hyb_ctx* ctx, int kind, int chebyshev_degree, int coarsest);
+
+/*
+ * hyb_amg_apply -- z = M^{-1} r, one V-cycle of the multigrid of hyb_set_preconditioner
+ *  (HYB_PC_AMG) for the current assembly. r, z: device, n_lambda doubles each, not
+ *  overlapping. Synchronises the context's stream. HYB_ERR_INVALID_ARG before an assembly or
+ *  when the preconditioner is not HYB_PC_AMG.
+ */
+int hyb_amg_apply(hyb_ctx* ctx, const double* r, double* z);
+
+/*
+ * hyb_amg_info -- levels of the multigrid (*levels), the unknowns of the first `cap` levels
+ *  (sizes, may be null) and the power estimates of lmax(D^{-1} A) of the smoothed levels
+ *  (lmax, may be null; 0 for the coarsest). Builds the multigrid if needed (as hyb_amg_apply).
+ */
+int hyb_amg_info(hyb_ctx* ctx, int* levels, int64_t* sizes, double* lmax, int cap);
+
 /*
  * hyb_barrier_selftest -- exercise the grid barrier of the fused PCG kernel.
  *  Runs `rounds` barrier-and-reduce steps over a cooperative grid (one block per

@@ -116,6 +116,10 @@ struct hyb_ctx {
   int32_t* col32 = nullptr;                // mixed: its padded column lists, one per face
   int op32 = 1;                            // mixed: PCG applies H from val32 (1) or from val (0)
   bool val32_ready = false;                // the FP32 operator matches the current assembly
+  int pc = HYB_PC_JACOBI;                  // PCG preconditioner
+  int pc_degree = 2, pc_coarsest = 512;    // multigrid: Chebyshev degree, coarsest-level size
+  Amg* amg = nullptr;
+  bool amg_ready = false;                  // the multigrid matches the current assembly
   std::vector<int32_t> h_list[2][2];       // host copies: [colour][path] (path 0 = FP64, 1 = FP32)
   double* Lstore = nullptr;
   double* zstore = nullptr;
@@ -452,6 +456,7 @@ int assemble_impl(hyb_ctx* c, const double* load, const double* ess, int mode) {
     if (e != cudaSuccess) return cuda_status(e);
   }
   c->val32_ready = false;                  // the FP32 operator is prepared by the next solve
+  c->amg_ready = false;                    // and so is the multigrid
   st = finish_phase(c);
   if (st == HYB_OK) c->mode = mode;
   return st;
@@ -609,7 +614,35 @@ int staticcond_assemble(hyb_ctx* ctx, const double* load, const double* ess) {
 namespace {
 
 // Diagonal PCG on the assembled H (or S) with right-hand side b, x0 = 0.
+// the multigrid of the current assembly (built on first use, its numeric part after every
+// assembly)
+int amg_prepare(hyb_ctx* c) {
+  int st;
+  if (!c->amg) {
+    st = amg_create(c->nx, c->ny, c->nz, c->sz.nfn, c->pc_degree, c->pc_coarsest, c->row_ptr, c->col, c->val,
+                    c->n_iface_axis, &c->amg);
+    if (st) return st;
+    c->amg_ready = false;
+  }
+  if (!c->amg_ready) {
+    if ((st = amg_numeric(c->amg, c->stream))) return st;
+    c->amg_ready = true;
+  }
+  return HYB_OK;
+}
+
 int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lambda, int* iters, double* rel_res) {
+  if (c->pc == HYB_PC_AMG) {
+    // CG preconditioned by the aggregation multigrid (Sec. 4: H is H^1-like), FP64 values of H
+    int st = amg_prepare(c);
+    if (st) return st;
+    const int tok = prof_begin(&c->prof, HYB_K_PCG_FUSED, c->stream);
+    st = amg_pcg(c->amg, b, rtol, maxit, lambda, c->r, c->p, c->q, c->flags, c->scal, c->partial, c->stream, iters,
+                 rel_res);
+    prof_end(&c->prof, tok, c->stream);
+    c->prof.collect();
+    return st;
+  }
   PcgArgs a{};
   a.n = c->n_lambda;
   a.row_ptr = c->row_ptr;
@@ -741,6 +774,43 @@ int hyb_set_natural_bc(hyb_ctx* c, int natural) {
   return HYB_OK;
 }
 
+int hyb_set_preconditioner(hyb_ctx* c, int kind, int chebyshev_degree, int coarsest) {
+  if (!c || (kind != HYB_PC_JACOBI && kind != HYB_PC_AMG)) return HYB_ERR_INVALID_ARG;
+  if (kind == HYB_PC_AMG && (chebyshev_degree < 1 || chebyshev_degree > 4 || coarsest < 1 || coarsest > 4096))
+    return HYB_ERR_INVALID_ARG;
+  if (kind == HYB_PC_AMG && (chebyshev_degree != c->pc_degree || coarsest != c->pc_coarsest)) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    amg_free(c->amg);
+    c->amg = nullptr;
+    c->amg_ready = false;
+    c->pc_degree = chebyshev_degree;
+    c->pc_coarsest = coarsest;
+  }
+  c->pc = kind;
+  return HYB_OK;
+}
+
+int hyb_amg_apply(hyb_ctx* c, const double* r, double* z) {
+  if (!c || !r || !z || c->mode == MODE_NONE || c->pc != HYB_PC_AMG) return HYB_ERR_INVALID_ARG;
+  int st = amg_prepare(c);
+  if (st) return st;
+  if ((st = amg_apply(c->amg, r, z, c->stream))) return st;
+  return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+int hyb_amg_info(hyb_ctx* c, int* levels, int64_t* sizes, double* lmax, int cap) {
+  if (!c || !levels || cap < 0 || c->mode == MODE_NONE || c->pc != HYB_PC_AMG) return HYB_ERR_INVALID_ARG;
+  int st = amg_prepare(c);
+  if (st) return st;
+  std::vector<int64_t> sz(64);
+  *levels = amg_levels(c->amg, sz.data(), 64);
+  for (int l = 0; l < *levels && l < cap; ++l) {
+    if (sizes) sizes[l] = sz[l];
+    if (lmax) lmax[l] = amg_lmax(c->amg, l);
+  }
+  return HYB_OK;
+}
+
 int hyb_set_mixed_operator(hyb_ctx* c, int fp32) {
   if (!c || (fp32 != 0 && fp32 != 1)) return HYB_ERR_INVALID_ARG;
   if (c->precision != HYB_MIXED) return HYB_ERR_INVALID_ARG;
@@ -838,6 +908,7 @@ int hyb_last_error_element(const hyb_ctx* c, int64_t* element) {
 void hyb_destroy(hyb_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  amg_free(c->amg);
   for (void* p : c->allocs) cudaFree(p);
   delete c;
 }

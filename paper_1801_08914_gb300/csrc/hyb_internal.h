@@ -96,6 +96,22 @@ cudaError_t launch_element(int k, int mode, const ElemArgs& a, cudaStream_t s, P
 cudaError_t launch_expand_cols(const int64_t* row_ptr, const int32_t* adj, const int32_t* adj_count,
                                int64_t n_faces, int nfn, int32_t* col, cudaStream_t s, Prof* prof);
 
+// Device scalars of a PCG solve: scal[] and flags[] slots (every PCG form, the host reads them)
+enum PcgScalar { S_RZ = 0, S_RR0 = 1, S_RR = 2, S_ALPHA = 3, S_BETA = 4, S_PQ = 5 };
+enum PcgFlag { F_IT = 0, F_CONV = 1, F_BRK = 2, F_TICKET = 3 };
+
+// Aggregation multigrid preconditioner of the reduced system (hyb_amg.cu).
+struct Amg;
+int amg_create(int nx, int ny, int nz, int nfn, int degree, int coarsest, const int64_t* row_ptr,
+               const int32_t* col, const double* val, const int64_t n_iface_axis[3], Amg** out);
+int amg_numeric(Amg* a, cudaStream_t s);   // after every assembly (values of H changed)
+int amg_apply(Amg* a, const double* r, double* z, cudaStream_t s);
+int amg_pcg(Amg* a, const double* b, double rtol, int maxit, double* x, double* r, double* p, double* q,
+            int* flags, double* scal, double* partial_unused, cudaStream_t s, int* iters, double* rel_res);
+int amg_levels(const Amg* a, int64_t* sizes, int cap);
+double amg_lmax(const Amg* a, int level);
+void amg_free(Amg* a);
+
 struct PcgArgs {
   int64_t n;
   const int64_t* row_ptr;

@@ -22,11 +22,6 @@
 namespace hyb {
 namespace {
 
-// scal[] slots
-enum { S_RZ = 0, S_RR0 = 1, S_RR = 2, S_ALPHA = 3, S_BETA = 4, S_PQ = 5 };
-// flags[] slots
-enum { F_IT = 0, F_CONV = 1, F_BRK = 2, F_TICKET = 3 };
-
 constexpr int kThreads = 256;
 
 // A problem takes no further iterations once converged, broken down or (maxit > 0) at maxit.

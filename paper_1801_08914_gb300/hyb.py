@@ -27,6 +27,8 @@ HYB_ERR_OOM = -8
 HYB_ERR_TIMEOUT = -9
 HYB_FP64 = 0
 HYB_MIXED = 1
+HYB_PC_JACOBI = 0
+HYB_PC_AMG = 1
 KERNEL_CLASSES = {"element": 0, "spmv": 1, "pcg_vector": 2, "recover": 3, "setup": 4, "pcg_fused": 5, "step": 6}
 
 EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recover",
@@ -35,6 +37,7 @@ EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recove
            "hyb_get_precision_split", "hyb_setup_batch", "hyb_assemble_reduced_batch", "hyb_solve_reduced_batch",
            "hyb_recover_batch", "hyb_batch_context", "hyb_batch_set_profiling", "hyb_batch_get_profile",
            "hyb_destroy_batch", "hyb_set_mixed_operator", "hyb_batch_step", "hyb_batch_step_kernels", "hyb_batch_get_autotune",
+           "hyb_set_preconditioner", "hyb_amg_apply", "hyb_amg_info",
            "hyb_last_error_element", "hyb_destroy", "hyb_status_string"]
 
 
@@ -85,6 +88,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_set_profiling.argtypes = [P, I]
     lib.hyb_set_pcg_fused.argtypes = [P, I]
     lib.hyb_set_mixed_operator.argtypes = [P, I]
+    lib.hyb_set_preconditioner.argtypes = [P, I, I, I]
+    lib.hyb_amg_apply.argtypes = [P, P, P]
+    lib.hyb_amg_info.argtypes = [P, ctypes.POINTER(I), P, P, I]
     lib.hyb_rsqrt_probe.argtypes = [ctypes.c_int64, P, P, P, P]
     lib.hyb_set_natural_bc.argtypes = [P, I]
     lib.hyb_refine.argtypes = [P, I, D, I, P, P, ctypes.POINTER(D)]
@@ -313,6 +319,29 @@ def hyb_set_mixed_operator(ctx, fp32, check=True):
     """Mixed contexts: the PCG applies H from its FP32 copy (True, default) or its FP64 values."""
     st = lib().hyb_set_mixed_operator(ctx.handle, int(bool(fp32)))
     return _check(st, "hyb_set_mixed_operator") if check else st
+
+
+def hyb_set_preconditioner(ctx, kind, chebyshev_degree=2, coarsest=512, check=True):
+    """PCG preconditioner: HYB_PC_JACOBI (the diagonal) or HYB_PC_AMG (aggregation multigrid)."""
+    st = lib().hyb_set_preconditioner(ctx.handle, int(kind), int(chebyshev_degree), int(coarsest))
+    return _check(st, "hyb_set_preconditioner") if check else st
+
+
+def hyb_amg_apply(ctx, r, z, check=True):
+    """z = M^{-1} r: one V-cycle of the context's multigrid (device tensors of n_lambda doubles)."""
+    st = lib().hyb_amg_apply(ctx.handle, _ptr(r, "r"), _ptr(z, "z"))
+    return _check(st, "hyb_amg_apply") if check else st
+
+
+def hyb_amg_info(ctx, cap=32):
+    """(levels, sizes of the levels, power estimates of lmax(D^-1 A) per smoothed level)."""
+    n = ctypes.c_int(0)
+    sizes = (ctypes.c_int64 * cap)()
+    lmax = (ctypes.c_double * cap)()
+    _check(lib().hyb_amg_info(ctx.handle, ctypes.byref(n), ctypes.cast(sizes, ctypes.c_void_p),
+                              ctypes.cast(lmax, ctypes.c_void_p), cap), "hyb_amg_info")
+    k = min(n.value, cap)
+    return n.value, [int(sizes[i]) for i in range(k)], [float(lmax[i]) for i in range(k)]
 
 
 def hyb_barrier_selftest(absent, rounds, stream=None):
