@@ -68,6 +68,10 @@ def parse_args(argv=None):
     ap.add_argument("--single-arm", action="store_true",
                     help="configs 3/5: the one-arm full-step measurement (--precision) instead of both arms")
     ap.add_argument("--no-full", action="store_true", help="configs 3/5: skip the one-pass full-path timing")
+    ap.add_argument("--no-amg", action="store_true",
+                    help="configs 3/5: skip the full-path pass with the multigrid-preconditioned solves")
+    ap.add_argument("--pc", choices=("jacobi", "amg"), default="jacobi",
+                    help="configs 1/2/softhard: PCG preconditioner of the timed step (default: the diagonal)")
     ap.add_argument("--no-errors", action="store_true", help="configs 3/5: skip the error measurement")
     ap.add_argument("--sh-order", type=int, default=1, help="softhard: RT order (mesh 2n x 2n x n of the paper's table)")
     ap.add_argument("--sh-p", type=float, default=-8.0, help="softhard: mass coefficient 10^p in the inclusion")
@@ -516,6 +520,8 @@ def workload_name(cfg, p, args, mixed=False, sc=False, theta=0.0, n32=0, n64=0):
         w = w.replace("FP64", f"mixed FP32/FP64 ({how}threshold {theta:g}: {n32} FP32 + {n64} FP64 elements)", 1)
     if args.refine and not args.assembly_only:
         w += f", {args.refine} FP64 refinement steps"
+    if getattr(args, "pc", "jacobi") == "amg" and not args.assembly_only:
+        w = w.replace("diag-PCG", "AMG-PCG (aggregation multigrid V-cycle)")
     if sc:
         w = w.replace("hybridization", "static condensation")
     if args.assembly_only:
@@ -548,6 +554,8 @@ def run_ours(args):
                         precision=hyb.HYB_MIXED if mixed else hyb.HYB_FP64,
                         contrast_threshold=args.threshold if mixed else 0.0)
     hyb.hyb_set_pcg_fused(ctx, args.pcg == "fused")
+    if args.pc == "amg":
+        hyb.hyb_set_preconditioner(ctx, hyb.HYB_PC_AMG, 2, 512)
     if p.natural:
         hyb.hyb_set_natural_bc(ctx, True)
     n64, n32, theta = ctx.precision_split()
@@ -1013,6 +1021,13 @@ def run_precision(args):
             u = torch.zeros(E, n_loc, dtype=torch.float64, device=dev)
             a["full"] = sampled(lambda: time_full_path(hyb, ctx, load, lam, u, args, args.refine if mixed else 0,
                                                        flush, stream))
+            if not args.no_amg:
+                # the same pass with the reduced solves preconditioned by the aggregation multigrid
+                hyb.hyb_set_preconditioner(ctx, hyb.HYB_PC_AMG, 2, 512)
+                a["full_amg"] = sampled(lambda: time_full_path(hyb, ctx, load, lam, u, args,
+                                                               args.refine if mixed else 0, flush, stream))
+                a["full_amg"]["amg_levels"] = hyb.hyb_amg_info(ctx)[1]
+                hyb.hyb_set_preconditioner(ctx, hyb.HYB_PC_JACOBI, 2, 512)
             del lam, u
         ctx.close()
         torch.cuda.synchronize()
@@ -1083,6 +1098,12 @@ def run_precision(args):
         fm, ff = arms["mixed"]["full"], arms["fp64"]["full"]
         line["full_step"]["mixed_over_fp64"] = fm["elements_per_s"] / ff["elements_per_s"]
         line["fp64"]["recover_roofline"] = recover_roofline_of(p.order, E, ff["recover_ms"], hbm_peak, fp64_peak)
+        if "full_amg" in arms["mixed"]:
+            am, af = arms["mixed"]["full_amg"], arms["fp64"]["full_amg"]
+            line["full_step_amg"] = {"mixed": am, "fp64": af, "mixed_over_fp64": am["elements_per_s"] / af["elements_per_s"],
+                                     "note": "the full_step pass with every reduced solve preconditioned by one V-cycle "
+                                             "of the aggregation multigrid (HYB_PC_AMG: Chebyshev degree 2, coarsest "
+                                             "<= 512 unknowns), its set-up inside the first solve"}
     if measure_err:
         try:
             line["errors"] = measure_errors(hyb, cfg, ERR_N, args, oracle_procs, dev)
