@@ -640,6 +640,7 @@ int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lamb
     st = amg_pcg(c->amg, b, rtol, maxit, lambda, c->r, c->p, c->q, c->flags, c->scal, c->partial, c->stream, iters,
                  rel_res);
     prof_end(&c->prof, tok, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HYB_ERR_CUDA;
     c->prof.collect();
     return st;
   }
