@@ -56,6 +56,18 @@ struct FaceOp {                    // level 0: the face-block CSR of H
   int64_t nfaces;
 };
 
+// level 0 from the FP32 copy of a mixed context: H_ij / (d_i d_j) rounded to FP32 (d = sqrt of
+// the diagonal), every face's column list padded to a multiple of 8 (value 0, column 0), so
+// (H v)_i = d_i sum_j Ht_ij (d_j v_j) with the products and row sums in FP32 over an FP32 copy
+// of d v that the kernel producing v writes beside it
+struct Face32Op {
+  const int64_t* fptr;
+  const int32_t* col;
+  const float* val;
+  const double* dsq;
+  int64_t nfaces;
+};
+
 struct GridOp {                    // levels >= 1: 27-point operator on a bx x by x bz grid
   const double* A;                 // [27][n]
   int bx, by, bz;
@@ -128,6 +140,10 @@ struct Vecs {
   int k;                   // STEP: step index (1..deg-1)
   int defer;               // x += din still pending
   int* flags;              // skip when the PCG has stopped (null: never)
+  const float* x32;        // FP32 level 0: the scaled FP32 copies of x (RES) and din (the others)
+  const float* din32;
+  float* out32;            // FP32 level 0: where the scaled copy of dout goes (null: none)
+  const double* dsq;
   double* partial;         // MATV: per-block partial sums of din . dout (null: none)
   int* ticket;
   double* scal;            // MATV with partials: PCG scalars (alpha = rz / pq)
@@ -138,13 +154,16 @@ __device__ __forceinline__ double epilogue(const Vecs& v, int64_t i, double w) {
   if constexpr (KIND == K_RES) {
     const double r = v.b[i] - w;
     v.r[i] = r;
-    v.dout[i] = v.dinv[i] * r * v.coef->inv_theta;
+    const double dn = v.dinv[i] * r * v.coef->inv_theta;
+    v.dout[i] = dn;
+    if (v.out32) v.out32[i] = (float)(v.dsq[i] * dn);
     return 0.0;
   } else if constexpr (KIND == K_STEP) {
     const double r = v.r[i] - w;
     v.r[i] = r;
     const double dn = fma(v.coef->c1[v.k], v.din[i], v.coef->c2[v.k] * v.dinv[i] * r);
     v.dout[i] = dn;
+    if (v.out32) v.out32[i] = (float)(v.dsq[i] * dn);
     v.x[i] += v.defer ? v.din[i] + dn : dn;
     return 0.0;
   } else if constexpr (KIND == K_FINAL) {
@@ -212,6 +231,48 @@ __global__ void __launch_bounds__(kT) face_kernel(FaceOp op, Vecs v) {
   finish_matv<KIND>(v, dot, sh);
 }
 
+// level 0 from the FP32 copy: eight lanes per face over the padded column list (one aligned
+// 32-byte sector of values per row and step), FP32 row sums combined across the lanes, widened
+// and scaled by d_i; lane g finishes the rows m = g, g + 8, ...
+template <int NFN, int KIND>
+__global__ void __launch_bounds__(kT) face32_kernel(Face32Op op, Vecs v) {
+  __shared__ double sh[kT];
+  if (stopped(v.flags)) return;
+  const int lane = threadIdx.x & 31, gl = lane & 7;
+  const int64_t f = ((int64_t)blockIdx.x * kT + threadIdx.x) >> 3;
+  const float* src = KIND == K_RES ? v.x32 : v.din32;
+  float acc[NFN];
+#pragma unroll
+  for (int m = 0; m < NFN; ++m) acc[m] = 0.0f;
+  if (f < op.nfaces) {
+    const int64_t c0 = op.fptr[f];
+    const int len = (int)(op.fptr[f + 1] - c0);
+    const float* vb = op.val + (int64_t)NFN * c0;
+#pragma unroll 2
+    for (int t = gl; t < len; t += 8) {
+      const float s = __ldg(src + __ldcs(op.col + c0 + t));
+#pragma unroll
+      for (int m = 0; m < NFN; ++m) acc[m] = fmaf(__ldcs(vb + (int64_t)m * len + t), s, acc[m]);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NFN; ++m) {
+    acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], 1);
+    acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], 2);
+    acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], 4);
+  }
+  double dot = 0.0;
+  if (f < op.nfaces) {
+#pragma unroll
+    for (int m = 0; m < NFN; ++m)
+      if ((m & 7) == gl) {
+        const int64_t i = f * NFN + m;
+        dot += epilogue<KIND>(v, i, (double)acc[m] * op.dsq[i]);
+      }
+  }
+  finish_matv<KIND>(v, dot, sh);
+}
+
 __device__ __forceinline__ void grid_xyz(int64_t i, int bx, int by, int& x, int& y, int& z) {
   x = (int)(i % bx);
   y = (int)((i / bx) % by);
@@ -249,6 +310,7 @@ __global__ void __launch_bounds__(kT) start_zero_kernel(int64_t n, Vecs v) {
     v.r[i] = b;
     v.dout[i] = d;
     v.x[i] = d;
+    if (v.out32) v.out32[i] = (float)(v.dsq[i] * d);
   }
 }
 
@@ -291,10 +353,14 @@ __global__ void __launch_bounds__(kT) restrict_grid_kernel(int fx, int fy, int f
 }
 
 __global__ void __launch_bounds__(kT) prolong_faces_kernel(int64_t n, int nfn, const int32_t* face_blk,
-                                                           const double* xc, double* x, const int* flags) {
+                                                           const double* xc, double* x, const int* flags,
+                                                           float* x32, const double* dsq) {
   if (stopped(flags)) return;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
-    x[i] += xc[face_blk[i / nfn]];
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const double xi = x[i] + xc[face_blk[i / nfn]];
+    x[i] = xi;
+    if (x32) x32[i] = (float)(dsq[i] * xi);     // the post-smoothing's first product reads it
+  }
 }
 
 __global__ void __launch_bounds__(kT) prolong_grid_kernel(int fx, int fy, int fz, int cx, int cy, const double* xc,
@@ -397,9 +463,12 @@ __global__ void __launch_bounds__(kT) grid_dinv_kernel(int64_t n, const double* 
     dinv[i] = 1.0 / A[13 * n + i];
 }
 
-__global__ void __launch_bounds__(kT) start_vector_kernel(int64_t n, double* v) {
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
-    v[i] = (double)((7919 * i) % 101) / 101.0 - 0.5;
+__global__ void __launch_bounds__(kT) start_vector_kernel(int64_t n, double* v, float* v32, const double* dsq) {
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const double s = (double)((7919 * i) % 101) / 101.0 - 0.5;
+    v[i] = s;
+    if (v32) v32[i] = (float)(dsq[i] * s);
+  }
 }
 
 // power step after w = A v: lam = v.w / v.Dv, u = D^-1 w, |u|^2 (partials, then the last block)
@@ -436,9 +505,14 @@ __global__ void __launch_bounds__(kT) power_reduce_kernel(int64_t n, const doubl
   }
 }
 
-__global__ void __launch_bounds__(kT) scale_kernel(int64_t n, const double* u, const double* s, double* v) {
+__global__ void __launch_bounds__(kT) scale_kernel(int64_t n, const double* u, const double* s, double* v, float* v32,
+                                                   const double* dsq) {
   const double f = s[1];
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) v[i] = u[i] * f;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const double vi = u[i] * f;
+    v[i] = vi;
+    if (v32) v32[i] = (float)(dsq[i] * vi);
+  }
 }
 
 // Chebyshev coefficients on [lmax / ratio, lmax], lmax = 1.1 lam
@@ -559,11 +633,14 @@ __global__ void __launch_bounds__(kT) pcg_rz_kernel(int64_t n, const double* r, 
 }
 
 __global__ void __launch_bounds__(kT) pcg_dir_kernel(int64_t n, const double* z, double* p, const int* flags,
-                                                     const double* scal) {
+                                                     const double* scal, float* p32, const double* dsq) {
   if (stopped(flags)) return;
   const double beta = scal[S_BETA];
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
-    p[i] = fma(beta, p[i], z[i]);
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const double pi = fma(beta, p[i], z[i]);
+    p[i] = pi;
+    if (p32) p32[i] = (float)(dsq[i] * pi);
+  }
 }
 
 // x += alpha p, r -= alpha q, rr = r.r; iteration count and convergence
@@ -605,6 +682,12 @@ struct Amg {
   int nfn = 0, degree = 2, coarsest = 512;
   int64_t nfaces = 0, n0 = 0;
   FaceOp H{};
+  // level-0 products from the FP32 copy (mixed contexts): the operator, scaled FP32 copies of
+  // the vectors the products gather (x of the V-cycle, the two directions, the PCG direction,
+  // the power iterate), and the operator the current numeric set-up was made for
+  bool use32 = false, numeric32 = false;
+  Face32Op H32{};
+  float *x32 = nullptr, *d32a = nullptr, *d32b = nullptr, *p32 = nullptr, *pv32 = nullptr;
   // aggregation of the faces (level 0 -> 1)
   int32_t* face_blk = nullptr;     // [nfaces]
   int32_t* blk_ptr = nullptr;      // [n1 + 1]
@@ -653,7 +736,16 @@ int64_t max_face_blocks(const Amg* a) { return (a->nfaces * 4 + kT - 1) / kT; }
 template <int KIND>
 cudaError_t level_op(const Amg* a, int l, const Vecs& v, cudaStream_t s) {
   const Amg::Level& L = a->lev[l];
-  if (l == 0) {
+  if (l == 0 && a->use32) {
+    const unsigned g = (unsigned)((a->nfaces * 8 + kT - 1) / kT);
+    switch (a->nfn) {
+      case 1: face32_kernel<1, KIND><<<g, kT, 0, s>>>(a->H32, v); break;
+      case 4: face32_kernel<4, KIND><<<g, kT, 0, s>>>(a->H32, v); break;
+      case 9: face32_kernel<9, KIND><<<g, kT, 0, s>>>(a->H32, v); break;
+      case 16: face32_kernel<16, KIND><<<g, kT, 0, s>>>(a->H32, v); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else if (l == 0) {
     const unsigned g = (unsigned)max_face_blocks(a);
     switch (a->nfn) {
       case 1: face_kernel<1, KIND><<<g, kT, 0, s>>>(a->H, v); break;
@@ -682,22 +774,33 @@ cudaError_t smooth(const Amg* a, int l, const double* b, double* x, bool zero, i
   v.coef = L.coef;
   v.flags = flags;
   double* d[2] = {L.d0, L.d1};
+  float* d32[2] = {nullptr, nullptr};
+  if (l == 0 && a->use32) {
+    d32[0] = a->d32a;
+    d32[1] = a->d32b;
+    v.x32 = a->x32;
+    v.dsq = a->H32.dsq;
+  }
   int cur = 0;
   cudaError_t e;
   bool defer;
   if (zero) {
     v.dout = d[cur];
+    v.out32 = d32[cur];
     start_zero_kernel<<<grid_for(L.n), kT, 0, s>>>(L.n, v);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     defer = false;
   } else {
     v.dout = d[cur];
+    v.out32 = d32[cur];
     if ((e = level_op<K_RES>(a, l, v, s)) != cudaSuccess) return e;
     defer = true;
   }
   for (int k = 1; k < a->degree; ++k) {
     v.din = d[cur];
+    v.din32 = d32[cur];
     v.dout = d[cur ^ 1];
+    v.out32 = d32[cur ^ 1];
     v.k = k;
     v.defer = defer;
     if ((e = level_op<K_STEP>(a, l, v, s)) != cudaSuccess) return e;
@@ -706,6 +809,8 @@ cudaError_t smooth(const Amg* a, int l, const double* b, double* x, bool zero, i
   }
   if (zero) {
     v.din = d[cur];
+    v.din32 = d32[cur];
+    v.out32 = nullptr;
     v.defer = defer;
     return level_op<K_FINAL>(a, l, v, s);
   }
@@ -733,7 +838,8 @@ cudaError_t vcycle(const Amg* a, int l, const double* b, double* x, int* flags, 
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = vcycle(a, l + 1, C.b, C.x, flags, s)) != cudaSuccess) return e;
   if (l == 0)
-    prolong_faces_kernel<<<grid_for(L.n), kT, 0, s>>>(L.n, a->nfn, a->face_blk, C.x, x, flags);
+    prolong_faces_kernel<<<grid_for(L.n), kT, 0, s>>>(L.n, a->nfn, a->face_blk, C.x, x, flags,
+                                                      a->use32 ? a->x32 : nullptr, a->H32.dsq);
   else
     prolong_grid_kernel<<<grid_for(L.n), kT, 0, s>>>(L.bx, L.by, L.bz, C.bx, C.by, C.x, x, flags);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -833,6 +939,24 @@ int amg_create(int nx, int ny, int nz, int nfn, int degree, int coarsest, const 
   return HYB_OK;
 }
 
+// Level-0 products from a mixed context's FP32 copy (on) or from the FP64 values (off).
+// Returns 1 when the choice changed (the numeric set-up must run again: the power estimate of
+// level 0 depends on the operator), 0 when not, or a negative status.
+int amg_set_fp32(Amg* a, bool on, const float* val32, const int32_t* col32, const int64_t* fptr32, const double* dsq) {
+  if (on) {
+    if (!val32 || !col32 || !fptr32 || !dsq) return HYB_ERR_INVALID_ARG;
+    int st;
+    if (!a->x32 && ((st = amg_alloc(a, &a->x32, a->n0)) || (st = amg_alloc(a, &a->d32a, a->n0)) ||
+                    (st = amg_alloc(a, &a->d32b, a->n0)) || (st = amg_alloc(a, &a->p32, a->n0)) ||
+                    (st = amg_alloc(a, &a->pv32, a->n0))))
+      return st;
+    a->H32 = Face32Op{fptr32, col32, val32, dsq, a->nfaces};
+  }
+  const bool changed = a->use32 != on;
+  a->use32 = on;
+  return changed ? 1 : 0;
+}
+
 // Numeric set-up after an assembly: coarse operators, diagonals, power estimates and
 // Chebyshev coefficients, the coarsest inverse. No host synchronisation but the final status.
 int amg_numeric(Amg* a, cudaStream_t s) {
@@ -859,15 +983,17 @@ int amg_numeric(Amg* a, cudaStream_t s) {
   // power estimates of every smoothed level
   for (int l = 0; l + 1 < nl; ++l) {
     const Amg::Level& L = a->lev[l];
-    start_vector_kernel<<<grid_for(L.n), kT, 0, s>>>(L.n, a->pv);
+    float* pv32 = l == 0 && a->use32 ? a->pv32 : nullptr;
+    start_vector_kernel<<<grid_for(L.n), kT, 0, s>>>(L.n, a->pv, pv32, a->H32.dsq);
     for (int it = 0; it < kPowerSteps; ++it) {
       Vecs v{};
       v.din = a->pv;
+      v.din32 = pv32;
       v.dout = a->pw;
       if ((e = level_op<K_MATV>(a, l, v, s)) != cudaSuccess) return cuda_status_of(e);
       power_reduce_kernel<<<grid_for(L.n), kT, 0, s>>>(L.n, a->pv, a->pw, L.dinv, a->pu, a->partial, a->ticket,
                                                        a->pscal + 2 * l);
-      scale_kernel<<<grid_for(L.n), kT, 0, s>>>(L.n, a->pu, a->pscal + 2 * l, a->pv);
+      scale_kernel<<<grid_for(L.n), kT, 0, s>>>(L.n, a->pu, a->pscal + 2 * l, a->pv, pv32, a->H32.dsq);
     }
     coef_kernel<<<1, 1, 0, s>>>(a->pscal + 2 * l, a->degree, L.coef);
   }
@@ -933,7 +1059,8 @@ int amg_pcg(Amg* a, const double* b, double rtol, int maxit, double* x, double* 
   pcg0_init_kernel<<<grid_for(n), kT, 0, s>>>(n, b, x, r, a->partial, flags, scal);
   if ((e = vcycle(a, 0, r, a->z, flags, s)) != cudaSuccess) return cuda_status_of(e);
   pcg_rz_kernel<<<grid_for(n), kT, 0, s>>>(n, r, a->z, a->partial, flags, scal, 1);
-  pcg_dir_kernel<<<grid_for(n), kT, 0, s>>>(n, a->z, p, flags, scal);
+  float* p32 = a->use32 ? a->p32 : nullptr;
+  pcg_dir_kernel<<<grid_for(n), kT, 0, s>>>(n, a->z, p, flags, scal, p32, a->H32.dsq);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status_of(e);
   const double rtol2 = rtol * rtol;
   if (a->iter_exec && (a->iter_b != b || a->iter_x != x || a->iter_rtol != rtol2 || a->iter_flags != flags ||
@@ -950,6 +1077,7 @@ int amg_pcg(Amg* a, const double* b, double rtol, int maxit, double* x, double* 
     if (e == cudaSuccess) {
       Vecs v{};
       v.din = p;
+      v.din32 = p32;
       v.dout = q;
       v.flags = flags;
       v.partial = a->partial;
@@ -962,7 +1090,7 @@ int amg_pcg(Amg* a, const double* b, double rtol, int maxit, double* x, double* 
       }
       if (ek == cudaSuccess) {
         pcg_rz_kernel<<<grid_for(n), kT, 0, cs>>>(n, r, a->z, a->partial, flags, scal, 0);
-        pcg_dir_kernel<<<grid_for(n), kT, 0, cs>>>(n, a->z, p, flags, scal);
+        pcg_dir_kernel<<<grid_for(n), kT, 0, cs>>>(n, a->z, p, flags, scal, p32, a->H32.dsq);
         ek = cudaGetLastError();
       }
       e = cudaStreamEndCapture(cs, &a->iter_graph);

@@ -614,8 +614,22 @@ int staticcond_assemble(hyb_ctx* ctx, const double* load, const double* ess) {
 namespace {
 
 // Diagonal PCG on the assembled H (or S) with right-hand side b, x0 = 0.
+// the FP32 operator of a mixed context applies (every element took the FP32 path; see solve_impl)
+bool use_op32(const hyb_ctx* c) {
+  return c->precision == HYB_MIXED && c->n_path[1] > 0 && c->n_path[0] == 0 && c->op32 && c->mode == MODE_HYB;
+}
+
+int prepare_op32(hyb_ctx* c) {
+  if (c->val32_ready) return HYB_OK;
+  cudaError_t e = launch_round_values(c->n_lambda, c->sz.nfn, c->row_ptr, c->col, c->val, c->fptr32, c->dsq,
+                                      c->val32, c->col32, c->stream, &c->prof);
+  if (e != cudaSuccess) return cuda_status(e);
+  c->val32_ready = true;
+  return HYB_OK;
+}
+
 // the multigrid of the current assembly (built on first use, its numeric part after every
-// assembly)
+// assembly); level 0 from the FP32 copy where the PCG uses it
 int amg_prepare(hyb_ctx* c) {
   int st;
   if (!c->amg) {
@@ -624,6 +638,11 @@ int amg_prepare(hyb_ctx* c) {
     if (st) return st;
     c->amg_ready = false;
   }
+  const bool want32 = use_op32(c);
+  if (want32 && (st = prepare_op32(c))) return st;
+  st = amg_set_fp32(c->amg, want32, c->val32, c->col32, c->fptr32, c->dsq);
+  if (st < 0) return st;
+  if (st == 1) c->amg_ready = false;
   if (!c->amg_ready) {
     if ((st = amg_numeric(c->amg, c->stream))) return st;
     c->amg_ready = true;
@@ -664,17 +683,12 @@ int solve_impl(hyb_ctx* c, const double* b, double rtol, int maxit, double* lamb
   // the FP32 operator only where every element took the FP32 path (contrast <= threshold
   // everywhere): an element above the threshold brings a near-null mode of H whose eigenvalue
   // the FP32 rounding cannot hold (soft-hard test, Sec. 6.1, mass 10^-8: PCG breakdown)
-  if (c->precision == HYB_MIXED && c->n_path[1] > 0 && c->n_path[0] == 0 && c->fused && c->op32 &&
-      c->mode == MODE_HYB) {
-    if (!c->val32_ready) {
-      // the solver's preparation of the operator, like D^-1 for the FP64 values: the scaled FP32
-      // copy of H (H carries the FP32 elimination's error anyway; its FP64 values stay the
-      // reference that hyb_refine's exact residual is measured against)
-      cudaError_t e = launch_round_values(c->n_lambda, c->sz.nfn, c->row_ptr, c->col, c->val, c->fptr32, c->dsq,
-                                          c->val32, c->col32, c->stream, &c->prof);
-      if (e != cudaSuccess) return cuda_status(e);
-      c->val32_ready = true;
-    }
+  if (use_op32(c) && c->fused) {
+    // the solver's preparation of the operator, like D^-1 for the FP64 values: the scaled FP32
+    // copy of H (H carries the FP32 elimination's error anyway; its FP64 values stay the
+    // reference that hyb_refine's exact residual is measured against)
+    int st = prepare_op32(c);
+    if (st) return st;
     a.val32 = c->val32;
     a.z32 = c->z32;
     a.dsq = c->dsq;

@@ -105,6 +105,7 @@ struct Amg;
 int amg_create(int nx, int ny, int nz, int nfn, int degree, int coarsest, const int64_t* row_ptr,
                const int32_t* col, const double* val, const int64_t n_iface_axis[3], Amg** out);
 int amg_numeric(Amg* a, cudaStream_t s);   // after every assembly (values of H changed)
+int amg_set_fp32(Amg* a, bool on, const float* val32, const int32_t* col32, const int64_t* fptr32, const double* dsq);
 int amg_apply(Amg* a, const double* r, double* z, cudaStream_t s);
 int amg_pcg(Amg* a, const double* b, double rtol, int maxit, double* x, double* r, double* p, double* q,
             int* flags, double* scal, double* partial_unused, cudaStream_t s, int* iters, double* rel_res);

@@ -155,3 +155,35 @@ def test_amg_mixed_refinement_accuracy():
         assert eu <= 1e-9
     finally:
         ctx.close()
+
+
+def test_amg_fp32_level0_in_mixed_contexts():
+    """A mixed context whose elements all took the FP32 path applies level 0 of the multigrid (its
+    smoothing products and the PCG's product) from the FP32 copy of H: one V-cycle within 1e-5 of
+    the same multigrid on the FP64 values (hyb_set_mixed_operator(ctx, 0)), FP32 rounding of the
+    scaled operator being the only difference, and AMG-PCG iteration counts within 3 of each other."""
+    import torch
+    from paper_1801_08914_gb300 import hyb
+    p = inputs.make_config(3, n=6)
+    ctx = setup_ctx(p, 2, 8, precision=hyb.HYB_MIXED, threshold=1e6)
+    try:
+        n64, n32, _ = ctx.precision_split()
+        assert n64 == 0 and n32 == p.alpha.size
+        n = ctx.sizes()["n_lambda"]
+        r = dev(np.random.default_rng(5).standard_normal(n))
+        z32 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        z64 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        hyb.hyb_amg_apply(ctx, r, z32)
+        lam32 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        it32, rr32, st32 = hyb.hyb_solve_reduced(ctx, 1e-10, 2000, lam32, check=False)
+        hyb.hyb_set_mixed_operator(ctx, 0)
+        hyb.hyb_amg_apply(ctx, r, z64)
+        lam64 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        it64, rr64, st64 = hyb.hyb_solve_reduced(ctx, 1e-10, 2000, lam64, check=False)
+        e = rel(z32.cpu().numpy(), z64.cpu().numpy())
+        el = rel(lam32.cpu().numpy(), lam64.cpu().numpy())
+        print(f"\nAMG FP32 level 0: V-cycle vs FP64 {e:.2e}; PCG {it32} vs {it64} its, lambda {el:.2e}")
+        assert st32 == hyb.HYB_OK and st64 == hyb.HYB_OK
+        assert e <= 1e-5 and abs(it32 - it64) <= 3 and el <= 1e-5
+    finally:
+        ctx.close()
