@@ -390,9 +390,11 @@ FUSED_TRAFFIC = {(2, 32, 1): 163.0e6}
 # per launch, 23.6 MB read + 578.2 MB written); per-element work is uniform, so a launch's
 # traffic is this times its elements
 ELEMENT_TRAFFIC_PER_ELEMENT = {3: 293.8e3}
-# DRAM bytes per element of the FP32 mixed-form element kernel (element_tiled_kernel<k>), from one
-# ncu capture of the unchanged kernel on a smaller mesh of the same order; empty until captured
-MIXED_ELEMENT_TRAFFIC_PER_ELEMENT = {}
+# DRAM bytes per element of the mixed element phase (mixed_load_kernel<k> + element_tiled_kernel<k>),
+# from ncu captures of the unchanged kernels on a smaller mesh of the same order (RT_2: 32^3,
+# colour 0, 16,384 elements: 18.4 + 37.8 MB and 204.0 + 1181.4 MB read + written;
+# profiles/element_tiled_kernel_rt2_32cube_mixed.md)
+MIXED_ELEMENT_TRAFFIC_PER_ELEMENT = {2: 87.99e3}
 
 
 def pcg_iteration_flops(n, nnz):
@@ -555,7 +557,7 @@ def run_ours(args):
                         contrast_threshold=args.threshold if mixed else 0.0)
     hyb.hyb_set_pcg_fused(ctx, args.pcg == "fused")
     if args.pc == "amg":
-        hyb.hyb_set_preconditioner(ctx, hyb.HYB_PC_AMG, 2, 512)
+        hyb.hyb_set_preconditioner(ctx, hyb.HYB_PC_AMG, 2, 64)
     if p.natural:
         hyb.hyb_set_natural_bc(ctx, True)
     n64, n32, theta = ctx.precision_split()
@@ -1040,11 +1042,11 @@ def run_precision(args):
                                                        flush, stream))
             if not args.no_amg:
                 # the same pass with the reduced solves preconditioned by the aggregation multigrid
-                hyb.hyb_set_preconditioner(ctx, hyb.HYB_PC_AMG, 2, 512)
+                hyb.hyb_set_preconditioner(ctx, hyb.HYB_PC_AMG, 2, 64)
                 a["full_amg"] = sampled(lambda: time_full_path(hyb, ctx, load, lam, u, args,
                                                                args.refine if mixed else 0, flush, stream))
                 a["full_amg"]["amg_levels"] = hyb.hyb_amg_info(ctx)[1]
-                hyb.hyb_set_preconditioner(ctx, hyb.HYB_PC_JACOBI, 2, 512)
+                hyb.hyb_set_preconditioner(ctx, hyb.HYB_PC_JACOBI, 2, 64)
             del lam, u
         ctx.close()
         torch.cuda.synchronize()
@@ -1067,21 +1069,26 @@ def run_precision(args):
     el_ms_m = pm["element"][0] / args.steps
     el_launch_m = pm["element"][1] / args.steps
     # the dominant kernel of the timed step: the FP32 mixed-form element kernel (every element
-    # of contrast <= the threshold); its algorithmic FP32 flops per launch over its average launch
+    # of contrast <= the threshold). Its profile class also holds mixed_load_kernel (the FP64
+    # load and G^{-1}, one launch before every element_tiled_kernel launch: ~10% of the phase in
+    # the ncu launch list), so the unit is that pair of launches per colour: algorithmic flops
+    # per pair over the pair's average time
     tflops = (n32 * f32 + n64 * f64) / (el_ms_m * 1e-3) / 1e12 if el_ms_m > 0 else None
+    pairs = el_launch_m / 2 if n64 == 0 else el_launch_m
     roof = {"kernel": f"element_tiled_kernel<{p.order}> (FP32 mixed-form elimination"
                       + (f") + element_kernel<{p.order}> (FP64)" if n64 else ")"),
             "bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": tflops / fp32_peak if tflops else None,
             "peak_source": "FP32 FMA throughput measured in this run (hyb_measure_fma_peak: independent FMA "
                            "chains on every SM)",
-            "traffic": MIXED_ELEMENT_TRAFFIC_PER_ELEMENT.get(p.order) and
-                       MIXED_ELEMENT_TRAFFIC_PER_ELEMENT[p.order] * E / el_launch_m,
+            "traffic": MIXED_ELEMENT_TRAFFIC_PER_ELEMENT.get(p.order) and n64 == 0 and
+                       MIXED_ELEMENT_TRAFFIC_PER_ELEMENT[p.order] * E / pairs,
             "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per element x elements per launch "
-                               "(profiles/element_tiled_kernel_rt2_rt3.md)"
+                               "(profiles/element_tiled_kernel_rt2_32cube_mixed.md)"
                                if p.order in MIXED_ELEMENT_TRAFFIC_PER_ELEMENT else None),
-            "algorithmic_flops_per_element": f32, "elements_per_launch": E / el_launch_m,
-            "avg_launch_ms": el_ms_m / el_launch_m, "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak}
+            "algorithmic_flops_per_element": f32, "unit_of_work": "one colour: mixed_load_kernel + element_tiled_kernel",
+            "elements_per_launch": E / pairs, "avg_launch_ms": el_ms_m / pairs,
+            "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak}
     pf = arms["fp64"]["prof"]
     el_ms_f = pf["element"][0] / args.steps
     tf64 = E * f64 / (el_ms_f * 1e-3) / 1e12 if el_ms_f > 0 else None
@@ -1120,7 +1127,7 @@ def run_precision(args):
             line["full_step_amg"] = {"mixed": am, "fp64": af, "mixed_over_fp64": am["elements_per_s"] / af["elements_per_s"],
                                      "note": "the full_step pass with every reduced solve preconditioned by one V-cycle "
                                              "of the aggregation multigrid (HYB_PC_AMG: Chebyshev degree 2, coarsest "
-                                             "<= 512 unknowns), its set-up inside the first solve"}
+                                             "<= 64 unknowns), its set-up inside the first solve"}
     if measure_err:
         try:
             line["errors"] = measure_errors(hyb, cfg, ERR_N, args, oracle_procs, dev)

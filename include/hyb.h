@@ -262,7 +262,8 @@ enum {
  *   - Chebyshev smoothing of degree `chebyshev_degree` (1..4) for D^{-1} A on [lmax/30, lmax],
  *     lmax = 1.1 x a 12-step power estimate, the same before and after the coarse correction
  *     (a symmetric positive definite V-cycle);
- *   - the coarsest level solved with its dense inverse (coarsest: 1..4096 unknowns).
+ * *   - the coarsest level solved with its dense inverse (coarsest: 1..4096 unknowns; formed by
+ *     Gauss-Jordan elimination in one CTA, so keep it small: 64 is a good default).
  *  Built on the first solve after hyb_setup (buffers: about 5 vectors of n_lambda doubles
  *  plus the coarse levels), its numeric part on the first solve after every assembly. The
  *  PCG starts from lambda = 0 and stops at ||r||_2 <= rtol ||b||_2, as with HYB_PC_JACOBI; it

@@ -321,7 +321,7 @@ def hyb_set_mixed_operator(ctx, fp32, check=True):
     return _check(st, "hyb_set_mixed_operator") if check else st
 
 
-def hyb_set_preconditioner(ctx, kind, chebyshev_degree=2, coarsest=512, check=True):
+def hyb_set_preconditioner(ctx, kind, chebyshev_degree=2, coarsest=64, check=True):
     """PCG preconditioner: HYB_PC_JACOBI (the diagonal) or HYB_PC_AMG (aggregation multigrid)."""
     st = lib().hyb_set_preconditioner(ctx.handle, int(kind), int(chebyshev_degree), int(coarsest))
     return _check(st, "hyb_set_preconditioner") if check else st
