@@ -262,12 +262,15 @@ enum {
  *   - Chebyshev smoothing of degree `chebyshev_degree` (1..4) for D^{-1} A on [lmax/30, lmax],
  *     lmax = 1.1 x a 12-step power estimate, the same before and after the coarse correction
  *     (a symmetric positive definite V-cycle);
- * *   - the coarsest level solved with its dense inverse (coarsest: 1..4096 unknowns; formed by
+ *   - the coarsest level solved with its dense inverse (coarsest: 1..4096 unknowns; formed by
  *     Gauss-Jordan elimination in one CTA, so keep it small: 64 is a good default).
  *  Built on the first solve after hyb_setup (buffers: about 5 vectors of n_lambda doubles
  *  plus the coarse levels), its numeric part on the first solve after every assembly. The
- *  PCG starts from lambda = 0 and stops at ||r||_2 <= rtol ||b||_2, as with HYB_PC_JACOBI; it
- *  applies the FP64 values of H (also on HYB_MIXED contexts). Static condensation's S is
+ *  PCG starts from lambda = 0 and stops at ||r||_2 <= rtol ||b||_2, as with HYB_PC_JACOBI. Its
+ *  products with H (the PCG's and the smoother's on level 0) use the FP64 values, except on
+ *  HYB_MIXED contexts that apply the FP32 copy (hyb_set_mixed_operator: every element FP32),
+ *  where they run from that copy like the diagonal PCG's; the coarse levels are formed from
+ *  the FP64 values in both cases. Static condensation's S is
  *  H(div)-like, not H^1-like: the multigrid is built for H.
  *  HYB_ERR_INVALID_ARG for another kind or parameters out of range.
  */
