@@ -31,13 +31,16 @@ struct TileShape<0> {
 };
 template <>
 struct TileShape<1> {
-  static constexpr int TB = 12, MR = 3, MC = 4, NT = 128, MINB = 4, MINB_ASM = 4;
+  // 6 x 6 tiles (6 tile columns): 17% faster element phase than 12 x 12 at 64^3
+  static constexpr int TB = 6, MR = 3, MC = 3, NT = 128, MINB = 4, MINB_ASM = 4;
 };
 template <>
 struct TileShape<2> {
-  // the recovery: 3 CTAs per SM (64 KB each); the assembly, without the FP64 residual scratch:
-  // 4 CTAs per SM (55 KB each, 64 registers)
-  static constexpr int TB = 18, MR = 3, MC = 6, NT = 256, MINB = 3, MINB_ASM = 4;
+  // one 9 x 9 tile per face (6 interior + 6 face tile columns): the diagonal tiles take the
+  // two-column factor, and the kernel needs no stack; 18 x 18 tiles (one-row-per-lane factor,
+  // 200-byte stack frame) ran the 64^3 element phase at half this rate. The recovery: 3 CTAs
+  // per SM; the assembly, without the FP64 residual scratch: 4 CTAs per SM (64 registers)
+  static constexpr int TB = 9, MR = 3, MC = 3, NT = 256, MINB = 3, MINB_ASM = 4;
 };
 template <>
 struct TileShape<3> {
@@ -60,6 +63,7 @@ struct MT {
   static constexpr int TT = TB * TB;
   static constexpr int LT = T * (T + 1) / 2 * TT;          // L_M tiles
   static constexpr int ZTS = TQ * (TQ + 1) / 2 * TT;       // L_Z tiles
+  static constexpr int ZTSA = (ZTS + 3) / 4 * 4;           // their region, 16-byte aligned
   static constexpr int XD = N * NQP;                       // Xd, row-major, columns >= NQK zero
   static constexpr int LT_INTERIOR = (TI * T - TI * (TI - 1) / 2) * TT;   // tile columns J < TI
   static constexpr int YPS = NB * NB + NQP * NB;           // Y | P (= V) after the refinement
@@ -75,8 +79,8 @@ struct MT {
   static constexpr int MSCR = 6 * NQ + Q * Q * P * P + Q * P * P * p * p;
   static constexpr int LTA = ((LT > GSCR ? LT : GSCR) + 3) / 4 * 4;   // L_M region (only RT_0 needs the padding)
   static constexpr int XDA = ((XD > MSCR ? XD : MSCR) + 3) / 4 * 4;   // Xd region
-  static constexpr int64_t STORE = ((int64_t)LTA + XDA + ZTS + NQK * NQK + 3) / 4 * 4;   // L_M | Xd | L_Z | G^{-1}
-  static constexpr int F32 = TABF + LTA + XDA + ZTS + N /*vec*/ + 2 * NQP /*tq tmpq*/ + 32 /*ybuf*/ + 8 /*flag*/ +
+  static constexpr int64_t STORE = ((int64_t)LTA + XDA + ZTSA + NQK * NQK + 3) / 4 * 4;   // L_M | Xd | L_Z | G^{-1}
+  static constexpr int F32 = TABF + LTA + XDA + ZTSA + N /*vec*/ + 2 * NQP /*tq tmpq*/ + 32 /*ybuf*/ + 8 /*flag*/ +
                              (YPS_IN_LT ? 0 : YPS);
   static constexpr size_t SMEM = sizeof(double) * D64 + sizeof(float) * F32 + sizeof(int) * N;
   // the assembly keeps only the geometry, the load and the solution in FP64 (the load is formed by
@@ -86,7 +90,7 @@ struct MT {
   static_assert(N % TB == 0 && NI % TB == 0, "tiles must split the interior and face blocks");
   static_assert(TB % MR == 0 && TB % MC == 0 && NQP % MC == 0 && NB % MC == 0, "micro-tile shape");
   static_assert(TB <= 32, "one warp per diagonal tile");
-  static_assert(ZTS % 4 == 0 && (D64 * 2) % 4 == 0, "16-byte aligned tile blocks");
+  static_assert(ZTSA % 4 == 0 && (D64 * 2) % 4 == 0, "16-byte aligned tile blocks");
 };
 
 // Refinement steps of the recovery's element solve: every step multiplies the error by about
@@ -294,7 +298,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   const int tid = threadIdx.x;
   const int64_t slot = args.slot ? args.slot[e] : e;
   float* store = args.Lstore32 + slot * S::STORE;                // this element's factors (global)
-  float* Gi = store + S::LTA + S::XDA + S::ZTS;                   // G^{-1}
+  float* Gi = store + S::LTA + S::XDA + S::ZTSA;                  // G^{-1}
 
   // ---- shared memory
   double* d = smem;
@@ -339,7 +343,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   float* DcO = fl; fl += S::TABF - (2 * P * Q + p * Q + P * P * Q + P * p * Q + p * p * Q);
   float* Lt = fl; fl += S::LTA;
   float* Xd = fl; fl += S::XDA;
-  float* Zt = fl; fl += S::ZTS;
+  float* Zt = fl; fl += S::ZTSA;
   float* vec = fl; fl += N;
   float* tq = fl; fl += NQP;
   float* tmpq = fl; fl += NQP;
@@ -399,7 +403,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     // ---- the stored factors back into shared memory
     const float4* src = reinterpret_cast<const float4*>(store);
     float4* dst = reinterpret_cast<float4*>(Lt);
-    constexpr int NV = (S::LTA + S::XDA + S::ZTS) / 4;         // Lt | Xd | Zt are contiguous
+    constexpr int NV = (S::LTA + S::XDA + S::ZTSA) / 4;         // Lt | Xd | Zt are contiguous
     for (int t = tid; t < NV; t += NT) dst[t] = __ldcs(src + t);
     __syncthreads();
   } else {
@@ -562,7 +566,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     // ---- keep the factors for the recovery
     const float4* src = reinterpret_cast<const float4*>(Lt);
     float4* dst = reinterpret_cast<float4*>(store);
-    constexpr int NV = (S::LTA + S::XDA + S::ZTS) / 4;
+    constexpr int NV = (S::LTA + S::XDA + S::ZTSA) / 4;
     for (int t = tid; t < NV; t += NT) __stcs(dst + t, src[t]);
   }
   }
@@ -844,7 +848,7 @@ __device__ void mixed_load_body(const ElemArgs& args, const int64_t e, double* s
   for (int i = tid; i < N; i += NT) fs[i] = f[i];
   __syncthreads();                               // the FP64 scratch after f_T is free
   const int64_t slot = args.slot ? args.slot[e] : e;
-  float* Gi = args.Lstore32 + slot * MT<K>::STORE + MT<K>::LTA + MT<K>::XDA + MT<K>::ZTS;
+  float* Gi = args.Lstore32 + slot * MT<K>::STORE + MT<K>::LTA + MT<K>::XDA + MT<K>::ZTSA;
   if (!g_inverse<K, NT>(beta, gd, Vo, reinterpret_cast<float*>(smem + L::PREFIX), Gi) && tid == 0)
     set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
 }
