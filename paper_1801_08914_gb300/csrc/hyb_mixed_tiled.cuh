@@ -64,7 +64,12 @@ struct MT {
   static constexpr int LT = T * (T + 1) / 2 * TT;          // L_M tiles
   static constexpr int ZTS = TQ * (TQ + 1) / 2 * TT;       // L_Z tiles
   static constexpr int ZTSA = (ZTS + 3) / 4 * 4;           // their region, 16-byte aligned
-  static constexpr int XD = N * NQP;                       // Xd, row-major, columns >= NQK zero
+  // Xd, row-major with XS columns: L_M^{-1} D' in columns < NQK (zero up to NQP); where it fits
+  // (RT_0..RT_2), column NQP carries the load f_T through the factorisation (y = L_M^{-1} f_T for
+  // the assembly's g_T) and the rest of the last MC-group is zero
+  static constexpr bool FUSED_F = K <= 2;
+  static constexpr int XS = NQP + (FUSED_F ? MC : 0);
+  static constexpr int XD = N * XS;
   static constexpr int LT_INTERIOR = (TI * T - TI * (TI - 1) / 2) * TT;   // tile columns J < TI
   static constexpr int YPS = NB * NB + NQP * NB;           // Y | P (= V) after the refinement
   static constexpr bool YPS_IN_LT = YPS <= LT_INTERIOR;
@@ -223,7 +228,7 @@ __device__ void mixed_solve_tiled(const float* Lt, const float* Xd, const float*
     float acc = 0.0f;
     if (a < NQK) {
       for (int b = lane; b < NQK; b += 32) acc = fmaf(Gi[a * NQK + b], t[b], acc);
-      for (int i = lane; i < N; i += 32) acc = fmaf(Xd[i * NQP + a], v[i], acc);
+      for (int i = lane; i < N; i += 32) acc = fmaf(Xd[i * S::XS + a], v[i], acc);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -236,7 +241,7 @@ __device__ void mixed_solve_tiled(const float* Lt, const float* Xd, const float*
   tiles::tile_bwd_vec<float, S::TB, NT>(Zt, S::TQ, t);
   for (int i = tid; i < N; i += NT) {
     float acc = v[i];
-    for (int a = 0; a < NQK; ++a) acc = fmaf(-Xd[i * NQP + a], t[a], acc);
+    for (int a = 0; a < NQK; ++a) acc = fmaf(-Xd[i * S::XS + a], t[a], acc);
     v[i] = acc;
   }
   __syncthreads();
@@ -503,10 +508,12 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
 
   // ---- D' (zero rows on essential dofs, zero columns beyond NQK) into Xd, then the tiled
   // Cholesky of M fused with Xd <- L_M^{-1} D'
-  for (int t = tid; t < N * NQP; t += NT) {
-    const int i = t / NQP, a = t % NQP;
+  for (int t = tid; t < N * S::XS; t += NT) {
+    const int i = t / S::XS, a = t % S::XS;
     float v = 0.f;
-    if (a < NQK && !is_e(i)) {
+    if (S::FUSED_F && !RECOVER && a == NQP) {
+      v = (float)f[i];                             // the load, carried through the factorisation
+    } else if (a < NQK && !is_e(i)) {
       const int code = dofcode[i];
       const int c = code & 3, i0 = (code >> 2) & 63, i1 = (code >> 8) & 63, i2 = (code >> 14) & 63;
       const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
@@ -516,7 +523,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     Xd[t] = v;
   }
   __syncthreads();
-  if (!chol_tiles32<TB, MR, MC, NT>(Lt, T, Xd, NQP, flag)) {
+  if (!chol_tiles32<TB, MR, MC, NT>(Lt, T, Xd, S::XS, flag)) {
     if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
     return;
   }
@@ -538,9 +545,9 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
       for (int k = 0; k < N; ++k) {
         float a[MR], b[MC];
 #pragma unroll
-        for (int i = 0; i < MR; ++i) a[i] = Xd[k * NQP + I * TB + r0 + i];
+        for (int i = 0; i < MR; ++i) a[i] = Xd[k * S::XS + I * TB + r0 + i];
 #pragma unroll
-        for (int j = 0; j < MC; ++j) b[j] = Xd[k * NQP + J * TB + c0 + j];
+        for (int j = 0; j < MC; ++j) b[j] = Xd[k * S::XS + J * TB + c0 + j];
 #pragma unroll
         for (int i = 0; i < MR; ++i)
 #pragma unroll
@@ -571,20 +578,50 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   }
   }
 
-  // ---- the refined element solve: g_T (assembly) or u_T (recovery)
-  refine_tiled<K>(f, x, qv, RECOVER ? kRefineSteps : kAssemblyRefineSteps, alpha, beta, bmask, g6, gd, Vc, Dc, Vo, DcO64, dofcode, Lt, Xd, Zt, Gi, r, ut, rq,
-                  U, Wv, Dv, xc, t1, t2, vec, tq, tmpq);
+  // ---- the refined element solve: u_T (recovery), or g_T (assembly) where the load column
+  // did not fit beside Xd
+  if constexpr (RECOVER || !S::FUSED_F)
+    refine_tiled<K>(f, x, qv, RECOVER ? kRefineSteps : kAssemblyRefineSteps, alpha, beta, bmask, g6, gd, Vc, Dc, Vo, DcO64,
+                    dofcode, Lt, Xd, Zt, Gi, r, ut, rq, U, Wv, Dv, xc, t1, t2, vec, tq, tmpq);
+  auto scatter_rhs = [&](auto xb) {              // g_T = D_c x_b on the interior faces
+    for (int ib = tid; ib < NB; ib += NT) {
+      const int a = ib / NFN, m1 = ib % NFN;
+      if (ef[a] < 0) continue;
+      const double v = ((a & 1) ? 1.0 : -1.0) * wf[m1] * (double)xb(ib);
+      const int64_t gi = (int64_t)ef[a] * NFN + m1;
+      if (args.colour == 1) args.rhs[gi] += v;
+      else args.rhs[gi] = v;
+    }
+  };
   if constexpr (RECOVER) {
     double* ue = u_out + e * (int64_t)N;
     for (int i = tid; i < N; i += NT) ue[i] = x[i];
   } else {
-    for (int ib = tid; ib < NB; ib += NT) {
-      const int a = ib / NFN, m1 = ib % NFN;
-      if (ef[a] < 0) continue;
-      const double v = ((a & 1) ? 1.0 : -1.0) * wf[m1] * x[NI + ib];
-      const int64_t gi = (int64_t)ef[a] * NFN + m1;
-      if (args.colour == 1) args.rhs[gi] += v;
-      else args.rhs[gi] = v;
+    if constexpr (S::FUSED_F) {
+      // (A^{-1} f)_b of the mixed form from y = L_M^{-1} f (column NQP of Xd, carried through
+      // the factorisation): t = Z^{-1} Xd^T y, v = y - Xd t, and (A^{-1} f)_b = L_bb^{-T} v_b =
+      // Y^T v_b once Y is formed below (the backward solve's face rows need only v_b). The
+      // same FP32 solve as the recovery's first step, without its two full triangular solves.
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int a = warp; a < NQP; a += NT / 32) {
+        float acc = 0.0f;
+        if (a < NQK)
+          for (int i = lane; i < N; i += 32) acc = fmaf(Xd[i * S::XS + a], Xd[i * S::XS + NQP], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) tq[a] = acc;
+      }
+      __syncthreads();
+      tiles::tile_fwd_vec<float, TB, NT>(Zt, TQ, tq);
+      tiles::tile_bwd_vec<float, TB, NT>(Zt, TQ, tq);
+      for (int j = tid; j < NB; j += NT) {
+        const float* xr = Xd + (NI + j) * S::XS;
+        float acc = xr[NQP];
+        for (int a = 0; a < NQK; ++a) acc = fmaf(-xr[a], tq[a], acc);
+        vec[NI + j] = acc;
+      }
+    } else {
+      scatter_rhs([&](int ib) { return x[NI + ib]; });
     }
 
     // ---- Y = L_M,bb^{-1}, P = Xd_b^T Y, V = L_Z^{-1} P, S = Y^T Y - V^T V. The buffers take the
@@ -595,6 +632,15 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0f : 0.0f;
     __syncthreads();
     tiles::tile_fwd_mat<float, TB, MR, MC, NT>(Lt, T, S::TI, Y, NB);
+    if constexpr (S::FUSED_F) {
+      __syncthreads();
+      // x_b = Y^T v_b (Y lower triangular, row-major), scattered as g_T = D_c x_b
+      scatter_rhs([&](int j) {
+        float acc = 0.0f;
+        for (int k = j; k < NB; ++k) acc = fmaf(Y[k * NB + j], vec[NI + k], acc);
+        return acc;
+      });
+    }
     {
       constexpr int RM = NQP / MR, CM = NB / MC;
       for (int it = tid; it < RM * CM; it += NT) {  // P[a][j] = sum_i Xd[NI + i][a] Y[i][j]
@@ -607,7 +653,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
         for (int k = 0; k < NB; ++k) {
           float a[MR], b[MC];
   #pragma unroll
-          for (int i = 0; i < MR; ++i) a[i] = Xd[(NI + k) * NQP + a0 + i];
+          for (int i = 0; i < MR; ++i) a[i] = Xd[(NI + k) * S::XS + a0 + i];
   #pragma unroll
           for (int j = 0; j < MC; ++j) b[j] = Y[k * NB + j0 + j];
   #pragma unroll
