@@ -102,10 +102,9 @@ struct MT {
 // kappa(M, Z) u_32 <= 5e-5, so one step takes the FP32 solve (1e-7) to ~5e-12, below what the
 // global FP64 refinement needs: its residual, the jump C u of the recovered flux, is only as
 // accurate as u_T. The assembly's load term g_T = C_T A^{-1} f_T is left at the FP32 solve's
-// accuracy: its error enters the reduced right-hand side as the FP32 S_T's error enters H, and
-// the global refinement, whose residual does not depend on g, removes both.
+// accuracy (no refinement step): its error enters the reduced right-hand side as the FP32 S_T's
+// error enters H, and the global refinement, whose residual does not depend on g, removes both.
 constexpr int kRefineSteps = 1;
-constexpr int kAssemblyRefineSteps = 0;
 
 using tiles::tcol;
 
@@ -578,11 +577,10 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   }
   }
 
-  // ---- the refined element solve: u_T (recovery), or g_T (assembly) where the load column
-  // did not fit beside Xd
-  if constexpr (RECOVER || !S::FUSED_F)
-    refine_tiled<K>(f, x, qv, RECOVER ? kRefineSteps : kAssemblyRefineSteps, alpha, beta, bmask, g6, gd, Vc, Dc, Vo, DcO64,
-                    dofcode, Lt, Xd, Zt, Gi, r, ut, rq, U, Wv, Dv, xc, t1, t2, vec, tq, tmpq);
+  // ---- the refined element solve: u_T (recovery)
+  if constexpr (RECOVER)
+    refine_tiled<K>(f, x, qv, kRefineSteps, alpha, beta, bmask, g6, gd, Vc, Dc, Vo, DcO64, dofcode, Lt, Xd, Zt, Gi, r,
+                    ut, rq, U, Wv, Dv, xc, t1, t2, vec, tq, tmpq);
   auto scatter_rhs = [&](auto xb) {              // g_T = D_c x_b on the interior faces
     for (int ib = tid; ib < NB; ib += NT) {
       const int a = ib / NFN, m1 = ib % NFN;
@@ -597,16 +595,23 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     double* ue = u_out + e * (int64_t)N;
     for (int i = tid; i < N; i += NT) ue[i] = x[i];
   } else {
-    if constexpr (S::FUSED_F) {
-      // (A^{-1} f)_b of the mixed form from y = L_M^{-1} f (column NQP of Xd, carried through
-      // the factorisation): t = Z^{-1} Xd^T y, v = y - Xd t, and (A^{-1} f)_b = L_bb^{-T} v_b =
-      // Y^T v_b once Y is formed below (the backward solve's face rows need only v_b). The
-      // same FP32 solve as the recovery's first step, without its two full triangular solves.
+    {
+      // (A^{-1} f)_b of the mixed form from y = L_M^{-1} f: t = Z^{-1} Xd^T y, v = y - Xd t, and
+      // (A^{-1} f)_b = L_bb^{-T} v_b = Y^T v_b once Y is formed below (the backward solve's face
+      // rows need only v_b). y is column NQP of Xd where the load rode through the
+      // factorisation (RT_0..RT_2), else one forward solve. The FP32 solve of the recovery's first
+      // step, without its backward solve (and, where fused, without its forward one).
       const int lane = tid & 31, warp = tid >> 5;
+      if constexpr (!S::FUSED_F) {
+        for (int i = tid; i < N; i += NT) vec[i] = (float)f[i];
+        __syncthreads();
+        tiles::tile_fwd_vec<float, TB, NT>(Lt, T, vec);
+      }
+      auto y = [&](int i) { return S::FUSED_F ? Xd[i * S::XS + NQP] : vec[i]; };
       for (int a = warp; a < NQP; a += NT / 32) {
         float acc = 0.0f;
         if (a < NQK)
-          for (int i = lane; i < N; i += 32) acc = fmaf(Xd[i * S::XS + a], Xd[i * S::XS + NQP], acc);
+          for (int i = lane; i < N; i += 32) acc = fmaf(Xd[i * S::XS + a], y(i), acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) tq[a] = acc;
@@ -616,12 +621,10 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
       tiles::tile_bwd_vec<float, TB, NT>(Zt, TQ, tq);
       for (int j = tid; j < NB; j += NT) {
         const float* xr = Xd + (NI + j) * S::XS;
-        float acc = xr[NQP];
+        float acc = y(NI + j);
         for (int a = 0; a < NQK; ++a) acc = fmaf(-xr[a], tq[a], acc);
         vec[NI + j] = acc;
       }
-    } else {
-      scatter_rhs([&](int ib) { return x[NI + ib]; });
     }
 
     // ---- Y = L_M,bb^{-1}, P = Xd_b^T Y, V = L_Z^{-1} P, S = Y^T Y - V^T V. The buffers take the
@@ -632,7 +635,7 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     for (int t = tid; t < NB * NB; t += NT) Y[t] = (t / NB == t % NB) ? 1.0f : 0.0f;
     __syncthreads();
     tiles::tile_fwd_mat<float, TB, MR, MC, NT>(Lt, T, S::TI, Y, NB);
-    if constexpr (S::FUSED_F) {
+    {
       __syncthreads();
       // x_b = Y^T v_b (Y lower triangular, row-major), scattered as g_T = D_c x_b
       scatter_rhs([&](int j) {
