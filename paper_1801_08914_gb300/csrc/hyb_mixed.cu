@@ -30,8 +30,12 @@ namespace hyb {
 
 __constant__ RefTables c_refm[kMaxOrder + 1];
 
+cudaError_t launch_mass_maps(cudaStream_t s);
+
+// The reference tables, then the per-order mass-assembly destination tables the element kernels read.
 cudaError_t upload_ref_tables_mixed(const RefTables* tabs, int count, cudaStream_t s) {
-  return cudaMemcpyToSymbolAsync(c_refm, tabs, sizeof(RefTables) * count, 0, cudaMemcpyHostToDevice, s);
+  const cudaError_t e = cudaMemcpyToSymbolAsync(c_refm, tabs, sizeof(RefTables) * count, 0, cudaMemcpyHostToDevice, s);
+  return e == cudaSuccess ? launch_mass_maps(s) : e;
 }
 
 namespace {
@@ -400,6 +404,14 @@ cudaError_t launch_mixed_k(const ElemArgs& a, cudaStream_t s, Prof* prof, bool r
 }
 
 }  // namespace
+
+cudaError_t launch_mass_maps(cudaStream_t s) {
+  mass_map_kernel<0><<<1, 192, 0, s>>>();
+  mass_map_kernel<1><<<1, 192, 0, s>>>();
+  mass_map_kernel<2><<<1, 192, 0, s>>>();
+  mass_map_kernel<3><<<1, 192, 0, s>>>();
+  return cudaGetLastError();
+}
 
 // FP32-path store per element: the tiles of L_M | Xd | L_Z | G^{-1} for the recovery.
 int64_t mixed_store_floats(int k) {

@@ -290,6 +290,88 @@ __device__ void refine_tiled(const double* f, double* x, double* q, int steps, d
   }
 }
 
+// ---- The alpha mass M = (alpha u, v) of RT_K by sum factorisation, one (c, c') component block
+// at a time: blk 0..2 the diagonal blocks (c, c), 3..5 the blocks (1, 0), (2, 0), (2, 1). Along
+// da (= c) the rows take the closed 1-D basis and the columns the closed (diagonal) or open one,
+// along db the rows take the open basis and the columns the open (diagonal) or closed one (db =
+// c' off the diagonal), and along the remaining direction dL both take the open basis. The last
+// contraction (over the dL quadrature points) writes output idx = ((((ia nja + ja) nib + ib) njb
+// + jb) p + iL) p + jL, i.e. M(local_index(c, i), local_index(c', j)) with i, j the 1-D indices
+// gathered per direction.
+template <int K, int blk>
+struct MassBlk {
+  static constexpr int P = K + 2, p = K + 1;
+  static constexpr int c = blk < 3 ? blk : (blk == 3 ? 1 : 2);
+  static constexpr int cp = blk < 3 ? blk : (blk == 5 ? 1 : 0);
+  static constexpr bool diag = c == cp;
+  static constexpr int da = c, db = diag ? (c + 1) % 3 : cp, dL = 3 - da - db;
+  static constexpr int nia = P, nja = diag ? P : p, nib = p, njb = diag ? p : P;
+  static constexpr int s2 = nia * nja * nib * njb;     // outputs of the second contraction
+  static constexpr int OUT = s2 * p * p;               // outputs of the last one
+};
+
+// Entries of one block before the symmetry cut, and each order's offset into the table below.
+__host__ __device__ constexpr int mass_map_per(int k) { return (k + 2) * (k + 2) * (k + 1) * (k + 1) * (k + 1) * (k + 1); }
+__host__ __device__ constexpr int mass_map_off(int k) { return k == 0 ? 0 : mass_map_off(k - 1) + 6 * mass_map_per(k - 1); }
+
+// Per order and block, the outputs of the last contraction that land in the stored lower
+// triangle of M, in increasing idx, each packed as (idx << 16) | (its offset in the L_M tile
+// layout); g_mass_cnt holds their number. Filled by mass_map_kernel (every context setup writes
+// the same values) so that the element kernel spends no integer work on local indices and tile
+// positions in that pass.
+__device__ uint32_t g_mass_map[mass_map_off(kMaxOrder + 1)];
+__device__ int g_mass_cnt[(kMaxOrder + 1) * 6];
+
+// Offset in the L_M tile layout of output idx of block blk, or -1 above the diagonal of M.
+template <int K, int blk>
+__device__ int mass_dst(int idx) {
+  using B = MassBlk<K, blk>;
+  using S = MT<K>;
+  constexpr int p = B::p, da = B::da, db = B::db, nja = B::nja, nib = B::nib, njb = B::njb;
+  constexpr int TB = S::TB, T = S::T, TT = S::TT;
+  int rr = idx;
+  const int jL = rr % p; rr /= p;
+  const int iL = rr % p; rr /= p;
+  const int jb = rr % njb; rr /= njb;
+  const int ib = rr % nib; rr /= nib;
+  const int ja = rr % nja, ia = rr / nja;
+  const int i0 = da == 0 ? ia : db == 0 ? ib : iL, i1 = da == 1 ? ia : db == 1 ? ib : iL;
+  const int i2 = da == 2 ? ia : db == 2 ? ib : iL;
+  const int j0 = da == 0 ? ja : db == 0 ? jb : jL, j1 = da == 1 ? ja : db == 1 ? jb : jL;
+  const int j2 = da == 2 ? ja : db == 2 ? jb : jL;
+  const int ra = local_index<K>(B::c, i0, i1, i2), sa = local_index<K>(B::cp, j0, j1, j2);
+  if (B::diag && ra < sa) return -1;
+  const int gi = ra >= sa ? ra : sa, gj = ra >= sa ? sa : ra;
+  return tcol(gi / TB, gj / TB, T) * TT + (gi % TB) + (gj % TB) * TB;
+}
+
+// One warp per block: the kept outputs compacted in order by ballots.
+template <int K>
+__global__ void __launch_bounds__(192) mass_map_kernel() {
+  static_assert(MT<K>::LT <= 65536 && mass_map_per(K) <= 65536, "16-bit fields");
+  const int blk = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* map = g_mass_map + mass_map_off(K) + blk * mass_map_per(K);
+  int n = 0;
+  for (int base = 0; base < mass_map_per(K); base += 32) {
+    const int idx = base + lane;
+    int d = -1;
+    if (idx < mass_map_per(K)) {
+      switch (blk) {
+        case 0: d = mass_dst<K, 0>(idx); break;
+        case 1: d = mass_dst<K, 1>(idx); break;
+        case 2: d = mass_dst<K, 2>(idx); break;
+        case 3: d = mass_dst<K, 3>(idx); break;
+        case 4: d = mass_dst<K, 4>(idx); break;
+        default: d = mass_dst<K, 5>(idx); break;
+      }
+    }
+    const unsigned keep = __ballot_sync(0xffffffffu, d >= 0);
+    if (d >= 0) map[n + __popc(keep & ((1u << lane) - 1u))] = ((uint32_t)idx << 16) | (uint32_t)d;
+    n += __popc(keep);
+  }
+  if (lane == 0) g_mass_cnt[K * 6 + blk] = n;
+}
+
 // ---- the element: factorisation (both modes), then either S_T / g_T (assembly) or the
 // recovery u_T = A^{-1}(f_T - C_T^T lambda).
 template <int K, bool RECOVER>
@@ -427,11 +509,11 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
     // index decompositions divide by constants
     auto mass_block = [&](auto blk_c) {
       constexpr int blk = decltype(blk_c)::value;
-      constexpr int c = blk < 3 ? blk : (blk == 3 ? 1 : 2);
-      constexpr int cp = blk < 3 ? blk : (blk == 5 ? 1 : 0);
-      constexpr bool diag = c == cp;
-      constexpr int da = c, db = diag ? (c + 1) % 3 : cp, dL = 3 - da - db;
-      constexpr int nia = P, nja = diag ? P : p, nib = p, njb = diag ? p : P;
+      using B = MassBlk<K, blk>;
+      constexpr int c = B::c, cp = B::cp;
+      constexpr bool diag = B::diag;
+      constexpr int da = B::da, db = B::db, dL = B::dL;
+      constexpr int nia = B::nia, nja = B::nja, nib = B::nib, njb = B::njb;
       constexpr int sa = da == 0 ? 1 : da == 1 ? Q : Q * Q;
       constexpr int sb = db == 0 ? 1 : db == 1 ? Q : Q * Q;
       constexpr int sL = dL == 0 ? 1 : dL == 1 ? Q : Q * Q;
@@ -465,26 +547,18 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
         T2[idx] = acc;
       }
       __syncthreads();
-      constexpr int s2 = nia * nja * nib * njb;
-      for (int idx = tid; idx < s2 * p * p; idx += NT) {
-        int rr = idx;
-        const int jL = rr % p; rr /= p;
-        const int iL = rr % p; rr /= p;
-        const int jb = rr % njb; rr /= njb;
-        const int ib = rr % nib; rr /= nib;
-        const int ja = rr % nja, ia = rr / nja;
-        const int i0 = da == 0 ? ia : db == 0 ? ib : iL, i1 = da == 1 ? ia : db == 1 ? ib : iL;
-        const int i2 = da == 2 ? ia : db == 2 ? ib : iL;
-        const int j0 = da == 0 ? ja : db == 0 ? jb : jL, j1 = da == 1 ? ja : db == 1 ? jb : jL;
-        const int j2 = da == 2 ? ja : db == 2 ? jb : jL;
-        const int ra = local_index<K>(c, i0, i1, i2), sa2 = local_index<K>(cp, j0, j1, j2);
-        if (diag && ra < sa2) continue;
-        const int tt = ((ia * nja + ja) * nib + ib) * njb + jb;
+      constexpr int s2 = B::s2;
+      // outputs in the lower triangle of M, with their tile offsets, from the per-order table
+      const uint32_t* map = g_mass_map + mass_map_off(K) + blk * mass_map_per(K);
+      const int cnt = g_mass_cnt[K * 6 + blk];
+      for (int t = tid; t < cnt; t += NT) {
+        const uint32_t m = __ldg(map + t);
+        const int idx = (int)(m >> 16);
+        const int tt = idx / (p * p), ij = idx - tt * (p * p);   // ij = iL p + jL
         float acc = 0.f;
 #pragma unroll
-        for (int qL = 0; qL < Q; ++qL) acc = fmaf(T2[qL * s2 + tt], VoVo[(iL * p + jL) * Q + qL], acc);
-        const int gi = ra >= sa2 ? ra : sa2, gj = ra >= sa2 ? sa2 : ra;
-        Lt[tcol(gi / TB, gj / TB, T) * TT + (gi % TB) + (gj % TB) * TB] = acc;
+        for (int qL = 0; qL < Q; ++qL) acc = fmaf(T2[qL * s2 + tt], VoVo[ij * Q + qL], acc);
+        Lt[m & 0xffffu] = acc;
       }
       __syncthreads();
     };
