@@ -560,7 +560,9 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
         for (int qL = 0; qL < Q; ++qL) acc = fmaf(T2[qL * s2 + tt], VoVo[ij * Q + qL], acc);
         Lt[m & 0xffffu] = acc;
       }
-      __syncthreads();
+      // the next block's first pass touches only T1 (last read before the barrier above) and
+      // its second pass, which overwrites T2, follows a barrier
+      if constexpr (blk == 5) __syncthreads();
     };
     mass_block(std::integral_constant<int, 0>{});
     mass_block(std::integral_constant<int, 1>{});
@@ -580,21 +582,26 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   }
 
   // ---- D' (zero rows on essential dofs, zero columns beyond NQK) into Xd, then the tiled
-  // Cholesky of M fused with Xd <- L_M^{-1} D'
-  for (int t = tid; t < N * S::XS; t += NT) {
-    const int i = t / S::XS, a = t % S::XS;
-    float v = 0.f;
-    if (S::FUSED_F && !RECOVER && a == NQP) {
-      v = (float)f[i];                             // the load, carried through the factorisation
-    } else if (a < NQK && !is_e(i)) {
-      const int code = dofcode[i];
-      const int c = code & 3, i0 = (code >> 2) & 63, i1 = (code >> 8) & 63, i2 = (code >> 14) & 63;
-      const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
-      const bool match = (c == 0 || i0 == a0) && (c == 1 || i1 == a1) && (c == 2 || i2 == a2);
-      if (match) v = DcO[(c == 0 ? i0 : c == 1 ? i1 : i2) * p + (c == 0 ? a0 : c == 1 ? a1 : a2)];
-    }
-    Xd[t] = v;
+  // Cholesky of M fused with Xd <- L_M^{-1} D'. The component-c function with 1-D nodes
+  // (i0, i1, i2) meets only the p functions of Q_k whose other two indices equal its own:
+  // D'(i, a) = DcO[i_c][a_c] there, zero elsewhere; so Xd is cleared and those p entries per free
+  // row written.
+  {
+    static_assert((N * S::XS + 3) / 4 * 4 <= S::XDA, "Xd cleared in whole float4");
+    float4* x4 = reinterpret_cast<float4*>(Xd);
+    for (int t = tid; t < (N * S::XS + 3) / 4; t += NT) x4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  __syncthreads();
+  for (int t = tid; t < N * p; t += NT) {
+    const int i = t / p, j = t - (t / p) * p;
+    if (is_e(i)) continue;
+    const int code = dofcode[i];
+    const int c = code & 3, i0 = (code >> 2) & 63, i1 = (code >> 8) & 63, i2 = (code >> 14) & 63;
+    const int a0 = c == 0 ? j : i0, a1 = c == 1 ? j : i1, a2 = c == 2 ? j : i2;
+    Xd[i * S::XS + a0 + p * (a1 + p * a2)] = DcO[(c == 0 ? i0 : c == 1 ? i1 : i2) * p + j];
+  }
+  if constexpr (S::FUSED_F)                        // the load, carried through the factorisation
+    for (int i = tid; i < N; i += NT) Xd[i * S::XS + NQP] = (float)f[i];
   __syncthreads();
   if (!chol_tiles32<TB, MR, MC, NT>(Lt, T, Xd, S::XS, flag)) {
     if (tid == 0) set_error(args.status, args.err_elem, HYB_ERR_NOT_SPD, e);
@@ -780,9 +787,15 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
         set_error(args.status, args.err_elem, HYB_ERR_TIMEOUT, e);
     } else {
       constexpr int RM = NB / MR, CM = NB / MC;
+      constexpr bool kMicroInFace = NFN % MR == 0 && NFN % MC == 0;
       for (int it = tid; it < RM * CM; it += NT) {
         const int i0 = (it / CM) * MR, j0 = (it % CM) * MC;
         if (i0 + MR - 1 < j0) continue;             // strictly above the diagonal
+        // where the micro-tiles split the face blocks, a micro-tile lies in one face pair: skip
+        // it whole when either face is on the boundary (put drops those entries)
+        if constexpr (kMicroInFace) {
+          if (ef[i0 / NFN] < 0 || ef[j0 / NFN] < 0) continue;
+        }
         float acc[MR][MC];
   #pragma unroll
         for (int i = 0; i < MR; ++i)
@@ -810,15 +823,42 @@ __device__ void element_tiled_body(const ElemArgs& args, const int64_t e, double
   #pragma unroll
             for (int j = 0; j < MC; ++j) acc[i][j] = fmaf(-a[i], b[j], acc[i][j]);
         }
+        if constexpr (kMicroInFace) {
+          // put with the face pair (a, b) decoded once per micro-tile; the same values and
+          // positions entry by entry
+          const int a = i0 / NFN, b = j0 / NFN, m10 = i0 - a * NFN, m20 = j0 - b * NFN;
+          const int64_t pab = boff[a * 6 + b], pba = boff[b * 6 + a];
+          const int64_t la = s_rlen[a], lb = s_rlen[b];
+          const bool neg = (a ^ b) & 1, add = a == b && args.colour == 1;
   #pragma unroll
-        for (int i = 0; i < MR; ++i)
+          for (int i = 0; i < MR; ++i)
   #pragma unroll
-          for (int j = 0; j < MC; ++j) {
-            const int ib = i0 + i, jb = j0 + j;
-            if (ib < jb) continue;
-            put(ib, jb, acc[i][j]);
-            if (ib != jb) put(jb, ib, acc[i][j]);
-          }
+            for (int j = 0; j < MC; ++j) {
+              const int ib = i0 + i, jb = j0 + j;
+              if (ib < jb) continue;
+              const int m1 = m10 + i, m2 = m20 + j;
+              const float w = acc[i][j] * (s_wf[m1] * s_wf[m2]);
+              const double v = dev::widen_f32(neg ? -w : w);
+              const int64_t pos = pab + m1 * la + m2;
+              if (add) args.val[pos] += v;
+              else args.val[pos] = v;
+              if (ib != jb) {
+                const int64_t pos2 = pba + m2 * lb + m1;
+                if (add) args.val[pos2] += v;
+                else args.val[pos2] = v;
+              }
+            }
+        } else {
+  #pragma unroll
+          for (int i = 0; i < MR; ++i)
+  #pragma unroll
+            for (int j = 0; j < MC; ++j) {
+              const int ib = i0 + i, jb = j0 + j;
+              if (ib < jb) continue;
+              put(ib, jb, acc[i][j]);
+              if (ib != jb) put(jb, ib, acc[i][j]);
+            }
+        }
       }
     }
   }
