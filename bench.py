@@ -392,9 +392,9 @@ FUSED_TRAFFIC = {(2, 32, 1): 163.0e6}
 ELEMENT_TRAFFIC_PER_ELEMENT = {3: 293.8e3}
 # DRAM bytes per element of the mixed element phase (mixed_load_kernel<k> + element_tiled_kernel<k>),
 # from ncu captures of the unchanged kernels on a smaller mesh of the same order (RT_2: 32^3,
-# colour 0, 16,384 elements: 18.28 + 10.72 MB and 205.07 + 1055.48 MB read + written;
+# colour 0, 16,384 elements: 18.28 + 10.72 MB and 205.49 + 1053.07 MB read + written;
 # profiles/element_tiled_kernel_rt2_32cube_mixed.md)
-MIXED_ELEMENT_TRAFFIC_PER_ELEMENT = {2: 78.7e3}
+MIXED_ELEMENT_TRAFFIC_PER_ELEMENT = {2: 78.6e3}
 
 
 def pcg_iteration_flops(n, nnz):
