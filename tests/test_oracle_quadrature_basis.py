@@ -113,3 +113,34 @@ def test_rt_basis_div_and_faces(k):
         flux = np.array(W) @ v[:, :, axis]
         sl = slice(b.n_interior + f * b.n_face_nodes, b.n_interior + (f + 1) * b.n_face_nodes)
         assert np.allclose(flux[sl], wf, atol=1e-14)
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_rt_divergence_lies_in_qk_with_tensor_sparsity(k):
+    """The reference divergence of every RT_k function lies in Q_k (Sec. 3.2 writes the
+    divergence coupling through Q_k): its values at the (k+1)^3 Gauss-Legendre nodes reproduce
+    it at random points through the Lagrange basis on those nodes. The open 1-D basis is that
+    Lagrange basis, so the x-component function with nodes (i0, i1, i2) has divergence
+    dL^c_{i0}(x) L^o_{i1}(y) L^o_{i2}(z), which vanishes at every node (a0, a1, a2) with
+    (a1, a2) != (i1, i2): at most k + 1 nonzeros per function, dL^c_{i0}(g_{a0}) there (and
+    cyclically for y and z)."""
+    b = RTBasis(k)
+    m = k + 1
+    g, _ = gauss_legendre(m)                           # the Q_k nodes of the mixed form
+    A = np.array([(a0, a1, a2) for a2 in range(m) for a1 in range(m) for a0 in range(m)])
+    _, Dv = b.eval(g[A])                               # Dv[r, i] = div phi_i at node A[r]
+    rng = np.random.default_rng(3)
+    pts = rng.random((9, 3))
+    _, div = b.eval(pts)
+    L = np.ones((pts.shape[0], m ** 3))
+    for d in range(3):
+        L *= lagrange(g, pts[:, d])[0][:, A[:, d]]
+    assert np.abs(L @ Dv - div).max() <= 1e-12 * max(1.0, np.abs(div).max())
+    _, dVc = lagrange(b.closed, g)                     # dVc[p, a] = dL^c_a(g_p)
+    for i, (c, idx) in enumerate(b.dofs):
+        expect = np.zeros(m ** 3)
+        for r, a in enumerate(A):
+            if all(a[d] == idx[d] for d in range(3) if d != c):
+                expect[r] = dVc[a[c], idx[c]]
+        assert np.count_nonzero(expect) <= m
+        assert np.abs(Dv[:, i] - expect).max() <= 1e-13 * max(1.0, np.abs(expect).max()), (k, i)
