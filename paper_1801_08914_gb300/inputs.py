@@ -36,6 +36,7 @@ STREAM_ALPHA = 2
 STREAM_CONTRAST = 3
 STREAM_LOAD = 4
 STREAM_BATCH = 5
+STREAM_LINES = 6
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -266,3 +267,128 @@ def batch_problem(p: int, seed0: int = 4000, nmin: int = 6, nmax: int = 24, cont
     """Problem p of the batched workload (seed seed0 + p)."""
     n, k = batch_shape(p, seed0, nmin, nmax)
     return random_problem(n, k, 0.2, seed0 + p, contrast[0], contrast[1], name=f"batch{p}")
+
+
+@dataclass
+class TwoLevelProblem:
+    """A mesh with a non-conforming interface: a coarse block of nx x ny x nzc cells on z in
+    [0, zI] under a fine block of mx x my x nzf cells on [zI, 1], with (mx, my) = (2 nx, 2 ny)
+    when refine (each coarse top face meets four fine bottom faces) and (nx, ny) otherwise (a
+    conforming interface, the same cells as one structured grid).
+
+    coarse_vertices : ((nzc+1)(ny+1)(nx+1), 3), vertex (i,j,l) at i + (nx+1)(j + (ny+1) l)
+    fine_vertices   : ((nzf+1)(my+1)(mx+1), 3), vertex (i,j,l) at i + (mx+1)(j + (my+1) l);
+                      layer l = 0 lies on the interface
+    alpha, beta     : (Ec + Ef,) per element: the coarse cells (i + nx (j + ny l)) first, then
+                      the fine cells (i + mx (j + my l))
+    load            : (Ec + Ef, n_loc) coefficients of f in the broken RT_k basis
+    Every boundary face is natural (no essential data).
+    """
+    nx: int
+    ny: int
+    nzc: int
+    nzf: int
+    order: int
+    refine: bool
+    coarse_vertices: np.ndarray
+    fine_vertices: np.ndarray
+    alpha: np.ndarray
+    beta: np.ndarray
+    load: np.ndarray
+    z_interface: float = 0.5
+
+    @property
+    def mx(self) -> int:
+        return 2 * self.nx if self.refine else self.nx
+
+    @property
+    def my(self) -> int:
+        return 2 * self.ny if self.refine else self.ny
+
+    @property
+    def n_coarse(self) -> int:
+        return self.nx * self.ny * self.nzc
+
+    @property
+    def n_fine(self) -> int:
+        return self.mx * self.my * self.nzf
+
+    @property
+    def n_elem(self) -> int:
+        return self.n_coarse + self.n_fine
+
+
+def two_level_problem(nx: int, ny: int, nzc: int, nzf: int, order: int, seed: int, refine: bool = True,
+                      lines: float = 0.0, gamma: float = 0.0, z_interface: float = 0.5,
+                      contrast=(0.1, 10.0)) -> TwoLevelProblem:
+    """Seeded two-level mesh (TwoLevelProblem) and its coefficients.
+
+    Grid lines: x_i = i / nx, y_j = j / ny, the coarse z lines l zI / nzc and the fine ones
+    zI + l (1 - zI) / nzf; with lines > 0 every interior line moves by U(-lines h, +lines h)
+    (h its spacing; x, then y, then coarse z, then fine z lines), which keeps every cell a box.
+    The fine x and y lines are the coarse ones and, when refine, their midpoints. With gamma > 0
+    every vertex off the domain boundary then moves by U(-gamma h, +gamma h) per coordinate (h the
+    block's spacing along that axis), except that coarse vertices on the interface move in x and
+    y only and the fine interface vertices are placed at the bilinear points (parameters 0, 1/2,
+    1) of the coarse top faces, so that four fine faces tile each coarse face exactly.
+    alpha ~ lognormal(0, 1), beta / alpha ~ 10^U(log10 contrast), N(0, 1) load coefficients.
+    """
+    def line_set(n, lo, hi, offset):
+        x = lo + (hi - lo) * np.arange(n + 1, dtype=np.float64) / n
+        if lines > 0.0 and n > 1:
+            u = uniform(seed, STREAM_LINES, n - 1, offset)
+            x[1:-1] += (2.0 * u - 1.0) * lines * (hi - lo) / n
+        return x
+
+    zI = z_interface
+    X = line_set(nx, 0.0, 1.0, 0)
+    Y = line_set(ny, 0.0, 1.0, nx)
+    Zc = line_set(nzc, 0.0, zI, nx + ny)
+    Zf = line_set(nzf, zI, 1.0, nx + ny + nzc)
+
+    def grid(xs, ys, zs):
+        L, J, I = np.meshgrid(np.arange(zs.size), np.arange(ys.size), np.arange(xs.size), indexing="ij")
+        return np.stack([xs[I.ravel()], ys[J.ravel()], zs[L.ravel()]], axis=1), I.ravel(), J.ravel(), L.ravel()
+
+    cv, ci, cj, cl = grid(X, Y, Zc)
+    if refine:
+        Xf = np.sort(np.concatenate([X, 0.5 * (X[1:] + X[:-1])]))
+        Yf = np.sort(np.concatenate([Y, 0.5 * (Y[1:] + Y[:-1])]))
+    else:
+        Xf, Yf = X, Y
+    fv, fi, fj, fl = grid(Xf, Yf, Zf)
+    mx, my = Xf.size - 1, Yf.size - 1
+    if gamma > 0.0:
+        h = np.array([1.0 / nx, 1.0 / ny, zI / nzc])
+        inner = (ci > 0) & (ci < nx) & (cj > 0) & (cj < ny) & (cl > 0)
+        n_in = int(inner.sum())
+        u = uniform(seed, STREAM_JITTER, 3 * n_in).reshape(n_in, 3)
+        mv = (2.0 * u - 1.0) * gamma * h
+        mv[cl[inner] == nzc, 2] = 0.0                      # the interface stays the plane z = zI
+        cv[inner] += mv
+        hf = np.array([1.0 / mx, 1.0 / my, (1.0 - zI) / nzf])
+        inner_f = (fi > 0) & (fi < mx) & (fj > 0) & (fj < my) & (fl > 0) & (fl < nzf)
+        n_f = int(inner_f.sum())
+        u = uniform(seed, STREAM_JITTER, 3 * n_f, 3 * n_in).reshape(n_f, 3)
+        fv[inner_f] += (2.0 * u - 1.0) * gamma * hf
+    # fine interface vertices on the coarse top faces (their bilinear points)
+    top = cv.reshape(nzc + 1, ny + 1, nx + 1, 3)[nzc]
+    fvr = fv.reshape(nzf + 1, my + 1, mx + 1, 3)
+    r = 2 if refine else 1
+    for q in range(my + 1):
+        j = min(q // r, ny - 1)
+        t = (q - r * j) / r
+        for p_ in range(mx + 1):
+            i = min(p_ // r, nx - 1)
+            s_ = (p_ - r * i) / r
+            fvr[0, q, p_] = ((1 - s_) * (1 - t) * top[j, i] + s_ * (1 - t) * top[j, i + 1] +
+                             (1 - s_) * t * top[j + 1, i] + s_ * t * top[j + 1, i + 1])
+    fv = fvr.reshape(-1, 3)
+    E = nx * ny * nzc + mx * my * nzf
+    nl = n_local_dofs(order)
+    alpha = np.exp(normal(seed, STREAM_ALPHA, E))
+    lo, hi = np.log10(contrast[0]), np.log10(contrast[1])
+    beta = alpha * 10.0 ** (lo + (hi - lo) * uniform(seed, STREAM_CONTRAST, E))
+    load = normal(seed, STREAM_LOAD, E * nl).reshape(E, nl)
+    return TwoLevelProblem(nx, ny, nzc, nzf, order, refine, cv, fv, alpha, beta, load, zI)
+
