@@ -133,6 +133,14 @@ def _ptr(t, name, dtype=torch.float64):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _need(t, name, count):
+    """The library trusts the extents it is given (plain device pointers): a tensor shorter than
+    the context's sizes would be read or written past its end, so lengths are checked here."""
+    if t is not None and isinstance(t, torch.Tensor) and t.numel() != count:
+        raise ValueError(f"{name} has {t.numel()} entries, expected {count}")
+    return t
+
+
 def _stream(stream):
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
@@ -179,6 +187,11 @@ class Context:
 
 def hyb_setup(vertices, nx, ny, nz, order, alpha, beta, precision=HYB_FP64, contrast_threshold=0.0,
               stream=None, check=True):
+    if min(int(nx), int(ny), int(nz)) > 0:              # otherwise the library reports HYB_ERR_INVALID_ARG
+        E = int(nx) * int(ny) * int(nz)
+        _need(vertices, "vertices", 3 * (int(nx) + 1) * (int(ny) + 1) * (int(nz) + 1))
+        _need(alpha, "alpha", E)
+        _need(beta, "beta", E)
     m = _Mesh(int(nx), int(ny), int(nz), _ptr(vertices, "vertices"))
     h = ctypes.c_void_p()
     st = lib().hyb_setup(ctypes.byref(m), int(order), _ptr(alpha, "alpha"), _ptr(beta, "beta"),
@@ -190,18 +203,37 @@ def hyb_setup(vertices, nx, ny, nz, order, alpha, beta, precision=HYB_FP64, cont
     return ctx, st
 
 
+def _need_elements(ctx, **tensors):
+    if not ctx.handle:                                  # a closed context: the library reports it
+        return
+    z = ctx.sizes()
+    for name, t in tensors.items():
+        _need(t, name, z["n_elem"] * z["n_loc"])
+
+
+def _need_lambda(ctx, **tensors):
+    if not ctx.handle:
+        return
+    n = ctx.sizes()["n_lambda"]
+    for name, t in tensors.items():
+        _need(t, name, n)
+
+
 def hyb_assemble_reduced(ctx, load, ess=None, check=True):
+    _need_elements(ctx, load=load, ess=ess)
     st = lib().hyb_assemble_reduced(ctx.handle, _ptr(load, "load"), _ptr(ess, "ess"))
     return _check(st, "hyb_assemble_reduced") if check else st
 
 
 def staticcond_assemble(ctx, load, ess=None, check=True):
+    _need_elements(ctx, load=load, ess=ess)
     st = lib().staticcond_assemble(ctx.handle, _ptr(load, "load"), _ptr(ess, "ess"))
     return _check(st, "staticcond_assemble") if check else st
 
 
 def hyb_solve_reduced(ctx, rtol, maxit, lam, check=True):
     """Returns (iterations, relative residual, status)."""
+    _need_lambda(ctx, lam=lam)
     it = ctypes.c_int()
     rr = ctypes.c_double()
     st = lib().hyb_solve_reduced(ctx.handle, float(rtol), int(maxit), _ptr(lam, "lambda"),
@@ -212,11 +244,15 @@ def hyb_solve_reduced(ctx, rtol, maxit, lam, check=True):
 
 
 def hyb_recover(ctx, lam, u, check=True):
+    _need_lambda(ctx, lam=lam)
+    _need_elements(ctx, u=u)
     st = lib().hyb_recover(ctx.handle, _ptr(lam, "lambda"), _ptr(u, "u"))
     return _check(st, "hyb_recover") if check else st
 
 
 def staticcond_recover(ctx, u_face, u, check=True):
+    _need_lambda(ctx, u_face=u_face)
+    _need_elements(ctx, u=u)
     st = lib().staticcond_recover(ctx.handle, _ptr(u_face, "u_face"), _ptr(u, "u"))
     return _check(st, "staticcond_recover") if check else st
 
@@ -289,6 +325,8 @@ def hyb_measure_fma_peak(fp64=True, stream=None):
 
 def hyb_refine(ctx, steps, inner_rtol, maxit, lam, u, check=True):
     """FP64 refinement steps on (lambda, u); returns (||C u|| / ||g|| per step, status)."""
+    _need_lambda(ctx, lam=lam)
+    _need_elements(ctx, u=u)
     jump = (ctypes.c_double * (int(steps) + 1))()
     st = lib().hyb_refine(ctx.handle, int(steps), float(inner_rtol), int(maxit), _ptr(lam, "lambda"),
                           _ptr(u, "u"), jump)
@@ -299,6 +337,8 @@ def hyb_refine(ctx, steps, inner_rtol, maxit, lam, u, check=True):
 
 def hyb_rsqrt_probe(x, out, positive_normal, stream=None):
     """Status; out / positive_normal receive the kernels' pivot inverse square root and check."""
+    _need(out, "out", x.numel())
+    _need(positive_normal, "positive_normal", x.numel())
     return lib().hyb_rsqrt_probe(int(x.numel()), _ptr(x, "x"), _ptr(out, "out"),
                                  _ptr(positive_normal, "positive_normal", torch.int32), _stream(stream))
 
@@ -329,6 +369,7 @@ def hyb_set_preconditioner(ctx, kind, chebyshev_degree=2, coarsest=64, check=Tru
 
 def hyb_amg_apply(ctx, r, z, check=True):
     """z = M^{-1} r: one V-cycle of the context's multigrid (device tensors of n_lambda doubles)."""
+    _need_lambda(ctx, r=r, z=z)
     st = lib().hyb_amg_apply(ctx.handle, _ptr(r, "r"), _ptr(z, "z"))
     return _check(st, "hyb_amg_apply") if check else st
 

@@ -68,3 +68,49 @@ def test_noalloc_binding_checks_sizes_before_the_call():
         hyb.hyb_pcg_solve_noalloc(bad, col, val, b, torch.zeros(n, dtype=f64), 1, 1e-12, 10)
     with pytest.raises(TypeError):                       # consistent sizes, but host memory
         hyb.hyb_pcg_solve_noalloc(rp, col, val, b, torch.zeros(n, dtype=f64), 1, 1e-12, 10)
+
+
+def test_context_bindings_check_sizes_before_the_call():
+    """Every binding that hands the library device buffers checks their lengths against the
+    mesh (hyb_setup) or the context's sizes first: a short buffer would be read or written
+    past its end. Checked on host tensors with a stand-in context (the size checks raise
+    before any pointer or handle reaches the library)."""
+    import pytest
+    import torch
+    from paper_1801_08914_gb300 import hyb
+    f64 = torch.float64
+
+    class Sized:
+        handle = 1                                       # never reaches the library here
+
+        def sizes(self):
+            return dict(n_elem=8, n_loc=6, n_lambda=12, nnz=0)
+
+    ctx = Sized()
+    lam, u, load = torch.zeros(12, dtype=f64), torch.zeros(8, 6, dtype=f64), torch.zeros(48, dtype=f64)
+    short_lam, short_u = torch.zeros(11, dtype=f64), torch.zeros(47, dtype=f64)
+    with pytest.raises(ValueError, match="vertices has"):
+        hyb.hyb_setup(torch.zeros(3 * 27 - 3, dtype=f64), 2, 2, 2, 0, torch.ones(8, dtype=f64),
+                      torch.ones(8, dtype=f64))
+    with pytest.raises(ValueError, match="beta has"):
+        hyb.hyb_setup(torch.zeros(3 * 27, dtype=f64), 2, 2, 2, 0, torch.ones(8, dtype=f64),
+                      torch.ones(7, dtype=f64))
+    with pytest.raises(TypeError):                       # nx = 0: no size check, the library decides
+        hyb.hyb_setup(torch.zeros(3 * 27, dtype=f64), 0, 2, 2, 0, torch.ones(8, dtype=f64),
+                      torch.ones(8, dtype=f64))
+    calls = [
+        lambda: hyb.hyb_assemble_reduced(ctx, short_u),
+        lambda: hyb.hyb_assemble_reduced(ctx, load, short_u),
+        lambda: hyb.staticcond_assemble(ctx, short_u),
+        lambda: hyb.hyb_solve_reduced(ctx, 1e-12, 10, short_lam),
+        lambda: hyb.hyb_recover(ctx, short_lam, u),
+        lambda: hyb.hyb_recover(ctx, lam, short_u),
+        lambda: hyb.staticcond_recover(ctx, short_lam, u),
+        lambda: hyb.hyb_refine(ctx, 1, 1e-6, 10, lam, short_u),
+        lambda: hyb.hyb_amg_apply(ctx, lam, short_lam),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError, match="entries, expected"):
+            call()
+    with pytest.raises(TypeError):                       # right sizes, host memory
+        hyb.hyb_recover(ctx, lam, u)
