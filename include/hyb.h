@@ -490,6 +490,37 @@ int hyb_batch_get_profile(const hyb_batch* b, int kernel_class, double* total_ms
 /* hyb_destroy_batch -- free the batch and every per-problem context; NULL is a no-op. */
 void hyb_destroy_batch(hyb_batch* b);
 
+/*
+ * hyb_two_level_layout -- multiplier layout of a two-level hexahedral mesh with master /
+ *  slave interface dofs (Example 2.1: P = [I 0; 0 I; 0 W_sm], C = [0 -W_sm I_s]; Fig. 5.1,
+ *  right). HOST memory only; no GPU work, no context.
+ *  The mesh: a coarse nx x ny x nzc block (elements e = i + nx (j + ny l)) under a fine block of
+ *  mx x my x nzf cells (elements nx ny nzc + i + mx (j + my l)), (mx, my) = (2 nx, 2 ny) when
+ *  refine (each coarse top face is tiled by four fine bottom faces) or (nx, ny) (a conforming
+ *  interface). Boundary faces carry no multiplier.
+ *  Multiplier faces, each with (k+1)^2 multipliers (lower tangential axis fastest): the
+ *  interior faces of the coarse block, then those of the fine block (each block numbered as
+ *  the structured meshes above), then the interface faces grouped by coarse face: coarse face
+ *  (I, J) owns faces F + r^2 (I + nx J) + a + r b for its sub-faces (a, b), r = 2 (refine) or 1,
+ *  F the number of faces before them. Multiplier id = face id (k+1)^2 + node.
+ *  nx, ny, nzc, nzf > 0 : block sizes; order : k (0..3); refine : 0 or 1.
+ *  n_lambda, nnz : out, the number of multipliers and of nonzeros of H's pattern.
+ *  elem_face : out or NULL, E x 6 int32: the face id of each local face (x0 x1 y0 y1 z0 z1) or
+ *   -1 on the boundary; a coarse top face with refine gets the first of its four ids.
+ *  W : out or NULL (written only with refine), 4 (k+1)^2 x (k+1)^2 doubles row-major: fine
+ *   dof (sub-face a + 2b, node p) = sum_r W[.][r] coarse dof r, the coarse face's Q_k normal
+ *   trace at the fine node times 1/4 (a dof is a flux density per unit reference area and a
+ *   fine reference face is a quarter of the coarse one).
+ *  row_ptr : out or NULL, n_lambda + 1 int64; col : out or NULL (needs row_ptr), nnz int32:
+ *   H's pattern, multipliers coupled when one element carries both; the rows of a face share
+ *   one sorted column list.
+ *  Call once with NULL arrays for the sizes, then with arrays of those sizes.
+ *  Errors: HYB_ERR_INVALID_ARG (non-positive sizes, null n_lambda / nnz, more than 2^31
+ *  multipliers), HYB_ERR_UNSUPPORTED_ORDER.
+ */
+int hyb_two_level_layout(int nx, int ny, int nzc, int nzf, int order, int refine, int64_t* n_lambda,
+                         int64_t* nnz, int32_t* elem_face, double* W, int64_t* row_ptr, int32_t* col);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhyb.so")
-SOURCES = ["hyb_api.cpp", "hyb_tables.cpp", "hyb_element.cu", "hyb_solve.cu", "hyb_recover.cu", "hyb_probe.cu", "hyb_mixed.cu",
+SOURCES = ["hyb_api.cpp", "hyb_tables.cpp", "hyb_two_level.cpp", "hyb_element.cu", "hyb_solve.cu", "hyb_recover.cu", "hyb_probe.cu", "hyb_mixed.cu",
            "hyb_amg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", "-I", os.path.join(ROOT, "include")]

@@ -83,6 +83,7 @@ __host__ __device__ constexpr int64_t fp64_store_doubles(int k) {
 
 // Host-side table construction (hyb_tables.cpp).
 void build_ref_tables(int k, RefTables* t);
+void build_interface_w(int k, double* W);   // 4 (k+1)^2 x (k+1)^2, row-major
 
 // Kernel launchers (hyb_element.cu, hyb_solve.cu, hyb_recover.cu). Return a cudaError_t.
 cudaError_t upload_ref_tables(const RefTables* tabs, int count, cudaStream_t s);

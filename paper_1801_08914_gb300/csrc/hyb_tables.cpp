@@ -109,4 +109,30 @@ void build_ref_tables(int k, RefTables* t) {
     }
 }
 
+// Map from the (k+1)^2 dofs of a coarse face to those of the four fine faces that tile it on a
+// 2:1 non-conforming interface (Example 2.1's W_sm; Fig. 5.1, right). A face dof is the normal
+// flux density per unit reference area at a Gauss-Legendre node; fine sub-face (a, b) covers
+// the coarse parameters [a/2, (a+1)/2] x [b/2, (b+1)/2], so its reference area is a quarter of
+// the coarse one's and its dof at node (p0, p1) is 1/4 of the coarse Q_k trace there:
+// W[(a + 2b) nfn + p0 + (k+1) p1][r0 + (k+1) r1] = L_r0((a + g_p0) / 2) L_r1((b + g_p1) / 2) / 4,
+// with L the Lagrange basis on the k+1 Gauss-Legendre nodes g. Row-major, 4 nfn x nfn.
+void build_interface_w(int k, double* W) {
+  const int p = k + 1, nfn = p * p;
+  double g[kMaxOpen], w[kMaxOpen];
+  gauss_legendre01(p, g, w);
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < 2; ++a)
+      for (int p1 = 0; p1 < p; ++p1)
+        for (int p0 = 0; p0 < p; ++p0) {
+          double* row = W + ((size_t)(a + 2 * b) * nfn + p0 + p * p1) * nfn;
+          for (int r1 = 0; r1 < p; ++r1)
+            for (int r0 = 0; r0 < p; ++r0) {
+              double v0, v1, dv;
+              lagrange_at(g, p, r0, 0.5 * (a + g[p0]), &v0, &dv);
+              lagrange_at(g, p, r1, 0.5 * (b + g[p1]), &v1, &dv);
+              row[r0 + p * r1] = 0.25 * v0 * v1;
+            }
+        }
+}
+
 }  // namespace hyb

@@ -37,7 +37,7 @@ EXPORTS = ["hyb_setup", "hyb_assemble_reduced", "hyb_solve_reduced", "hyb_recove
            "hyb_get_precision_split", "hyb_setup_batch", "hyb_assemble_reduced_batch", "hyb_solve_reduced_batch",
            "hyb_recover_batch", "hyb_batch_context", "hyb_batch_set_profiling", "hyb_batch_get_profile",
            "hyb_destroy_batch", "hyb_set_mixed_operator", "hyb_batch_step", "hyb_batch_step_kernels", "hyb_batch_get_autotune",
-           "hyb_set_preconditioner", "hyb_amg_apply", "hyb_amg_info",
+           "hyb_set_preconditioner", "hyb_amg_apply", "hyb_amg_info", "hyb_two_level_layout",
            "hyb_last_error_element", "hyb_destroy", "hyb_status_string"]
 
 
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.hyb_set_preconditioner.argtypes = [P, I, I, I]
     lib.hyb_amg_apply.argtypes = [P, P, P]
     lib.hyb_amg_info.argtypes = [P, ctypes.POINTER(I), P, P, I]
+    lib.hyb_two_level_layout.argtypes = [I, I, I, I, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P, P, P]
     lib.hyb_rsqrt_probe.argtypes = [ctypes.c_int64, P, P, P, P]
     lib.hyb_set_natural_bc.argtypes = [P, I]
     lib.hyb_refine.argtypes = [P, I, D, I, P, P, ctypes.POINTER(D)]
@@ -383,6 +384,27 @@ def hyb_amg_info(ctx, cap=32):
                               ctypes.cast(lmax, ctypes.c_void_p), cap), "hyb_amg_info")
     k = min(n.value, cap)
     return n.value, [int(sizes[i]) for i in range(k)], [float(lmax[i]) for i in range(k)]
+
+
+def hyb_two_level_layout(nx, ny, nzc, nzf, order, refine=True):
+    """Host-only multiplier layout of a two-level mesh (see include/hyb.h): dict with n_lambda,
+    elem_face (E x 6 int32), W ((4 (k+1)^2) x (k+1)^2, refine only), row_ptr and col (numpy)."""
+    import numpy as np
+    nl, nnz = ctypes.c_int64(), ctypes.c_int64()
+    args = (int(nx), int(ny), int(nzc), int(nzf), int(order), int(bool(refine)))
+    _check(lib().hyb_two_level_layout(*args, ctypes.byref(nl), ctypes.byref(nnz), None, None, None, None),
+           "hyb_two_level_layout")
+    r = 2 if refine else 1
+    E = nx * ny * nzc + (r * nx) * (r * ny) * nzf
+    nfn = (order + 1) ** 2
+    ef = np.empty((E, 6), dtype=np.int32)
+    W = np.zeros((4 * nfn, nfn)) if refine else None
+    row_ptr = np.empty(nl.value + 1, dtype=np.int64)
+    col = np.empty(nnz.value, dtype=np.int32)
+    ptr = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
+    _check(lib().hyb_two_level_layout(*args, ctypes.byref(nl), ctypes.byref(nnz), ptr(ef), ptr(W), ptr(row_ptr),
+                                      ptr(col)), "hyb_two_level_layout")
+    return dict(n_lambda=nl.value, elem_face=ef, W=W, row_ptr=row_ptr, col=col)
 
 
 def hyb_barrier_selftest(absent, rounds, stream=None):
